@@ -1,0 +1,17 @@
+"""Plain FP64 CPU oracle for the sketched flexible Golub-Kahan solvers.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg are the only code allowed to import it.  It shares no code with
+the GPU library (paper_2605_22281_gb300) and the GPU library never imports it.
+
+Modules:
+  sketch  - SplitMix64 and the sparse-sign / Gaussian / identity sketches (Section 2.7)
+  sfl     - Algorithm 1 (sFLSQR) and Algorithm 2 (sFLSMR) with window-ell
+            orthogonalization (eq. (FGK)), Householder small least squares,
+            identity / fixed-diagonal / reweighting flexible operators, and the
+            discrepancy stop of eq. (discrP).
+"""
+from .sketch import (DenseSketch, IdentitySketch, SparseSign, draw_hash, gaussian, sparse_sign_column,
+                     sparse_sign_rows, splitmix64_stream)
+from .sfl import (STOP_BREAKDOWN, STOP_DISCREPANCY, STOP_MAXIT, FixedDiag, Identity, Reweighting,
+                  discrepancy_tol, householder_lstsq, sflsmr, sflsqr, sketches_for)

@@ -1,0 +1,242 @@
+"""Seeded synthetic CT workloads (input data only).
+
+This module builds the inputs that both the CPU oracle and the GPU solver are
+run on: parallel-beam Siddon projectors A (CSR), pixel-driven unmatched
+back-projectors B (CSR), random-ellipse and sparse phantoms, and noisy
+sinograms b = A x_true + e with an exact noise level (the noise model of the
+discrepancy principle, eq. (discrP) in Section 1.1).  It contains none of the
+solver arithmetic and imports neither the oracle nor the GPU package.
+
+The geometry conventions live in ``ctgen.c``.  The C helpers are compiled on
+first use with the host gcc (OpenMP, ``-ffp-contract=off`` so that x86-64 and
+aarch64 produce identical arrays).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ctgen.c")
+_SO = os.path.join(_HERE, "_ctgen.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build() -> str:
+    """Compile ctgen.c into _ctgen.so next to it (idempotent)."""
+    if os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            f64p = ctypes.POINTER(ctypes.c_double)
+            for name in ("siddon_count", "pixel_count"):
+                getattr(lib, name).argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p]
+                getattr(lib, name).restype = None
+            for name in ("siddon_fill", "pixel_fill"):
+                getattr(lib, name).argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p, i32p, f64p]
+                getattr(lib, name).restype = None
+            lib.csr_matvec.argtypes = [ctypes.c_int64, i64p, i32p, f64p, f64p, f64p]
+            lib.csr_matvec.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+@dataclass
+class CSR:
+    """A CSR matrix as plain arrays: int64 row pointers, int32 columns, f64 values."""
+    shape: tuple
+    rowptr: np.ndarray
+    colidx: np.ndarray
+    values: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def rowptr32(self) -> np.ndarray:
+        assert self.nnz < 2**31
+        return self.rowptr.astype(np.int32)
+
+    def scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.values, self.colidx, self.rowptr), shape=self.shape)
+
+    def matvec(self, x: np.ndarray) -> np.ndarray:
+        """y = A x with the OpenMP C helper (used to synthesise b)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.empty(self.shape[0], dtype=np.float64)
+        _load().csr_matvec(self.shape[0], _ptr(self.rowptr, ctypes.c_int64), _ptr(self.colidx, ctypes.c_int32),
+                           _ptr(self.values, ctypes.c_double), _ptr(x, ctypes.c_double), _ptr(y, ctypes.c_double))
+        return y
+
+
+def _two_pass(count_fn, fill_fn, rows: int, N: int, n_angles: int, n_bins: int) -> tuple:
+    cnt = np.zeros(rows, dtype=np.int64)
+    count_fn(N, n_angles, n_bins, _ptr(cnt, ctypes.c_int64))
+    rowptr = np.zeros(rows + 1, dtype=np.int64)
+    np.cumsum(cnt, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    fill_fn(N, n_angles, n_bins, _ptr(rowptr, ctypes.c_int64), _ptr(col, ctypes.c_int32), _ptr(val, ctypes.c_double))
+    return rowptr, col, val
+
+
+def siddon_projector(N: int, n_angles: int, n_bins: int) -> CSR:
+    """Ray-driven parallel-beam projector A (m = n_angles*n_bins rows, n = N*N columns)."""
+    lib = _load()
+    m = n_angles * n_bins
+    rowptr, col, val = _two_pass(lib.siddon_count, lib.siddon_fill, m, N, n_angles, n_bins)
+    return CSR((m, N * N), rowptr, col, val)
+
+
+def pixel_backprojector(N: int, n_angles: int, n_bins: int) -> CSR:
+    """Pixel-driven linear-interpolation back-projector B (n x m), B != A^T."""
+    lib = _load()
+    n = N * N
+    rowptr, col, val = _two_pass(lib.pixel_count, lib.pixel_fill, n, N, n_angles, n_bins)
+    return CSR((n, n_angles * n_bins), rowptr, col, val)
+
+
+def detector_bins(N: int) -> int:
+    """Number of unit bins that cover the image diagonal: ceil(N*sqrt(2))."""
+    return int(math.ceil(N * math.sqrt(2.0) - 1e-9))
+
+
+def ellipse_phantom(N: int, rng: np.random.Generator, count: int = 6) -> np.ndarray:
+    """Sum of `count` random ellipses on [-1,1]^2 (centre uniform in the disc of
+    radius 0.6, semi-axes U[0.1,0.5], orientation U[0,pi), intensity U[0.2,1]).
+    Returned as a length N*N vector, index iy*N + ix."""
+    c = (np.arange(N) + 0.5) / N * 2.0 - 1.0
+    X, Y = np.meshgrid(c, c)  # Y[iy, ix], X[iy, ix]
+    img = np.zeros((N, N))
+    for _ in range(count):
+        r = 0.6 * math.sqrt(rng.uniform())
+        phi = rng.uniform(0.0, 2.0 * math.pi)
+        cx, cy = r * math.cos(phi), r * math.sin(phi)
+        a, b = rng.uniform(0.1, 0.5), rng.uniform(0.1, 0.5)
+        psi = rng.uniform(0.0, math.pi)
+        val = rng.uniform(0.2, 1.0)
+        xr = (X - cx) * math.cos(psi) + (Y - cy) * math.sin(psi)
+        yr = -(X - cx) * math.sin(psi) + (Y - cy) * math.cos(psi)
+        img[(xr / a) ** 2 + (yr / b) ** 2 <= 1.0] += val
+    return img.reshape(-1)
+
+
+def sparse_phantom(N: int, rng: np.random.Generator, frac: float = 0.05) -> np.ndarray:
+    """`frac` of the pixels (uniform, without replacement) set to U[0,1], the rest 0."""
+    n = N * N
+    x = np.zeros(n)
+    k = int(round(frac * n))
+    idx = rng.choice(n, size=k, replace=False)
+    x[idx] = rng.uniform(0.0, 1.0, size=k)
+    return x
+
+
+def add_noise(b_true: np.ndarray, level: float, rng: np.random.Generator) -> tuple:
+    """b = b_true + e with ||e||_2 = level * ||b_true||_2 exactly (white Gaussian
+    direction).  Returns (b, ||e||_2)."""
+    g = rng.standard_normal(b_true.shape[0])
+    e = level * np.linalg.norm(b_true) * g / np.linalg.norm(g)
+    return b_true + e, float(np.linalg.norm(e))
+
+
+@dataclass
+class Problem:
+    """One synthetic CT problem: operator(s), phantoms, data and solver settings."""
+    name: str
+    N: int
+    n_angles: int
+    n_bins: int
+    A: CSR
+    B: CSR | None
+    x_true: np.ndarray          # (n,) or (n, nrhs)
+    b: np.ndarray               # (m,) or (m, nrhs)
+    noise_norm: np.ndarray      # (nrhs,)
+    settings: dict = field(default_factory=dict)
+
+
+# Workload definitions: named by what they are (image size, geometry, method).
+WORKLOADS = {
+    # sFLSQR on a 64x64 image, 60 angles x 91 bins, 6 ellipses, 1% noise.
+    "ct64_sflsqr": dict(N=64, n_angles=60, phantom="ellipses", nrhs=1, levels=(0.01,), data_seed=1,
+                        unmatched=False,
+                        settings=dict(method="sflsqr", s=200, zeta=8, window=2, maxit=100, eta=1.01,
+                                      precond="identity", seed=42)),
+    # sFLSMR with an unmatched pixel-driven back-projector, 256x256 image,
+    # 180 angles x 363 bins, 5%-sparse phantom, 2% noise, reweighting preconditioner.
+    "ct256_sflsmr_unmatched": dict(N=256, n_angles=180, phantom="sparse", nrhs=1, levels=(0.02,), data_seed=2,
+                                   unmatched=True,
+                                   settings=dict(method="sflsmr", s=400, zeta=8, window=2, maxit=200, eta=1.01,
+                                                 precond="irw", irw_eps=1e-4, seed=43)),
+    # sFLSQR at scale: 1024x1024, 360 angles x 1449 bins, 1% noise.
+    "ct1024_sflsqr": dict(N=1024, n_angles=360, phantom="ellipses", nrhs=1, levels=(0.01,), data_seed=3,
+                          unmatched=False,
+                          settings=dict(method="sflsqr", s=600, zeta=8, window=4, maxit=300, eta=1.01,
+                                        precond="identity", seed=44)),
+    # 64 sinograms of 512x512 phantoms through one 360 x 725 operator,
+    # noise levels log-uniform in [0.5%, 5%].
+    "ct512_batch64": dict(N=512, n_angles=360, phantom="ellipses", nrhs=64, levels="loguniform", data_seed=4,
+                          unmatched=False,
+                          settings=dict(method="sflsqr", s=401, zeta=8, window=2, maxit=200, eta=1.01,
+                                        precond="identity", seed=45)),
+    # fixed-k = 30 differentiable solves, 256x256, batch 16, diagonal weight.
+    "ct256_diff16": dict(N=256, n_angles=180, phantom="ellipses", nrhs=16, levels=(0.01,), data_seed=5,
+                         unmatched=False,
+                         settings=dict(method="sflsqr", s=61, zeta=8, window=2, maxit=30, eta=1.01,
+                                       precond="diag", seed=46, weight_seed=47)),
+}
+
+
+def make(name: str, nrhs: int | None = None, **over) -> Problem:
+    """Build a named workload.  `nrhs` may shrink a batched workload; `over`
+    may override N / n_angles (for reduced-size test cases of the same recipe)."""
+    spec = dict(WORKLOADS[name])
+    N = over.get("N", spec["N"])
+    n_angles = over.get("n_angles", spec["n_angles"])
+    n_bins = detector_bins(N)
+    A = siddon_projector(N, n_angles, n_bins)
+    B = pixel_backprojector(N, n_angles, n_bins) if spec["unmatched"] else None
+    k = spec["nrhs"] if nrhs is None else nrhs
+    xs, bs, enorms = [], [], []
+    for j in range(k):
+        rng = np.random.default_rng(spec["data_seed"] + j)
+        x = ellipse_phantom(N, rng) if spec["phantom"] == "ellipses" else sparse_phantom(N, rng)
+        if spec["levels"] == "loguniform":
+            level = float(math.exp(rng.uniform(math.log(0.005), math.log(0.05))))
+        else:
+            level = spec["levels"][0]
+        b, en = add_noise(A.matvec(x), level, rng)
+        xs.append(x); bs.append(b); enorms.append(en)
+    settings = dict(spec["settings"])
+    if settings.get("precond") == "diag":
+        settings["weight"] = np.random.default_rng(settings["weight_seed"]).uniform(0.5, 1.5, size=N * N)
+    if k == 1:
+        x_true, b = xs[0], bs[0]
+    else:
+        x_true, b = np.stack(xs, axis=1), np.stack(bs, axis=1)
+    return Problem(name, N, n_angles, n_bins, A, B, x_true, b, np.array(enorms), settings)
