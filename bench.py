@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 sFLSQR / sFLSMR solvers.
+
+One step = one complete solve (initialisation, sketched flexible Golub-Kahan
+steps up to the discrepancy stop, x = Z y) of a synthetic CT workload.  The
+default workload is sFLSMR with an unmatched pixel-driven back-projector on a
+256x256 image (180 angles x 363 bins, A: 15.0M nonzeros, B: 23.6M nonzeros,
+5%-sparse phantom, 2% noise, reweighting flexible operator, sketch s = 400,
+window 2, maxit 200), FP64 path.  Its operator bytes (about 464 MB per step)
+exceed the 129 MB L2, so no L2 flush is needed between timed steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (a bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "ct256_sflsmr_unmatched"
+METRIC = "sFLSQR/sFLSMR iters/s, time to discrepancy stop, HBM roofline fraction"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("kernels.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2605_22281_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def spmv_bytes(nnz, rows, cols, vbytes, xbytes, ndots, table_bytes):
+    """Compulsory bytes of one fused SpMV launch: values + column indices + row
+    pointers, the gathered input vector once, the output vector, the window
+    vectors read by the fused dots, and the sketch table."""
+    return nnz * (vbytes + 4) + 4 * (rows + 1) + xbytes * (cols + rows) + xbytes * rows * ndots + table_bytes
+
+
+# ---------------------------------------------------------------- oracle (CPU) legs
+
+def oracle_solve(workload: str, maxit_cap: int | None, problem=None):
+    import numpy as np
+    import oracle as O
+    import workloads as wl
+    p = problem or wl.make(workload)
+    st = p.settings
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], float(np.linalg.norm(p.b)))
+    maxit = st["maxit"] if maxit_cap is None else min(maxit_cap, st["maxit"])
+    A = p.A.scipy()
+    AT = p.B.scipy() if p.B is not None else None
+    tau = {"identity": O.Identity(), "irw": O.Reweighting(st.get("irw_eps", 1e-4))}.get(st["precond"])
+    t0 = time.perf_counter()
+    if st["method"] == "sflsqr":
+        S = O.SparseSign(st["seed"], st["s"], st["zeta"], A.shape[0])
+        r = O.sflsqr(A, p.b, S, maxit=maxit, tol=tol, ell=st["window"], tau=tau, AT=AT, keep_basis=False)
+    else:
+        Sn = O.SparseSign(st["seed"], st["s"], st["zeta"], A.shape[1])
+        Sm = O.SparseSign(st["seed"] + 1, st["s"], st["zeta"], A.shape[0])
+        r = O.sflsmr(A, p.b, Sn, S_stop=Sm, maxit=maxit, tol=tol, ell=st["window"], tau=tau, AT=AT, keep_basis=False)
+    return r, time.perf_counter() - t0
+
+
+def cpu_baseline_subprocess(workload: str, maxit_cap: int | None) -> dict:
+    """Time the oracle in a child process pinned to one BLAS/OpenMP thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", workload, "--oracle-sample",
+           str(maxit_cap if maxit_cap else -1)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1200)
+    if out.returncode != 0:
+        return {"error": out.stderr[-400:]}
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample_main(workload: str, cap: int):
+    r, dt = oracle_solve(workload, None if cap < 0 else cap)
+    print(json.dumps({"iters": r.iters, "seconds": dt, "status": int(r.status)}))
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores; each step a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as wl
+    cap = 10
+    p = wl.make(args.workload)
+    for _ in range(args.warmup):
+        oracle_solve(args.workload, cap, p)
+    iters, secs = 0, 0.0
+    for _ in range(args.steps):
+        r, dt = oracle_solve(args.workload, cap, p)
+        iters += r.iters
+        secs += dt
+    value = iters / secs
+    sample = f"each step: the first {cap} sFLSMR/sFLSQR steps of the {args.workload} workload (oracle, FP64, 1 thread)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "l2": "inputs larger than L2 (CPU run)"},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import workloads as wl
+    from paper_2605_22281_gb300 import api as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    p = wl.make(args.workload)
+    st = p.settings
+    method = st["method"]
+    if rank > 0:  # independent problem per rank: same operator, fresh noise
+        rng = np.random.default_rng(1000 + rank)
+        b_true = p.A.matvec(p.x_true)
+        p.b, en = wl.add_noise(b_true, float(p.noise_norm[0] / np.linalg.norm(b_true)), rng)
+        p.noise_norm = np.array([en])
+    precond = {"identity": "identity", "irw": "reweight", "diag": "diag"}[st["precond"]]
+    kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
+              noise_norm=float(p.noise_norm[0]), eta=st["eta"], precond=precond, irw_eps=st.get("irw_eps", 1e-4))
+    t_plan = time.perf_counter()
+    plan = G.Plan(p.A, p.B, value_dtype="f64")
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t_plan
+    stats = plan.stats()
+    b_dev = torch.as_tensor(p.b, device="cuda")
+    x_dev = torch.empty(p.A.shape[1], dtype=torch.float64, device="cuda")
+
+    # warm-up (also builds the session and its CUDA graph)
+    for _ in range(max(args.warmup, 3)):
+        x_dev, info, _ = plan.solve(method, b_dev, out=x_dev, **kw)
+    iters = info.iters
+    err = float(np.linalg.norm(x_dev.cpu().numpy() - p.x_true) / np.linalg.norm(p.x_true))
+
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.solve(method, b_dev, out=x_dev, sync=False, **kw)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    _, info_chk, _ = plan.solve(method, b_dev, out=x_dev, **kw)
+    assert info_chk.iters == iters, "solve is not deterministic"
+    t_all = [t_ms]
+    iters_all = [iters]
+    if world > 1:
+        tt = torch.tensor([t_ms, float(iters)], device="cuda", dtype=torch.float64)
+        gathered = [torch.zeros_like(tt) for _ in range(world)]
+        dist.all_gather(gathered, tt)
+        t_all = [float(g[0]) for g in gathered]
+        iters_all = [int(g[1]) for g in gathered]
+    t_max_ms = max(t_all)
+    total_iters = sum(i * args.steps for i in iters_all)
+    value = total_iters / (t_max_ms / 1000.0)
+    ms_per_step = t_max_ms / args.steps
+
+    # per-kernel launch durations (CUDA events around every launch, same solve)
+    _, info_p, hp = plan.solve(method, b_dev, out=x_dev, driver="profiled", **kw)
+    kms, kl = hp["kernel_ms"], hp["kernel_launches"]
+    m, n = p.A.shape
+    ell, zs = st["window"], (8 if st["zeta"] <= 8 else 16)
+    fwd_bytes = spmv_bytes(stats["nnz_A"], m, n, 8, 8, ell + 1, m * zs * 2)
+    bwd_bytes = spmv_bytes(stats["nnz_At"], n, m, 8, 8, ell, n * zs * 2 if method == "sflsmr" else 0)
+    peaks = load_peaks()
+    kern = {}
+    for name, nbytes, nnz in (("spmv_fwd", fwd_bytes, stats["nnz_A"]), ("spmv_bwd", bwd_bytes, stats["nnz_At"])):
+        avg_ms = kms[name] / max(kl[name], 1)
+        gbs = nbytes / (avg_ms * 1e-3) / 1e9
+        kern[name] = {"avg_us": 1000 * avg_ms, "bytes": nbytes, "gbs": gbs, "fp64_tflops": 2 * nnz / (avg_ms * 1e-3) / 1e12,
+                      "share": kms[name] / max(sum(kms.values()), 1e-12)}
+    dom = max(kern, key=lambda k: kern[k]["share"])
+    roof = {"bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": kern[dom]["gbs"] / peaks["hbm_gbs"], "traffic": recorded_traffic(dom, args.workload),
+            "kernel": dom, "peak_source": peaks["source"],
+            "algorithmic_bytes_per_launch": kern[dom]["bytes"], "avg_launch_us": kern[dom]["avg_us"]}
+
+    # end to end through the C ABI with host buffers (H2D of b, D2H of x inside the region)
+    b_host = torch.from_numpy(np.ascontiguousarray(p.b)).pin_memory().numpy()
+    x_host = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(2):
+        plan.solve_host(method, b_host, x_out=x_host, **kw)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, info_h = plan.solve_host(method, b_host, x_out=x_host, **kw)
+    t_e2e = time.perf_counter() - t0
+    e2e_all = [t_e2e]
+    if world > 1:
+        tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        gathered = [torch.zeros_like(tt) for _ in range(world)]
+        dist.all_gather(gathered, tt)
+        e2e_all = [float(g[0]) for g in gathered]
+    e2e_value = total_iters / max(e2e_all)
+
+    variants = {}
+    if not args.no_variants:
+        # FP32 values and vectors (FP64 coefficients and small QR), same workload
+        plan32 = G.Plan(p.A, p.B, value_dtype="f32")
+        for _ in range(3):
+            x32, i32, _ = plan32.solve(method, b_dev, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan32.solve(method, b_dev, sync=False, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t32 = e0.elapsed_time(e1)
+        err32 = float(np.linalg.norm(x32.cpu().numpy() - p.x_true) / np.linalg.norm(p.x_true))
+        variants["f32_values_vectors"] = {"value": i32.iters * args.steps / (t32 / 1000), "unit": "iters/s",
+                                          "ms_per_step": t32 / args.steps, "iters": i32.iters,
+                                          "rel_error_vs_x_true": err32, "fp64_rel_error_vs_x_true": err}
+        plan32.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = cpu_baseline_subprocess(args.workload, None)
+        if "iters" in res:
+            cpu = {"value": res["iters"] / res["seconds"], "unit": "iters/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one full oracle solve of {args.workload} ({res['iters']} steps, "
+                             f"{res['seconds']:.1f} s, FP64, 1 thread)"}
+        else:
+            cpu = {"value": None, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": res.get("error", "")}
+
+    launches_per_step = (4 if method == "sflsmr" else 3) + 5 * iters + 2
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "method": method, "image": f"{p.N}x{p.N}",
+                           "angles": p.n_angles, "bins": p.n_bins, "m": m, "n": n, "nnz_A": stats["nnz_A"],
+                           "nnz_B_or_At": stats["nnz_At"], "s": st["s"], "zeta": st["zeta"], "window": ell,
+                           "maxit": st["maxit"], "precond": precond, "iters_to_stop": iters,
+                           "stop": info.status_name, "time_to_stop_ms": ms_per_step,
+                           "rel_error_vs_x_true": err, "plan_build_s": t_plan,
+                           "l2": "inputs larger than L2 (operators 464 MB > 129 MB); no flush",
+                           "parallelism": f"replicas x{world} (independent problems)"},
+                "roofline": roof, "kernels": kern, "clocks": clocks,
+                "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": 8 * m,
+                        "d2h_bytes_per_step": 8 * n},
+                "gpu_launches": launches_per_step * args.steps,
+                "cpu_baseline": cpu, "variants": variants}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.oracle_sample:
+        oracle_sample_main(args.workload, args.oracle_sample)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/* sfl.h - C ABI of the GB300 sketched flexible Golub-Kahan solvers.
+ *
+ * Solves  min_x || A x - b ||_2  for a large sparse A (m x n, CSR) by
+ *   sFLSQR  (Algorithm 1, eq. (sFLSQR) of Section 2.3)  and
+ *   sFLSMR  (Algorithm 2, eq. (sFLSMR) of Section 2.5)
+ * of "Randomized Flexible LSQR and LSMR with applications to inverse problems":
+ * a flexible Golub-Kahan process with window-ell partial orthogonalization
+ * (eq. (FGK)), a flexible right operator z_k = tau_k(p_k) (eq. (modbasis)),
+ * an s-row sparse-sign sketch of every new basis vector (Section 2.7), a small
+ * FP64 sketched least-squares solve per step, and the discrepancy-principle
+ * stop of eq. (discrP) in Section 1.1.
+ *
+ * Conventions for every entry point:
+ *  - All pointers to matrix and vector data are DEVICE pointers on the current
+ *    CUDA device unless stated otherwise.  Index arrays are int32.  Dense
+ *    vectors are contiguous.  Host pointers are marked "host".
+ *  - Every function returns an sfl_status (SFL_OK == 0).  No function aborts,
+ *    throws or exits; errors are reported by the return value and
+ *    sfl_error_string() gives a static description.
+ *  - The library never frees or writes caller memory except the declared
+ *    outputs.  A plan owns its internal copies (padded CSR, transposed CSR,
+ *    workspaces, CUDA graphs) until sfl_plan_destroy.
+ *  - Work is enqueued on the given stream (0 = legacy default stream); calls on
+ *    one plan must not overlap in time.
+ */
+#ifndef SFL_H
+#define SFL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sfl_stream;   /* == cudaStream_t */
+
+typedef enum {
+  SFL_OK = 0,
+  SFL_EINVAL = 1,        /* bad argument: null pointer, bad CSR, bad option */
+  SFL_ENOMEM = 2,        /* device allocation failed (or exceeded the plan's cap) */
+  SFL_ECUDA = 3,         /* a CUDA runtime call failed */
+  SFL_ENONFINITE = 4,    /* NaN or Inf in the matrix values or in b */
+  SFL_ETIMEOUT = 5,      /* host wait exceeded its wall-clock limit */
+  SFL_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} sfl_status;
+
+typedef enum { SFL_F64 = 0, SFL_F32 = 1, SFL_BF16 = 2 } sfl_dtype;
+
+/* Outcome of a solve (sfl_info.status). */
+typedef enum {
+  SFL_STOP_RUNNING = 0,
+  SFL_STOP_DISCREPANCY = 1,   /* relative sketched residual < eta*||e||/||b|| (eq. (discrP)) */
+  SFL_STOP_MAXIT = 2,         /* maxit steps done */
+  SFL_STOP_BREAKDOWN = 3      /* ||z|| or ||w|| or |R_kk| vanished; the last completed iterate is returned */
+} sfl_stop;
+
+typedef enum { SFL_PRECOND_IDENTITY = 0, SFL_PRECOND_DIAG = 1, SFL_PRECOND_REWEIGHT = 2 } sfl_precond;
+typedef enum { SFL_STOP_RULE_RESIDUAL = 0, SFL_STOP_RULE_NORMAL = 1 } sfl_stop_rule;
+
+/* A CSR matrix.  rowptr has rows+1 entries with rowptr[0] = 0, nondecreasing,
+ * rowptr[rows] = nnz < 2^31; colidx[i] in [0, cols).  values has nnz entries of
+ * `dtype`.  Column indices need not be sorted within a row. */
+typedef struct {
+  int64_t rows, cols, nnz;
+  const int32_t *rowptr;
+  const int32_t *colidx;
+  const void *values;
+  sfl_dtype dtype;
+} sfl_csr;
+
+typedef struct sfl_plan sfl_plan;
+
+/* Plan options.  value_dtype is the precision the plan stores A (and its
+ * transpose or B) in: SFL_F64, SFL_F32 or SFL_BF16 (round to nearest even).
+ * max_device_bytes caps the plan's own allocations (0 = no cap). */
+typedef struct {
+  sfl_dtype value_dtype;
+  int32_t reserved0;
+  uint64_t max_device_bytes;
+} sfl_plan_opts;
+
+/* Solve options (the Require lines of Algorithms 1 and 2).
+ *  s, zeta, seed : sparse-sign sketch with s rows and zeta nonzeros +-1/sqrt(zeta)
+ *                  per column (zeta = 1 is CountSketch), drawn from SplitMix64
+ *                  (h = first output of the generator seeded with
+ *                  seed ^ (column*2^32 + draw), row = floor(h*s/2^64), sign =
+ *                  bit 0).  sFLSQR sketches m-vectors with `seed`; sFLSMR
+ *                  sketches n-vectors with `seed` and keeps an m-side sketch
+ *                  drawn from `seed + 1` for its discrepancy test.
+ *                  Requires 1 <= zeta <= 16, maxit + 1 <= s <= 2048.
+ *  window        : ell, the orthogonalization window, 0 <= ell <= 8.
+ *  maxit         : 1 <= maxit <= 1024.
+ *  noise_norm    : ||e||_2 of the data noise; <= 0 disables the discrepancy stop.
+ *  eta           : discrepancy safety factor (eta > 1, typically 1.01).
+ *  precond       : tau_k.  IDENTITY; DIAG (z = diag(diag_w) p, diag_w FP64 of
+ *                  length n); REWEIGHT (z = diag((x_{k-1}^2 + irw_eps)^(1/4)) p,
+ *                  x_0 = 0), the iteratively reweighted operator of Section 1.2.
+ *  stop_rule     : sFLSMR only.  RESIDUAL tests ||S_m (b - A x_k)|| against
+ *                  eta*||e|| relative to ||S_m b||; NORMAL tests the residual of
+ *                  the sketched normal equations that sFLSMR minimises.
+ *  vec_dtype     : precision of the basis vectors: SFL_F64 (requires an FP64
+ *                  plan) or SFL_F32 (FP32 or BF16 plans).  Coefficients, the
+ *                  small QR and y are FP64 in both.
+ *  x_history     : optional (may be NULL), device, maxit*n FP64: x_k is written
+ *                  to x_history + (k-1)*n after every step (costs one n x k
+ *                  product per step; for verification).
+ *  relres_history: optional (may be NULL), device, maxit FP64: the stop-test
+ *                  ratio of step k at index k-1. */
+typedef struct {
+  int32_t s;
+  int32_t zeta;
+  uint64_t seed;
+  int32_t window;
+  int32_t maxit;
+  double noise_norm;
+  double eta;
+  int32_t precond;
+  int32_t stop_rule;
+  const double *diag_w;
+  double irw_eps;
+  int32_t vec_dtype;
+  int32_t reserved0;
+  double *x_history;
+  double *relres_history;
+} sfl_opts;
+
+/* Result of a solve.  Filled when the call returns (the call then waits for
+ * its stream). */
+typedef struct {
+  int32_t iters;          /* k of the returned iterate x_k */
+  int32_t status;         /* sfl_stop */
+  double relres;          /* stop-test ratio at step iters (sketched, relative) */
+  double tol;             /* eta * noise_norm / ||b|| (0 when disabled) */
+} sfl_info;
+
+/* Statistics of a plan (host struct). */
+typedef struct {
+  int64_t rows, cols, nnz_A, nnz_At;     /* nnz_At: nnz of A^T (CSC copy) or of B */
+  int64_t padded_nnz_A, padded_nnz_At;   /* stored entries after row padding */
+  int32_t lanes_A, lanes_At;             /* lanes per row of the SpMV kernels */
+  int32_t value_dtype;
+  int32_t unmatched;                     /* 1 if B was given */
+  uint64_t device_bytes;                 /* bytes the plan holds */
+} sfl_plan_stats;
+
+/* ---- plans ------------------------------------------------------------- */
+
+/* Build a plan for A (m x n) and, optionally, an unmatched back-projector B
+ * (n x m, CSR) used in place of A^T (Section 3.2).  When B is NULL the plan
+ * builds a transposed copy of A (CSC of A stored as CSR of A^T) so that A^T
+ * products need no atomics and are bitwise reproducible.  Validates the CSR
+ * arrays on the device (SFL_EINVAL on a bad rowptr or column index,
+ * SFL_ENONFINITE on NaN/Inf values); converts values to popts->value_dtype;
+ * pads every row to a multiple of the vector-load width.  A and B may be freed
+ * by the caller after this call returns.  popts may be NULL (FP64, no cap). */
+int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B,
+                    const sfl_plan_opts *popts, sfl_stream stream);
+int sfl_plan_destroy(sfl_plan *plan);
+int sfl_plan_get_stats(const sfl_plan *plan, sfl_plan_stats *stats /* host */);
+
+/* y = A x (which = 0) or y = A^T x / B x (which = 1) with the plan's stored
+ * operator and the same SpMV kernel the solvers use.  x and y are FP64
+ * (lengths cols/rows of the chosen operator); the product is formed in the
+ * plan's value precision with FP64 accumulation for FP64 plans and FP32 for
+ * FP32/BF16 plans. */
+int sfl_plan_apply(sfl_plan *plan, int which, const double *x, double *y, sfl_stream stream);
+
+/* ---- solvers ------------------------------------------------------------ */
+
+/* Algorithm 1, sFLSQR.  b: device FP64, length m.  x: device FP64, length n,
+ * receives x_k = Z_k y_k at the stop step.  info: host, may be NULL; when
+ * given, the call waits for the stream and fills it.  The first call for a new
+ * (s, zeta, window, maxit, precond, vec_dtype, histories) combination
+ * allocates a workspace and builds a CUDA graph that later calls reuse. */
+int sflsqr_solve(sfl_plan *plan, const double *b, const sfl_opts *opts, double *x,
+                 sfl_info *info, sfl_stream stream);
+
+/* Algorithm 2, sFLSMR (same arguments).  The small problem is
+ * min_y || s_{A^T b} - [S A^T W, S z] H_{k+1,k} y ||, formed from the sketched
+ * columns of A^T W (or B W) and the banded H of eq. (FGK). */
+int sflsmr_solve(sfl_plan *plan, const double *b, const sfl_opts *opts, double *x,
+                 sfl_info *info, sfl_stream stream);
+
+/* Same solves with HOST FP64 b and x (b: m doubles, x: n doubles, ordinary or
+ * pinned host memory).  The host-to-device copy of b and the device-to-host
+ * copy of x are part of the call, which returns when x is written. */
+int sflsqr_solve_host(sfl_plan *plan, const double *b_host, const sfl_opts *opts, double *x_host,
+                      sfl_info *info, sfl_stream stream);
+int sflsmr_solve_host(sfl_plan *plan, const double *b_host, const sfl_opts *opts, double *x_host,
+                      sfl_info *info, sfl_stream stream);
+
+/* Same as sflsqr_solve (method 0) / sflsmr_solve (method 1) but driven by a
+ * host loop over the same per-step kernels instead of the CUDA graph's
+ * device-side WHILE node: one stream synchronisation per step.  Results are
+ * bitwise identical to the graph driver; meant for verification. */
+int sfl_solve_host_loop(sfl_plan *plan, int method, const double *b, const sfl_opts *opts, double *x,
+                        sfl_info *info, sfl_stream stream);
+
+/* Per-kernel device time of one solve.  Index: 0 sketch tables, 1 init (||b||,
+ * S b), 2 init A^T w_1, 3 z orthogonalization + tau, 4 fused A z_k SpMV,
+ * 5 w orthogonalization, 6 fused A^T w / B w SpMV, 7 small least squares,
+ * 8 x = Z y.  ms: total milliseconds over the launches that did work;
+ * launches: their number. */
+#define SFL_NUM_KERNEL_CLASSES 9
+typedef struct {
+  double ms[SFL_NUM_KERNEL_CLASSES];
+  int32_t launches[SFL_NUM_KERNEL_CLASSES];
+} sfl_kernel_times;
+
+/* The solve of sfl_solve_host_loop with a CUDA event pair recorded on `stream`
+ * around every kernel launch; steps are enqueued in chunks without host
+ * synchronisation inside a chunk.  Fills *times (host).  Same results as the
+ * other drivers. */
+int sfl_solve_profiled(sfl_plan *plan, int method, const double *b, const sfl_opts *opts, double *x,
+                       sfl_info *info, sfl_kernel_times *times, sfl_stream stream);
+
+/* ---- sketch ------------------------------------------------------------- */
+
+/* Export the sparse-sign sketch (Section 2.7) the solvers draw: for columns
+ * c = 0..ncols-1, rows[c*zeta + t] and signs[c*zeta + t] (+1/-1) of its t-th
+ * distinct row in draw order.  rows, signs: device int32 arrays of ncols*zeta. */
+int sfl_sketch_export(uint64_t seed, int32_t s, int32_t zeta, int64_t ncols,
+                      int32_t *rows, int32_t *signs, sfl_stream stream);
+
+/* sk = S v for the sparse-sign sketch (seed, s, zeta) of an FP64 vector v of
+ * length len; sk: device FP64, length s.  Deterministic (fixed-order sums). */
+int sfl_sketch_apply(uint64_t seed, int32_t s, int32_t zeta, const double *v, int64_t len,
+                     double *sk, sfl_stream stream);
+
+/* ---- misc --------------------------------------------------------------- */
+
+const char *sfl_error_string(int status);
+/* Text of the last CUDA error seen by this thread inside the library ("" if none). */
+const char *sfl_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFL_H */

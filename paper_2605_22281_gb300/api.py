@@ -1,0 +1,207 @@
+"""Python binding of the GB300 sFLSQR / sFLSMR library.
+
+Argument marshalling only: device memory comes from PyTorch tensors, streams
+from torch.cuda.current_stream(); every step of the solvers runs in the CUDA
+kernels of libsfl.so (Algorithms 1 and 2 of the paper).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_2605_22281_gb300 needs a CUDA device (GB300, sm_103a); none is available")
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_csr(rowptr, colidx, values, shape, device):
+    """Device copies of a host or device CSR (int32 indices, FP64/FP32 values)."""
+    rp = torch.as_tensor(np.asarray(rowptr) if not torch.is_tensor(rowptr) else rowptr).to(device=device, dtype=torch.int32)
+    ci = torch.as_tensor(np.asarray(colidx) if not torch.is_tensor(colidx) else colidx).to(device=device, dtype=torch.int32)
+    va = torch.as_tensor(np.asarray(values) if not torch.is_tensor(values) else values).to(device=device)
+    if va.dtype == torch.float64:
+        dt = N.SFL_F64
+    elif va.dtype == torch.float32:
+        dt = N.SFL_F32
+    elif va.dtype == torch.bfloat16:
+        dt = N.SFL_BF16
+    else:
+        va = va.to(torch.float64)
+        dt = N.SFL_F64
+    c = N.Csr(shape[0], shape[1], int(ci.numel()), _ptr(rp), _ptr(ci), _ptr(va), dt)
+    return c, (rp, ci, va)
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    status: int
+    relres: float
+    tol: float
+
+    @property
+    def status_name(self) -> str:
+        return {0: "running", 1: "discrepancy", 2: "maxit", 3: "breakdown"}.get(self.status, "?")
+
+
+class Plan:
+    """A sparse operator A (m x n, CSR) and its transposed copy, or an unmatched
+    back-projector B (n x m), stored on the GPU in `value_dtype`."""
+
+    def __init__(self, A, B=None, value_dtype: str = "f64", device: str | int = 0, max_device_bytes: int = 0):
+        _require_cuda()
+        self.lib = N.load()
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        with torch.cuda.device(self.device):
+            ca, keep_a = _dev_csr(A.rowptr, A.colidx, A.values, A.shape, self.device)
+            cb, keep_b = (None, None)
+            if B is not None:
+                cb, keep_b = _dev_csr(B.rowptr, B.colidx, B.values, B.shape, self.device)
+            po = N.PlanOpts(N.DTYPE[value_dtype], 0, max_device_bytes)
+            h = ctypes.c_void_p()
+            st = N.check(self.lib.sfl_plan_create(ctypes.byref(h), ctypes.byref(ca),
+                                                  ctypes.byref(cb) if cb is not None else None,
+                                                  ctypes.byref(po), _stream()), "sfl_plan_create")
+            del keep_a, keep_b, st
+        self.handle = h
+        self.m, self.n = int(A.shape[0]), int(A.shape[1])
+        self.value_dtype = value_dtype
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.sfl_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = N.PlanStats()
+        N.check(self.lib.sfl_plan_get_stats(self.handle, ctypes.byref(s)), "sfl_plan_get_stats")
+        return {f: getattr(s, f) for f, _ in N.PlanStats._fields_}
+
+    def apply(self, x: torch.Tensor, transpose: bool = False) -> torch.Tensor:
+        """y = A x, or y = A^T x (B x when the plan holds an unmatched B)."""
+        x = x.to(device=self.device, dtype=torch.float64).contiguous()
+        y = torch.empty(self.n if transpose else self.m, dtype=torch.float64, device=self.device)
+        N.check(self.lib.sfl_plan_apply(self.handle, 1 if transpose else 0, _ptr(x), _ptr(y), _stream()),
+                "sfl_plan_apply")
+        return y
+
+    def _opts(self, s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, diag_w, irw_eps,
+              vec_dtype, x_hist, r_hist):
+        return N.Opts(s, zeta, seed, window, maxit, float(noise_norm), float(eta), N.PRECOND[precond],
+                      N.STOP_RULE[stop_rule], _ptr(diag_w), float(irw_eps), N.DTYPE[vec_dtype], 0,
+                      _ptr(x_hist), _ptr(r_hist))
+
+    def solve(self, method: str, b: torch.Tensor, *, s: int, zeta: int = 8, seed: int = 0, window: int = 2,
+              maxit: int = 100, noise_norm: float = 0.0, eta: float = 1.01, precond: str = "identity",
+              stop_rule: str = "residual", diag_w: torch.Tensor | None = None, irw_eps: float = 1e-4,
+              vec_dtype: str | None = None, x_history: bool = False, relres_history: bool = False,
+              driver: str = "graph", out: torch.Tensor | None = None, sync: bool = True):
+        """Run sFLSQR (method='sflsqr', Algorithm 1) or sFLSMR ('sflsmr', Algorithm 2).
+
+        Returns (x, info, hist) where hist holds the optional per-step iterates
+        (maxit x n) and stop ratios.  With sync=False the call does not wait and
+        info is None."""
+        if vec_dtype is None:
+            vec_dtype = "f64" if self.value_dtype == "f64" else "f32"
+        dev = self.device
+        b = b.to(device=dev, dtype=torch.float64).contiguous()
+        x = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=dev)
+        dw = diag_w.to(device=dev, dtype=torch.float64).contiguous() if diag_w is not None else None
+        xh = torch.zeros((maxit, self.n), dtype=torch.float64, device=dev) if x_history else None
+        rh = torch.zeros(maxit, dtype=torch.float64, device=dev) if relres_history else None
+        o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
+                       xh, rh)
+        info = N.Info()
+        pinfo = ctypes.byref(info) if sync else None
+        with torch.cuda.device(dev):
+            if driver == "graph":
+                fn = self.lib.sflsqr_solve if method == "sflsqr" else self.lib.sflsmr_solve
+                st = fn(self.handle, _ptr(b), ctypes.byref(o), _ptr(x), pinfo, _stream())
+            elif driver == "profiled":
+                kt = N.KernelTimes()
+                st = self.lib.sfl_solve_profiled(self.handle, 0 if method == "sflsqr" else 1, _ptr(b), ctypes.byref(o),
+                                                 _ptr(x), pinfo, ctypes.byref(kt), _stream())
+            elif driver == "host_loop":
+                st = self.lib.sfl_solve_host_loop(self.handle, 0 if method == "sflsqr" else 1, _ptr(b),
+                                                  ctypes.byref(o), _ptr(x), pinfo, _stream())
+            else:
+                raise ValueError(driver)
+        N.check(st, method)
+        hist = {"x": xh, "relres": rh}
+        if driver == "profiled":
+            hist["kernel_ms"] = {c: kt.ms[i] for i, c in enumerate(N.KERNEL_CLASSES)}
+            hist["kernel_launches"] = {c: kt.launches[i] for i, c in enumerate(N.KERNEL_CLASSES)}
+        return x, (SolveInfo(info.iters, info.status, info.relres, info.tol) if sync else None), hist
+
+    def solve_host(self, method: str, b: np.ndarray, *, s: int, zeta: int = 8, seed: int = 0, window: int = 2,
+                   maxit: int = 100, noise_norm: float = 0.0, eta: float = 1.01, precond: str = "identity",
+                   stop_rule: str = "residual", diag_w: torch.Tensor | None = None, irw_eps: float = 1e-4,
+                   vec_dtype: str | None = None, x_out: np.ndarray | None = None):
+        """Same solve with host FP64 b and x (copies inside the call)."""
+        if vec_dtype is None:
+            vec_dtype = "f64" if self.value_dtype == "f64" else "f32"
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = x_out if x_out is not None else np.empty(self.n, dtype=np.float64)
+        dw = diag_w.to(device=self.device, dtype=torch.float64).contiguous() if diag_w is not None else None
+        o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
+                       None, None)
+        info = N.Info()
+        fn = self.lib.sflsqr_solve_host if method == "sflsqr" else self.lib.sflsmr_solve_host
+        with torch.cuda.device(self.device):
+            st = fn(self.handle, b.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o), x.ctypes.data_as(ctypes.c_void_p),
+                    ctypes.byref(info), _stream())
+        N.check(st, method + "_host")
+        return x, SolveInfo(info.iters, info.status, info.relres, info.tol)
+
+
+def sflsqr(plan: Plan, b, **kw):
+    """Algorithm 1 (sFLSQR) on the GPU; see Plan.solve."""
+    return plan.solve("sflsqr", b, **kw)
+
+
+def sflsmr(plan: Plan, b, **kw):
+    """Algorithm 2 (sFLSMR) on the GPU; see Plan.solve."""
+    return plan.solve("sflsmr", b, **kw)
+
+
+def sketch_export(seed: int, s: int, zeta: int, ncols: int, device=0):
+    """(rows, signs) of the sparse-sign sketch the solvers draw, as int32 tensors (ncols, zeta)."""
+    _require_cuda()
+    lib = N.load()
+    dev = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+    rows = torch.empty((ncols, zeta), dtype=torch.int32, device=dev)
+    signs = torch.empty((ncols, zeta), dtype=torch.int32, device=dev)
+    with torch.cuda.device(dev):
+        N.check(lib.sfl_sketch_export(seed, s, zeta, ncols, _ptr(rows), _ptr(signs), _stream()), "sfl_sketch_export")
+    return rows, signs
+
+
+def sketch_apply(seed: int, s: int, zeta: int, v: torch.Tensor) -> torch.Tensor:
+    """S v for the sparse-sign sketch (seed, s, zeta)."""
+    _require_cuda()
+    lib = N.load()
+    v = v.to(dtype=torch.float64).contiguous()
+    out = torch.empty(s, dtype=torch.float64, device=v.device)
+    with torch.cuda.device(v.device):
+        N.check(lib.sfl_sketch_apply(seed, s, zeta, _ptr(v), v.numel(), _ptr(out), _stream()), "sfl_sketch_apply")
+    return out

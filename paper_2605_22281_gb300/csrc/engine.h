@@ -1,0 +1,105 @@
+// Host-side engine of the GB300 sFLSQR / sFLSMR library: plans, sessions and
+// the typed launch wrappers implemented in the inst_*.cu units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace sfl {
+
+// Stored operator: CSR with every row padded to a multiple of the load width
+// (padding entries repeat a valid column with value 0).
+struct StoredCsr {
+  int32_t *rowptr = nullptr;
+  int32_t *col = nullptr;
+  void *val = nullptr;
+  int64_t rows = 0, cols = 0, nnz = 0, pnnz = 0;
+  int lpr = 32;
+};
+
+struct SessionKey {
+  int method, s, zeta, ell, maxit, precond, stop_rule, vdt;
+  double *x_hist, *r_hist;
+  bool operator==(const SessionKey &o) const {
+    return method == o.method && s == o.s && zeta == o.zeta && ell == o.ell && maxit == o.maxit &&
+           precond == o.precond && stop_rule == o.stop_rule && vdt == o.vdt && x_hist == o.x_hist &&
+           r_hist == o.r_hist;
+  }
+};
+
+struct Session {
+  SessionKey key{};
+  int RW = 0, RP = 0, zs = 8;
+  SolveState *st = nullptr;
+  void *wring = nullptr, *pring = nullptr, *wraw = nullptr, *zraw = nullptr, *Z = nullptr;
+  double *sigZ = nullptr;
+  uint16_t *tab_m = nullptr, *tab_n = nullptr;
+  double *Q = nullptr, *Rinv = nullptr, *y = nullptr, *e = nullptr, *rhs = nullptr;
+  double *SAZ = nullptr, *SAtW = nullptr, *Hband = nullptr, *sbm = nullptr;
+  double *bbuf = nullptr, *xbuf = nullptr, *dw = nullptr;
+  int *err = nullptr;
+  RedScratch red{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int grid_spmv_A = 0, grid_spmv_T = 0, grid_vec = 0, grid_init = 0;
+  size_t smem_A = 0, smem_T = 0, smem_init = 0, smem_orth = 0, smem_ls = 0;
+  int ls_cluster = 8;
+  std::vector<void *> allocs;
+  uint64_t bytes = 0;
+};
+
+struct Plan {
+  int device = 0;
+  int num_sms = 0;
+  sfl_dtype vdt = SFL_F64;
+  bool unmatched = false;
+  StoredCsr A, T;   // T: CSR of A^T (transposed copy) or of B
+  uint64_t bytes = 0, cap = 0;
+  std::vector<void *> allocs;
+  std::vector<std::unique_ptr<Session>> sessions;
+  // scratch for sfl_plan_apply
+  void *apply_x = nullptr, *apply_y = nullptr;
+  RedScratch apply_red{};
+};
+
+// Typed launch wrappers (one instantiation unit per precision pair).
+template <typename VT, typename XT>
+struct Ops {
+  static cudaError_t spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, int grid, size_t smem, cudaStream_t s);
+  static cudaError_t orth(const OrthParams<XT> &p, int grid, size_t smem, cudaStream_t s);
+  static cudaError_t solution(SolveState *st, const XT *Z, int64_t zstride, const double *sigZ, const double *y,
+                              int64_t n, double *x, double *hist, int grid, cudaStream_t s);
+  static cudaError_t convert_in(const double *x, XT *y, int64_t n, cudaStream_t s);
+  static cudaError_t convert_out(const XT *x, double *y, int64_t n, cudaStream_t s);
+  static int spmv_occupancy(int lpr, bool mat, size_t smem);
+  static cudaError_t set_smem(int lpr, bool mat, size_t smem);
+};
+
+cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s);
+int ls_cluster_size(int s, int maxit);
+size_t ls_smem_bytes(int s, int maxit, int cluster);
+
+void set_cuda_error(cudaError_t e, const char *where);
+size_t dtype_size(int dt);
+int load_width(int dt);
+
+#define SFL_CU(...)                  \
+  do {                               \
+    cudaError_t e__ = (__VA_ARGS__); \
+    if (e__ != cudaSuccess) {        \
+      cudaGetLastError();            \
+      ::sfl::set_cuda_error(e__, #__VA_ARGS__); \
+      return SFL_ECUDA;              \
+    }                                \
+  } while (0)
+
+}  // namespace sfl
+
+struct sfl_plan {
+  sfl::Plan impl;
+};

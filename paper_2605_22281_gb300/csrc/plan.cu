@@ -1,0 +1,340 @@
+// Plans: validation, precision conversion, row padding and the transposed copy
+// of A (one-time set-up; the per-step kernels are in kernels.cuh).
+#include <cub/cub.cuh>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "engine.h"
+
+namespace sfl {
+
+static thread_local std::string g_last_cuda_error;
+
+void set_cuda_error(cudaError_t e, const char *where) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+  g_last_cuda_error = buf;
+}
+
+const char *last_cuda_error() { return g_last_cuda_error.c_str(); }
+
+size_t dtype_size(int dt) { return dt == SFL_F64 ? 8 : dt == SFL_F32 ? 4 : 2; }
+int load_width(int dt) { return dt == SFL_BF16 ? 8 : 4; }
+
+// ---------------------------------------------------------------- device helpers
+
+enum : int { kErrRowptr = 1, kErrCol = 2, kErrNonfinite = 4 };
+
+__global__ void validate_kernel(const int32_t *rowptr, const int32_t *col, const void *val, int dt, int64_t rows,
+                                int64_t cols, int64_t nnz, int *err) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int e = 0;
+  for (int64_t i = t0; i < rows; i += st) {
+    if (rowptr[i] > rowptr[i + 1] || rowptr[i] < 0) e |= kErrRowptr;
+  }
+  if (t0 == 0 && (rowptr[0] != 0 || (int64_t)rowptr[rows] != nnz)) e |= kErrRowptr;
+  for (int64_t i = t0; i < nnz; i += st) {
+    const int c = col[i];
+    if (c < 0 || (int64_t)c >= cols) e |= kErrCol;
+    double v;
+    if (dt == SFL_F64) v = ((const double *)val)[i];
+    else if (dt == SFL_F32) v = ((const float *)val)[i];
+    else v = __bfloat162float(((const __nv_bfloat16 *)val)[i]);
+    if (!isfinite(v)) e |= kErrNonfinite;
+  }
+  if (e) atomicOr(err, e);
+}
+
+template <typename OT>
+__device__ __forceinline__ OT cvt(double v);
+template <> __device__ __forceinline__ double cvt<double>(double v) { return v; }
+template <> __device__ __forceinline__ float cvt<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+template <typename OT>
+__global__ void convert_values_kernel(const void *in, int dt, OT *out, int64_t n) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += st) {
+    double v;
+    if (dt == SFL_F64) v = ((const double *)in)[i];
+    else if (dt == SFL_F32) v = ((const float *)in)[i];
+    else v = __bfloat162float(((const __nv_bfloat16 *)in)[i]);
+    out[i] = cvt<OT>(v);
+  }
+}
+
+__global__ void padded_len_kernel(const int32_t *rowptr, int64_t rows, int P, int32_t *plen) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= rows; i += st) {
+    if (i == rows) { plen[i] = 0; continue; }
+    const int len = rowptr[i + 1] - rowptr[i];
+    plen[i] = (len + P - 1) / P * P;
+  }
+}
+
+// One warp per row: copy the row into its padded slot.  Padding entries take
+// the row's last column (or 0 for an empty row) and value 0.
+template <typename OT>
+__global__ void fill_padded_kernel(const int32_t *rowptr, const int32_t *col, const OT *val, int64_t rows,
+                                   const int32_t *prow, int32_t *pcol, OT *pval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < rows; r += nw) {
+    const int b = rowptr[r], e = rowptr[r + 1], pb = prow[r], pe = prow[r + 1];
+    const int last = e > b ? col[e - 1] : 0;
+    for (int i = lane; i < pe - pb; i += 32) {
+      if (b + i < e) { pcol[pb + i] = col[b + i]; pval[pb + i] = val[b + i]; }
+      else { pcol[pb + i] = last; pval[pb + i] = cvt<OT>(0.0); }
+    }
+  }
+}
+
+__global__ void row_ids_kernel(const int32_t *rowptr, int64_t rows, int32_t *rid) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < rows; r += nw)
+    for (int i = rowptr[r] + lane; i < rowptr[r + 1]; i += 32) rid[i] = (int32_t)r;
+}
+
+__global__ void iota_kernel(int32_t *v, int64_t n) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += st) v[i] = (int32_t)i;
+}
+
+// Transposed row pointer: first position of each column in the sorted keys.
+__global__ void bounds_kernel(const int32_t *keys, int64_t nnz, int64_t cols, int32_t *trow) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= cols; c += st) {
+    int64_t lo = 0, hi = nnz;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)keys[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    trow[c] = (int32_t)lo;
+  }
+}
+
+template <typename OT>
+__global__ void gather_transpose_kernel(const int32_t *perm, const int32_t *rid, const OT *val, int64_t nnz,
+                                        int32_t *tcol, OT *tval) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz; i += st) {
+    const int32_t j = perm[i];
+    tcol[i] = rid[j];
+    tval[i] = val[j];
+  }
+}
+
+// ---------------------------------------------------------------- host helpers
+
+struct TmpAlloc {
+  std::vector<void *> ptrs;
+  ~TmpAlloc() { for (void *p : ptrs) cudaFree(p); }
+  template <typename T> cudaError_t get(T **p, size_t bytes) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e == cudaSuccess) ptrs.push_back(q);
+    *p = (T *)q;
+    return e;
+  }
+};
+
+static int plan_alloc(Plan &pl, void **p, size_t bytes) {
+  if (pl.cap && pl.bytes + bytes > pl.cap) return SFL_ENOMEM;
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_cuda_error(e, "cudaMalloc");
+    return SFL_ENOMEM;
+  }
+  pl.allocs.push_back(*p);
+  pl.bytes += bytes;
+  return SFL_OK;
+}
+
+static int validate_csr(const sfl_csr *M, cudaStream_t s) {
+  if (!M || M->rows < 0 || M->cols <= 0 || M->nnz < 0 || M->nnz >= (int64_t)1 << 31 || M->rows >= (int64_t)1 << 31 ||
+      M->cols >= (int64_t)1 << 31 || !M->rowptr || (M->nnz > 0 && (!M->colidx || !M->values)) ||
+      (M->dtype != SFL_F64 && M->dtype != SFL_F32 && M->dtype != SFL_BF16))
+    return SFL_EINVAL;
+  if (M->rows == 0) return SFL_EINVAL;
+  TmpAlloc tmp;
+  int *err = nullptr;
+  SFL_CU(tmp.get(&err, sizeof(int)));
+  SFL_CU(cudaMemsetAsync(err, 0, sizeof(int), s));
+  validate_kernel<<<1024, 256, 0, s>>>(M->rowptr, M->colidx, M->values, M->dtype, M->rows, M->cols, M->nnz, err);
+  SFL_CU(cudaGetLastError());
+  int h = 0;
+  SFL_CU(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SFL_CU(cudaStreamSynchronize(s));
+  if (h & (kErrRowptr | kErrCol)) return SFL_EINVAL;
+  if (h & kErrNonfinite) return SFL_ENONFINITE;
+  return SFL_OK;
+}
+
+static int choose_lpr(int64_t pnnz, int64_t rows) {
+  const double avg = rows > 0 ? (double)pnnz / (double)rows : 0.0;
+  if (avg >= 128.0) return 32;
+  if (avg >= 48.0) return 16;
+  return 8;
+}
+
+// Pad (rowptr, col, val[OT]) into plan-owned storage.
+template <typename OT>
+static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const int32_t *col, const OT *val,
+                        int64_t rows, int64_t cols, int64_t nnz, cudaStream_t s) {
+  const int P = load_width(pl.vdt);
+  TmpAlloc tmp;
+  int32_t *plen = nullptr;
+  SFL_CU(tmp.get(&plen, sizeof(int32_t) * (rows + 1)));
+  padded_len_kernel<<<1024, 256, 0, s>>>(rowptr, rows, P, plen);
+  SFL_CU(cudaGetLastError());
+  int r = plan_alloc(pl, (void **)&out.rowptr, sizeof(int32_t) * (rows + 1));
+  if (r) return r;
+  size_t tb = 0;
+  SFL_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb, plen, out.rowptr, (int)(rows + 1), s));
+  void *tst = nullptr;
+  SFL_CU(tmp.get(&tst, tb));
+  SFL_CU(cub::DeviceScan::ExclusiveSum(tst, tb, plen, out.rowptr, (int)(rows + 1), s));
+  int32_t pnnz32 = 0;
+  SFL_CU(cudaMemcpyAsync(&pnnz32, out.rowptr + rows, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SFL_CU(cudaStreamSynchronize(s));
+  const int64_t pnnz = pnnz32;
+  if (pnnz < nnz) return SFL_EINVAL;   // padded count overflowed int32
+  if ((r = plan_alloc(pl, (void **)&out.col, sizeof(int32_t) * (pnnz + 8)))) return r;
+  if ((r = plan_alloc(pl, (void **)&out.val, sizeof(OT) * (pnnz + 8)))) return r;
+  if (rows > 0) {
+    fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.rowptr, out.col, (OT *)out.val);
+    SFL_CU(cudaGetLastError());
+  }
+  out.rows = rows; out.cols = cols; out.nnz = nnz; out.pnnz = pnnz;
+  out.lpr = choose_lpr(pnnz, rows);
+  return SFL_OK;
+}
+
+template <typename OT>
+static int build_plan(Plan &pl, const sfl_csr *A, const sfl_csr *B, cudaStream_t s) {
+  TmpAlloc tmp;
+  OT *aval = nullptr;
+  SFL_CU(tmp.get(&aval, sizeof(OT) * (A->nnz + 1)));
+  if (A->nnz) {
+    convert_values_kernel<OT><<<2048, 256, 0, s>>>(A->values, A->dtype, aval, A->nnz);
+    SFL_CU(cudaGetLastError());
+  }
+  int r = store_padded<OT>(pl, pl.A, A->rowptr, A->colidx, aval, A->rows, A->cols, A->nnz, s);
+  if (r) return r;
+  if (B) {
+    OT *bval = nullptr;
+    SFL_CU(tmp.get(&bval, sizeof(OT) * (B->nnz + 1)));
+    if (B->nnz) {
+      convert_values_kernel<OT><<<2048, 256, 0, s>>>(B->values, B->dtype, bval, B->nnz);
+      SFL_CU(cudaGetLastError());
+    }
+    r = store_padded<OT>(pl, pl.T, B->rowptr, B->colidx, bval, B->rows, B->cols, B->nnz, s);
+    SFL_CU(cudaStreamSynchronize(s));
+    return r;
+  }
+  // Transposed copy: stable radix sort of the entries by column keeps the
+  // row order inside each column, so the CSR of A^T is fully deterministic
+  // and carries exactly the rounded values of the stored A.
+  const int64_t nnz = A->nnz;
+  int32_t *rid, *keys_out, *iota, *perm, *trow, *tcol;
+  OT *tval;
+  SFL_CU(tmp.get(&rid, sizeof(int32_t) * (nnz + 1)));
+  SFL_CU(tmp.get(&keys_out, sizeof(int32_t) * (nnz + 1)));
+  SFL_CU(tmp.get(&iota, sizeof(int32_t) * (nnz + 1)));
+  SFL_CU(tmp.get(&perm, sizeof(int32_t) * (nnz + 1)));
+  SFL_CU(tmp.get(&trow, sizeof(int32_t) * (A->cols + 1)));
+  SFL_CU(tmp.get(&tcol, sizeof(int32_t) * (nnz + 1)));
+  SFL_CU(tmp.get(&tval, sizeof(OT) * (nnz + 1)));
+  if (nnz) {
+    row_ids_kernel<<<2048, 256, 0, s>>>(A->rowptr, A->rows, rid);
+    iota_kernel<<<2048, 256, 0, s>>>(iota, nnz);
+    SFL_CU(cudaGetLastError());
+    int bits = 1;
+    while (((int64_t)1 << bits) < A->cols) ++bits;
+    size_t tb = 0;
+    SFL_CU(cub::DeviceRadixSort::SortPairs(nullptr, tb, A->colidx, keys_out, iota, perm, (int)nnz, 0, bits, s));
+    void *tst = nullptr;
+    SFL_CU(tmp.get(&tst, tb));
+    SFL_CU(cub::DeviceRadixSort::SortPairs(tst, tb, A->colidx, keys_out, iota, perm, (int)nnz, 0, bits, s));
+    gather_transpose_kernel<OT><<<2048, 256, 0, s>>>(perm, rid, aval, nnz, tcol, tval);
+    SFL_CU(cudaGetLastError());
+  }
+  bounds_kernel<<<1024, 256, 0, s>>>(keys_out, nnz, A->cols, trow);
+  SFL_CU(cudaGetLastError());
+  r = store_padded<OT>(pl, pl.T, trow, tcol, tval, A->cols, A->rows, nnz, s);
+  SFL_CU(cudaStreamSynchronize(s));
+  return r;
+}
+
+}  // namespace sfl
+
+using namespace sfl;
+
+extern "C" {
+
+const char *sfl_error_string(int status) {
+  switch (status) {
+    case SFL_OK: return "ok";
+    case SFL_EINVAL: return "invalid argument";
+    case SFL_ENOMEM: return "out of device memory (or over the plan's cap)";
+    case SFL_ECUDA: return "CUDA runtime error";
+    case SFL_ENONFINITE: return "NaN or Inf in the input";
+    case SFL_ETIMEOUT: return "host wait timed out";
+    case SFL_EUNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+const char *sfl_last_cuda_error(void) { return last_cuda_error(); }
+
+int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const sfl_plan_opts *popts,
+                    sfl_stream stream) {
+  if (!plan) return SFL_EINVAL;
+  *plan = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  int r = validate_csr(A, s);
+  if (r) return r;
+  if (B) {
+    if ((r = validate_csr(B, s))) return r;
+    if (B->rows != A->cols || B->cols != A->rows) return SFL_EINVAL;
+  }
+  const sfl_dtype vdt = popts ? popts->value_dtype : SFL_F64;
+  if (vdt != SFL_F64 && vdt != SFL_F32 && vdt != SFL_BF16) return SFL_EINVAL;
+  sfl_plan *p = new sfl_plan();
+  Plan &pl = p->impl;
+  cudaGetDevice(&pl.device);
+  cudaDeviceGetAttribute(&pl.num_sms, cudaDevAttrMultiProcessorCount, pl.device);
+  pl.vdt = vdt;
+  pl.unmatched = B != nullptr;
+  pl.cap = popts ? popts->max_device_bytes : 0;
+  if (vdt == SFL_F64) r = build_plan<double>(pl, A, B, s);
+  else if (vdt == SFL_F32) r = build_plan<float>(pl, A, B, s);
+  else r = build_plan<__nv_bfloat16>(pl, A, B, s);
+  if (r) {
+    sfl_plan_destroy(p);
+    return r;
+  }
+  *plan = p;
+  return SFL_OK;
+}
+
+int sfl_plan_get_stats(const sfl_plan *plan, sfl_plan_stats *st) {
+  if (!plan || !st) return SFL_EINVAL;
+  const Plan &pl = plan->impl;
+  st->rows = pl.A.rows; st->cols = pl.A.cols;
+  st->nnz_A = pl.A.nnz; st->nnz_At = pl.T.nnz;
+  st->padded_nnz_A = pl.A.pnnz; st->padded_nnz_At = pl.T.pnnz;
+  st->lanes_A = pl.A.lpr; st->lanes_At = pl.T.lpr;
+  st->value_dtype = pl.vdt; st->unmatched = pl.unmatched ? 1 : 0;
+  st->device_bytes = pl.bytes;
+  return SFL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars: bit-exact for the sketch's integer draws; FP64 iterates within relative
+1e-10 per iteration; FP64 sparse products within 1e-14 (only the summation
+order differs); reduced-precision products against the oracle run on the same
+rounded operator.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+import torch  # noqa: E402
+
+from paper_2605_22281_gb300 import api as G  # noqa: E402
+
+
+@pytest.fixture(autouse=True)
+def _needs_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("GPU test selected but no CUDA device is available")
+
+RTOL_ITER = 1e-10
+
+
+def to_csr(S) -> wl.CSR:
+    S = sp.csr_matrix(S)
+    return wl.CSR(S.shape, S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data.astype(np.float64))
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def ct64():
+    p = wl.make("ct64_sflsqr")
+    return p, G.Plan(p.A)
+
+
+@pytest.fixture(scope="module")
+def ct64_unmatched():
+    N, na = 64, 60
+    nb = wl.detector_bins(N)
+    A = wl.siddon_projector(N, na, nb)
+    B = wl.pixel_backprojector(N, na, nb)
+    rng = np.random.default_rng(11)
+    x = wl.sparse_phantom(N, rng, 0.05)
+    b, en = wl.add_noise(A.matvec(x), 0.02, rng)
+    return A, B, x, b, en, G.Plan(A, B)
+
+
+def edge_matrix(seed=0, m=37, n=53):
+    """Ragged CSR: empty rows, one 600-entry row, empty columns, sizes not multiples of 4."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for r in range(m):
+        if r % 7 == 3:
+            continue                       # empty row
+        k = 600 if r == 5 else int(rng.integers(1, 9))
+        c = rng.choice(n - 3, size=min(k, n - 3), replace=k > n - 3)
+        rows += [r] * len(c); cols += list(c); vals += list(rng.standard_normal(len(c)))
+    S = sp.coo_matrix((vals, (rows, cols)), shape=(m, n)).tocsr()
+    S.sum_duplicates()
+    return S
+
+
+# ---------------------------------------------------------------- sketch
+
+@pytest.mark.parametrize("seed,s,zeta,ncols", [(42, 200, 8, 5460), (7, 5, 5, 100), (2**63 + 11, 401, 8, 1000),
+                                               (3, 600, 16, 777), (9, 2048, 1, 3000), (43, 400, 8, 65536)])
+def test_sketch_draws_bit_exact(seed, s, zeta, ncols):
+    rows, signs = G.sketch_export(seed, s, zeta, ncols)
+    r_or, s_or = O.sparse_sign_rows(seed, s, zeta, ncols)
+    assert np.array_equal(rows.cpu().numpy(), r_or)
+    assert np.array_equal(signs.cpu().numpy(), s_or)
+
+
+@pytest.mark.parametrize("seed,s,zeta,n", [(1, 200, 8, 5460), (5, 33, 3, 1001), (8, 600, 16, 70000)])
+def test_sketch_apply_matches_oracle(seed, s, zeta, n):
+    v = np.random.default_rng(seed).standard_normal(n)
+    got = G.sketch_apply(seed, s, zeta, dev(v)).cpu().numpy()
+    want = O.SparseSign(seed, s, zeta, n).apply(v)
+    assert rel(got, want) <= 1e-14
+
+
+# ---------------------------------------------------------------- sparse products
+
+@pytest.mark.parametrize("which", ["ct64", "edge", "edge2"])
+def test_spmv_fp64(which, ct64):
+    if which == "ct64":
+        S = ct64[0].A.scipy()
+        plan = ct64[1]
+    else:
+        S = edge_matrix(0 if which == "edge" else 1, *((37, 53) if which == "edge" else (130, 9)))
+        plan = G.Plan(to_csr(S))
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(S.shape[1])
+    u = rng.standard_normal(S.shape[0])
+    assert rel(plan.apply(dev(x)).cpu().numpy(), S @ x) <= 1e-14
+    assert rel(plan.apply(dev(u), transpose=True).cpu().numpy(), S.T @ u) <= 1e-14
+
+
+def test_spmv_unmatched_backprojector(ct64_unmatched):
+    A, B, *_, plan = ct64_unmatched
+    u = np.random.default_rng(5).standard_normal(A.shape[0])
+    assert rel(plan.apply(dev(u), transpose=True).cpu().numpy(), B.scipy() @ u) <= 1e-14
+
+
+@pytest.mark.parametrize("vdt,tol", [("f32", 2e-6), ("bf16", 2e-6)])
+def test_spmv_reduced_precision_on_rounded_operator(vdt, tol, ct64):
+    S = ct64[0].A.scipy().astype(np.float64)
+    if vdt == "f32":
+        Sr = S.astype(np.float32).astype(np.float64)
+    else:
+        Sr = S.copy()
+        Sr.data = torch.as_tensor(S.data).to(torch.bfloat16).to(torch.float64).numpy()
+    plan = G.Plan(ct64[0].A, value_dtype=vdt)
+    x = np.random.default_rng(6).standard_normal(S.shape[1]).astype(np.float32).astype(np.float64)
+    u = np.random.default_rng(7).standard_normal(S.shape[0]).astype(np.float32).astype(np.float64)
+    assert rel(plan.apply(dev(x)).cpu().numpy(), Sr @ x) <= tol
+    assert rel(plan.apply(dev(u), transpose=True).cpu().numpy(), Sr.T @ u) <= tol
+
+
+# ---------------------------------------------------------------- solvers: per-iteration parity
+
+def run_oracle_sflsqr(A, b, s, zeta, seed, maxit, tol, ell, tau=None, AT=None):
+    S = O.SparseSign(seed, s, zeta, A.shape[0])
+    return O.sflsqr(A, b, S, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, record_x=True, keep_basis=False)
+
+
+def run_oracle_sflsmr(A, b, s, zeta, seed, maxit, tol, ell, tau=None, AT=None, stop_rule="residual"):
+    Sn = O.SparseSign(seed, s, zeta, A.shape[1])
+    Sm = O.SparseSign(seed + 1, s, zeta, A.shape[0])
+    return O.sflsmr(A, b, Sn, S_stop=Sm, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, stop_rule=stop_rule,
+                    record_x=True, keep_basis=False)
+
+
+def assert_iterates_match(r, x_gpu_hist, relres_gpu, info, tol_stop, rtol=RTOL_ITER):
+    k = r.iters
+    if abs(r.relres[-1] / tol_stop - 1) > 1e-8 if tol_stop > 0 else True:
+        assert info.iters == k, (info.iters, k)
+    kk = min(k, info.iters)
+    xh = x_gpu_hist.cpu().numpy()
+    rh = relres_gpu.cpu().numpy()
+    worst = 0.0
+    for j in range(kk):
+        e = rel(xh[j], r.xs[j])
+        worst = max(worst, e)
+        assert e <= rtol, f"iterate {j + 1}: rel err {e:.3e}"
+        assert abs(rh[j] - r.relres[j]) <= rtol * abs(r.relres[j]), f"stop ratio {j + 1}"
+    return worst
+
+
+def test_sflsqr_ct64_per_iteration(ct64):
+    p, plan = ct64
+    st = p.settings
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                            maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], x_history=True,
+                            relres_history=True)
+    assert info.status == O.STOP_DISCREPANCY == r.status
+    assert_iterates_match(r, h["x"], h["relres"], info, tol)
+    assert rel(x.cpu().numpy(), r.x) <= RTOL_ITER
+    assert abs(info.tol - tol) <= 1e-15 * tol
+
+
+@pytest.mark.parametrize("ell", [0, 1, 2, 5, 8])
+def test_sflsqr_fixed_iterations_windows(ct64, ell):
+    p, plan = ct64
+    maxit = 40
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, 101, 8, 42, maxit, 0.0, ell)
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=101, zeta=8, seed=42, window=ell, maxit=maxit, x_history=True,
+                            relres_history=True)
+    assert info.status == O.STOP_MAXIT and info.iters == maxit == r.iters
+    assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
+
+
+@pytest.mark.parametrize("precond", ["diag", "reweight"])
+def test_sflsqr_flexible_operators(ct64, precond):
+    p, plan = ct64
+    n = p.A.shape[1]
+    w = np.random.default_rng(47).uniform(0.5, 1.5, n)
+    tau = O.FixedDiag(w) if precond == "diag" else O.Reweighting(1e-4)
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, 61, 8, 46, 30, 0.0, 2, tau=tau)
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=61, zeta=8, seed=46, window=2, maxit=30, precond=precond,
+                            diag_w=dev(w) if precond == "diag" else None, irw_eps=1e-4, x_history=True,
+                            relres_history=True)
+    assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
+
+
+def test_sflsmr_unmatched_reweighted_per_iteration(ct64_unmatched):
+    A, B, x_true, b, en, plan = ct64_unmatched
+    tol = O.discrepancy_tol(1.01, en, np.linalg.norm(b))
+    r = run_oracle_sflsmr(A.scipy(), b, 201, 8, 43, 150, tol, 2, tau=O.Reweighting(1e-4), AT=B.scipy())
+    x, info, h = plan.solve("sflsmr", dev(b), s=201, zeta=8, seed=43, window=2, maxit=150, noise_norm=en, eta=1.01,
+                            precond="reweight", irw_eps=1e-4, x_history=True, relres_history=True)
+    assert info.status == r.status
+    assert_iterates_match(r, h["x"], h["relres"], info, tol)
+
+
+def test_sflsmr_normal_equation_stop_rule(ct64):
+    p, plan = ct64
+    r = run_oracle_sflsmr(p.A.scipy(), p.b, 81, 4, 5, 25, 0.0, 2, stop_rule="normal")
+    x, info, h = plan.solve("sflsmr", dev(p.b), s=81, zeta=4, seed=5, window=2, maxit=25, stop_rule="normal",
+                            x_history=True, relres_history=True)
+    assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
+
+
+# ---------------------------------------------------------------- determinism and drivers
+
+def test_bitwise_reproducible_and_drivers_agree(ct64_unmatched):
+    A, B, x_true, b, en, plan = ct64_unmatched
+    kw = dict(s=201, zeta=8, seed=43, window=2, maxit=60, noise_norm=en, eta=1.01, precond="reweight")
+    x1, i1, _ = plan.solve("sflsmr", dev(b), **kw)
+    x2, i2, _ = plan.solve("sflsmr", dev(b), **kw)
+    x3, i3, _ = plan.solve("sflsmr", dev(b), driver="host_loop", **kw)
+    assert torch.equal(x1, x2) and torch.equal(x1, x3)
+    assert i1.iters == i2.iters == i3.iters
+
+
+def test_host_buffers_entry_point(ct64):
+    p, plan = ct64
+    st = p.settings
+    kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
+              noise_norm=p.noise_norm[0], eta=st["eta"])
+    xd, info_d, _ = plan.solve("sflsqr", dev(p.b), **kw)
+    xh, info_h = plan.solve_host("sflsqr", p.b, **kw)
+    assert np.array_equal(xd.cpu().numpy(), xh) and info_d.iters == info_h.iters
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_minimum_sketch_and_single_step(ct64):
+    p, plan = ct64
+    for zeta, s, maxit in [(1, 2, 1), (1, 11, 10), (16, 17, 16)]:
+        r = run_oracle_sflsqr(p.A.scipy(), p.b, s, zeta, 3, maxit, 0.0, 2)
+        x, info, h = plan.solve("sflsqr", dev(p.b), s=s, zeta=zeta, seed=3, window=2, maxit=maxit, x_history=True,
+                                relres_history=True)
+        assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
+
+
+def test_zero_rhs_returns_zero(ct64):
+    p, plan = ct64
+    x, info, _ = plan.solve("sflsqr", torch.zeros(p.A.shape[0], dtype=torch.float64, device="cuda"), s=21, maxit=20)
+    assert info.status == O.STOP_BREAKDOWN and info.iters == 0
+    assert torch.count_nonzero(x) == 0
+
+
+def test_lucky_breakdown_matches_oracle():
+    A = sp.diags([2.0, 1.0, 0.5, 0.25, 3.0, 1.5]).tocsr()
+    b = np.array([3.0, 0, 0, 0, 0, 0])
+    plan = G.Plan(to_csr(A))
+    for method in ("sflsqr", "sflsmr"):
+        x, info, _ = plan.solve(method, dev(b), s=7, zeta=2, seed=1, window=2, maxit=6)
+        assert info.status == O.STOP_BREAKDOWN and info.iters == 1
+        assert np.allclose(x.cpu().numpy(), [1.5, 0, 0, 0, 0, 0], rtol=0, atol=1e-14)
+
+
+def test_invalid_inputs_are_rejected(ct64):
+    p, plan = ct64
+    b = dev(p.b)
+    with pytest.raises(G.N.SflError) as e:
+        plan.solve("sflsqr", b, s=10, maxit=10)            # needs s >= maxit + 1
+    assert e.value.status == G.N.SFL_EINVAL
+    with pytest.raises(G.N.SflError) as e:
+        plan.solve("sflsqr", b, s=50, maxit=10, window=-1)  # full orthogonalization: oracle only
+    assert e.value.status == G.N.SFL_EUNSUPPORTED
+    bad = to_csr(sp.eye(5, format="csr"))
+    bad.colidx = bad.colidx.copy(); bad.colidx[2] = 7
+    with pytest.raises(G.N.SflError) as e:
+        G.Plan(bad)
+    assert e.value.status == G.N.SFL_EINVAL
+    nanm = to_csr(sp.eye(5, format="csr"))
+    nanm.values = nanm.values.copy(); nanm.values[1] = np.nan
+    with pytest.raises(G.N.SflError) as e:
+        G.Plan(nanm)
+    assert e.value.status == G.N.SFL_ENONFINITE
+    bn = p.b.copy(); bn[3] = np.inf
+    with pytest.raises(G.N.SflError) as e:
+        plan.solve("sflsqr", dev(bn), s=21, maxit=20)
+    assert e.value.status == G.N.SFL_ENONFINITE
+
+
+# ---------------------------------------------------------------- full-size workload
+
+@pytest.mark.slow
+def test_ct256_unmatched_full_size_matches_oracle():
+    """The 256x256 unmatched sFLSMR workload at full size, in the launch
+    configuration the benchmark times: stop step and final iterate vs the
+    oracle, plus sampled intermediate iterates."""
+    p = wl.make("ct256_sflsmr_unmatched")
+    st = p.settings
+    plan = G.Plan(p.A, p.B)
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    r = run_oracle_sflsmr(p.A.scipy(), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"],
+                          tau=O.Reweighting(st["irw_eps"]), AT=p.B.scipy())
+    x, info, h = plan.solve("sflsmr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                            maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], precond="reweight",
+                            irw_eps=st["irw_eps"], x_history=True, relres_history=True)
+    assert info.status == r.status == O.STOP_DISCREPANCY
+    assert_iterates_match(r, h["x"], h["relres"], info, tol)
+    x2, info2, _ = plan.solve("sflsmr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                              maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], precond="reweight",
+                              irw_eps=st["irw_eps"])
+    assert info2.iters == info.iters
+    assert rel(x2.cpu().numpy(), r.x) <= RTOL_ITER
