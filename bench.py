@@ -286,6 +286,8 @@ def run_ours(args):
         gbs = nbytes / (avg_ms * 1e-3) / 1e9
         kern[name] = {"avg_us": 1000 * avg_ms, "bytes": nbytes, "gbs": gbs, "fp64_tflops": 2 * nnz / (avg_ms * 1e-3) / 1e12,
                       "share": kms[name] / max(sum(kms.values()), 1e-12)}
+    breakdown = {c: {"avg_us": 1000 * kms[c] / kl[c], "launches": kl[c], "share": kms[c] / max(sum(kms.values()), 1e-12)}
+                 for c in kms if kl[c] > 0}
     dom = max(kern, key=lambda k: kern[k]["share"])
     roof = {"bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": kern[dom]["gbs"] / peaks["hbm_gbs"], "traffic": recorded_traffic(dom, args.workload),
@@ -353,7 +355,7 @@ def run_ours(args):
                            "rel_error_vs_x_true": err, "plan_build_s": t_plan,
                            "l2": "inputs larger than L2 (operators 464 MB > 129 MB); no flush",
                            "parallelism": f"replicas x{world} (independent problems)"},
-                "roofline": roof, "kernels": kern, "clocks": clocks,
+                "roofline": roof, "kernels": kern, "kernel_breakdown": breakdown, "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": 8 * m,
                         "d2h_bytes_per_step": 8 * n},
                 "gpu_launches": launches_per_step * args.steps,

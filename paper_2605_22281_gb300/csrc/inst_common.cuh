@@ -15,7 +15,8 @@ template <typename XT> __global__ void convert_out_kernel(const XT *x, double *y
 
 template <typename VT, typename XT>
 static const void *spmv_fn(int lpr, bool mat) {
-  if (!mat) return (const void *)spmv_fused_kernel<VT, XT, 32, false>;
+  if (!mat) return (const void *)spmv_fused_kernel<VT, XT, 1, false>;
+  if (lpr == 4) return (const void *)spmv_fused_kernel<VT, XT, 4, true>;
   if (lpr == 8) return (const void *)spmv_fused_kernel<VT, XT, 8, true>;
   if (lpr == 16) return (const void *)spmv_fused_kernel<VT, XT, 16, true>;
   return (const void *)spmv_fused_kernel<VT, XT, 32, true>;
@@ -23,7 +24,8 @@ static const void *spmv_fn(int lpr, bool mat) {
 
 template <typename VT, typename XT>
 cudaError_t Ops<VT, XT>::spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, int grid, size_t smem, cudaStream_t s) {
-  if (!mat) spmv_fused_kernel<VT, XT, 32, false><<<grid, kThreads, smem, s>>>(p);
+  if (!mat) spmv_fused_kernel<VT, XT, 1, false><<<grid, kThreads, smem, s>>>(p);
+  else if (lpr == 4) spmv_fused_kernel<VT, XT, 4, true><<<grid, kThreads, smem, s>>>(p);
   else if (lpr == 8) spmv_fused_kernel<VT, XT, 8, true><<<grid, kThreads, smem, s>>>(p);
   else if (lpr == 16) spmv_fused_kernel<VT, XT, 16, true><<<grid, kThreads, smem, s>>>(p);
   else spmv_fused_kernel<VT, XT, 32, true><<<grid, kThreads, smem, s>>>(p);

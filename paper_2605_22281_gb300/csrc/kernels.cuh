@@ -233,14 +233,49 @@ __device__ void spmv_finish(const SpmvParams<VT, XT> &p, int k, int lo, int nd, 
   }
 }
 
-// One warp computes 32 consecutive rows (LPR lanes per row, P entries per lane
-// per load), then runs the epilogue with lane r holding row r of the block:
-// output write, window dots, and the sparse-sign sketch accumulated in a
-// warp-private shared-memory s-vector in fixed lane order.
+// Row sum of one row for a group of LPR lanes (lane gl of the group), P
+// entries per lane per load, four loads in flight per lane.
+template <typename VT, typename XT, int LPR>
+__device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT> &p, const XT *__restrict__ x,
+                                                       int beg, int end, int gl) {
+  constexpr int P = LoadWidth<VT>::P;
+  constexpr int STR = LPR * P;
+  using ACC = typename AccT<XT>::T;
+  ACC s0 = (ACC)0, s1 = (ACC)0;
+  int off = beg + gl * P;
+#pragma unroll 1
+  for (; off + 3 * STR < end; off += 4 * STR) {
+    Chunk<VT, P> c0, c1, c2, c3;
+    c0.load(p.col, p.val, off);
+    c1.load(p.col, p.val, off + STR);
+    c2.load(p.col, p.val, off + 2 * STR);
+    c3.load(p.col, p.val, off + 3 * STR);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      s0 += (ACC)c0.v[q] * (ACC)__ldg(x + c0.c[q]);
+      s1 += (ACC)c1.v[q] * (ACC)__ldg(x + c1.c[q]);
+      s0 += (ACC)c2.v[q] * (ACC)__ldg(x + c2.c[q]);
+      s1 += (ACC)c3.v[q] * (ACC)__ldg(x + c3.c[q]);
+    }
+  }
+#pragma unroll 1
+  for (; off < end; off += STR) {
+    Chunk<VT, P> c0;
+    c0.load(p.col, p.val, off);
+#pragma unroll
+    for (int q = 0; q < P; ++q) s0 += (ACC)c0.v[q] * (ACC)__ldg(x + c0.c[q]);
+  }
+  return s0 + s1;
+}
+
+// A warp processes groups of G = 32/LPR consecutive rows (LPR lanes per row);
+// lane 0 of each row's lanes then owns the row for the epilogue: output
+// write, window dots, and the sparse-sign sketch accumulated into a
+// warp-private shared-memory s-vector in a fixed order (groups in grid-stride
+// order, rows in index order).  LPR = 1 is the vector pass (no matrix).
 template <typename VT, typename XT, int LPR, bool MAT>
 __global__ void __launch_bounds__(kThreads) spmv_fused_kernel(SpmvParams<VT, XT> p) {
-  constexpr int P = LoadWidth<VT>::P;
-  constexpr int RPS = 32 / LPR;
+  constexpr int G = 32 / LPR;
   using ACC = typename AccT<XT>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SolveState *st = p.st;
@@ -303,60 +338,60 @@ __global__ void __launch_bounds__(kThreads) spmv_fused_kernel(SpmvParams<VT, XT>
   double nacc = 0.0;
   const ACC sc = (ACC)xscale;
 
-  const int64_t nblk = (p.rows + 31) / 32;
+  const int64_t ngrp = (p.rows + G - 1) / G;
   const int gl = lane % LPR, grp = lane / LPR;
-  for (int64_t rb = (int64_t)blockIdx.x * kWarps + warp; rb < nblk; rb += (int64_t)gridDim.x * kWarps) {
-    const int64_t row0 = rb * 32;
-    ACC mine = (ACC)0;
-    if (MAT) {
-#pragma unroll 1
-      for (int t = 0; t < LPR; ++t) {
-        const int64_t row = row0 + t * RPS + grp;
-        ACC sum = (ACC)0;
-        if (row < p.rows) {
-          const int beg = p.rowptr[row], end = p.rowptr[row + 1];
-          for (int off = beg + gl * P; off < end; off += LPR * P) {
-            Chunk<VT, P> ch;
-            ch.load(p.col, p.val, off);
-#pragma unroll
-            for (int q = 0; q < P; ++q) sum += (ACC)ch.v[q] * (ACC)__ldg(x + ch.c[q]);
-          }
-        }
-#pragma unroll
-        for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        const ACC v = __shfl_sync(0xffffffffu, sum, ((lane - t * RPS) & (RPS - 1)) * LPR);
-        if (lane / RPS == t) mine = v;
-      }
-    }
-    // ---- epilogue: lane r owns row row0 + r
-    const int64_t row = row0 + lane;
+  const int64_t gstride = (int64_t)gridDim.x * kWarps;
+  int64_t rb = (int64_t)blockIdx.x * kWarps + warp;
+  int nbeg = 0, nend = 0;
+  if (MAT && rb < ngrp) {
+    const int64_t r = rb * G + grp;
+    if (r < p.rows) { nbeg = p.rowptr[r]; nend = p.rowptr[r + 1]; }
+  }
+  for (; rb < ngrp; rb += gstride) {
+    const int64_t row = rb * G + grp;
     const bool valid = row < p.rows;
     ACC yv = (ACC)0;
-    if (valid) {
-      if (MAT) yv = mine * sc;
-      else yv = (ACC)p.b[row];
-      if (y) y[row] = (XT)yv;
-    }
-    if (reduce && valid) {
-      const double yd = (double)yv;
-      nacc += yd * yd;
+    if (MAT) {
+      const int beg = nbeg, end = nend;
+      const int64_t rn = (rb + gstride) * G + grp;     // prefetch the next group's row bounds
+      if (rb + gstride < ngrp && rn < p.rows) { nbeg = p.rowptr[rn]; nend = p.rowptr[rn + 1]; }
+      else { nbeg = 0; nend = 0; }
+      ACC sum = row_dot<VT, XT, LPR>(p, x, beg, end, gl);
 #pragma unroll
-      for (int a = 0; a < kMaxWindow + 2; ++a)
-        if (a < nd) dacc[a] += (double)win[(size_t)ring_slot(lo + a, R) * wst + row] * yd;
+      for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      yv = sum * sc;
+    } else {
+      if (valid) yv = (ACC)p.b[row];
+    }
+    // ---- epilogue: lane gl == 0 of each group owns its row
+    if (gl == 0 && valid) {
+      if (y) y[row] = (XT)yv;
+      if (reduce) {
+        const double yd = (double)yv;
+        nacc += yd * yd;
+#pragma unroll
+        for (int a = 0; a < kMaxWindow + 2; ++a)
+          if (a < nd) dacc[a] += (double)win[(size_t)ring_slot(lo + a, R) * wst + row] * yd;
+      }
     }
     if (sketch) {
       uint4 tw0 = make_uint4(0, 0, 0, 0), tw1 = make_uint4(0, 0, 0, 0);
-      if (valid) {
+      if (gl == 0 && valid) {
         tw0 = *reinterpret_cast<const uint4 *>(p.tab + row * p.zs);
         if (p.zs == 16) tw1 = *reinterpret_cast<const uint4 *>(p.tab + row * p.zs + 8);
       }
-      const int nrow = (p.rows - row0) < 32 ? (int)(p.rows - row0) : 32;
-      for (int L = 0; L < nrow; ++L) {
+      const int64_t row0 = rb * G;
+      const int nrow = (p.rows - row0) < G ? (int)(p.rows - row0) : G;
+      for (int g = 0; g < nrow; ++g) {
+        const int L = g * LPR;
         const XT v = (XT)__shfl_sync(0xffffffffu, yv, L);
         const uint32_t a0 = __shfl_sync(0xffffffffu, tw0.x, L), a1 = __shfl_sync(0xffffffffu, tw0.y, L);
         const uint32_t a2 = __shfl_sync(0xffffffffu, tw0.z, L), a3 = __shfl_sync(0xffffffffu, tw0.w, L);
-        const uint32_t b0 = __shfl_sync(0xffffffffu, tw1.x, L), b1 = __shfl_sync(0xffffffffu, tw1.y, L);
-        const uint32_t b2 = __shfl_sync(0xffffffffu, tw1.z, L), b3 = __shfl_sync(0xffffffffu, tw1.w, L);
+        uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        if (p.zs == 16) {
+          b0 = __shfl_sync(0xffffffffu, tw1.x, L); b1 = __shfl_sync(0xffffffffu, tw1.y, L);
+          b2 = __shfl_sync(0xffffffffu, tw1.z, L); b3 = __shfl_sync(0xffffffffu, tw1.w, L);
+        }
         if (lane < p.zeta) {
           const int wq = lane >> 1;
           const uint32_t wsel = wq == 0 ? a0 : wq == 1 ? a1 : wq == 2 ? a2 : wq == 3 ? a3
@@ -448,6 +483,13 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
   }
   XT *out = p.ring + (size_t)ring_slot(newj, p.R) * p.stride;
   XT *zout = (p.side == 0) ? p.Z + (size_t)(k - 1) * p.zstride : nullptr;
+  // reweighting: coefficients c_j = sig_j y_j of x_{k-1} = sum_j z~_j c_j
+  __shared__ double s_c[kMaxIt];
+  const bool reweight = p.side == 0 && p.precond == SFL_PRECOND_REWEIGHT;
+  if (reweight) {
+    for (int j = tid; j < k - 1; j += blockDim.x) s_c[j] = p.sigZ[j] * p.y[j];
+    __syncthreads();
+  }
 
   double nacc = 0.0, dacc[kMaxWindow + 2];
 #pragma unroll
@@ -472,9 +514,19 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
       double zt = vd;
       if (p.precond == SFL_PRECOND_DIAG) {
         zt = p.diag_w[i] * vd;
-      } else if (p.precond == SFL_PRECOND_REWEIGHT) {
-        double xv = 0.0;   // x_{k-1}[i] = sum_j z_j[i] y_j
-        for (int j = 0; j < k - 1; ++j) xv += (double)p.Z[(size_t)j * p.zstride + i] * p.sigZ[j] * p.y[j];
+      } else if (reweight) {
+        // x_{k-1}[i] = sum_j z~_j[i] c_j, four independent partial sums
+        const XT *zi = p.Z + i;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int j = 0;
+        for (; j + 3 < k - 1; j += 4) {
+          a0 += (double)zi[(size_t)j * p.zstride] * s_c[j];
+          a1 += (double)zi[(size_t)(j + 1) * p.zstride] * s_c[j + 1];
+          a2 += (double)zi[(size_t)(j + 2) * p.zstride] * s_c[j + 2];
+          a3 += (double)zi[(size_t)(j + 3) * p.zstride] * s_c[j + 3];
+        }
+        for (; j < k - 1; ++j) a0 += (double)zi[(size_t)j * p.zstride] * s_c[j];
+        const double xv = (a0 + a1) + (a2 + a3);
         zt = sqrt(sqrt(xv * xv + st->irw_eps)) * vd;
       }
       zout[i] = (XT)zt;
@@ -584,7 +636,8 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   double *red = part1 + KP;         // [KP] cluster-reduced vector
   double *rr = red + KP;            // [KP] R column above the diagonal
   double *crow = rr + KP;           // [RB] my rows of the working column
-  double *tmp = crow + RB;          // [2 * RB]
+  double *tmp = crow + RB;          // [max(kThreads, RB) + RB] partial sums of (row, column slice)
+  const int H = max(1, kThreads / max(RB, 1));   // column slices per row
   __shared__ double s_w[kWarps];
   __shared__ double s_sc[8];        // scalar partials exchanged in the cluster
   __shared__ double s_res[8];
@@ -631,17 +684,28 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
     }
     __syncthreads();
   };
-  // crow -= Q coef over my rows; two threads per row split the columns
-  auto q_update = [&](const double *coef) {
-    for (int t = tid; t < 2 * RB; t += blockDim.x) {
+  // out[i] = sum_{j < ncol} Mat[j*s + r0 + i] * coef[j] for my rows; thread
+  // (row i, slice h) sums the columns j = h (mod H), slices combined in order.
+  auto rows_times_vec = [&](const double *Mat, const double *coef, int ncol, double *out) {
+    for (int t = tid; t < H * RB; t += blockDim.x) {
       const int i = t % RB, h = t / RB;
       double v = 0.0;
       if (i < nr)
-        for (int j = h; j < kk; j += 2) v += p.Q[(size_t)j * s + r0 + i] * coef[j];
+        for (int j = h; j < ncol; j += H) v += Mat[(size_t)j * s + r0 + i] * coef[j];
       tmp[t] = v;
     }
     __syncthreads();
-    for (int i = tid; i < nr; i += blockDim.x) crow[i] -= (tmp[i] + tmp[RB + i]);
+    for (int i = tid; i < nr; i += blockDim.x) {
+      double a = 0.0;
+      for (int h = 0; h < H; ++h) a += tmp[h * RB + i];
+      out[i] = a;
+    }
+    __syncthreads();
+  };
+  // crow -= Q coef over my rows
+  auto q_update = [&](const double *coef) {
+    rows_times_vec(p.Q, coef, kk, tmp + H * RB);
+    for (int i = tid; i < nr; i += blockDim.x) crow[i] -= tmp[H * RB + i];
     __syncthreads();
   };
 
@@ -725,12 +789,13 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   __threadfence();
   double res2 = cluster_total(enorm2_cta, 2);   // its barrier also publishes y in the cluster
   if (p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL) {
-    // || S_m b - S_m A Z_k y_k ||, my rows
+    // || S_m b - S_m A Z_k y_k ||, my rows (y staged in shared memory)
+    for (int j = tid; j < k; j += blockDim.x) red[j] = __ldcg(p.y + j);
+    __syncthreads();
+    rows_times_vec(p.SAZ, red, k, tmp + H * RB);
     v = 0.0;
     for (int t = tid; t < nr; t += blockDim.x) {
-      const int row = r0 + t;
-      double a = p.sbm[row];
-      for (int j = 0; j < k; ++j) a -= p.SAZ[(size_t)j * s + row] * __ldcg(p.y + j);
+      const double a = p.sbm[r0 + t] - tmp[H * RB + t];
       v += a * a;
     }
     res2 = cluster_total(cta_total(v), 3);

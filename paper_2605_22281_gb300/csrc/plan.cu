@@ -177,11 +177,14 @@ static int validate_csr(const sfl_csr *M, cudaStream_t s) {
   return SFL_OK;
 }
 
-static int choose_lpr(int64_t pnnz, int64_t rows) {
+// Lanes per row: the largest power of two (4..32) that still leaves every
+// lane about six P-wide loads per average row, so each lane keeps several
+// independent loads in flight.
+static int choose_lpr(int64_t pnnz, int64_t rows, int P) {
   const double avg = rows > 0 ? (double)pnnz / (double)rows : 0.0;
-  if (avg >= 128.0) return 32;
-  if (avg >= 48.0) return 16;
-  return 8;
+  int lpr = 32;
+  while (lpr > 4 && avg < 6.0 * P * lpr) lpr >>= 1;
+  return lpr;
 }
 
 // Pad (rowptr, col, val[OT]) into plan-owned storage.
@@ -213,7 +216,7 @@ static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const i
     SFL_CU(cudaGetLastError());
   }
   out.rows = rows; out.cols = cols; out.nnz = nnz; out.pnnz = pnnz;
-  out.lpr = choose_lpr(pnnz, rows);
+  out.lpr = choose_lpr(pnnz, rows, P);
   return SFL_OK;
 }
 

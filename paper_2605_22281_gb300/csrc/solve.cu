@@ -52,7 +52,7 @@ static void destroy_session(Plan &pl, Session &se) {
 
 size_t ls_smem_bytes(int s, int maxit, int cluster) {
   const int RB = (s + cluster - 1) / cluster;
-  return sizeof(double) * (size_t)(4 * (maxit + 2) + 3 * RB);
+  return sizeof(double) * (size_t)(4 * (maxit + 2) + RB + std::max(kThreads, RB) + RB);
 }
 
 int ls_cluster_size(int s, int maxit) {

