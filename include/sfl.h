@@ -228,6 +228,22 @@ int sfl_sketch_export(uint64_t seed, int32_t s, int32_t zeta, int64_t ncols,
 int sfl_sketch_apply(uint64_t seed, int32_t s, int32_t zeta, const double *v, int64_t len,
                      double *sk, sfl_stream stream);
 
+/* sk = S v exactly as sfl_sketch_apply computes it, but allocating nothing.
+ * The paper has no counterpart: this exists for callers that may not call
+ * cudaMalloc, such as code whose device memory is handed out up front by a
+ * caching allocator that owns the pool, or latency-critical loops where an
+ * allocation would synchronise the device.  The draws are regenerated in the
+ * kernel and the reduction scratch is a fixed ~2.2 MB array inside the
+ * library, reserved on every GPU that loads it until the process exits.
+ * Limits: 1 <= zeta <= 16, zeta <= s <= 1024 (larger s returns SFL_EINVAL).
+ * The first call on each device looks up the scratch address on that device;
+ * make that first call before any stream capture.  All calls on a device share
+ * the scratch, so calls that overlap in time on the GPU (different streams or
+ * threads) race; serialise them.  Same results as sfl_sketch_apply up to the
+ * order of summation (relative difference ~1e-16). */
+int sfl_sketch_apply_noalloc(uint64_t seed, int32_t s, int32_t zeta, const double *v, int64_t len,
+                             double *sk, sfl_stream stream);
+
 /* ---- misc --------------------------------------------------------------- */
 
 const char *sfl_error_string(int status);

@@ -74,6 +74,8 @@ _SIGNATURES = {
                                           ctypes.POINTER(KernelTimes), _P]),
     "sfl_sketch_export": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, _P, _P]),
     "sfl_sketch_apply": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P, _P]),
+    "sfl_sketch_apply_noalloc": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64,
+                                                _P, _P]),
     "sfl_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sfl_last_cuda_error": (ctypes.c_char_p, []),
 }

@@ -205,3 +205,17 @@ def sketch_apply(seed: int, s: int, zeta: int, v: torch.Tensor) -> torch.Tensor:
     with torch.cuda.device(v.device):
         N.check(lib.sfl_sketch_apply(seed, s, zeta, _ptr(v), v.numel(), _ptr(out), _stream()), "sfl_sketch_apply")
     return out
+
+
+def sketch_apply_noalloc(seed: int, s: int, zeta: int, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """S v through the allocation-free entry point (s <= 1024).  For callers
+    that may not allocate device memory; pass a preallocated `out`."""
+    _require_cuda()
+    lib = N.load()
+    v = v.to(dtype=torch.float64).contiguous()
+    if out is None:
+        out = torch.empty(s, dtype=torch.float64, device=v.device)
+    with torch.cuda.device(v.device):
+        N.check(lib.sfl_sketch_apply_noalloc(seed, s, zeta, _ptr(v), v.numel(), _ptr(out), _stream()),
+                "sfl_sketch_apply_noalloc")
+    return out
