@@ -276,9 +276,9 @@ def run_ours(args):
     _, info_p, hp = plan.solve(method, b_dev, out=x_dev, driver="profiled", **kw)
     kms, kl = hp["kernel_ms"], hp["kernel_launches"]
     m, n = p.A.shape
-    ell, zs = st["window"], (8 if st["zeta"] <= 8 else 16)
-    fwd_bytes = spmv_bytes(stats["nnz_A"], m, n, 8, 8, ell + 1, m * zs * 2)
-    bwd_bytes = spmv_bytes(stats["nnz_At"], n, m, 8, 8, ell, n * zs * 2 if method == "sflsmr" else 0)
+    ell = st["window"]
+    fwd_bytes = spmv_bytes(stats["nnz_A"], m, n, 8, 8, ell + 1, 0)
+    bwd_bytes = spmv_bytes(stats["nnz_At"], n, m, 8, 8, ell, 0)
     peaks = load_peaks()
     kern = {}
     for name, nbytes, nnz in (("spmv_fwd", fwd_bytes, stats["nnz_A"]), ("spmv_bwd", bwd_bytes, stats["nnz_At"])):
@@ -342,7 +342,8 @@ def run_ours(args):
         else:
             cpu = {"value": None, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": res.get("error", "")}
 
-    launches_per_step = (4 if method == "sflsmr" else 3) + 5 * iters + 2
+    # reset + ||b|| pass + A^T w_1 + initial sketch(es), six kernels per step, x = Z y
+    launches_per_step = 1 + 2 + (2 if method == "sflsmr" else 1) + 6 * iters + 1
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

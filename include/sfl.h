@@ -197,12 +197,12 @@ int sflsmr_solve_host(sfl_plan *plan, const double *b_host, const sfl_opts *opts
 int sfl_solve_host_loop(sfl_plan *plan, int method, const double *b, const sfl_opts *opts, double *x,
                         sfl_info *info, sfl_stream stream);
 
-/* Per-kernel device time of one solve.  Index: 0 sketch tables, 1 init (||b||,
- * S b), 2 init A^T w_1, 3 z orthogonalization + tau, 4 fused A z_k SpMV,
- * 5 w orthogonalization, 6 fused A^T w / B w SpMV, 7 small least squares,
- * 8 x = Z y.  ms: total milliseconds over the launches that did work;
- * launches: their number. */
-#define SFL_NUM_KERNEL_CLASSES 9
+/* Per-kernel device time of one solve.  Index: 0 initial sketches (S b, and
+ * S A^T b for sFLSMR), 1 init ||b||, 2 init A^T w_1, 3 z orthogonalization +
+ * tau, 4 fused A z_k SpMV, 5 w orthogonalization, 6 fused A^T w / B w SpMV,
+ * 7 small least squares, 8 x = Z y, 9 per-step sketches.  ms: total
+ * milliseconds over the launches that did work; launches: their number. */
+#define SFL_NUM_KERNEL_CLASSES 10
 typedef struct {
   double ms[SFL_NUM_KERNEL_CLASSES];
   int32_t launches[SFL_NUM_KERNEL_CLASSES];

@@ -44,11 +44,11 @@ class Info(ctypes.Structure):
 
 
 class KernelTimes(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 9), ("launches", ctypes.c_int32 * 9)]
+    _fields_ = [("ms", ctypes.c_double * 10), ("launches", ctypes.c_int32 * 10)]
 
 
-KERNEL_CLASSES = ["sketch_tables", "init_b", "init_bwd", "orth_z", "spmv_fwd", "orth_w", "spmv_bwd", "small_ls",
-                  "solution"]
+KERNEL_CLASSES = ["sketch_init", "init_b", "init_bwd", "orth_z", "spmv_fwd", "orth_w", "spmv_bwd", "small_ls",
+                  "solution", "sketch"]
 
 
 class PlanStats(ctypes.Structure):

@@ -110,6 +110,94 @@ __device__ __forceinline__ bool grid_reduce(const double *vals, int cnt, const R
   return true;
 }
 
+// Stride (doubles) of one CTA's record in a partial-sum buffer.
+constexpr int kPartStride = 16;
+
+// Copy the device solve state into shared memory (one coalesced pass).
+__device__ __forceinline__ void stage_state(const SolveState *st, SolveState *sst) {
+  static_assert(sizeof(SolveState) % sizeof(double) == 0, "state must be a whole number of doubles");
+  const double *src = reinterpret_cast<const double *>(st);
+  double *dst = reinterpret_cast<double *>(sst);
+  for (int i = threadIdx.x; i < (int)(sizeof(SolveState) / sizeof(double)); i += blockDim.x) dst[i] = __ldcg(src + i);
+  __syncthreads();
+}
+
+// Sum over the 8 warp values w[0..7] as a balanced tree (3 dependent adds).
+__device__ __forceinline__ double tree8(const double *w) {
+  return ((w[0] + w[1]) + (w[2] + w[3])) + ((w[4] + w[5]) + (w[6] + w[7]));
+}
+
+// Totals of NQ <= kPartStride quantities over the per-CTA records of a
+// producer kernel with G CTAs (part[b * kPartStride + q]).  Every CTA of the
+// consumer computes the same values in the same fixed order: warp w sums a
+// contiguous slice of records (lanes strided), folds the lanes with a
+// butterfly, and the 8 warp sums are combined as a tree.  FP64 additions on
+// this GPU have a long latency, so every dependent chain is kept short and the
+// NQ chains are independent.  wsum: smem [kWarps * kPartStride]; out: smem
+// [kPartStride].  All threads call.
+template <int NQ>
+__device__ __forceinline__ void reduce_partials_n(const double *part, int G, double *wsum, double *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (G + kWarps - 1) / kWarps;
+  const int b0 = warp * per, b1 = min(G, b0 + per);
+  double a[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) a[q] = 0.0;
+  for (int b = b0 + lane; b < b1; b += 32) {
+    double v[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = __ldcg(part + (size_t)b * kPartStride + q);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) a[q] += v[q];
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    a[q] = warp_sum(a[q]);
+    if (lane == 0) wsum[warp * kPartStride + q] = a[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double w[kWarps];
+    for (int v = 0; v < kWarps; ++v) w[v] = wsum[v * kPartStride + threadIdx.x];
+    out[threadIdx.x] = tree8(w);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void reduce_partials(const double *part, int G, int nq, double *wsum, double *out) {
+  switch (nq) {
+    case 1: reduce_partials_n<1>(part, G, wsum, out); break;
+    case 2: reduce_partials_n<2>(part, G, wsum, out); break;
+    case 3: reduce_partials_n<3>(part, G, wsum, out); break;
+    case 4: reduce_partials_n<4>(part, G, wsum, out); break;
+    case 5: reduce_partials_n<5>(part, G, wsum, out); break;
+    case 6: reduce_partials_n<6>(part, G, wsum, out); break;
+    case 7: reduce_partials_n<7>(part, G, wsum, out); break;
+    case 8: reduce_partials_n<8>(part, G, wsum, out); break;
+    case 9: reduce_partials_n<9>(part, G, wsum, out); break;
+    default: reduce_partials_n<10>(part, G, wsum, out); break;
+  }
+}
+
+// Per-CTA totals of NQ per-thread values, written to this CTA's record of a
+// partial-sum buffer: lanes fold by butterfly, warps combine as a tree.
+// wsum: smem [kWarps * kPartStride].  All threads call.
+template <int NQ>
+__device__ __forceinline__ void store_partials(const double (&v)[NQ], double *wsum, double *part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const double a = warp_sum(v[q]);
+    if (lane == 0) wsum[warp * kPartStride + q] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double w[kWarps];
+    for (int u = 0; u < kWarps; ++u) w[u] = wsum[u * kPartStride + threadIdx.x];
+    part[(size_t)blockIdx.x * kPartStride + threadIdx.x] = tree8(w);
+  }
+}
+
 // Sum of per-warp values held in lane 0 of each warp (smem scratch wtmp[kWarps]),
 // fixed order; result valid in all threads after the call.
 __device__ __forceinline__ double cta_sum(double v, double *wtmp) {
@@ -126,6 +214,13 @@ __device__ __forceinline__ double cta_sum(double v, double *wtmp) {
 
 template <typename T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
 template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+// Bytes of dynamic shared memory this launch received.
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+  uint32_t v;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
 
 // Ring slot of basis vector j (1-based).
 __device__ __forceinline__ int ring_slot(int j, int R) { return j % R; }

@@ -34,16 +34,24 @@ struct SessionKey {
 
 struct Session {
   SessionKey key{};
-  int RW = 0, RP = 0, zs = 8;
+  int RW = 0, RP = 0;
   SolveState *st = nullptr;
   void *wring = nullptr, *pring = nullptr, *wraw = nullptr, *zraw = nullptr, *Z = nullptr;
   double *sigZ = nullptr;
-  uint16_t *tab_m = nullptr, *tab_n = nullptr;
+  // row-major sparse-sign tables (S_m; S_n for sFLSMR) for the seed tab_seed
+  int32_t *skM_row = nullptr, *skN_row = nullptr;
+  uint32_t *skM_ent = nullptr, *skN_ent = nullptr;
+  uint32_t *sk_kin = nullptr, *sk_vin = nullptr, *sk_kout = nullptr;
+  void *sk_cub = nullptr;
+  size_t sk_cub_bytes = 0;
+  bool tab_valid = false;
+  uint64_t tab_seed = 0;
   double *Q = nullptr, *Rinv = nullptr, *y = nullptr, *e = nullptr, *rhs = nullptr;
   double *SAZ = nullptr, *SAtW = nullptr, *Hband = nullptr, *sbm = nullptr;
   double *bbuf = nullptr, *xbuf = nullptr, *dw = nullptr;
   int *err = nullptr;
-  RedScratch red{};
+  Partials part{};                     // per-CTA partial sums of the reducing kernels
+  int32_t *wrowA = nullptr, *wrowT = nullptr;   // nnz-balanced row range of every warp
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int grid_spmv_A = 0, grid_spmv_T = 0, grid_vec = 0, grid_init = 0;
@@ -78,6 +86,7 @@ struct Ops {
   static cudaError_t convert_out(const XT *x, double *y, int64_t n, cudaStream_t s);
   static int spmv_occupancy(int lpr, bool mat, size_t smem);
   static cudaError_t set_smem(int lpr, bool mat, size_t smem);
+  static cudaError_t set_orth_smem(size_t smem);
 };
 
 cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s);

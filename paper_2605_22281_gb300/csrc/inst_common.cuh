@@ -38,6 +38,12 @@ cudaError_t Ops<VT, XT>::set_smem(int lpr, bool mat, size_t smem) {
 }
 
 template <typename VT, typename XT>
+cudaError_t Ops<VT, XT>::set_orth_smem(size_t smem) {
+  return cudaFuncSetAttribute((const void *)orth_update_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+template <typename VT, typename XT>
 int Ops<VT, XT>::spmv_occupancy(int lpr, bool mat, size_t smem) {
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_fn<VT, XT>(lpr, mat), kThreads, smem) != cudaSuccess)

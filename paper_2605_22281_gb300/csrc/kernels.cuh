@@ -60,15 +60,25 @@ static __global__ void sketch_table_kernel(uint64_t seed, const uint64_t *seed_s
   if (tab) for (int q = cnt; q < zs; ++q) tab[c * zs + q] = 0xFFFFu;
 }
 
-// ---------------------------------------------------------------- fused SpMV
+// ---------------------------------------------------------------- step kernels
+
+// Partial-sum buffers: each producing kernel stores one record per CTA; the
+// next kernel on the stream reduces them (reduce_partials) and derives the
+// scalars of the step identically in every CTA.  CTA 0 persists them.
+struct Partials {
+  double *b;     // init pass: ||b||^2                       -> init A^T w_1
+  double *z;     // A^T w products: ||z||^2, <p_j, z>         -> z update of the next step
+  double *p;     // z update: ||p~_k||^2, <p~_k, p~_j>        -> A z_k product
+  double *w;     // A z_k product: ||w||^2, <w_j, w>          -> w update
+  double *wn;    // w update: ||w~_{k+1}||^2, <w~_{k+1}, w~_j> -> A^T w_{k+1} product
+};
 
 enum SpmvMode : int {
   kModeApply = 0,    // plain y = A x
-  kModeInitB = 1,    // row value = b_i: ||b||^2, S_m b, w~_1 = b
-  kModeInitBwd = 2,  // z = A^T w_1, ||z||^2, (sFLSMR) S_n z
-  kModeFwd = 3,      // w = A z_k, window dots with w_j, ||w||^2, S_m w
-  kModeBwd = 4,      // z = A^T w_{k+1}, window dots with p_j, ||z||^2, (sFLSMR) S_n z
-  kModeSketch = 5    // row value = b_i: sk_out = S b only
+  kModeInitB = 1,    // row value = b_i: ||b||^2, w~_1 = b
+  kModeInitBwd = 2,  // z = A^T w_1, ||z||^2
+  kModeFwd = 3,      // w = A z_k, window dots with w_j, ||w||^2
+  kModeBwd = 4       // z = A^T w_{k+1}, window dots with p_j, ||z||^2
 };
 
 template <typename VT, typename XT>
@@ -77,33 +87,23 @@ struct SpmvParams {
   const int32_t *col;
   const VT *val;
   int64_t rows;
+  const int32_t *wrow;      // row range of every warp (nnz balanced), gridDim*kWarps + 1 entries
   int mode;
   int method;
-  int stop_rule;
   int ell;
-  int s;
-  int zeta;
-  int zs;
-  int maxit;
+  int G_prev;               // CTAs of the kernel whose partials this one reduces
   const XT *x;              // kModeApply: input vector
   const double *b;          // kModeInitB
-  XT *y;                    // output (kModeApply / kModeInitB: explicit)
+  XT *y;                    // output (kModeApply)
   SolveState *st;
   XT *wring; int64_t wstride; int RW;   // ring of w~ (m-vectors)
   XT *pring; int64_t pstride; int RP;   // ring of p~ (n-vectors)
   XT *Z; int64_t zstride;               // z~_j columns
-  const double *sigZ;
+  double *sigZ;
   XT *wraw;                             // w = A z_k
   XT *zraw;                             // z = A^T w
-  const uint16_t *tab;                  // sketch table of the output space (or null)
-  double *SAZ;     // sFLSQR: LS columns S_m A z_k;  sFLSMR: m-side stop columns
-  double *SAtW;    // sFLSMR: S_n A^T w_j columns (s x (maxit+1))
-  double *Hband;   // sFLSMR: columns of H, (ell+2) entries per column
-  double *rhs;     // LS right-hand side
-  double *e;       // LS residual vector
-  double *sbm;     // sFLSMR residual rule: S_m b
-  double *sk_out;  // kModeSketch output
-  RedScratch red;
+  double *Hband;                        // sFLSMR: columns of H, (ell+2) entries per column
+  Partials part;
 };
 
 // Loads of P consecutive stored entries (P*4 bytes of indices, P*sizeof(VT) of values).
@@ -149,92 +149,20 @@ template <> struct LoadWidth<__nv_bfloat16> { static constexpr int P = 8; };
 
 template <typename XT> struct AccT { using T = XT; };
 
-// Finisher of the fused SpMV: runs in the single CTA holding the final sums.
-//   tot[0] = ||y||^2, tot[1..nd] = window dots, tot[1+nd ..] = unscaled sketch.
-template <typename VT, typename XT>
-__device__ void spmv_finish(const SpmvParams<VT, XT> &p, int k, int lo, int nd, const double *tot, double *wtmp) {
-  SolveState *st = p.st;
-  const int tid = threadIdx.x;
-  const double isz = 1.0 / sqrt((double)p.zeta);
-  const double *sk = tot + 1 + nd;
-  if (p.mode == kModeSketch) {
-    for (int i = tid; i < p.s; i += blockDim.x) p.sk_out[i] = sk[i] * isz;
-  } else if (p.mode == kModeInitB) {
-    double *dst = (p.method == kSFLSQR) ? p.rhs : p.sbm;
-    double ss = 0.0;
-    for (int i = tid; i < p.s; i += blockDim.x) {
-      const double v = sk[i] * isz;
-      dst[i] = v;
-      if (p.method == kSFLSQR) p.e[i] = v;
-      ss += v * v;
-    }
-    ss = cta_sum(ss, wtmp);
-    if (tid == 0) {
-      const double beta = sqrt(tot[0]);
-      st->beta0 = beta;
-      st->sig_w[ring_slot(1, p.RW)] = 1.0 / beta;
-      st->tol = (st->noise_norm > 0.0) ? st->eta * st->noise_norm / beta : 0.0;
-      if (p.method == kSFLSQR || p.stop_rule == SFL_STOP_RULE_RESIDUAL) st->stop_den = sqrt(ss);
-      if (!(beta > 0.0)) st->stop = SFL_STOP_BREAKDOWN;
-      if (!isfinite(tot[0]) || !isfinite(ss)) st->stop = kStopNonfinite;
-    }
-  } else if (p.mode == kModeInitBwd) {
-    if (p.method == kSFLSMR) {
-      double ss = 0.0;
-      const double beta = st->beta0;
-      for (int i = tid; i < p.s; i += blockDim.x) {
-        const double v = sk[i] * isz;
-        p.SAtW[i] = v;
-        p.rhs[i] = beta * v;
-        p.e[i] = beta * v;
-        ss += (beta * v) * (beta * v);
-      }
-      ss = cta_sum(ss, wtmp);
-      if (tid == 0 && p.stop_rule == SFL_STOP_RULE_NORMAL) st->stop_den = sqrt(ss);
-    }
-    if (tid == 0) st->znorm_raw2 = tot[0];
-  } else if (p.mode == kModeFwd) {
-    double *col = p.SAZ + (size_t)(k - 1) * p.s;
-    for (int i = tid; i < p.s; i += blockDim.x) col[i] = sk[i] * isz;
-    if (tid == 0) {
-      st->wnorm_raw2 = tot[0];
-      // MGS coefficients through the window Gram matrix:
-      // h_j = <w_j, w> - sum_{i<j} h_i <w_j, w_i>
-      double h[kMaxWindow + 2];
-      for (int a = 0; a < nd; ++a) {
-        const int ja = lo + a;
-        double v = tot[1 + a] * st->sig_w[ring_slot(ja, p.RW)];
-        for (int c = 0; c < a; ++c) v -= h[c] * st->gram_w[ring_slot(ja, p.RW)][ring_slot(lo + c, p.RW)];
-        h[a] = v;
-        st->hw[a] = v;
-      }
-      if (p.method == kSFLSMR) {
-        double *hb = p.Hband + (size_t)(k - 1) * (p.ell + 2);
-        for (int q = 0; q < p.ell + 2; ++q) hb[q] = 0.0;
-        for (int a = 0; a < nd; ++a) hb[(lo + a) - k + p.ell] = h[a];
-      }
-    }
-  } else if (p.mode == kModeBwd) {
-    if (p.method == kSFLSMR) {
-      double *col = p.SAtW + (size_t)k * p.s;
-      for (int i = tid; i < p.s; i += blockDim.x) col[i] = sk[i] * isz;
-    }
-    if (tid == 0) {
-      st->znorm_raw2 = tot[0];
-      double c[kMaxWindow + 2];
-      for (int a = 0; a < nd; ++a) {
-        const int ja = lo + a;
-        double v = tot[1 + a] * st->sig_p[ring_slot(ja, p.RP)];
-        for (int q = 0; q < a; ++q) v -= c[q] * st->gram_p[ring_slot(ja, p.RP)][ring_slot(lo + q, p.RP)];
-        c[a] = v;
-        st->cz[a] = v;
-      }
-    }
+// Row sum of one row for a group of LPR lanes (lane gl of the group), P
+// entries per lane per load.  Every iteration issues four loads per lane
+// (those past the row end are predicated off and contribute zero), so a row
+// costs ceil(loads / 4) memory round trips instead of one per leftover load.
+template <typename VT, int P>
+__device__ __forceinline__ void load_or_zero(Chunk<VT, P> &c, const int32_t *col, const VT *val, int off, bool ok) {
+  if (ok) {
+    c.load(col, val, off);
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) { c.c[q] = 0; c.v[q] = 0; }
   }
 }
 
-// Row sum of one row for a group of LPR lanes (lane gl of the group), P
-// entries per lane per load, four loads in flight per lane.
 template <typename VT, typename XT, int LPR>
 __device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT> &p, const XT *__restrict__ x,
                                                        int beg, int end, int gl) {
@@ -242,14 +170,13 @@ __device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT>
   constexpr int STR = LPR * P;
   using ACC = typename AccT<XT>::T;
   ACC s0 = (ACC)0, s1 = (ACC)0;
-  int off = beg + gl * P;
 #pragma unroll 1
-  for (; off + 3 * STR < end; off += 4 * STR) {
+  for (int off = beg + gl * P; off < end; off += 4 * STR) {
     Chunk<VT, P> c0, c1, c2, c3;
     c0.load(p.col, p.val, off);
-    c1.load(p.col, p.val, off + STR);
-    c2.load(p.col, p.val, off + 2 * STR);
-    c3.load(p.col, p.val, off + 3 * STR);
+    load_or_zero(c1, p.col, p.val, off + STR, off + STR < end);
+    load_or_zero(c2, p.col, p.val, off + 2 * STR, off + 2 * STR < end);
+    load_or_zero(c3, p.col, p.val, off + 3 * STR, off + 3 * STR < end);
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       s0 += (ACC)c0.v[q] * (ACC)__ldg(x + c0.c[q]);
@@ -258,181 +185,343 @@ __device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT>
       s1 += (ACC)c3.v[q] * (ACC)__ldg(x + c3.c[q]);
     }
   }
-#pragma unroll 1
-  for (; off < end; off += STR) {
-    Chunk<VT, P> c0;
-    c0.load(p.col, p.val, off);
-#pragma unroll
-    for (int q = 0; q < P; ++q) s0 += (ACC)c0.v[q] * (ACC)__ldg(x + c0.c[q]);
-  }
   return s0 + s1;
 }
 
-// A warp processes groups of G = 32/LPR consecutive rows (LPR lanes per row);
-// lane 0 of each row's lanes then owns the row for the epilogue: output
-// write, window dots, and the sparse-sign sketch accumulated into a
-// warp-private shared-memory s-vector in a fixed order (groups in grid-stride
-// order, rows in index order).  LPR = 1 is the vector pass (no matrix).
-template <typename VT, typename XT, int LPR, bool MAT>
-__global__ void __launch_bounds__(kThreads) spmv_fused_kernel(SpmvParams<VT, XT> p) {
+// MGS coefficients of a window through its Gram matrix (unit vectors):
+// c_a = d_a sig_a - sum_{b<a} c_b <v_a, v_b>, for window vectors lo..lo+nd-1.
+__device__ __forceinline__ void mgs_coefficients(const double *dots, int nd, int lo, int R, const double *sig,
+                                                 const double (*gram)[kRing], double *c) {
+  for (int a = 0; a < nd; ++a) {
+    const int sa = ring_slot(lo + a, R);
+    double v = dots[a] * sig[sa];
+    for (int q = 0; q < a; ++q) v -= c[q] * gram[sa][ring_slot(lo + q, R)];
+    c[a] = v;
+  }
+}
+
+// Rows [r0, r1) of one warp, in 32-row blocks: groups of LPR lanes run one row
+// each in LPR substeps; per-lane partial sums are stashed in shared memory and
+// lane r adds its row's partials in order, so the epilogue (output, norm,
+// window dots) runs with lane r owning row r and every FP64 instruction on a
+// full warp.  LPR = 1 is the vector pass (no matrix; the row value is b_r).
+template <typename VT, typename XT, int LPR, bool MAT, int ND>
+__device__ __forceinline__ void spmv_rows(const SpmvParams<VT, XT> &p, int64_t r0, int64_t r1,
+                                          const XT *__restrict__ x, XT *y, double xscale, const XT *win, int64_t wst,
+                                          int R, int lo, double (&acc)[ND + 1], typename AccT<XT>::T *stash) {
   constexpr int G = 32 / LPR;
   using ACC = typename AccT<XT>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SolveState *st = p.st;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31;
+  const int gl = lane % LPR, grp = lane / LPR;
+  const ACC sc = (ACC)xscale;
+  for (int64_t row0 = r0; row0 < r1; row0 += 32) {
+    const int64_t row = row0 + lane;
+    const bool valid = row < r1;
+    ACC yv = (ACC)0;
+    if (MAT) {
+      // lane r holds rowptr[row0 + r]; rows past r1 read rowptr[r1] (empty ranges)
+      const int rp = p.rowptr[valid ? row : r1];
+      const int rp_last = p.rowptr[(row0 + 32) < r1 ? (row0 + 32) : r1];
+      int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
+      if (lane == 31) rp_next = rp_last;
+#pragma unroll 1
+      for (int t = 0; t < LPR; ++t) {
+        const int r = t * G + grp;
+        const int beg = __shfl_sync(0xffffffffu, rp, r);
+        const int end = __shfl_sync(0xffffffffu, rp_next, r);
+        stash[t * 32 + lane] = row_dot<VT, XT, LPR>(p, x, beg, end, gl);
+      }
+      __syncwarp();
+      const int t = lane / G, g = lane % G;
+      ACC s = (ACC)0;
+#pragma unroll
+      for (int l = 0; l < LPR; ++l) s += stash[t * 32 + g * LPR + l];
+      __syncwarp();
+      yv = s * sc;
+    } else {
+      if (valid) yv = (ACC)p.b[row];
+    }
+    if (valid) y[row] = (XT)yv;
+    const double yd = valid ? (double)yv : 0.0;
+    acc[0] += yd * yd;
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+      acc[1 + a] += valid ? (double)win[(size_t)ring_slot(lo + a, R) * wst + row] * yd : 0.0;
+  }
+}
 
-  // ---- resolve the step's operands from the device state
+template <typename VT, typename XT, int LPR, bool MAT, int ND>
+__device__ __forceinline__ void spmv_run(const SpmvParams<VT, XT> &p, const XT *x, XT *y, double xscale,
+                                         const XT *win, int64_t wst, int R, int lo, double *outpart, bool reduce,
+                                         unsigned char *smem_raw, double *wsum) {
+  using ACC = typename AccT<XT>::T;
+  const int warp = threadIdx.x >> 5;
+  ACC *stash = reinterpret_cast<ACC *>(smem_raw) + warp * 32 * (LPR > 1 ? LPR : 1);
+  double acc[ND + 1];
+#pragma unroll
+  for (int a = 0; a <= ND; ++a) acc[a] = 0.0;
+  const int gw = blockIdx.x * kWarps + warp;
+  int64_t r0, r1;
+  if (p.wrow) { r0 = p.wrow[gw]; r1 = p.wrow[gw + 1]; }
+  else {
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    r0 = (p.rows * gw) / W; r1 = (p.rows * (gw + 1)) / W;
+  }
+  spmv_rows<VT, XT, LPR, MAT, ND>(p, r0, r1, x, y, xscale, win, wst, R, lo, acc, stash);
+  if (!reduce) return;
+  __syncthreads();
+  store_partials<ND + 1>(acc, wsum, outpart);
+}
+
+__host__ __device__ inline size_t spmv_smem_bytes(int lpr, size_t acc_bytes) {
+  return acc_bytes * kWarps * 32 * (lpr > 1 ? lpr : 1);
+}
+
+// Fused SpMV of one step.  The prologue stages the solve state and reduces the
+// previous kernel's partial sums into the scalars this product needs (scale of
+// its input, breakdown decisions); CTA 0 records them in the device state.
+template <typename VT, typename XT, int LPR, bool MAT>
+__global__ void __launch_bounds__(kThreads, 2) spmv_fused_kernel(SpmvParams<VT, XT> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SolveState sst;
+  __shared__ double wsum[kWarps * kPartStride];
+  __shared__ double tot[kPartStride];
+  // a launch with too little shared memory does nothing (never writes out of bounds)
+  if (dynamic_smem_bytes() < spmv_smem_bytes(LPR, sizeof(typename AccT<XT>::T))) return;
+  const bool cta0 = blockIdx.x == 0 && threadIdx.x == 0;
   int k = 0, lo = 1, nd = 0;
   const XT *x = p.x;
   XT *y = p.y;
   const XT *win = nullptr; int64_t wst = 0; int R = 1;
   double xscale = 1.0;
-  bool sketch = false, reduce = true;
+  double *outpart = nullptr;
+  bool reduce = true;
   if (p.mode == kModeApply) {
     reduce = false;
-  } else if (p.mode == kModeSketch) {
-    sketch = true;
   } else {
-    if (st->stop) return;
-    k = st->k + 1;
+    stage_state(p.st, &sst);
+    if (sst.stop) return;
+    k = sst.k + 1;
     if (p.mode == kModeInitB) {
       y = p.wring + (size_t)ring_slot(1, p.RW) * p.wstride;
-      sketch = true;
+      outpart = p.part.b;
     } else if (p.mode == kModeInitBwd) {
+      reduce_partials(p.part.b, p.G_prev, 1, wsum, tot);
+      const double beta = sqrt(tot[0]);
+      if (cta0) {
+        SolveState *st = p.st;
+        st->beta0 = beta;
+        st->sig_w[ring_slot(1, p.RW)] = 1.0 / beta;
+        st->tol = (sst.noise_norm > 0.0) ? sst.eta * sst.noise_norm / beta : 0.0;
+        if (!(beta > 0.0)) st->stop = SFL_STOP_BREAKDOWN;
+        if (!isfinite(tot[0])) st->stop = kStopNonfinite;
+      }
+      if (!(beta > 0.0) || !isfinite(tot[0])) return;
       x = p.wring + (size_t)ring_slot(1, p.RW) * p.wstride;
-      xscale = st->sig_w[ring_slot(1, p.RW)];
+      xscale = 1.0 / beta;
       y = p.zraw;
-      sketch = (p.method == kSFLSMR);
+      outpart = p.part.z;
     } else if (p.mode == kModeFwd) {
+      // alpha_k = ||p~_k|| from the z update; breakdown test; Gram row of p_k
+      const int lz = max(1, k - p.ell), ndz = k - lz;          // window of the z update
+      reduce_partials(p.part.p, p.G_prev, 1 + ndz, wsum, tot);
+      const double alpha = sqrt(tot[0]);
+      const bool bad = !(alpha > 1e-300) || !(alpha > 1e-14 * sqrt(sst.znorm_raw2)) || !isfinite(tot[0]);
+      if (cta0) {
+        SolveState *st = p.st;
+        if (bad) {
+          st->stop = isfinite(tot[0]) ? SFL_STOP_BREAKDOWN : kStopNonfinite;
+        } else {
+          const int ns = ring_slot(k, p.RP);
+          st->alpha = alpha;
+          st->sig_p[ns] = 1.0 / alpha;
+          p.sigZ[k - 1] = 1.0 / alpha;
+          for (int a = 0; a < ndz; ++a) {
+            const int sa = ring_slot(lz + a, p.RP);
+            const double g = tot[1 + a] * sst.sig_p[sa] / alpha;
+            st->gram_p[ns][sa] = g; st->gram_p[sa][ns] = g;
+          }
+        }
+      }
+      if (bad) return;
       x = p.Z + (size_t)(k - 1) * p.zstride;
-      xscale = p.sigZ[k - 1];
+      xscale = 1.0 / alpha;
       y = p.wraw;
       lo = max(1, k - p.ell); nd = k - lo + 1;
       win = p.wring; wst = p.wstride; R = p.RW;
-      sketch = true;
+      outpart = p.part.w;
     } else {  // kModeBwd
-      if (st->lucky) return;
+      // beta_{k+1} = ||w~_{k+1}|| from the w update; lucky-breakdown test; Gram row of w_{k+1}
+      const int lw = max(1, k - p.ell), ndw = k - lw + 1;      // window of the w update
+      reduce_partials(p.part.wn, p.G_prev, 1 + ndw, wsum, tot);
+      const double beta = sqrt(tot[0]);
+      const bool nonfinite = !isfinite(tot[0]);
+      const bool lucky = !(beta > 1e-300) || !(beta > 1e-14 * sqrt(sst.wnorm_raw2));
+      if (cta0) {
+        SolveState *st = p.st;
+        if (nonfinite) {
+          st->stop = kStopNonfinite;
+        } else if (lucky) {
+          st->lucky = 1;                 // step k is still solved; there is no w_{k+1}
+          st->betak = 0.0;
+        } else {
+          const int ns = ring_slot(k + 1, p.RW);
+          st->betak = beta;
+          st->sig_w[ns] = 1.0 / beta;
+          if (p.method == kSFLSMR) p.Hband[(size_t)(k - 1) * (p.ell + 2) + p.ell + 1] = beta;
+          for (int a = 0; a < ndw; ++a) {
+            const int sa = ring_slot(lw + a, p.RW);
+            const double g = tot[1 + a] * sst.sig_w[sa] / beta;
+            st->gram_w[ns][sa] = g; st->gram_w[sa][ns] = g;
+          }
+        }
+      }
+      if (nonfinite || lucky) return;
       x = p.wring + (size_t)ring_slot(k + 1, p.RW) * p.wstride;
-      xscale = st->sig_w[ring_slot(k + 1, p.RW)];
+      xscale = 1.0 / beta;
       y = p.zraw;
       lo = max(1, k + 1 - p.ell); nd = k - lo + 1;
       win = p.pring; wst = p.pstride; R = p.RP;
-      sketch = (p.method == kSFLSMR);
+      outpart = p.part.z;
     }
   }
-  XT *skacc = reinterpret_cast<XT *>(smem_raw);            // [kWarps][s] when sketching
-  double *vals = reinterpret_cast<double *>(smem_raw + (sketch ? sizeof(XT) * kWarps * p.s : 0));
-  const int nvals = 1 + nd + (sketch ? p.s : 0);
-  double *wtmp = vals + nvals;                             // [kWarps * (kMaxWindow + 3)]
-  __shared__ int s_flag;
+  if (!MAT) {     // vector pass: no window dots
+    spmv_run<VT, XT, LPR, MAT, 0>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum);
+    return;
+  }
+  switch (nd) {   // the window size is a compile-time constant inside the body
+    case 0: spmv_run<VT, XT, LPR, MAT, 0>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    case 1: spmv_run<VT, XT, LPR, MAT, 1>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    case 2: spmv_run<VT, XT, LPR, MAT, 2>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    case 3: spmv_run<VT, XT, LPR, MAT, 3>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    case 4: spmv_run<VT, XT, LPR, MAT, 4>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    case 5: spmv_run<VT, XT, LPR, MAT, 5>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    case 6: spmv_run<VT, XT, LPR, MAT, 6>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    case 7: spmv_run<VT, XT, LPR, MAT, 7>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    case 8: spmv_run<VT, XT, LPR, MAT, 8>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+    default: spmv_run<VT, XT, LPR, MAT, 9>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+  }
+}
 
-  if (sketch) {
-    for (int i = tid; i < kWarps * p.s; i += blockDim.x) skacc[i] = (XT)0;
-    __syncthreads();
+// Row range of every warp so that each warp gets about the same number of
+// stored entries (rows are never split).  W warps, W + 1 boundaries.
+static __global__ void balance_rows_kernel(const int32_t *rowptr, int64_t rows, int W, int32_t *wrow) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w > W) return;
+  const int64_t nnz = rowptr[rows];
+  const int64_t target = (nnz * w) / W;
+  int64_t lo = 0, hi = rows;          // first row whose start is >= target
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)rowptr[mid] < target) lo = mid + 1; else hi = mid;
   }
-  XT *myacc = skacc + warp * p.s;
+  wrow[w] = (int32_t)(w == W ? rows : lo);
+}
 
-  double dacc[kMaxWindow + 2];
-#pragma unroll
-  for (int a = 0; a < kMaxWindow + 2; ++a) dacc[a] = 0.0;
-  double nacc = 0.0;
-  const ACC sc = (ACC)xscale;
+// ---------------------------------------------------------------- sketch (gather form)
 
-  const int64_t ngrp = (p.rows + G - 1) / G;
-  const int gl = lane % LPR, grp = lane / LPR;
-  const int64_t gstride = (int64_t)gridDim.x * kWarps;
-  int64_t rb = (int64_t)blockIdx.x * kWarps + warp;
-  int nbeg = 0, nend = 0;
-  if (MAT && rb < ngrp) {
-    const int64_t r = rb * G + grp;
-    if (r < p.rows) { nbeg = p.rowptr[r]; nend = p.rowptr[r + 1]; }
+// Draws of every column as (row, column | sign bit) pairs in column-major
+// order, for the stable sort that builds the row-major sketch table.
+static __global__ void sketch_pairs_kernel(uint64_t seed, int s, int zeta, int64_t ncols, uint32_t *keys,
+                                           uint32_t *vals, int *err) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  int rows[kMaxZeta];
+  int cnt = 0;
+  for (uint32_t t = 0; cnt < zeta && t < 1000000u; ++t) {
+    const uint64_t h = splitmix64_first(seed ^ (((uint64_t)c << 32) + t));
+    const int r = (int)__umul64hi(h, (uint64_t)s);
+    bool dup = false;
+    for (int q = 0; q < cnt; ++q) dup |= (rows[q] == r);
+    if (dup) continue;
+    rows[cnt] = r;
+    keys[c * zeta + cnt] = (uint32_t)r;
+    vals[c * zeta + cnt] = (uint32_t)c | ((uint32_t)(h & 1ull) << 31);
+    ++cnt;
   }
-  for (; rb < ngrp; rb += gstride) {
-    const int64_t row = rb * G + grp;
-    const bool valid = row < p.rows;
-    ACC yv = (ACC)0;
-    if (MAT) {
-      const int beg = nbeg, end = nend;
-      const int64_t rn = (rb + gstride) * G + grp;     // prefetch the next group's row bounds
-      if (rb + gstride < ngrp && rn < p.rows) { nbeg = p.rowptr[rn]; nend = p.rowptr[rn + 1]; }
-      else { nbeg = 0; nend = 0; }
-      ACC sum = row_dot<VT, XT, LPR>(p, x, beg, end, gl);
-#pragma unroll
-      for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      yv = sum * sc;
-    } else {
-      if (valid) yv = (ACC)p.b[row];
-    }
-    // ---- epilogue: lane gl == 0 of each group owns its row
-    if (gl == 0 && valid) {
-      if (y) y[row] = (XT)yv;
-      if (reduce) {
-        const double yd = (double)yv;
-        nacc += yd * yd;
-#pragma unroll
-        for (int a = 0; a < kMaxWindow + 2; ++a)
-          if (a < nd) dacc[a] += (double)win[(size_t)ring_slot(lo + a, R) * wst + row] * yd;
-      }
-    }
-    if (sketch) {
-      uint4 tw0 = make_uint4(0, 0, 0, 0), tw1 = make_uint4(0, 0, 0, 0);
-      if (gl == 0 && valid) {
-        tw0 = *reinterpret_cast<const uint4 *>(p.tab + row * p.zs);
-        if (p.zs == 16) tw1 = *reinterpret_cast<const uint4 *>(p.tab + row * p.zs + 8);
-      }
-      const int64_t row0 = rb * G;
-      const int nrow = (p.rows - row0) < G ? (int)(p.rows - row0) : G;
-      for (int g = 0; g < nrow; ++g) {
-        const int L = g * LPR;
-        const XT v = (XT)__shfl_sync(0xffffffffu, yv, L);
-        const uint32_t a0 = __shfl_sync(0xffffffffu, tw0.x, L), a1 = __shfl_sync(0xffffffffu, tw0.y, L);
-        const uint32_t a2 = __shfl_sync(0xffffffffu, tw0.z, L), a3 = __shfl_sync(0xffffffffu, tw0.w, L);
-        uint32_t b0 = 0, b1 = 0, b2 = 0, b3 = 0;
-        if (p.zs == 16) {
-          b0 = __shfl_sync(0xffffffffu, tw1.x, L); b1 = __shfl_sync(0xffffffffu, tw1.y, L);
-          b2 = __shfl_sync(0xffffffffu, tw1.z, L); b3 = __shfl_sync(0xffffffffu, tw1.w, L);
-        }
-        if (lane < p.zeta) {
-          const int wq = lane >> 1;
-          const uint32_t wsel = wq == 0 ? a0 : wq == 1 ? a1 : wq == 2 ? a2 : wq == 3 ? a3
-                              : wq == 4 ? b0 : wq == 5 ? b1 : wq == 6 ? b2 : b3;
-          const uint32_t ent = (lane & 1) ? (wsel >> 16) : (wsel & 0xFFFFu);
-          const int r = (int)(ent & 0x7FFFu);
-          myacc[r] += (ent & 0x8000u) ? -v : v;
-        }
-        __syncwarp();
-      }
-    }
+  if (cnt < zeta) {            // never expected; keep every entry in range and report it
+    atomicExch(err, 1);
+    for (; cnt < zeta; ++cnt) { keys[c * zeta + cnt] = 0u; vals[c * zeta + cnt] = (uint32_t)c; }
   }
-  if (!reduce) return;
+}
 
-  // ---- CTA totals in fixed order
-  {
-    double v = warp_sum(nacc);
-    if (lane == 0) wtmp[warp * (kMaxWindow + 3)] = v;
-#pragma unroll
-    for (int a = 0; a < kMaxWindow + 2; ++a) {
-      if (a < nd) {
-        v = warp_sum(dacc[a]);
-        if (lane == 0) wtmp[warp * (kMaxWindow + 3) + 1 + a] = v;
-      }
-    }
+// Row pointer of the sorted sketch table: first entry of each row.
+static __global__ void sketch_rowptr_kernel(const uint32_t *keys, int64_t nent, int s, int32_t *rowptr) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > s) return;
+  int64_t lo = 0, hi = nent;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)keys[mid] < r) lo = mid + 1; else hi = mid;
   }
+  rowptr[r] = (int32_t)lo;
+}
+
+enum SketchMode : int {
+  kSkPlain = 0,    // sk_out = S v (v FP64)
+  kSkInitB = 1,    // S_m b: sFLSQR right-hand side, or sFLSMR's residual-rule S_m b
+  kSkInitBwd = 2,  // sFLSMR: S_n A^T w_1 -> first column of S A^T W, right-hand side beta * it
+  kSkStep = 3      // S_m w (LS column / stop column) and, for sFLSMR, S_n z (new column of S A^T W)
+};
+
+template <typename XT>
+struct SketchParams {
+  int mode, method, s;
+  double isz;                              // 1 / sqrt(zeta)
+  SolveState *st;
+  const double *v64;                       // kSkPlain / kSkInitB input
+  const XT *wraw, *zraw;                   // kSkStep / kSkInitBwd inputs
+  const int32_t *rowM; const uint32_t *entM;   // m-side table (S_m)
+  const int32_t *rowN; const uint32_t *entN;   // n-side table (S_n)
+  double *SAZ, *SAtW, *rhs, *e, *sbm, *sk_out;
+};
+
+// One CTA per sketch row: sum of +-v[c] over the row's entries (thread-strided
+// partial sums combined in fixed order), times 1/sqrt(zeta).
+template <typename XT>
+__global__ void __launch_bounds__(kThreads) sketch_rows_kernel(SketchParams<XT> p) {
+  __shared__ double wsum[kWarps];
+  int k = 0;
+  double beta = 1.0;
+  if (p.mode != kSkPlain) {
+    const SolveState *st = p.st;
+    if (__ldcg(&st->stop)) return;
+    k = __ldcg(&st->k) + 1;
+    if (p.mode == kSkStep && blockIdx.x >= p.s && __ldcg(&st->lucky)) return;   // no z at a lucky breakdown
+    if (p.mode == kSkInitBwd) beta = __ldcg(&st->beta0);
+  }
+  const int which = blockIdx.x / p.s, r = blockIdx.x % p.s;
+  const bool nside = (p.mode == kSkInitBwd) || (p.mode == kSkStep && which == 1);
+  const int32_t *rowptr = nside ? p.rowN : p.rowM;
+  const uint32_t *ent = nside ? p.entN : p.entM;
+  double a = 0.0;
+  const int b0 = rowptr[r], b1 = rowptr[r + 1];
+  for (int i = b0 + (int)threadIdx.x; i < b1; i += blockDim.x) {
+    const uint32_t e = __ldg(ent + i);
+    const uint32_t c = e & 0x7FFFFFFFu;
+    double v;
+    if (p.mode == kSkPlain || p.mode == kSkInitB) v = p.v64[c];
+    else v = (double)(nside ? p.zraw[c] : p.wraw[c]);
+    a += (e >> 31) ? -v : v;
+  }
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = a;
   __syncthreads();
-  for (int i = tid; i < 1 + nd; i += blockDim.x) {
-    double acc = 0.0;
-    for (int w = 0; w < kWarps; ++w) acc += wtmp[w * (kMaxWindow + 3) + i];
-    vals[i] = acc;
+  if (threadIdx.x != 0) return;
+  const double val = tree8(wsum) * p.isz;
+  if (p.mode == kSkPlain) {
+    p.sk_out[r] = val;
+  } else if (p.mode == kSkStep) {
+    if (which == 0) p.SAZ[(size_t)(k - 1) * p.s + r] = val;
+    else p.SAtW[(size_t)k * p.s + r] = val;
+  } else if (p.mode == kSkInitB) {
+    if (p.method == kSFLSQR) { p.rhs[r] = val; p.e[r] = val; }
+    else p.sbm[r] = val;
+  } else {   // kSkInitBwd
+    p.SAtW[r] = val;
+    p.rhs[r] = beta * val;
+    p.e[r] = beta * val;
   }
-  if (sketch) {
-    for (int i = tid; i < p.s; i += blockDim.x) {
-      double acc = 0.0;
-      for (int w = 0; w < kWarps; ++w) acc += (double)skacc[w * p.s + i];
-      vals[1 + nd + i] = acc;
-    }
-  }
-  __syncthreads();
-  if (grid_reduce(vals, nvals, p.red, vals, &s_flag)) spmv_finish(p, k, lo, nd, vals, wtmp);
 }
 
 // ---------------------------------------------------------------- orthogonalization updates
@@ -442,74 +531,54 @@ struct OrthParams {
   SolveState *st;
   int side;            // 0: z side (p ring, tau, Z), 1: w side (w ring)
   int ell;
+  int method;
+  int G_prev;          // CTAs of the product kernel whose partials this one reduces
   int64_t len;
   const XT *raw;       // z (n) or w (m) before orthogonalization
   XT *ring; int64_t stride; int R;
   XT *Z; int64_t zstride;   // z side: Z columns
-  double *sigZ;
+  const double *sigZ;
   int precond;
   const double *diag_w;     // SFL_PRECOND_DIAG
   const double *y;          // LS solution y_{k-1} (SFL_PRECOND_REWEIGHT)
-  double *Hband;            // sFLSMR: H_{k+1,k}
-  int method;
-  RedScratch red;
+  double *Hband;            // sFLSMR: column k of H (rows lo..k)
+  Partials part;
 };
 
 // z side: p~_k = z - sum_{j=lo}^{k-1} c_j p_j, z~_k = tau_k(p~_k);
 // w side: w~_{k+1} = w - sum_{j=lo}^{k} h_j w_j.
-// Reduces ||new||^2 and <new, v_j> over the window (for the next Gram rows).
-template <typename XT>
-__global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p) {
-  SolveState *st = p.st;
-  if (st->stop) return;
-  const int k = st->k + 1;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int lo, hi, newj;
-  if (p.side == 0) { lo = max(1, k - p.ell); hi = k - 1; newj = k; }
-  else { lo = max(1, k - p.ell); hi = k; newj = k + 1; }
-  const int nd = hi - lo + 1 > 0 ? hi - lo + 1 : 0;
-  double coef[kMaxWindow + 2];
-  const XT *vj[kMaxWindow + 2];
+// Stores this CTA's ||new||^2 and <new, v~_j> over the window.  ND (the
+// window size) is a compile-time constant, so no FP64 instruction is issued
+// for an unused window slot.
+template <typename XT, int ND>
+__device__ __forceinline__ void orth_run(const OrthParams<XT> &p, const SolveState &sst, int k, int lo, int newj,
+                                         const double *coefs, const double *s_c, bool reweight, double *wsum) {
+  double coef[ND > 0 ? ND : 1];
+  const XT *vj[ND > 0 ? ND : 1];
 #pragma unroll
-  for (int a = 0; a < kMaxWindow + 2; ++a) {
-    coef[a] = 0.0;
-    vj[a] = p.ring;
-    if (a < nd) {
-      const int slot = ring_slot(lo + a, p.R);
-      const double sg = (p.side == 0) ? st->sig_p[slot] : st->sig_w[slot];
-      coef[a] = ((p.side == 0) ? st->cz[a] : st->hw[a]) * sg;
-      vj[a] = p.ring + (size_t)slot * p.stride;
-    }
+  for (int a = 0; a < ND; ++a) {
+    const int slot = ring_slot(lo + a, p.R);
+    const double sg = (p.side == 0) ? sst.sig_p[slot] : sst.sig_w[slot];
+    coef[a] = coefs[a] * sg;
+    vj[a] = p.ring + (size_t)slot * p.stride;
   }
   XT *out = p.ring + (size_t)ring_slot(newj, p.R) * p.stride;
   XT *zout = (p.side == 0) ? p.Z + (size_t)(k - 1) * p.zstride : nullptr;
-  // reweighting: coefficients c_j = sig_j y_j of x_{k-1} = sum_j z~_j c_j
-  __shared__ double s_c[kMaxIt];
-  const bool reweight = p.side == 0 && p.precond == SFL_PRECOND_REWEIGHT;
-  if (reweight) {
-    for (int j = tid; j < k - 1; j += blockDim.x) s_c[j] = p.sigZ[j] * p.y[j];
-    __syncthreads();
-  }
-
-  double nacc = 0.0, dacc[kMaxWindow + 2];
+  double acc[ND + 1];
 #pragma unroll
-  for (int a = 0; a < kMaxWindow + 2; ++a) dacc[a] = 0.0;
+  for (int a = 0; a <= ND; ++a) acc[a] = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + tid; i < p.len; i += stride) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.len; i += stride) {
     double v = (double)p.raw[i];
-    double old[kMaxWindow + 2];
+    double old[ND > 0 ? ND : 1];
 #pragma unroll
-    for (int a = 0; a < kMaxWindow + 2; ++a) {
-      old[a] = 0.0;
-      if (a < nd) { old[a] = (double)vj[a][i]; v -= coef[a] * old[a]; }
-    }
+    for (int a = 0; a < ND; ++a) { old[a] = (double)vj[a][i]; v -= coef[a] * old[a]; }
     const XT vx = (XT)v;
     out[i] = vx;
     const double vd = (double)vx;
-    nacc += vd * vd;
+    acc[0] += vd * vd;
 #pragma unroll
-    for (int a = 0; a < kMaxWindow + 2; ++a)
-      if (a < nd) dacc[a] += vd * old[a];
+    for (int a = 0; a < ND; ++a) acc[1 + a] += vd * old[a];
     if (p.side == 0) {
       double zt = vd;
       if (p.precond == SFL_PRECOND_DIAG) {
@@ -527,66 +596,69 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
         }
         for (; j < k - 1; ++j) a0 += (double)zi[(size_t)j * p.zstride] * s_c[j];
         const double xv = (a0 + a1) + (a2 + a3);
-        zt = sqrt(sqrt(xv * xv + st->irw_eps)) * vd;
+        zt = sqrt(sqrt(xv * xv + sst.irw_eps)) * vd;
       }
       zout[i] = (XT)zt;
     }
   }
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *vals = reinterpret_cast<double *>(smem_raw);
-  double *wtmp = vals + (kMaxWindow + 3);
-  __shared__ int s_flag;
-  {
-    double v = warp_sum(nacc);
-    if (lane == 0) wtmp[warp * (kMaxWindow + 3)] = v;
-#pragma unroll
-    for (int a = 0; a < kMaxWindow + 2; ++a) {
-      if (a < nd) {
-        v = warp_sum(dacc[a]);
-        if (lane == 0) wtmp[warp * (kMaxWindow + 3) + 1 + a] = v;
+  __syncthreads();
+  store_partials<ND + 1>(acc, wsum, p.side == 0 ? p.part.p : p.part.wn);
+}
+
+template <typename XT>
+__global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p) {
+  extern __shared__ __align__(16) double s_c[];     // [maxit] reweighting coefficients
+  __shared__ SolveState sst;
+  __shared__ double wsum[kWarps * kPartStride];
+  __shared__ double tot[kPartStride];
+  __shared__ double coefs[kMaxWindow + 2];
+  stage_state(p.st, &sst);
+  if (sst.stop) return;
+  const int k = sst.k + 1;
+  if (dynamic_smem_bytes() < sizeof(double) * (size_t)k) return;
+  const bool cta0 = blockIdx.x == 0 && threadIdx.x == 0;
+  int lo, nd, newj;
+  if (p.side == 0) {
+    // coefficients of z against p_lo..p_{k-1} from the A^T w product's dots
+    lo = max(1, k - p.ell); nd = k - lo; newj = k;
+    reduce_partials(p.part.z, p.G_prev, 1 + nd, wsum, tot);
+    if (threadIdx.x == 0) mgs_coefficients(tot + 1, nd, lo, p.R, sst.sig_p, sst.gram_p, coefs);
+    if (cta0) p.st->znorm_raw2 = tot[0];
+  } else {
+    // coefficients of w against w_lo..w_k (column k of H) from the A z_k product's dots
+    lo = max(1, k - p.ell); nd = k - lo + 1; newj = k + 1;
+    reduce_partials(p.part.w, p.G_prev, 1 + nd, wsum, tot);
+    if (threadIdx.x == 0) mgs_coefficients(tot + 1, nd, lo, p.R, sst.sig_w, sst.gram_w, coefs);
+    if (cta0) {
+      p.st->wnorm_raw2 = tot[0];
+      for (int a = 0; a < nd; ++a) p.st->hw[a] = coefs[a];
+      if (p.method == kSFLSMR) {
+        double *hb = p.Hband + (size_t)(k - 1) * (p.ell + 2);
+        for (int q = 0; q < p.ell + 2; ++q) hb[q] = 0.0;
+        for (int a = 0; a < nd; ++a) hb[(lo + a) - k + p.ell] = coefs[a];
       }
     }
   }
+  // reweighting: coefficients c_j = sig_j y_j of x_{k-1} = sum_j z~_j c_j
+  const bool reweight = p.side == 0 && p.precond == SFL_PRECOND_REWEIGHT;
+  if (reweight)
+    for (int j = threadIdx.x; j < k - 1; j += blockDim.x) s_c[j] = p.sigZ[j] * p.y[j];
   __syncthreads();
-  if (tid < 1 + nd) {
-    double acc = 0.0;
-    for (int w = 0; w < kWarps; ++w) acc += wtmp[w * (kMaxWindow + 3) + tid];
-    vals[tid] = acc;
-  }
-  __syncthreads();
-  if (!grid_reduce(vals, 1 + nd, p.red, vals, &s_flag)) return;
-  if (tid != 0) return;
-  const double nrm = sqrt(vals[0]);
-  const int ns = ring_slot(newj, p.R);
-  if (p.side == 0) {
-    const double raw = sqrt(st->znorm_raw2);
-    if (!(nrm > 1e-300) || !(nrm > 1e-14 * raw)) { st->stop = isfinite(vals[0]) ? SFL_STOP_BREAKDOWN : kStopNonfinite; return; }
-    st->alpha = nrm;
-    st->sig_p[ns] = 1.0 / nrm;
-    p.sigZ[k - 1] = 1.0 / nrm;
-    for (int a = 0; a < nd; ++a) {
-      const int sa = ring_slot(lo + a, p.R);
-      const double g = vals[1 + a] * st->sig_p[sa] / nrm;
-      st->gram_p[ns][sa] = g; st->gram_p[sa][ns] = g;
-    }
-  } else {
-    const double raw = sqrt(st->wnorm_raw2);
-    if (!isfinite(vals[0])) { st->stop = kStopNonfinite; return; }
-    if (!(nrm > 1e-300) || !(nrm > 1e-14 * raw)) {
-      st->lucky = 1;       // step k is still solved; no w_{k+1}
-      st->betak = 0.0;
-      return;
-    }
-    st->betak = nrm;
-    st->sig_w[ns] = 1.0 / nrm;
-    if (p.method == kSFLSMR) p.Hband[(size_t)(k - 1) * (p.ell + 2) + p.ell + 1] = nrm;
-    for (int a = 0; a < nd; ++a) {
-      const int sa = ring_slot(lo + a, p.R);
-      const double g = vals[1 + a] * st->sig_w[sa] / nrm;
-      st->gram_w[ns][sa] = g; st->gram_w[sa][ns] = g;
-    }
+  switch (nd) {
+    case 0: orth_run<XT, 0>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 1: orth_run<XT, 1>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 2: orth_run<XT, 2>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 3: orth_run<XT, 3>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 4: orth_run<XT, 4>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 5: orth_run<XT, 5>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 6: orth_run<XT, 6>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 7: orth_run<XT, 7>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 8: orth_run<XT, 8>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    default: orth_run<XT, 9>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
   }
 }
+
+__host__ __device__ inline size_t orth_smem_bytes(int maxit) { return sizeof(double) * (size_t)(maxit + 1); }
 
 // ---------------------------------------------------------------- small FP64 least squares
 
@@ -601,6 +673,7 @@ struct LsParams {
   const double *SAtW; // sFLSMR
   const double *Hband;
   const double *sbm;  // sFLSMR residual rule: S_m b
+  const double *rhs;  // right-hand side of the small problem
   double *relres_hist;
   cudaGraphConditionalHandle cond;
   int use_cond;
@@ -629,6 +702,11 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   const int RB = (s + CL - 1) / CL;
   const int r0 = min(s, rank * RB), r1 = min(s, r0 + RB), nr = r1 - r0;
   const int KP = p.maxit + 2;
+  // every CTA of the cluster got the same shared memory: all leave together
+  if (dynamic_smem_bytes() < sizeof(double) * (size_t)(4 * KP + RB + max(kThreads, RB) + RB)) {
+    if (rank == 0 && tid == 0 && p.use_cond) cudaGraphSetConditional(p.cond, 0u);
+    return;
+  }
 
   extern __shared__ __align__(16) double lsm[];
   double *part0 = lsm;              // [KP] partial vectors exchanged in the cluster (double-buffered)
@@ -788,6 +866,15 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   }
   __threadfence();
   double res2 = cluster_total(enorm2_cta, 2);   // its barrier also publishes y in the cluster
+  // denominator of the stop ratio, once: ||s_b|| (sFLSQR), ||S_m b|| (sFLSMR,
+  // residual rule) or ||s_{A^T b}|| (sFLSMR, normal-equation rule)
+  double den = st->stop_den;
+  if (k == 1) {
+    const double *dv = (p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL) ? p.sbm : p.rhs;
+    v = 0.0;
+    for (int i = tid; i < nr; i += blockDim.x) v += dv[r0 + i] * dv[r0 + i];
+    den = sqrt(cluster_total(cta_total(v), 4));
+  }
   if (p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL) {
     // || S_m b - S_m A Z_k y_k ||, my rows (y staged in shared memory)
     for (int j = tid; j < k; j += blockDim.x) red[j] = __ldcg(p.y + j);
@@ -802,7 +889,8 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   }
   cl.sync();   // no CTA leaves while a peer may still read its shared memory
   if (rank == 0 && tid == 0) {
-    const double rel = sqrt(res2) / st->stop_den;
+    if (k == 1) st->stop_den = den;
+    const double rel = sqrt(res2) / den;
     st->relres = rel;
     if (p.relres_hist) p.relres_hist[kk] = rel;
     if (k == 1) st->R11 = rho;

@@ -1,7 +1,10 @@
 // Solve driver: per-configuration sessions (workspace + CUDA graph whose body
 // is one step of Algorithm 1 / 2 inside a device-controlled WHILE node), the
 // solver entry points, plan apply/destroy and the sketch entry points.
+#include <cub/cub.cuh>
+
 #include <chrono>
+#include <functional>
 #include <cstring>
 #include <thread>
 
@@ -97,36 +100,81 @@ cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t 
   return cudaLaunchKernelEx(&cfg, ls_step_kernel, p);
 }
 
-static size_t spmv_smem(int s, size_t xsize) {
-  return xsize * (size_t)kWarps * s + sizeof(double) * (size_t)(1 + kMaxWindow + 2 + s + kWarps * (kMaxWindow + 3));
+// Row-major sparse-sign table for ncols columns: pairs (row, column|sign) in
+// column-major draw order, stably sorted by row, so every row lists its
+// columns in increasing order (deterministic).
+struct SketchTableTmp {
+  uint32_t *kin = nullptr, *vin = nullptr, *kout = nullptr;
+  void *cub = nullptr;
+  size_t cub_bytes = 0;
+};
+
+static int build_sketch_table(uint64_t seed, int s, int zeta, int64_t ncols, int32_t *rowptr, uint32_t *ent,
+                              SketchTableTmp &t, int *err, cudaStream_t st) {
+  const int64_t nent = ncols * zeta;
+  sketch_pairs_kernel<<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>(seed, s, zeta, ncols, t.kin, t.vin, err);
+  SFL_CU(cudaGetLastError());
+  int bits = 1;
+  while ((1 << bits) < s) ++bits;
+  size_t need = 0;
+  SFL_CU(cub::DeviceRadixSort::SortPairs(nullptr, need, t.kin, t.kout, t.vin, ent, (int)nent, 0, bits, st));
+  if (need > t.cub_bytes) return SFL_ENOMEM;
+  SFL_CU(cub::DeviceRadixSort::SortPairs(t.cub, need, t.kin, t.kout, t.vin, ent, (int)nent, 0, bits, st));
+  sketch_rowptr_kernel<<<(s + 256) / 256, 256, 0, st>>>(t.kout, nent, s, rowptr);
+  SFL_CU(cudaGetLastError());
+  return SFL_OK;
 }
-static size_t orth_smem() { return sizeof(double) * (size_t)(kMaxWindow + 3) * (1 + kWarps); }
+
+static size_t sketch_sort_bytes(int64_t nent, int s) {
+  int bits = 1;
+  while ((1 << bits) < s) ++bits;
+  size_t need = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, need, (uint32_t *)nullptr, (uint32_t *)nullptr, (uint32_t *)nullptr,
+                                  (uint32_t *)nullptr, (int)nent, 0, bits);
+  return need;
+}
 
 template <typename VT, typename XT>
 struct Engine {
   using O = Ops<VT, XT>;
+  using ACC = typename AccT<XT>::T;
 
   static SpmvParams<VT, XT> base_params(const Plan &pl, const Session &se, const StoredCsr &M, int mode) {
     SpmvParams<VT, XT> p{};
     p.rowptr = M.rowptr; p.col = M.col; p.val = (const VT *)M.val; p.rows = M.rows;
     p.mode = mode;
-    p.method = se.key.method; p.stop_rule = se.key.stop_rule;
-    p.ell = se.key.ell; p.s = se.key.s; p.zeta = se.key.zeta; p.zs = se.zs; p.maxit = se.key.maxit;
+    p.method = se.key.method;
+    p.ell = se.key.ell;
     p.st = se.st;
+    p.part = se.part;
+    if (mode == kModeFwd) { p.wrow = se.wrowA; p.G_prev = se.grid_vec; }
+    else if (mode == kModeBwd) { p.wrow = se.wrowT; p.G_prev = se.grid_vec; }
+    else if (mode == kModeInitBwd) { p.wrow = se.wrowT; p.G_prev = se.grid_init; }
     p.wring = (XT *)se.wring; p.wstride = pl.A.rows; p.RW = se.RW;
     p.pring = (XT *)se.pring; p.pstride = pl.A.cols; p.RP = se.RP;
     p.Z = (XT *)se.Z; p.zstride = pl.A.cols; p.sigZ = se.sigZ;
     p.wraw = (XT *)se.wraw; p.zraw = (XT *)se.zraw;
-    p.SAZ = se.SAZ; p.SAtW = se.SAtW; p.Hband = se.Hband; p.rhs = se.rhs; p.e = se.e; p.sbm = se.sbm;
-    p.red = se.red;
+    p.Hband = se.Hband;
     return p;
+  }
+
+  static SketchParams<XT> sketch_params(const Session &se, int mode) {
+    SketchParams<XT> q{};
+    q.mode = mode; q.method = se.key.method; q.s = se.key.s; q.isz = 1.0 / std::sqrt((double)se.key.zeta);
+    q.st = se.st;
+    q.v64 = se.bbuf;
+    q.wraw = (const XT *)se.wraw; q.zraw = (const XT *)se.zraw;
+    q.rowM = se.skM_row; q.entM = se.skM_ent; q.rowN = se.skN_row; q.entN = se.skN_ent;
+    q.SAZ = se.SAZ; q.SAtW = se.SAtW; q.rhs = se.rhs; q.e = se.e; q.sbm = se.sbm;
+    return q;
   }
 
   static OrthParams<XT> orth_params(const Plan &pl, const Session &se, int side) {
     OrthParams<XT> o{};
     o.st = se.st; o.side = side; o.ell = se.key.ell;
     o.method = se.key.method;
-    o.red = se.red;
+    o.part = se.part;
+    o.G_prev = side == 0 ? se.grid_spmv_T : se.grid_spmv_A;
     o.Hband = se.Hband;
     if (side == 0) {
       o.len = pl.A.cols; o.raw = (const XT *)se.zraw; o.ring = (XT *)se.pring; o.stride = pl.A.cols; o.R = se.RP;
@@ -144,46 +192,70 @@ struct Engine {
     q.st = se.st; q.method = se.key.method; q.s = se.key.s; q.maxit = se.key.maxit; q.ell = se.key.ell;
     q.stop_rule = se.key.stop_rule;
     q.Q = se.Q; q.Rinv = se.Rinv; q.y = se.y; q.e = se.e;
-    q.SAZ = se.SAZ; q.SAtW = se.SAtW; q.Hband = se.Hband; q.sbm = se.sbm;
+    q.SAZ = se.SAZ; q.SAtW = se.SAtW; q.Hband = se.Hband; q.sbm = se.sbm; q.rhs = se.rhs;
     q.relres_hist = se.key.r_hist;
     q.cond = h; q.use_cond = use_cond;
     return q;
   }
 
-  static int enqueue_prologue(const Plan &pl, const Session &se, cudaStream_t s) {
-    const int64_t m = pl.A.rows, n = pl.A.cols;
-    const int method = se.key.method;
-    const uint64_t *seed_src = &se.st->seed;
-    // m-side sketch: S_m for sFLSQR, the stop sketch (seed + 1) for sFLSMR
-    sketch_table_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(0, seed_src, method == kSFLSMR ? 1 : 0,
-                                                                     se.key.s, se.key.zeta, m, se.zs, se.tab_m,
-                                                                     nullptr, nullptr, se.err);
-    SFL_CU(cudaGetLastError());
-    if (method == kSFLSMR) {
-      sketch_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(0, seed_src, 0, se.key.s, se.key.zeta, n, se.zs,
-                                                                       se.tab_n, nullptr, nullptr, se.err);
-      SFL_CU(cudaGetLastError());
+  // Kernel classes of the profiled driver (sfl_kernel_times index).
+  enum { kKSketchInit = 0, kKInitB, kKInitBwd, kKOrthZ, kKFwd, kKOrthW, kKBwd, kKLs, kKSolution, kKSketch };
+
+  template <typename F> static int launch_one(int cls, F &&f, const std::function<int(int, std::function<int()>)> *tm) {
+    if (tm) return (*tm)(cls, std::function<int()>(f));
+    return f();
+  }
+
+  static int k_sketch(const Session &se, int mode, int grid, cudaStream_t s) {
+    sketch_rows_kernel<XT><<<grid, kThreads, 0, s>>>(sketch_params(se, mode));
+    return cudaGetLastError() == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  }
+  static int k_spmv(const Plan &pl, const Session &se, int mode, cudaStream_t s) {
+    const bool fwd = (mode == kModeFwd || mode == kModeInitB);
+    const StoredCsr &M = fwd ? pl.A : pl.T;
+    SpmvParams<VT, XT> p = base_params(pl, se, M, mode);
+    if (mode == kModeInitB) {
+      p.rows = pl.A.rows;
+      p.b = se.bbuf;
+      return O::spmv(p, 1, false, se.grid_init, se.smem_init, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
     }
-    SpmvParams<VT, XT> p = base_params(pl, se, pl.A, kModeInitB);
-    p.rows = m; p.b = se.bbuf; p.tab = se.tab_m;
-    SFL_CU(O::spmv(p, 32, false, se.grid_init, se.smem_init, s));
-    p = base_params(pl, se, pl.T, kModeInitBwd);
-    p.tab = se.tab_n;
-    SFL_CU(O::spmv(p, pl.T.lpr, true, se.grid_spmv_T, se.smem_T, s));
+    const int grid = fwd ? se.grid_spmv_A : se.grid_spmv_T;
+    const size_t smem = fwd ? se.smem_A : se.smem_T;
+    return O::spmv(p, M.lpr, true, grid, smem, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  }
+  static int k_orth(const Plan &pl, const Session &se, int side, cudaStream_t s) {
+    return O::orth(orth_params(pl, se, side), se.grid_vec, se.smem_orth, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  }
+
+  using Timer = std::function<int(int, std::function<int()>)>;
+
+  static int enqueue_prologue(const Plan &pl, const Session &se, cudaStream_t s, const Timer *tm = nullptr) {
+    int r;
+    if ((r = launch_one(kKInitB, [&] { return k_spmv(pl, se, kModeInitB, s); }, tm))) return r;
+    if ((r = launch_one(kKInitBwd, [&] { return k_spmv(pl, se, kModeInitBwd, s); }, tm))) return r;
+    if ((r = launch_one(kKSketchInit, [&] {
+           int q = k_sketch(se, kSkInitB, se.key.s, s);
+           if (!q && se.key.method == kSFLSMR) q = k_sketch(se, kSkInitBwd, se.key.s, s);
+           return q;
+         }, tm)))
+      return r;
     return SFL_OK;
   }
 
   static int enqueue_body(const Plan &pl, const Session &se, cudaStream_t s, int use_cond,
-                          cudaGraphConditionalHandle h) {
-    SFL_CU(O::orth(orth_params(pl, se, 0), se.grid_vec, se.smem_orth, s));
-    SpmvParams<VT, XT> p = base_params(pl, se, pl.A, kModeFwd);
-    p.tab = se.tab_m;
-    SFL_CU(O::spmv(p, pl.A.lpr, true, se.grid_spmv_A, se.smem_A, s));
-    SFL_CU(O::orth(orth_params(pl, se, 1), se.grid_vec, se.smem_orth, s));
-    p = base_params(pl, se, pl.T, kModeBwd);
-    p.tab = se.tab_n;
-    SFL_CU(O::spmv(p, pl.T.lpr, true, se.grid_spmv_T, se.smem_T, s));
-    SFL_CU(launch_ls(ls_params(se, use_cond, h), se.ls_cluster, se.smem_ls, s));
+                          cudaGraphConditionalHandle h, const Timer *tm = nullptr) {
+    int r;
+    if ((r = launch_one(kKOrthZ, [&] { return k_orth(pl, se, 0, s); }, tm))) return r;
+    if ((r = launch_one(kKFwd, [&] { return k_spmv(pl, se, kModeFwd, s); }, tm))) return r;
+    if ((r = launch_one(kKOrthW, [&] { return k_orth(pl, se, 1, s); }, tm))) return r;
+    if ((r = launch_one(kKBwd, [&] { return k_spmv(pl, se, kModeBwd, s); }, tm))) return r;
+    const int gsk = se.key.s * (se.key.method == kSFLSMR ? 2 : 1);
+    if ((r = launch_one(kKSketch, [&] { return k_sketch(se, kSkStep, gsk, s); }, tm))) return r;
+    if ((r = launch_one(kKLs, [&] {
+           return launch_ls(ls_params(se, use_cond, h), se.ls_cluster, se.smem_ls, s) == cudaSuccess ? SFL_OK
+                                                                                                       : SFL_ECUDA;
+         }, tm)))
+      return r;
     if (se.key.x_hist) {
       SFL_CU(O::solution(se.st, (const XT *)se.Z, pl.A.cols, se.sigZ, se.y, pl.A.cols, nullptr, se.key.x_hist,
                          se.grid_vec, s));
@@ -193,12 +265,14 @@ struct Engine {
     return SFL_OK;
   }
 
-  static int enqueue_epilogue(const Plan &pl, const Session &se, cudaStream_t s) {
-    return O::solution(se.st, (const XT *)se.Z, pl.A.cols, se.sigZ, se.y, pl.A.cols, se.xbuf, nullptr, se.grid_vec,
-                       s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  static int enqueue_epilogue(const Plan &pl, const Session &se, cudaStream_t s, const Timer *tm = nullptr) {
+    return launch_one(kKSolution, [&] {
+      return O::solution(se.st, (const XT *)se.Z, pl.A.cols, se.sigZ, se.y, pl.A.cols, se.xbuf, nullptr, se.grid_vec,
+                         s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
+    }, tm);
   }
 
-  static int build_graph(const Plan &pl, Session &se, cudaStream_t s) {
+  static int build_graph(const Plan &pl, Session &se) {
     cudaStream_t cs;
     SFL_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     int r = SFL_OK;
@@ -245,7 +319,6 @@ struct Engine {
     if (gp) cudaGraphDestroy(gp);
     if (ge) cudaGraphDestroy(ge);
     cudaStreamDestroy(cs);
-    (void)s;
     return r;
   }
 
@@ -253,11 +326,10 @@ struct Engine {
     auto se = std::make_unique<Session>();
     se->key = key;
     const int64_t m = pl.A.rows, n = pl.A.cols;
-    const int S = key.s, K = key.maxit, ell = key.ell;
+    const int S = key.s, K = key.maxit, ell = key.ell, Z = key.zeta;
     const size_t xs = sizeof(XT);
     se->RW = ell + 2;
     se->RP = ell + 1;
-    se->zs = key.zeta <= 8 ? 8 : 16;
     int r;
 #define SA(ptr, bytes) if ((r = session_alloc(pl, *se, (void **)&(ptr), (bytes)))) { destroy_session(pl, *se); return r; }
     SA(se->st, sizeof(SolveState));
@@ -267,8 +339,18 @@ struct Engine {
     SA(se->zraw, xs * n);
     SA(se->Z, xs * (size_t)n * K);
     SA(se->sigZ, sizeof(double) * K);
-    SA(se->tab_m, sizeof(uint16_t) * se->zs * m);
-    if (key.method == kSFLSMR) SA(se->tab_n, sizeof(uint16_t) * se->zs * n);
+    SA(se->skM_row, sizeof(int32_t) * (S + 1));
+    SA(se->skM_ent, sizeof(uint32_t) * (size_t)Z * m);
+    if (key.method == kSFLSMR) {
+      SA(se->skN_row, sizeof(int32_t) * (S + 1));
+      SA(se->skN_ent, sizeof(uint32_t) * (size_t)Z * n);
+    }
+    const int64_t nent = (int64_t)Z * std::max(m, n);
+    SA(se->sk_kin, sizeof(uint32_t) * nent);
+    SA(se->sk_vin, sizeof(uint32_t) * nent);
+    SA(se->sk_kout, sizeof(uint32_t) * nent);
+    se->sk_cub_bytes = sketch_sort_bytes(nent, S) + 256;
+    SA(se->sk_cub, se->sk_cub_bytes);
     SA(se->Q, sizeof(double) * (size_t)S * K);
     SA(se->Rinv, sizeof(double) * (size_t)K * K);
     SA(se->y, sizeof(double) * K);
@@ -283,65 +365,89 @@ struct Engine {
     if (key.precond == SFL_PRECOND_DIAG) SA(se->dw, sizeof(double) * n);
     SA(se->err, sizeof(int));
     // launch shapes
-    const size_t smem = spmv_smem(S, xs);
-    if (smem > 200 * 1024) { destroy_session(pl, *se); return SFL_EUNSUPPORTED; }
-    se->smem_A = se->smem_T = se->smem_init = smem;
-    SFL_CU(O::set_smem(pl.A.lpr, true, smem));
-    SFL_CU(O::set_smem(pl.T.lpr, true, smem));
-    SFL_CU(O::set_smem(32, false, smem));
-    auto grid_of = [&](int lpr, bool mat) {
+    se->smem_A = spmv_smem_bytes(pl.A.lpr, sizeof(ACC));
+    se->smem_T = spmv_smem_bytes(pl.T.lpr, sizeof(ACC));
+    se->smem_init = spmv_smem_bytes(1, sizeof(ACC));
+    SFL_CU(O::set_smem(pl.A.lpr, true, se->smem_A));
+    SFL_CU(O::set_smem(pl.T.lpr, true, se->smem_T));
+    SFL_CU(O::set_smem(1, false, se->smem_init));
+    auto grid_of = [&](int lpr, bool mat, size_t smem) {
       int occ = O::spmv_occupancy(lpr, mat, smem);
       if (occ < 1) occ = 1;
       if (occ > 8) occ = 8;
       return std::min(pl.num_sms * occ, kGroup * kMaxGroups);
     };
-    se->grid_spmv_A = grid_of(pl.A.lpr, true);
-    se->grid_spmv_T = grid_of(pl.T.lpr, true);
-    se->grid_init = grid_of(32, false);
-    se->grid_vec = std::min(pl.num_sms * 4, kGroup * kMaxGroups);
-    se->smem_orth = orth_smem();
+    se->grid_spmv_A = grid_of(pl.A.lpr, true, se->smem_A);
+    se->grid_spmv_T = grid_of(pl.T.lpr, true, se->smem_T);
+    se->grid_init = grid_of(1, false, se->smem_init);
+    se->grid_vec = std::min(pl.num_sms * 2, kGroup * kMaxGroups);
+    se->smem_orth = orth_smem_bytes(K);
+    SFL_CU(O::set_orth_smem(se->smem_orth));
     se->ls_cluster = ls_cluster_size(S, K);
     if (se->ls_cluster < 1) { destroy_session(pl, *se); return SFL_EUNSUPPORTED; }
     se->smem_ls = ls_smem_bytes(S, K, se->ls_cluster);
     SFL_CU(cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se->smem_ls));
     const int gmax = std::max(std::max(se->grid_spmv_A, se->grid_spmv_T), std::max(se->grid_init, se->grid_vec));
-    se->red.stride = S + kMaxWindow + 8;
-    SA(se->red.part, sizeof(double) * (size_t)gmax * se->red.stride);
-    SA(se->red.gpart, sizeof(double) * (size_t)kMaxGroups * se->red.stride);
-    SA(se->red.cnt, sizeof(unsigned) * (kMaxGroups + 1));
+    const size_t pbytes = sizeof(double) * (size_t)gmax * kPartStride;
+    SA(se->part.b, pbytes);
+    SA(se->part.z, pbytes);
+    SA(se->part.p, pbytes);
+    SA(se->part.w, pbytes);
+    SA(se->part.wn, pbytes);
+    // row range of every warp of the two products, balanced by stored entries
+    const int WA = se->grid_spmv_A * kWarps, WT = se->grid_spmv_T * kWarps;
+    SA(se->wrowA, sizeof(int32_t) * (WA + 1));
+    SA(se->wrowT, sizeof(int32_t) * (WT + 1));
 #undef SA
-    SFL_CU(cudaMemsetAsync(se->red.cnt, 0, sizeof(unsigned) * (kMaxGroups + 1), s));
+    balance_rows_kernel<<<(WA + 256) / 256, 256, 0, s>>>(pl.A.rowptr, pl.A.rows, WA, se->wrowA);
+    balance_rows_kernel<<<(WT + 256) / 256, 256, 0, s>>>(pl.T.rowptr, pl.T.rows, WT, se->wrowT);
+    SFL_CU(cudaGetLastError());
     SFL_CU(cudaMemsetAsync(se->err, 0, sizeof(int), s));
     SFL_CU(cudaMemsetAsync(se->Hband, 0, sizeof(double) * (size_t)K * (ell + 2), s));
     SFL_CU(cudaStreamSynchronize(s));
-    if ((r = build_graph(pl, *se, s))) { destroy_session(pl, *se); return r; }
+    if ((r = build_graph(pl, *se))) { destroy_session(pl, *se); return r; }
     *out = se.get();
     pl.sessions.push_back(std::move(se));
     return SFL_OK;
   }
 
-  // Host-driven pass with a CUDA event pair around every launch.
+  // Row-major sketch tables for `seed` (kept until the seed changes).
+  static int ensure_tables(const Plan &pl, Session &se, uint64_t seed, cudaStream_t s) {
+    if (se.tab_valid && se.tab_seed == seed) return SFL_OK;
+    SketchTableTmp t;
+    t.kin = se.sk_kin; t.vin = se.sk_vin; t.kout = se.sk_kout; t.cub = se.sk_cub; t.cub_bytes = se.sk_cub_bytes;
+    const bool mr = se.key.method == kSFLSMR;
+    int r = build_sketch_table(seed + (mr ? 1 : 0), se.key.s, se.key.zeta, pl.A.rows, se.skM_row, se.skM_ent, t, se.err, s);
+    if (!r && mr) r = build_sketch_table(seed, se.key.s, se.key.zeta, pl.A.cols, se.skN_row, se.skN_ent, t, se.err, s);
+    if (r) return r;
+    se.tab_valid = true;
+    se.tab_seed = seed;
+    return SFL_OK;
+  }
+
+  // Host-driven pass with a CUDA event pair around every launch; steps are
+  // enqueued in chunks without host synchronisation inside a chunk.
   static int run_profiled(const Plan &pl, const Session &se, cudaStream_t s, sfl_kernel_times *kt) {
     constexpr int kChunk = 8;
-    constexpr int kEv = 2 * (6 * kChunk + 8);
+    constexpr int kEv = 2 * (8 * kChunk + 8);
     cudaEvent_t ev[kEv];
     for (int i = 0; i < kEv; ++i) SFL_CU(cudaEventCreate(&ev[i]));
     struct Rec { int cls, step; };
     std::vector<Rec> recs;
-    int nev = 0;
-    int r = SFL_OK;
-    auto timed = [&](int cls, int step, auto &&launch) -> int {
+    int nev = 0, cur_step = -1;
+    Timer tm = [&](int cls, std::function<int()> f) -> int {
       cudaEventRecord(ev[nev], s);
-      int q = launch();
+      int q = f();
       cudaEventRecord(ev[nev + 1], s);
-      recs.push_back({cls, step});
+      recs.push_back({cls, cur_step});
       nev += 2;
       return q;
     };
     auto flush = [&](int done_steps) -> int {
+      if (nev == 0) return SFL_OK;
       SFL_CU(cudaEventSynchronize(ev[nev - 1]));
       for (size_t i = 0; i < recs.size(); ++i) {
-        if (recs[i].step >= done_steps && recs[i].step >= 0) continue;   // returned early after the stop
+        if (recs[i].step >= 0 && recs[i].step >= done_steps) continue;   // returned early after the stop
         float ms = 0.f;
         SFL_CU(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
         kt->ms[recs[i].cls] += ms;
@@ -351,53 +457,14 @@ struct Engine {
       nev = 0;
       return SFL_OK;
     };
-    const int64_t m = pl.A.rows, n = pl.A.cols;
-    const int method = se.key.method;
-    const uint64_t *seed_src = &se.st->seed;
-    r = timed(0, -1, [&] {
-      sketch_table_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(0, seed_src, method == kSFLSMR ? 1 : 0, se.key.s,
-                                                                       se.key.zeta, m, se.zs, se.tab_m, nullptr,
-                                                                       nullptr, se.err);
-      if (method == kSFLSMR)
-        sketch_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(0, seed_src, 0, se.key.s, se.key.zeta, n,
-                                                                         se.zs, se.tab_n, nullptr, nullptr, se.err);
-      return cudaGetLastError() == cudaSuccess ? SFL_OK : SFL_ECUDA;
-    });
-    if (r) return r;
-    r = timed(1, -1, [&] {
-      SpmvParams<VT, XT> p = base_params(pl, se, pl.A, kModeInitB);
-      p.rows = m; p.b = se.bbuf; p.tab = se.tab_m;
-      return O::spmv(p, 32, false, se.grid_init, se.smem_init, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
-    });
-    if (r) return r;
-    r = timed(2, -1, [&] {
-      SpmvParams<VT, XT> p = base_params(pl, se, pl.T, kModeInitBwd);
-      p.tab = se.tab_n;
-      return O::spmv(p, pl.T.lpr, true, se.grid_spmv_T, se.smem_T, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
-    });
+    int r = enqueue_prologue(pl, se, s, &tm);
     if (r) return r;
     if ((r = flush(0))) return r;
     int done = 0;
     for (int it0 = 0; it0 < se.key.maxit; it0 += kChunk) {
       for (int it = it0; it < std::min(it0 + kChunk, se.key.maxit); ++it) {
-        r = timed(3, it, [&] { return O::orth(orth_params(pl, se, 0), se.grid_vec, se.smem_orth, s) == cudaSuccess ? SFL_OK : SFL_ECUDA; });
-        if (r) return r;
-        r = timed(4, it, [&] {
-          SpmvParams<VT, XT> p = base_params(pl, se, pl.A, kModeFwd);
-          p.tab = se.tab_m;
-          return O::spmv(p, pl.A.lpr, true, se.grid_spmv_A, se.smem_A, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
-        });
-        if (r) return r;
-        r = timed(5, it, [&] { return O::orth(orth_params(pl, se, 1), se.grid_vec, se.smem_orth, s) == cudaSuccess ? SFL_OK : SFL_ECUDA; });
-        if (r) return r;
-        r = timed(6, it, [&] {
-          SpmvParams<VT, XT> p = base_params(pl, se, pl.T, kModeBwd);
-          p.tab = se.tab_n;
-          return O::spmv(p, pl.T.lpr, true, se.grid_spmv_T, se.smem_T, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
-        });
-        if (r) return r;
-        r = timed(7, it, [&] { return launch_ls(ls_params(se, 0, 0), se.ls_cluster, se.smem_ls, s) == cudaSuccess ? SFL_OK : SFL_ECUDA; });
-        if (r) return r;
+        cur_step = it;
+        if ((r = enqueue_body(pl, se, s, 0, 0, &tm))) return r;
       }
       int hk[2] = {0, 0};
       SFL_CU(cudaMemcpyAsync(hk, &se.st->k, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -406,8 +473,8 @@ struct Engine {
       if ((r = flush(done))) return r;
       if (hk[1]) break;
     }
-    r = timed(8, -1, [&] { return enqueue_epilogue(pl, se, s); });
-    if (r) return r;
+    cur_step = -1;
+    if ((r = enqueue_epilogue(pl, se, s, &tm))) return r;
     if ((r = flush(done))) return r;
     for (int i = 0; i < kEv; ++i) cudaEventDestroy(ev[i]);
     return SFL_OK;
@@ -481,6 +548,7 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
     if ((r = E::create(pl, key, q.s, &se))) return r;
   }
   const int64_t m = pl.A.rows, n = pl.A.cols;
+  if ((r = E::ensure_tables(pl, *se, o->seed, q.s))) return r;
   SFL_CU(cudaMemcpyAsync(se->bbuf, q.b, sizeof(double) * m, q.b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                          q.s));
   if (o->precond == SFL_PRECOND_DIAG)
@@ -531,10 +599,12 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
   SpmvParams<VT, XT> p{};
   p.rowptr = M.rowptr; p.col = M.col; p.val = (const VT *)M.val; p.rows = M.rows;
   p.mode = kModeApply;
-  const int grid = pl.num_sms * 4;
+  const int grid = pl.num_sms * 2;
+  const size_t smem = spmv_smem_bytes(M.lpr, sizeof(typename AccT<XT>::T));
+  SFL_CU(Ops<VT, XT>::set_smem(M.lpr, true, smem));
   if (std::is_same<XT, double>::value) {
     p.x = (const XT *)x; p.y = (XT *)y;
-    SFL_CU(Ops<VT, XT>::spmv(p, M.lpr, true, grid, 0, s));
+    SFL_CU(Ops<VT, XT>::spmv(p, M.lpr, true, grid, smem, s));
     return SFL_OK;
   }
   if (!pl.apply_x) {
@@ -546,7 +616,7 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
   }
   SFL_CU(Ops<VT, XT>::convert_in(x, (XT *)pl.apply_x, M.cols, s));
   p.x = (const XT *)pl.apply_x; p.y = (XT *)pl.apply_y;
-  SFL_CU(Ops<VT, XT>::spmv(p, M.lpr, true, grid, 0, s));
+  SFL_CU(Ops<VT, XT>::spmv(p, M.lpr, true, grid, smem, s));
   SFL_CU(Ops<VT, XT>::convert_out((const XT *)pl.apply_y, y, M.rows, s));
   return SFL_OK;
 }
@@ -633,42 +703,34 @@ int sfl_sketch_apply(uint64_t seed, int32_t s, int32_t zeta, const double *v, in
                      sfl_stream stream) {
   if (!v || !sk || zeta < 1 || zeta > kMaxZeta || s < zeta || s > kMaxS || len < 1) return SFL_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int zs = zeta <= 8 ? 8 : 16;
-  const size_t smem = spmv_smem(s, sizeof(double));
-  const int grid = std::min(sms * 2, kGroup * kMaxGroups);
-  const int stride = s + kMaxWindow + 8;
-  uint16_t *tab = nullptr;
-  double *part = nullptr, *gpart = nullptr;
-  unsigned *cnt = nullptr;
+  const int64_t nent = len * zeta;
+  SketchTableTmp t;
+  int32_t *row = nullptr;
+  uint32_t *ent = nullptr;
   int *err = nullptr;
   int r = SFL_OK;
-  do {
-    if (cudaMalloc(&tab, sizeof(uint16_t) * zs * len) != cudaSuccess || cudaMalloc(&part, sizeof(double) * grid * stride) != cudaSuccess ||
-        cudaMalloc(&gpart, sizeof(double) * kMaxGroups * stride) != cudaSuccess ||
-        cudaMalloc(&cnt, sizeof(unsigned) * (kMaxGroups + 1)) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
-      cudaGetLastError();
-      r = SFL_ENOMEM;
-      break;
-    }
-    cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (kMaxGroups + 1), st);
+  t.cub_bytes = sketch_sort_bytes(nent, s) + 256;
+  if (cudaMalloc(&t.kin, 4 * nent) != cudaSuccess || cudaMalloc(&t.vin, 4 * nent) != cudaSuccess ||
+      cudaMalloc(&t.kout, 4 * nent) != cudaSuccess || cudaMalloc(&t.cub, t.cub_bytes) != cudaSuccess ||
+      cudaMalloc(&row, 4 * (s + 1)) != cudaSuccess || cudaMalloc(&ent, 4 * nent) != cudaSuccess ||
+      cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    r = SFL_ENOMEM;
+  }
+  if (!r) {
     cudaMemsetAsync(err, 0, sizeof(int), st);
-    sketch_table_kernel<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(seed, nullptr, 0, s, zeta, len, zs, tab, nullptr,
-                                                                        nullptr, err);
-    SpmvParams<double, double> p{};
-    p.rows = len; p.mode = kModeSketch; p.s = s; p.zeta = zeta; p.zs = zs; p.b = v; p.tab = tab; p.sk_out = sk;
-    p.red.part = part; p.red.gpart = gpart; p.red.cnt = cnt; p.red.stride = stride;
-    if (Ops<double, double>::set_smem(32, false, smem) != cudaSuccess ||
-        Ops<double, double>::spmv(p, 32, false, grid, smem, st) != cudaSuccess) { r = SFL_ECUDA; break; }
-    if (cudaStreamSynchronize(st) != cudaSuccess) { r = SFL_ECUDA; break; }
+    r = build_sketch_table(seed, s, zeta, len, row, ent, t, err, st);
+  }
+  if (!r) {
+    SketchParams<double> p{};
+    p.mode = kSkPlain; p.s = s; p.isz = 1.0 / std::sqrt((double)zeta); p.v64 = v; p.rowM = row; p.entM = ent; p.sk_out = sk;
+    sketch_rows_kernel<double><<<s, kThreads, 0, st>>>(p);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) r = SFL_ECUDA;
     int h = 0;
-    cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (h) r = SFL_EINVAL;
-  } while (0);
+    if (!r && cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && h) r = SFL_EINVAL;
+  }
   if (r == SFL_ECUDA) set_cuda_error(cudaGetLastError(), "sfl_sketch_apply");
-  cudaFree(tab); cudaFree(part); cudaFree(gpart); cudaFree(cnt); cudaFree(err);
+  cudaFree(t.kin); cudaFree(t.vin); cudaFree(t.kout); cudaFree(t.cub); cudaFree(row); cudaFree(ent); cudaFree(err);
   return r;
 }
 
