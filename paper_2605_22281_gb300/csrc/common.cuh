@@ -127,76 +127,70 @@ __device__ __forceinline__ double tree8(const double *w) {
   return ((w[0] + w[1]) + (w[2] + w[3])) + ((w[4] + w[5]) + (w[6] + w[7]));
 }
 
+// FP64 on this GPU issues one warp-instruction per ~79 cycles per SM
+// sub-partition, whatever the number of active lanes, and a dependent FP64
+// add takes 64 cycles.  The reductions below therefore use few, full-warp
+// FP64 instructions and short dependency chains; their order is fixed, so
+// results are bitwise reproducible.
+
 // Totals of NQ <= kPartStride quantities over the per-CTA records of a
 // producer kernel with G CTAs (part[b * kPartStride + q]).  Every CTA of the
-// consumer computes the same values in the same fixed order: warp w sums a
-// contiguous slice of records (lanes strided), folds the lanes with a
-// butterfly, and the 8 warp sums are combined as a tree.  FP64 additions on
-// this GPU have a long latency, so every dependent chain is kept short and the
-// NQ chains are independent.  wsum: smem [kWarps * kPartStride]; out: smem
-// [kPartStride].  All threads call.
+// consumer computes the same values: warp q (and q + kWarps) sums quantity q
+// over all records, lanes strided with four independent accumulators, then a
+// butterfly.  out: smem [kPartStride].  All threads call.
 template <int NQ>
-__device__ __forceinline__ void reduce_partials_n(const double *part, int G, double *wsum, double *out) {
+__device__ __forceinline__ void reduce_partials_n(const double *part, int G, double *out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int per = (G + kWarps - 1) / kWarps;
-  const int b0 = warp * per, b1 = min(G, b0 + per);
-  double a[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) a[q] = 0.0;
-  for (int b = b0 + lane; b < b1; b += 32) {
-    double v[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = __ldcg(part + (size_t)b * kPartStride + q);
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) a[q] += v[q];
-  }
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    a[q] = warp_sum(a[q]);
-    if (lane == 0) wsum[warp * kPartStride + q] = a[q];
-  }
-  __syncthreads();
-  if (threadIdx.x < NQ) {
-    double w[kWarps];
-    for (int v = 0; v < kWarps; ++v) w[v] = wsum[v * kPartStride + threadIdx.x];
-    out[threadIdx.x] = tree8(w);
+  for (int q = warp; q < NQ; q += kWarps) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = lane;
+    for (; b + 96 < G; b += 128) {
+      a0 += __ldcg(part + (size_t)b * kPartStride + q);
+      a1 += __ldcg(part + (size_t)(b + 32) * kPartStride + q);
+      a2 += __ldcg(part + (size_t)(b + 64) * kPartStride + q);
+      a3 += __ldcg(part + (size_t)(b + 96) * kPartStride + q);
+    }
+    for (; b < G; b += 32) a0 += __ldcg(part + (size_t)b * kPartStride + q);
+    const double a = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) out[q] = a;
   }
   __syncthreads();
 }
 
 __device__ __forceinline__ void reduce_partials(const double *part, int G, int nq, double *wsum, double *out) {
+  (void)wsum;
   switch (nq) {
-    case 1: reduce_partials_n<1>(part, G, wsum, out); break;
-    case 2: reduce_partials_n<2>(part, G, wsum, out); break;
-    case 3: reduce_partials_n<3>(part, G, wsum, out); break;
-    case 4: reduce_partials_n<4>(part, G, wsum, out); break;
-    case 5: reduce_partials_n<5>(part, G, wsum, out); break;
-    case 6: reduce_partials_n<6>(part, G, wsum, out); break;
-    case 7: reduce_partials_n<7>(part, G, wsum, out); break;
-    case 8: reduce_partials_n<8>(part, G, wsum, out); break;
-    case 9: reduce_partials_n<9>(part, G, wsum, out); break;
-    default: reduce_partials_n<10>(part, G, wsum, out); break;
+    case 1: reduce_partials_n<1>(part, G, out); break;
+    case 2: reduce_partials_n<2>(part, G, out); break;
+    case 3: reduce_partials_n<3>(part, G, out); break;
+    case 4: reduce_partials_n<4>(part, G, out); break;
+    case 5: reduce_partials_n<5>(part, G, out); break;
+    case 6: reduce_partials_n<6>(part, G, out); break;
+    case 7: reduce_partials_n<7>(part, G, out); break;
+    case 8: reduce_partials_n<8>(part, G, out); break;
+    case 9: reduce_partials_n<9>(part, G, out); break;
+    default: reduce_partials_n<10>(part, G, out); break;
   }
 }
 
 // Per-CTA totals of NQ per-thread values, written to this CTA's record of a
-// partial-sum buffer: lanes fold by butterfly, warps combine as a tree.
-// wsum: smem [kWarps * kPartStride].  All threads call.
+// partial-sum buffer.  Threads park their values in shared memory (no FP64
+// work); warp q adds the 8 values of its lanes as a tree and folds the lanes
+// with a butterfly.  scr: smem [NQ * kThreads].  All threads call.
 template <int NQ>
-__device__ __forceinline__ void store_partials(const double (&v)[NQ], double *wsum, double *part) {
+__device__ __forceinline__ void store_partials(const double (&v)[NQ], double *scr, double *part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    const double a = warp_sum(v[q]);
-    if (lane == 0) wsum[warp * kPartStride + q] = a;
-  }
+  for (int q = 0; q < NQ; ++q) scr[q * kThreads + threadIdx.x] = v[q];
   __syncthreads();
-  if (threadIdx.x < NQ) {
-    double w[kWarps];
-    for (int u = 0; u < kWarps; ++u) w[u] = wsum[u * kPartStride + threadIdx.x];
-    part[(size_t)blockIdx.x * kPartStride + threadIdx.x] = tree8(w);
+  for (int q = warp; q < NQ; q += kWarps) {
+    const double *s = scr + q * kThreads + lane;
+    const double a = ((s[0] + s[32]) + (s[64] + s[96])) + ((s[128] + s[160]) + (s[192] + s[224]));
+    const double t = warp_sum(a);
+    if (lane == 0) part[(size_t)blockIdx.x * kPartStride + q] = t;
   }
 }
+static_assert(kThreads == 256, "store_partials adds 8 values per lane");
 
 // Sum of per-warp values held in lane 0 of each warp (smem scratch wtmp[kWarps]),
 // fixed order; result valid in all threads after the call.

@@ -57,6 +57,7 @@ struct Session {
   int grid_spmv_A = 0, grid_spmv_T = 0, grid_vec = 0, grid_init = 0;
   size_t smem_A = 0, smem_T = 0, smem_init = 0, smem_orth = 0, smem_ls = 0;
   int ls_cluster = 8;
+  int ls_stage = 0;
   std::vector<void *> allocs;
   uint64_t bytes = 0;
 };
@@ -92,6 +93,7 @@ struct Ops {
 cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s);
 int ls_cluster_size(int s, int maxit);
 size_t ls_smem_bytes(int s, int maxit, int cluster);
+int ls_stage_q(int s, int maxit, int cluster);
 
 void set_cuda_error(cudaError_t e, const char *where);
 size_t dtype_size(int dt);

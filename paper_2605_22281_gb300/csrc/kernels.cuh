@@ -284,7 +284,7 @@ template <typename VT, typename XT, int LPR, bool MAT>
 __global__ void __launch_bounds__(kThreads, 2) spmv_fused_kernel(SpmvParams<VT, XT> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SolveState sst;
-  __shared__ double wsum[kWarps * kPartStride];
+  __shared__ double wsum[(kMaxWindow + 2) * kThreads];   // reduction scratch
   __shared__ double tot[kPartStride];
   // a launch with too little shared memory does nothing (never writes out of bounds)
   if (dynamic_smem_bytes() < spmv_smem_bytes(LPR, sizeof(typename AccT<XT>::T))) return;
@@ -405,15 +405,30 @@ __global__ void __launch_bounds__(kThreads, 2) spmv_fused_kernel(SpmvParams<VT, 
 
 // Row range of every warp so that each warp gets about the same number of
 // stored entries (rows are never split).  W warps, W + 1 boundaries.
-static __global__ void balance_rows_kernel(const int32_t *rowptr, int64_t rows, int W, int32_t *wrow) {
+// Row cost for the warp partition of a product: the row's 4-load iterations
+// (ceil(len / unit), unit = 4 * lanes per row * load width) in quarter
+// iterations, plus one quarter for the row's share of the per-row work
+// (bounds, stash, output).  Warps over short rows run more iterations per
+// stored entry than warps over long rows, so entries alone do not balance.
+static __global__ void row_cost_kernel(const int32_t *rowptr, int64_t rows, int unit, int64_t *cost) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i > rows) return;
+  if (i == rows) { cost[i] = 0; return; }
+  const int len = rowptr[i + 1] - rowptr[i];
+  cost[i] = 4 * (int64_t)((len + unit - 1) / unit) + 1;
+}
+
+// Row range of every warp: warp w starts at the first row whose cost prefix
+// reaches w/W of the total (prefix[rows] = total).
+static __global__ void balance_rows_kernel(const int64_t *prefix, int64_t rows, int W, int32_t *wrow) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w > W) return;
-  const int64_t nnz = rowptr[rows];
-  const int64_t target = (nnz * w) / W;
+  const int64_t total = prefix[rows];
+  const int64_t target = (int64_t)(((__int128)total * w) / W);
   int64_t lo = 0, hi = rows;          // first row whose start is >= target
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)rowptr[mid] < target) lo = mid + 1; else hi = mid;
+    if (prefix[mid] < target) lo = mid + 1; else hi = mid;
   }
   wrow[w] = (int32_t)(w == W ? rows : lo);
 }
@@ -476,51 +491,80 @@ struct SketchParams {
   double *SAZ, *SAtW, *rhs, *e, *sbm, *sk_out;
 };
 
-// One CTA per sketch row: sum of +-v[c] over the row's entries (thread-strided
-// partial sums combined in fixed order), times 1/sqrt(zeta).
+// One CTA of kSkWarps warps per sketch row: sum of +-v[c] over the row's
+// entries (threads strided, four independent accumulators, warp butterflies,
+// warps added in order), times 1/sqrt(zeta).  The sign is applied to the bit
+// pattern, so each entry costs one add.  Vectors held in FP64 accumulate in
+// FP64; reduced-precision vectors accumulate in FP32.  Rows rows_total =
+// (number of sketches) * s, one CTA each.
+constexpr int kSkWarps = 4;
+
+__device__ __forceinline__ double flip_sign(double v, uint32_t e) {
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(e >> 31) << 63));
+}
+__device__ __forceinline__ float flip_sign(float v, uint32_t e) {
+  return __uint_as_float(__float_as_uint(v) ^ (e & 0x80000000u));
+}
+
+template <typename T, typename VT>
+__device__ __forceinline__ T sketch_row_sum(const int32_t *rowptr, const uint32_t *ent, const VT *v, int r) {
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  constexpr int B = kSkWarps * 32;
+  const int b0 = rowptr[r], b1 = rowptr[r + 1];
+  int i = b0 + threadIdx.x;
+  for (; i + 3 * B < b1; i += 4 * B) {
+    const uint32_t e0 = __ldg(ent + i), e1 = __ldg(ent + i + B), e2 = __ldg(ent + i + 2 * B), e3 = __ldg(ent + i + 3 * B);
+    a0 += flip_sign((T)v[e0 & 0x7FFFFFFFu], e0);
+    a1 += flip_sign((T)v[e1 & 0x7FFFFFFFu], e1);
+    a2 += flip_sign((T)v[e2 & 0x7FFFFFFFu], e2);
+    a3 += flip_sign((T)v[e3 & 0x7FFFFFFFu], e3);
+  }
+  for (; i < b1; i += B) {
+    const uint32_t e = __ldg(ent + i);
+    a0 += flip_sign((T)v[e & 0x7FFFFFFFu], e);
+  }
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
 template <typename XT>
-__global__ void __launch_bounds__(kThreads) sketch_rows_kernel(SketchParams<XT> p) {
-  __shared__ double wsum[kWarps];
+__global__ void __launch_bounds__(kSkWarps * 32) sketch_rows_kernel(SketchParams<XT> p, int rows_total) {
+  __shared__ double wpart[kSkWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gr = blockIdx.x;
+  if (gr >= rows_total) return;
   int k = 0;
   double beta = 1.0;
   if (p.mode != kSkPlain) {
     const SolveState *st = p.st;
     if (__ldcg(&st->stop)) return;
     k = __ldcg(&st->k) + 1;
-    if (p.mode == kSkStep && blockIdx.x >= p.s && __ldcg(&st->lucky)) return;   // no z at a lucky breakdown
+    if (p.mode == kSkStep && gr >= p.s && __ldcg(&st->lucky)) return;   // no z at a lucky breakdown
     if (p.mode == kSkInitBwd) beta = __ldcg(&st->beta0);
   }
-  const int which = blockIdx.x / p.s, r = blockIdx.x % p.s;
+  const int which = gr / p.s, r = gr % p.s;
   const bool nside = (p.mode == kSkInitBwd) || (p.mode == kSkStep && which == 1);
   const int32_t *rowptr = nside ? p.rowN : p.rowM;
   const uint32_t *ent = nside ? p.entN : p.entM;
-  double a = 0.0;
-  const int b0 = rowptr[r], b1 = rowptr[r + 1];
-  for (int i = b0 + (int)threadIdx.x; i < b1; i += blockDim.x) {
-    const uint32_t e = __ldg(ent + i);
-    const uint32_t c = e & 0x7FFFFFFFu;
-    double v;
-    if (p.mode == kSkPlain || p.mode == kSkInitB) v = p.v64[c];
-    else v = (double)(nside ? p.zraw[c] : p.wraw[c]);
-    a += (e >> 31) ? -v : v;
-  }
-  a = warp_sum(a);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = a;
+  double t;
+  if (p.mode == kSkPlain || p.mode == kSkInitB) t = sketch_row_sum<double>(rowptr, ent, p.v64, r);
+  else t = (double)sketch_row_sum<typename AccT<XT>::T>(rowptr, ent, nside ? p.zraw : p.wraw, r);
+  if (lane == 0) wpart[warp] = t;
   __syncthreads();
   if (threadIdx.x != 0) return;
-  const double val = tree8(wsum) * p.isz;
+  static_assert(kSkWarps == 4, "warp totals are added as a pair of pairs");
+  const double v = ((wpart[0] + wpart[1]) + (wpart[2] + wpart[3])) * p.isz;
   if (p.mode == kSkPlain) {
-    p.sk_out[r] = val;
+    p.sk_out[r] = v;
   } else if (p.mode == kSkStep) {
-    if (which == 0) p.SAZ[(size_t)(k - 1) * p.s + r] = val;
-    else p.SAtW[(size_t)k * p.s + r] = val;
+    if (which == 0) p.SAZ[(size_t)(k - 1) * p.s + r] = v;
+    else p.SAtW[(size_t)k * p.s + r] = v;
   } else if (p.mode == kSkInitB) {
-    if (p.method == kSFLSQR) { p.rhs[r] = val; p.e[r] = val; }
-    else p.sbm[r] = val;
+    if (p.method == kSFLSQR) { p.rhs[r] = v; p.e[r] = v; }
+    else p.sbm[r] = v;
   } else {   // kSkInitBwd
-    p.SAtW[r] = val;
-    p.rhs[r] = beta * val;
-    p.e[r] = beta * val;
+    p.SAtW[r] = v;
+    p.rhs[r] = beta * v;
+    p.e[r] = beta * v;
   }
 }
 
@@ -609,7 +653,7 @@ template <typename XT>
 __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p) {
   extern __shared__ __align__(16) double s_c[];     // [maxit] reweighting coefficients
   __shared__ SolveState sst;
-  __shared__ double wsum[kWarps * kPartStride];
+  __shared__ double wsum[(kMaxWindow + 2) * kThreads];   // reduction scratch
   __shared__ double tot[kPartStride];
   __shared__ double coefs[kMaxWindow + 2];
   stage_state(p.st, &sst);
@@ -665,7 +709,8 @@ __host__ __device__ inline size_t orth_smem_bytes(int maxit) { return sizeof(dou
 struct LsParams {
   SolveState *st;
   int method, s, maxit, ell, stop_rule;
-  double *Q;          // s x maxit, column-major: orthonormal basis of the sketched columns
+  int stage_q;        // 1: each CTA copies its block of Q rows into shared memory first
+  double *Q;          // s x maxit, row-major: orthonormal basis of the sketched columns
   double *Rinv;       // maxit x maxit, row-major: inverse of the triangular factor
   double *y;          // maxit
   double *e;          // s: residual of the small problem
@@ -679,12 +724,29 @@ struct LsParams {
   int use_cond;
 };
 
+constexpr int kMaxCluster = 16;
+
+// Shared-memory plan of the least-squares step (in doubles), identical on the
+// host (launch size) and the device (guard): four vectors of maxit+2, three
+// row blocks, slice partials, and optionally the staged Q block with an odd
+// row stride (no bank conflicts between rows).
+__host__ __device__ inline int ls_rows_per_cta(int s, int cl) { return (s + cl - 1) / cl; }
+__host__ __device__ inline int ls_qld(int maxit) { return maxit | 1; }
+__host__ __device__ inline size_t ls_smem_doubles(int s, int maxit, int cl, int stage) {
+  const int RB = ls_rows_per_cta(s, cl);
+  size_t n = 4 * (size_t)(maxit + 2) + 3 * (size_t)RB + (size_t)(RB > kThreads ? RB : kThreads);
+  if (stage) n += (size_t)RB * ls_qld(maxit);
+  return n;
+}
+
 // One thread-block cluster appends column k of the sketched matrix to an
 // explicit-Q QR by classical Gram-Schmidt applied twice (CGS2), updates the
 // residual e, the inverse triangular factor and y_k = y_{k-1} + gamma_k
 // Rinv[:,k], and evaluates the stop test.  Rows of Q are split in blocks over
-// the CTAs of the cluster; partial sums are exchanged through distributed
-// shared memory and summed in CTA order (deterministic).
+// the CTAs of the cluster.  Q^T c runs one thread per column (no per-column
+// reductions); partial vectors are exchanged through distributed shared
+// memory and every CTA adds the ranks' values as the same fixed tree, so all
+// CTAs hold bitwise identical totals and take the same branches.
 static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
@@ -693,102 +755,123 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   // Every CTA reads the flags before the first cluster barrier; rank 0 writes
   // them only after the last one, so all CTAs take the same branches.
   const int stop0 = st->stop, lucky = st->lucky;
-  if (stop0) {
+  if (stop0 || CL > kMaxCluster) {
     if (rank == 0 && tid == 0 && p.use_cond) cudaGraphSetConditional(p.cond, 0u);
     return;
   }
   const int k = st->k + 1, kk = k - 1;
   const int s = p.s;
-  const int RB = (s + CL - 1) / CL;
+  const int RB = ls_rows_per_cta(s, CL);
   const int r0 = min(s, rank * RB), r1 = min(s, r0 + RB), nr = r1 - r0;
   const int KP = p.maxit + 2;
   // every CTA of the cluster got the same shared memory: all leave together
-  if (dynamic_smem_bytes() < sizeof(double) * (size_t)(4 * KP + RB + max(kThreads, RB) + RB)) {
+  if (dynamic_smem_bytes() < sizeof(double) * ls_smem_doubles(s, p.maxit, CL, p.stage_q)) {
     if (rank == 0 && tid == 0 && p.use_cond) cudaGraphSetConditional(p.cond, 0u);
     return;
   }
 
   extern __shared__ __align__(16) double lsm[];
-  double *part0 = lsm;              // [KP] partial vectors exchanged in the cluster (double-buffered)
-  double *part1 = part0 + KP;
+  double *part0 = lsm;              // [KP] partial vectors exchanged in the cluster (pass 1)
+  double *part1 = part0 + KP;       // [KP] (pass 2)
   double *red = part1 + KP;         // [KP] cluster-reduced vector
   double *rr = red + KP;            // [KP] R column above the diagonal
   double *crow = rr + KP;           // [RB] my rows of the working column
-  double *tmp = crow + RB;          // [max(kThreads, RB) + RB] partial sums of (row, column slice)
+  double *ecur = crow + RB;         // [RB] my rows of e
+  double *upd = ecur + RB;          // [RB] my rows of a matrix-vector product
+  double *tmp = upd + RB;           // [max(kThreads, RB)] slice partials
+  double *Qs = tmp + max(kThreads, RB);   // [RB x ldq] staged Q block
   const int H = max(1, kThreads / max(RB, 1));   // column slices per row
-  __shared__ double s_w[kWarps];
-  __shared__ double s_sc[8];        // scalar partials exchanged in the cluster
-  __shared__ double s_res[8];
+  __shared__ double s_sc[2][4];     // scalar partials exchanged in the cluster
+  __shared__ double s_res[2][4];
 
-  // CTA total of one value per thread, fixed order; valid in all threads.
-  auto cta_total = [&](double v) -> double {
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) s_w[warp] = v;
-    __syncthreads();
-    double a = 0.0;
-    for (int w = 0; w < kWarps; ++w) a += s_w[w];
-    return a;
-  };
-  // Cluster total of a scalar: each CTA publishes s_sc[slot], then every CTA
-  // sums the published values in rank order.
-  auto cluster_total = [&](double cta_val, int slot) -> double {
-    if (tid == 0) s_sc[slot] = cta_val;
+  // my block of Q rows: staged copy or the global rows
+  const double *Qb = p.stage_q ? Qs : p.Q + (size_t)r0 * p.maxit;
+  const int64_t qld = p.stage_q ? ls_qld(p.maxit) : p.maxit;
+
+  // Totals over the cluster of per-CTA vectors buf[0..cnt): every CTA sums
+  // the ranks' entries as one fixed tree (ranks past CL add zero).
+  auto cluster_allreduce_vec = [&](double *buf, int cnt, double *dst) {
     cl.sync();
-    if (tid == 0) {
-      double a = 0.0;
-      for (int b = 0; b < CL; ++b) a += cl.map_shared_rank(s_sc, b)[slot];
-      s_res[slot] = a;
-    }
-    __syncthreads();
-    return s_res[slot];
-  };
-  auto cluster_sum_vec = [&](double *buf, int cnt, double *dst) {
-    cl.sync();
-    for (int j = tid; j < cnt; j += blockDim.x) {
-      double acc = 0.0;
-      for (int b = 0; b < CL; ++b) acc += cl.map_shared_rank(buf, b)[j];
-      dst[j] = acc;
+    for (int j = tid; j < cnt; j += kThreads) {
+      double v[kMaxCluster];
+#pragma unroll
+      for (int b = 0; b < kMaxCluster; ++b) v[b] = (b < CL) ? cl.map_shared_rank(buf, b)[j] : 0.0;
+#pragma unroll
+      for (int w = kMaxCluster / 2; w >= 1; w >>= 1)
+#pragma unroll
+        for (int b = 0; b < w; ++b) v[b] += v[b + w];
+      dst[j] = v[0];
     }
     __syncthreads();
   };
-  // partial Q^T c over my rows -> buf[0..kk-1]
+  // Totals over the cluster of up to three scalars whose per-lane partials
+  // are held by warp 0 (lane sums, then rank sums, both butterflies).
+  auto cluster_allreduce_sc = [&](double a0, double a1, double a2, int nq, int slot) {
+    if (warp == 0) {
+      a0 = warp_sum(a0);
+      a1 = nq > 1 ? warp_sum(a1) : 0.0;
+      a2 = nq > 2 ? warp_sum(a2) : 0.0;
+      if (lane == 0) { s_sc[slot][0] = a0; s_sc[slot][1] = a1; s_sc[slot][2] = a2; }
+    }
+    cl.sync();
+    if (warp == 0) {
+      double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+      if (lane < CL) {
+        const double *r = cl.map_shared_rank(&s_sc[slot][0], lane);
+        b0 = r[0]; b1 = r[1]; b2 = r[2];
+      }
+      b0 = warp_sum(b0);
+      b1 = nq > 1 ? warp_sum(b1) : 0.0;
+      b2 = nq > 2 ? warp_sum(b2) : 0.0;
+      if (lane == 0) { s_res[slot][0] = b0; s_res[slot][1] = b1; s_res[slot][2] = b2; }
+    }
+    __syncthreads();
+  };
+  // buf[j] = sum_i Q[r0+i][j] crow[i] over my rows, one thread per column
   auto qt_partial = [&](double *buf) {
-    for (int j = warp; j < kk; j += kWarps) {
-      double v = 0.0;
-      for (int i = lane; i < nr; i += 32) v += p.Q[(size_t)j * s + r0 + i] * crow[i];
-      v = warp_sum(v);
-      if (lane == 0) buf[j] = v;
+    for (int j = tid; j < kk; j += kThreads) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int i = 0;
+      for (; i + 3 < nr; i += 4) {
+        a0 += Qb[(size_t)i * qld + j] * crow[i];
+        a1 += Qb[(size_t)(i + 1) * qld + j] * crow[i + 1];
+        a2 += Qb[(size_t)(i + 2) * qld + j] * crow[i + 2];
+        a3 += Qb[(size_t)(i + 3) * qld + j] * crow[i + 3];
+      }
+      for (; i < nr; ++i) a0 += Qb[(size_t)i * qld + j] * crow[i];
+      buf[j] = (a0 + a1) + (a2 + a3);
     }
-    __syncthreads();
   };
-  // out[i] = sum_{j < ncol} Mat[j*s + r0 + i] * coef[j] for my rows; thread
-  // (row i, slice h) sums the columns j = h (mod H), slices combined in order.
-  auto rows_times_vec = [&](const double *Mat, const double *coef, int ncol, double *out) {
-    for (int t = tid; t < H * RB; t += blockDim.x) {
+  // out[i] = sum_{j < ncol} M(i, j) coef[j] for my rows, M(i, j) = M[i*rs + j*cs];
+  // thread (row i, slice h) sums the columns j = h (mod H), slices added in order.
+  auto rows_times_vec = [&](const double *M, int64_t rs, int64_t cs, const double *coef, int ncol, double *out) {
+    for (int t = tid; t < H * RB; t += kThreads) {
       const int i = t % RB, h = t / RB;
-      double v = 0.0;
-      if (i < nr)
-        for (int j = h; j < ncol; j += H) v += Mat[(size_t)j * s + r0 + i] * coef[j];
-      tmp[t] = v;
+      double a0 = 0.0, a1 = 0.0;
+      if (i < nr) {
+        const double *mi = M + (size_t)i * rs;
+        int j = h;
+        for (; j + H < ncol; j += 2 * H) {
+          a0 += mi[(size_t)j * cs] * coef[j];
+          a1 += mi[(size_t)(j + H) * cs] * coef[j + H];
+        }
+        if (j < ncol) a0 += mi[(size_t)j * cs] * coef[j];
+      }
+      tmp[t] = a0 + a1;
     }
     __syncthreads();
-    for (int i = tid; i < nr; i += blockDim.x) {
-      double a = 0.0;
-      for (int h = 0; h < H; ++h) a += tmp[h * RB + i];
-      out[i] = a;
+    for (int i = tid; i < nr; i += kThreads) {
+      double a0 = 0.0, a1 = 0.0;
+      int h = 0;
+      for (; h + 1 < H; h += 2) { a0 += tmp[h * RB + i]; a1 += tmp[(h + 1) * RB + i]; }
+      if (h < H) a0 += tmp[h * RB + i];
+      out[i] = a0 + a1;
     }
-    __syncthreads();
-  };
-  // crow -= Q coef over my rows
-  auto q_update = [&](const double *coef) {
-    rows_times_vec(p.Q, coef, kk, tmp + H * RB);
-    for (int i = tid; i < nr; i += blockDim.x) crow[i] -= tmp[H * RB + i];
     __syncthreads();
   };
 
-  // ---- 0. the new column, my rows
-  for (int i = tid; i < nr; i += blockDim.x) {
+  // ---- 0. the new column and e, my rows; the Q block
+  for (int i = tid; i < nr; i += kThreads) {
     const int row = r0 + i;
     double c;
     if (p.method == kSFLSQR) {
@@ -804,25 +887,47 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
       }
     }
     crow[i] = c;
+    ecur[i] = p.e[row];
+  }
+  if (p.stage_q && kk > 0) {
+    const int ldq = ls_qld(p.maxit);
+    for (int t = tid; t < nr * kk; t += kThreads) {
+      const int i = t / kk, j = t - i * kk;
+      Qs[(size_t)i * ldq + j] = p.Q[(size_t)(r0 + i) * p.maxit + j];
+    }
   }
   __syncthreads();
 
   // ---- 1-4. classical Gram-Schmidt twice against the first kk columns
   if (kk > 0) {
     qt_partial(part0);
-    cluster_sum_vec(part0, kk, red);
-    q_update(red);
-    for (int j = tid; j < kk; j += blockDim.x) rr[j] = red[j];
+    cluster_allreduce_vec(part0, kk, red);
+    for (int j = tid; j < kk; j += kThreads) rr[j] = red[j];
+    rows_times_vec(Qb, qld, 1, red, kk, upd);
+    for (int i = tid; i < nr; i += kThreads) crow[i] -= upd[i];
     __syncthreads();
     qt_partial(part1);
-    cluster_sum_vec(part1, kk, red);
-    q_update(red);
-    for (int j = tid; j < kk; j += blockDim.x) rr[j] += red[j];
+    cluster_allreduce_vec(part1, kk, red);
+    for (int j = tid; j < kk; j += kThreads) rr[j] += red[j];
+    rows_times_vec(Qb, qld, 1, red, kk, upd);
+    for (int i = tid; i < nr; i += kThreads) crow[i] -= upd[i];
     __syncthreads();
   }
-  double v = 0.0;
-  for (int i = tid; i < nr; i += blockDim.x) v += crow[i] * crow[i];
-  const double rho = sqrt(cluster_total(cta_total(v), 0));
+  // ---- 5. ||c||^2, <c, e> and (first step) the stop-ratio denominator:
+  // ||s_b|| (sFLSQR), ||S_m b|| (sFLSMR, residual rule) or ||s_{A^T b}||
+  // (sFLSMR, normal-equation rule)
+  {
+    const double *dv = (p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL) ? p.sbm : p.rhs;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    if (warp == 0)
+      for (int i = lane; i < nr; i += 32) {
+        a0 += crow[i] * crow[i];
+        a1 += crow[i] * ecur[i];
+        if (k == 1) a2 += dv[r0 + i] * dv[r0 + i];
+      }
+    cluster_allreduce_sc(a0, a1, a2, k == 1 ? 3 : 2, 0);
+  }
+  const double rho = sqrt(s_res[0][0]);
   const double R11 = (k == 1) ? rho : st->R11;
   if (!(rho > 1e-300) || !(rho > 1e-14 * R11) || !isfinite(rho)) {
     cl.sync();   // no CTA leaves while a peer may still read its shared memory
@@ -832,24 +937,18 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
     }
     return;
   }
-  // ---- 5. q_k = c / rho, gamma_k = <q_k, e>, e -= gamma_k q_k
+  const double den = (k == 1) ? sqrt(s_res[0][2]) : st->stop_den;
+  // ---- 6. q_k = c / rho, gamma_k = <q_k, e>, e -= gamma_k q_k
   const double irho = 1.0 / rho;
-  v = 0.0;
-  for (int i = tid; i < nr; i += blockDim.x) {
+  const double gamma = s_res[0][1] * irho;
+  for (int i = tid; i < nr; i += kThreads) {
     const double q = crow[i] * irho;
-    p.Q[(size_t)kk * s + r0 + i] = q;
-    crow[i] = q;
-    v += q * p.e[r0 + i];
-  }
-  const double gamma = cluster_total(cta_total(v), 1);
-  v = 0.0;
-  for (int i = tid; i < nr; i += blockDim.x) {
-    const double ei = p.e[r0 + i] - gamma * crow[i];
+    p.Q[(size_t)(r0 + i) * p.maxit + kk] = q;
+    const double ei = ecur[i] - gamma * q;
     p.e[r0 + i] = ei;
-    v += ei * ei;
+    ecur[i] = ei;
   }
-  const double enorm2_cta = cta_total(v);
-  // ---- 6. column kk of R^{-1} and y_k = [y_{k-1}; 0] + gamma_k R^{-1}[:, kk]
+  // ---- 7. column kk of R^{-1} and y_k = [y_{k-1}; 0] + gamma_k R^{-1}[:, kk]
   for (int i = rank * kWarps + warp; i < kk; i += CL * kWarps) {
     double a = 0.0;
     for (int j = i + lane; j < kk; j += 32) a += p.Rinv[(size_t)i * p.maxit + j] * rr[j];
@@ -864,29 +963,29 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
     p.Rinv[(size_t)kk * p.maxit + kk] = irho;
     p.y[kk] = gamma * irho;
   }
-  __threadfence();
-  double res2 = cluster_total(enorm2_cta, 2);   // its barrier also publishes y in the cluster
-  // denominator of the stop ratio, once: ||s_b|| (sFLSQR), ||S_m b|| (sFLSMR,
-  // residual rule) or ||s_{A^T b}|| (sFLSMR, normal-equation rule)
-  double den = st->stop_den;
-  if (k == 1) {
-    const double *dv = (p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL) ? p.sbm : p.rhs;
-    v = 0.0;
-    for (int i = tid; i < nr; i += blockDim.x) v += dv[r0 + i] * dv[r0 + i];
-    den = sqrt(cluster_total(cta_total(v), 4));
-  }
+  __syncthreads();
+  // ---- 8. residual of the stop test
   if (p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL) {
-    // || S_m b - S_m A Z_k y_k ||, my rows (y staged in shared memory)
-    for (int j = tid; j < k; j += blockDim.x) red[j] = __ldcg(p.y + j);
+    // || S_m b - S_m A Z_k y_k ||, my rows; y is published in the cluster first
+    __threadfence();
+    cl.sync();
+    for (int j = tid; j < k; j += kThreads) red[j] = __ldcg(p.y + j);
     __syncthreads();
-    rows_times_vec(p.SAZ, red, k, tmp + H * RB);
-    v = 0.0;
-    for (int t = tid; t < nr; t += blockDim.x) {
-      const double a = p.sbm[r0 + t] - tmp[H * RB + t];
-      v += a * a;
-    }
-    res2 = cluster_total(cta_total(v), 3);
+    rows_times_vec(p.SAZ + r0, 1, s, red, k, upd);
+    double a0 = 0.0;
+    if (warp == 0)
+      for (int i = lane; i < nr; i += 32) {
+        const double d = p.sbm[r0 + i] - upd[i];
+        a0 += d * d;
+      }
+    cluster_allreduce_sc(a0, 0.0, 0.0, 1, 1);
+  } else {
+    double a0 = 0.0;
+    if (warp == 0)
+      for (int i = lane; i < nr; i += 32) a0 += ecur[i] * ecur[i];
+    cluster_allreduce_sc(a0, 0.0, 0.0, 1, 1);
   }
+  const double res2 = s_res[1][0];
   cl.sync();   // no CTA leaves while a peer may still read its shared memory
   if (rank == 0 && tid == 0) {
     if (k == 1) st->stop_den = den;

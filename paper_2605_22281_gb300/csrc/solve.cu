@@ -53,14 +53,22 @@ static void destroy_session(Plan &pl, Session &se) {
   se.bytes = 0;
 }
 
+// The Q block of a CTA is staged in shared memory when the whole plan stays
+// within this budget (it then serves the four Q products of a step).
+constexpr size_t kLsStageBudget = 160 * 1024;
+
+int ls_stage_q(int s, int maxit, int cluster) {
+  return sizeof(double) * ls_smem_doubles(s, maxit, cluster, 1) <= kLsStageBudget ? 1 : 0;
+}
+
 size_t ls_smem_bytes(int s, int maxit, int cluster) {
-  const int RB = (s + cluster - 1) / cluster;
-  return sizeof(double) * (size_t)(4 * (maxit + 2) + RB + std::max(kThreads, RB) + RB);
+  return sizeof(double) * ls_smem_doubles(s, maxit, cluster, ls_stage_q(s, maxit, cluster));
 }
 
 int ls_cluster_size(int s, int maxit) {
   cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   for (int cl : {16, 8, 4, 2, 1}) {
+    static_assert(kMaxCluster == 16, "largest cluster tried");
     const size_t smem = ls_smem_bytes(s, maxit, cl);
     if (cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
@@ -98,6 +106,41 @@ cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, ls_step_kernel, p);
+}
+
+// Row range of each of W warps over the rows of M, balanced by row cost
+// (cost per row, exclusive scan, binary search per warp).  Temporaries are
+// freed before returning; the caller synchronises the stream.
+static int balance_rows(const StoredCsr &M, int P, int W, int32_t *wrow, cudaStream_t s) {
+  const int64_t rows = M.rows;
+  const int unit = 4 * M.lpr * P;
+  int64_t *cost = nullptr, *prefix = nullptr;
+  void *tst = nullptr;
+  size_t tb = 0;
+  int r = SFL_OK;
+  auto fail = [&](cudaError_t e, const char *what) {
+    set_cuda_error(e, what);
+    return SFL_ECUDA;
+  };
+  cudaError_t e = cub::DeviceScan::ExclusiveSum(nullptr, tb, (int64_t *)nullptr, (int64_t *)nullptr, (int)(rows + 1), s);
+  if (e == cudaSuccess) e = cudaMalloc(&cost, sizeof(int64_t) * (rows + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&prefix, sizeof(int64_t) * (rows + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&tst, tb ? tb : 16);
+  if (e == cudaSuccess) {
+    row_cost_kernel<<<(unsigned)((rows + 256) / 256), 256, 0, s>>>(M.rowptr, rows, unit, cost);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(tst, tb, cost, prefix, (int)(rows + 1), s);
+  if (e == cudaSuccess) {
+    balance_rows_kernel<<<(W + 256) / 256, 256, 0, s>>>(prefix, rows, W, wrow);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { cudaGetLastError(); r = fail(e, "row balance"); }
+  cudaFree(cost);
+  cudaFree(prefix);
+  cudaFree(tst);
+  return r;
 }
 
 // Row-major sparse-sign table for ncols columns: pairs (row, column|sign) in
@@ -191,6 +234,7 @@ struct Engine {
     LsParams q{};
     q.st = se.st; q.method = se.key.method; q.s = se.key.s; q.maxit = se.key.maxit; q.ell = se.key.ell;
     q.stop_rule = se.key.stop_rule;
+    q.stage_q = se.ls_stage;
     q.Q = se.Q; q.Rinv = se.Rinv; q.y = se.y; q.e = se.e;
     q.SAZ = se.SAZ; q.SAtW = se.SAtW; q.Hband = se.Hband; q.sbm = se.sbm; q.rhs = se.rhs;
     q.relres_hist = se.key.r_hist;
@@ -206,8 +250,8 @@ struct Engine {
     return f();
   }
 
-  static int k_sketch(const Session &se, int mode, int grid, cudaStream_t s) {
-    sketch_rows_kernel<XT><<<grid, kThreads, 0, s>>>(sketch_params(se, mode));
+  static int k_sketch(const Session &se, int mode, int rows, cudaStream_t s) {
+    sketch_rows_kernel<XT><<<rows, kSkWarps * 32, 0, s>>>(sketch_params(se, mode), rows);
     return cudaGetLastError() == cudaSuccess ? SFL_OK : SFL_ECUDA;
   }
   static int k_spmv(const Plan &pl, const Session &se, int mode, cudaStream_t s) {
@@ -386,6 +430,7 @@ struct Engine {
     se->ls_cluster = ls_cluster_size(S, K);
     if (se->ls_cluster < 1) { destroy_session(pl, *se); return SFL_EUNSUPPORTED; }
     se->smem_ls = ls_smem_bytes(S, K, se->ls_cluster);
+    se->ls_stage = ls_stage_q(S, K, se->ls_cluster);
     SFL_CU(cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se->smem_ls));
     const int gmax = std::max(std::max(se->grid_spmv_A, se->grid_spmv_T), std::max(se->grid_init, se->grid_vec));
     const size_t pbytes = sizeof(double) * (size_t)gmax * kPartStride;
@@ -394,14 +439,16 @@ struct Engine {
     SA(se->part.p, pbytes);
     SA(se->part.w, pbytes);
     SA(se->part.wn, pbytes);
-    // row range of every warp of the two products, balanced by stored entries
+    // row range of every warp of the two products, balanced by row cost
     const int WA = se->grid_spmv_A * kWarps, WT = se->grid_spmv_T * kWarps;
     SA(se->wrowA, sizeof(int32_t) * (WA + 1));
     SA(se->wrowT, sizeof(int32_t) * (WT + 1));
 #undef SA
-    balance_rows_kernel<<<(WA + 256) / 256, 256, 0, s>>>(pl.A.rowptr, pl.A.rows, WA, se->wrowA);
-    balance_rows_kernel<<<(WT + 256) / 256, 256, 0, s>>>(pl.T.rowptr, pl.T.rows, WT, se->wrowT);
-    SFL_CU(cudaGetLastError());
+    const int P = load_width(pl.vdt);
+    if ((r = balance_rows(pl.A, P, WA, se->wrowA, s)) || (r = balance_rows(pl.T, P, WT, se->wrowT, s))) {
+      destroy_session(pl, *se);
+      return r;
+    }
     SFL_CU(cudaMemsetAsync(se->err, 0, sizeof(int), s));
     SFL_CU(cudaMemsetAsync(se->Hband, 0, sizeof(double) * (size_t)K * (ell + 2), s));
     SFL_CU(cudaStreamSynchronize(s));
@@ -724,7 +771,7 @@ int sfl_sketch_apply(uint64_t seed, int32_t s, int32_t zeta, const double *v, in
   if (!r) {
     SketchParams<double> p{};
     p.mode = kSkPlain; p.s = s; p.isz = 1.0 / std::sqrt((double)zeta); p.v64 = v; p.rowM = row; p.entM = ent; p.sk_out = sk;
-    sketch_rows_kernel<double><<<s, kThreads, 0, st>>>(p);
+    sketch_rows_kernel<double><<<s, kSkWarps * 32, 0, st>>>(p, s);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) r = SFL_ECUDA;
     int h = 0;
     if (!r && cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && h) r = SFL_EINVAL;
