@@ -110,8 +110,11 @@ __device__ __forceinline__ bool grid_reduce(const double *vals, int cnt, const R
   return true;
 }
 
-// Stride (doubles) of one CTA's record in a partial-sum buffer.
+// Partial-sum buffers hold up to kPartStride quantities for up to kPartCap
+// producer CTAs, quantity-major: part[q * kPartCap + cta], so that a warp
+// reading one quantity over consecutive CTAs makes coalesced loads.
 constexpr int kPartStride = 16;
+constexpr int kPartCap = kGroup * kMaxGroups;   // largest grid of any step kernel
 
 // Copy the device solve state into shared memory (one coalesced pass).
 __device__ __forceinline__ void stage_state(const SolveState *st, SolveState *sst) {
@@ -134,24 +137,30 @@ __device__ __forceinline__ double tree8(const double *w) {
 // results are bitwise reproducible.
 
 // Totals of NQ <= kPartStride quantities over the per-CTA records of a
-// producer kernel with G CTAs (part[b * kPartStride + q]).  Every CTA of the
-// consumer computes the same values: warp q (and q + kWarps) sums quantity q
-// over all records, lanes strided with four independent accumulators, then a
-// butterfly.  out: smem [kPartStride].  All threads call.
+// producer kernel with G CTAs (part[q * kPartCap + b]).  Every CTA of the
+// consumer computes the same values: warp q (and q + kWarps) sums quantity q.
+// Each lane issues all its loads at once (kRedLoads records, one L2 round
+// trip for G <= 32 * kRedLoads), adds them as a fixed tree, then the lanes
+// fold with a butterfly.  out: smem [kPartStride].  All threads call.
+constexpr int kRedLoads = 16;
+
 template <int NQ>
 __device__ __forceinline__ void reduce_partials_n(const double *part, int G, double *out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = warp; q < NQ; q += kWarps) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int b = lane;
-    for (; b + 96 < G; b += 128) {
-      a0 += __ldcg(part + (size_t)b * kPartStride + q);
-      a1 += __ldcg(part + (size_t)(b + 32) * kPartStride + q);
-      a2 += __ldcg(part + (size_t)(b + 64) * kPartStride + q);
-      a3 += __ldcg(part + (size_t)(b + 96) * kPartStride + q);
+    double v[kRedLoads];
+#pragma unroll
+    for (int t = 0; t < kRedLoads; ++t) {
+      const int b = lane + 32 * t;
+      v[t] = b < G ? __ldcg(part + (size_t)q * kPartCap + b) : 0.0;
     }
-    for (; b < G; b += 32) a0 += __ldcg(part + (size_t)b * kPartStride + q);
-    const double a = warp_sum((a0 + a1) + (a2 + a3));
+#pragma unroll
+    for (int w = kRedLoads / 2; w >= 1; w >>= 1)
+#pragma unroll
+      for (int t = 0; t < w; ++t) v[t] += v[t + w];
+    double a = v[0];
+    for (int b = lane + 32 * kRedLoads; b < G; b += 32) a += __ldcg(part + (size_t)q * kPartCap + b);
+    a = warp_sum(a);
     if (lane == 0) out[q] = a;
   }
   __syncthreads();
@@ -187,7 +196,7 @@ __device__ __forceinline__ void store_partials(const double (&v)[NQ], double *sc
     const double *s = scr + q * kThreads + lane;
     const double a = ((s[0] + s[32]) + (s[64] + s[96])) + ((s[128] + s[160]) + (s[192] + s[224]));
     const double t = warp_sum(a);
-    if (lane == 0) part[(size_t)blockIdx.x * kPartStride + q] = t;
+    if (lane == 0) part[(size_t)q * kPartCap + blockIdx.x] = t;
   }
 }
 static_assert(kThreads == 256, "store_partials adds 8 values per lane");
@@ -218,5 +227,13 @@ __device__ __forceinline__ uint32_t dynamic_smem_bytes() {
 
 // Ring slot of basis vector j (1-based).
 __device__ __forceinline__ int ring_slot(int j, int R) { return j % R; }
+
+// Programmatic dependent launch.  griddep_wait blocks until the grid this one
+// depends on has completed and its writes are visible (it returns at once for
+// a launch without that dependency); griddep_launch_dependents lets the next
+// kernel of the stream start launching its CTAs, which then wait in their own
+// griddep_wait.  Every step kernel calls both before touching shared state.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 }  // namespace sfl

@@ -76,11 +76,33 @@ struct Plan {
   RedScratch apply_red{};
 };
 
+// Kernel launch, optionally with a programmatic dependency on the previous
+// kernel of the stream (the kernel then waits in griddep_wait; inside a
+// captured graph this becomes a programmatic edge).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (pdl) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Typed launch wrappers (one instantiation unit per precision pair).
 template <typename VT, typename XT>
 struct Ops {
-  static cudaError_t spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, int grid, size_t smem, cudaStream_t s);
-  static cudaError_t orth(const OrthParams<XT> &p, int grid, size_t smem, cudaStream_t s);
+  static cudaError_t spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, int grid, size_t smem, cudaStream_t s,
+                          bool pdl = false);
+  static cudaError_t orth(const OrthParams<XT> &p, int grid, size_t smem, cudaStream_t s, bool pdl = false);
   static cudaError_t solution(SolveState *st, const XT *Z, int64_t zstride, const double *sigZ, const double *y,
                               int64_t n, double *x, double *hist, int grid, cudaStream_t s);
   static cudaError_t convert_in(const double *x, XT *y, int64_t n, cudaStream_t s);
@@ -90,10 +112,10 @@ struct Ops {
   static cudaError_t set_orth_smem(size_t smem);
 };
 
-cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s);
-int ls_cluster_size(int s, int maxit);
-size_t ls_smem_bytes(int s, int maxit, int cluster);
-int ls_stage_q(int s, int maxit, int cluster);
+cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s, bool pdl = false);
+int ls_cluster_size(int s, int maxit, bool saz);
+size_t ls_smem_bytes(int s, int maxit, int cluster, bool saz);
+int ls_stage_plan(int s, int maxit, int cluster, bool saz);
 
 void set_cuda_error(cudaError_t e, const char *where);
 size_t dtype_size(int dt);

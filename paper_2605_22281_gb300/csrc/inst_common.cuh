@@ -23,13 +23,15 @@ static const void *spmv_fn(int lpr, bool mat) {
 }
 
 template <typename VT, typename XT>
-cudaError_t Ops<VT, XT>::spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, int grid, size_t smem, cudaStream_t s) {
-  if (!mat) spmv_fused_kernel<VT, XT, 1, false><<<grid, kThreads, smem, s>>>(p);
-  else if (lpr == 4) spmv_fused_kernel<VT, XT, 4, true><<<grid, kThreads, smem, s>>>(p);
-  else if (lpr == 8) spmv_fused_kernel<VT, XT, 8, true><<<grid, kThreads, smem, s>>>(p);
-  else if (lpr == 16) spmv_fused_kernel<VT, XT, 16, true><<<grid, kThreads, smem, s>>>(p);
-  else spmv_fused_kernel<VT, XT, 32, true><<<grid, kThreads, smem, s>>>(p);
-  return cudaGetLastError();
+cudaError_t Ops<VT, XT>::spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, int grid, size_t smem, cudaStream_t s,
+                              bool pdl) {
+  void (*kern)(SpmvParams<VT, XT>);
+  if (!mat) kern = spmv_fused_kernel<VT, XT, 1, false>;
+  else if (lpr == 4) kern = spmv_fused_kernel<VT, XT, 4, true>;
+  else if (lpr == 8) kern = spmv_fused_kernel<VT, XT, 8, true>;
+  else if (lpr == 16) kern = spmv_fused_kernel<VT, XT, 16, true>;
+  else kern = spmv_fused_kernel<VT, XT, 32, true>;
+  return launch_k(kern, dim3(grid), dim3(kThreads), smem, s, pdl, p);
 }
 
 template <typename VT, typename XT>
@@ -52,9 +54,8 @@ int Ops<VT, XT>::spmv_occupancy(int lpr, bool mat, size_t smem) {
 }
 
 template <typename VT, typename XT>
-cudaError_t Ops<VT, XT>::orth(const OrthParams<XT> &p, int grid, size_t smem, cudaStream_t s) {
-  orth_update_kernel<XT><<<grid, kThreads, smem, s>>>(p);
-  return cudaGetLastError();
+cudaError_t Ops<VT, XT>::orth(const OrthParams<XT> &p, int grid, size_t smem, cudaStream_t s, bool pdl) {
+  return launch_k(orth_update_kernel<XT>, dim3(grid), dim3(kThreads), smem, s, pdl, p);
 }
 
 template <typename VT, typename XT>

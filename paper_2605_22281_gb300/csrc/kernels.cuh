@@ -170,19 +170,33 @@ __device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT>
   constexpr int STR = LPR * P;
   using ACC = typename AccT<XT>::T;
   ACC s0 = (ACC)0, s1 = (ACC)0;
+  // Chunk slots (LPR*P entries each) of this group's row and the largest over
+  // the warp: FP64 instructions cost a full issue slot whatever the number of
+  // active lanes, so chunks past every group's row end are skipped outright
+  // (warp-uniform branches) rather than multiplied by zero.
+  const int nslot = (end - beg + STR - 1) / STR;
+  const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)nslot);
 #pragma unroll 1
-  for (int off = beg + gl * P; off < end; off += 4 * STR) {
+  for (int j = 0; j < nmax; j += 4) {
+    const int off = beg + gl * P + j * STR;
     Chunk<VT, P> c0, c1, c2, c3;
-    c0.load(p.col, p.val, off);
+    load_or_zero(c0, p.col, p.val, off, off < end);
     load_or_zero(c1, p.col, p.val, off + STR, off + STR < end);
     load_or_zero(c2, p.col, p.val, off + 2 * STR, off + 2 * STR < end);
     load_or_zero(c3, p.col, p.val, off + 3 * STR, off + 3 * STR < end);
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      s0 += (ACC)c0.v[q] * (ACC)__ldg(x + c0.c[q]);
-      s1 += (ACC)c1.v[q] * (ACC)__ldg(x + c1.c[q]);
-      s0 += (ACC)c2.v[q] * (ACC)__ldg(x + c2.c[q]);
-      s1 += (ACC)c3.v[q] * (ACC)__ldg(x + c3.c[q]);
+    for (int q = 0; q < P; ++q) s0 += (ACC)c0.v[q] * (ACC)__ldg(x + c0.c[q]);
+    if (j + 1 < nmax) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) s1 += (ACC)c1.v[q] * (ACC)__ldg(x + c1.c[q]);
+    }
+    if (j + 2 < nmax) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) s0 += (ACC)c2.v[q] * (ACC)__ldg(x + c2.c[q]);
+    }
+    if (j + 3 < nmax) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) s1 += (ACC)c3.v[q] * (ACC)__ldg(x + c3.c[q]);
     }
   }
   return s0 + s1;
@@ -202,18 +216,17 @@ __device__ __forceinline__ void mgs_coefficients(const double *dots, int nd, int
 
 // Rows [r0, r1) of one warp, in 32-row blocks: groups of LPR lanes run one row
 // each in LPR substeps; per-lane partial sums are stashed in shared memory and
-// lane r adds its row's partials in order, so the epilogue (output, norm,
-// window dots) runs with lane r owning row r and every FP64 instruction on a
-// full warp.  LPR = 1 is the vector pass (no matrix; the row value is b_r).
-template <typename VT, typename XT, int LPR, bool MAT, int ND>
-__device__ __forceinline__ void spmv_rows(const SpmvParams<VT, XT> &p, int64_t r0, int64_t r1,
-                                          const XT *__restrict__ x, XT *y, double xscale, const XT *win, int64_t wst,
-                                          int R, int lo, double (&acc)[ND + 1], typename AccT<XT>::T *stash) {
+// lane r adds its row's partials in order, so the output and ||y||^2 run with
+// lane r owning row r and every FP64 instruction on a full warp.  LPR = 1 is
+// the vector pass (no matrix; the row value is b_r).
+template <typename VT, typename XT, int LPR, bool MAT>
+__device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, int64_t r0, int64_t r1,
+                                            const XT *__restrict__ x, XT *y, typename AccT<XT>::T *stash) {
   constexpr int G = 32 / LPR;
   using ACC = typename AccT<XT>::T;
   const int lane = threadIdx.x & 31;
   const int gl = lane % LPR, grp = lane / LPR;
-  const ACC sc = (ACC)xscale;
+  double nrm = 0.0;
   for (int64_t row0 = r0; row0 < r1; row0 += 32) {
     const int64_t row = row0 + lane;
     const bool valid = row < r1;
@@ -237,38 +250,45 @@ __device__ __forceinline__ void spmv_rows(const SpmvParams<VT, XT> &p, int64_t r
 #pragma unroll
       for (int l = 0; l < LPR; ++l) s += stash[t * 32 + g * LPR + l];
       __syncwarp();
-      yv = s * sc;
+      yv = s;
     } else {
       if (valid) yv = (ACC)p.b[row];
     }
     if (valid) y[row] = (XT)yv;
     const double yd = valid ? (double)yv : 0.0;
-    acc[0] += yd * yd;
+    nrm += yd * yd;
+  }
+  return nrm;
+}
+
+// Window dots <v_j, y> over the warp's rows, after the products: lane r
+// re-reads the output of row r it stored itself, so the row loop above keeps
+// no per-window registers.
+template <typename XT, int ND>
+__device__ __forceinline__ void spmv_window_dots(int64_t r0, int64_t r1, const XT *y, const XT *win, int64_t wst,
+                                                 int R, int lo, double (&acc)[ND + 1]) {
+  const int lane = threadIdx.x & 31;
+  const XT *wv[ND > 0 ? ND : 1];
 #pragma unroll
-    for (int a = 0; a < ND; ++a)
-      acc[1 + a] += valid ? (double)win[(size_t)ring_slot(lo + a, R) * wst + row] * yd : 0.0;
+  for (int a = 0; a < ND; ++a) wv[a] = win + (size_t)ring_slot(lo + a, R) * wst;
+  for (int64_t row0 = r0; row0 < r1; row0 += 32) {
+    const int64_t row = row0 + lane;
+    if (row < r1) {
+      const double yd = (double)y[row];
+#pragma unroll
+      for (int a = 0; a < ND; ++a) acc[1 + a] += (double)wv[a][row] * yd;
+    }
   }
 }
 
-template <typename VT, typename XT, int LPR, bool MAT, int ND>
-__device__ __forceinline__ void spmv_run(const SpmvParams<VT, XT> &p, const XT *x, XT *y, double xscale,
-                                         const XT *win, int64_t wst, int R, int lo, double *outpart, bool reduce,
-                                         unsigned char *smem_raw, double *wsum) {
-  using ACC = typename AccT<XT>::T;
-  const int warp = threadIdx.x >> 5;
-  ACC *stash = reinterpret_cast<ACC *>(smem_raw) + warp * 32 * (LPR > 1 ? LPR : 1);
+template <typename XT, int ND>
+__device__ __forceinline__ void spmv_finish(int64_t r0, int64_t r1, const XT *y, const XT *win, int64_t wst, int R,
+                                            int lo, double nrm, double *outpart, double *wsum) {
   double acc[ND + 1];
+  acc[0] = nrm;
 #pragma unroll
-  for (int a = 0; a <= ND; ++a) acc[a] = 0.0;
-  const int gw = blockIdx.x * kWarps + warp;
-  int64_t r0, r1;
-  if (p.wrow) { r0 = p.wrow[gw]; r1 = p.wrow[gw + 1]; }
-  else {
-    const int64_t W = (int64_t)gridDim.x * kWarps;
-    r0 = (p.rows * gw) / W; r1 = (p.rows * (gw + 1)) / W;
-  }
-  spmv_rows<VT, XT, LPR, MAT, ND>(p, r0, r1, x, y, xscale, win, wst, R, lo, acc, stash);
-  if (!reduce) return;
+  for (int a = 1; a <= ND; ++a) acc[a] = 0.0;
+  spmv_window_dots<XT, ND>(r0, r1, y, win, wst, R, lo, acc);
   __syncthreads();
   store_partials<ND + 1>(acc, wsum, outpart);
 }
@@ -277,9 +297,76 @@ __host__ __device__ inline size_t spmv_smem_bytes(int lpr, size_t acc_bytes) {
   return acc_bytes * kWarps * 32 * (lpr > 1 ? lpr : 1);
 }
 
-// Fused SpMV of one step.  The prologue stages the solve state and reduces the
-// previous kernel's partial sums into the scalars this product needs (scale of
-// its input, breakdown decisions); CTA 0 records them in the device state.
+// Scalars booked by CTA 0 of a product (all its threads call): it stages the
+// solve state, reduces the records of the kernel before the product and
+// writes the step's scalars to the device state.  The other CTAs never need
+// them: products store unscaled outputs and their consumers apply the scale.
+template <typename VT, typename XT>
+__device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k, SolveState *sst, double *tot) {
+  stage_state(p.st, sst);
+  SolveState *st = p.st;
+  const bool t0 = threadIdx.x == 0;
+  if (p.mode == kModeInitBwd) {
+    // beta_1 = ||b||, w_1 = b / beta_1
+    reduce_partials_n<1>(p.part.b, p.G_prev, tot);
+    if (!t0) return;
+    const double beta = sqrt(tot[0]);
+    st->beta0 = beta;
+    st->sig_w[ring_slot(1, p.RW)] = 1.0 / beta;
+    st->tol = (sst->noise_norm > 0.0) ? sst->eta * sst->noise_norm / beta : 0.0;
+    if (!(beta > 0.0)) st->stop = SFL_STOP_BREAKDOWN;
+    if (!isfinite(tot[0])) st->stop = kStopNonfinite;
+  } else if (p.mode == kModeFwd) {
+    // alpha_k = ||p~_k|| from the z update; breakdown test; Gram row of p_k
+    const int lz = max(1, k - p.ell), ndz = k - lz;          // window of the z update
+    reduce_partials(p.part.p, p.G_prev, 1 + ndz, nullptr, tot);
+    if (!t0) return;
+    const double alpha = sqrt(tot[0]);
+    const bool bad = !(alpha > 1e-300) || !(alpha > 1e-14 * sqrt(sst->znorm_raw2)) || !isfinite(tot[0]);
+    if (bad) {
+      st->stop = isfinite(tot[0]) ? SFL_STOP_BREAKDOWN : kStopNonfinite;
+      return;
+    }
+    const double ia = 1.0 / alpha;
+    const int ns = ring_slot(k, p.RP);
+    st->alpha = alpha;
+    st->sig_p[ns] = ia;
+    p.sigZ[k - 1] = ia;
+    for (int a = 0; a < ndz; ++a) {
+      const int sa = ring_slot(lz + a, p.RP);
+      const double g = tot[1 + a] * sst->sig_p[sa] * ia;
+      st->gram_p[ns][sa] = g; st->gram_p[sa][ns] = g;
+    }
+  } else {   // kModeBwd
+    // beta_{k+1} = ||w~_{k+1}|| from the w update; lucky-breakdown test; Gram row of w_{k+1}
+    const int lw = max(1, k - p.ell), ndw = k - lw + 1;      // window of the w update
+    reduce_partials(p.part.wn, p.G_prev, 1 + ndw, nullptr, tot);
+    if (!t0) return;
+    const double beta = sqrt(tot[0]);
+    if (!isfinite(tot[0])) {
+      st->stop = kStopNonfinite;
+    } else if (!(beta > 1e-300) || !(beta > 1e-14 * sqrt(sst->wnorm_raw2))) {
+      st->lucky = 1;                 // step k is still solved; there is no w_{k+1}
+      st->betak = 0.0;
+    } else {
+      const double ib = 1.0 / beta;
+      const int ns = ring_slot(k + 1, p.RW);
+      st->betak = beta;
+      st->sig_w[ns] = ib;
+      if (p.method == kSFLSMR) p.Hband[(size_t)(k - 1) * (p.ell + 2) + p.ell + 1] = beta;
+      for (int a = 0; a < ndw; ++a) {
+        const int sa = ring_slot(lw + a, p.RW);
+        const double g = tot[1 + a] * sst->sig_w[sa] * ib;
+        st->gram_w[ns][sa] = g; st->gram_w[sa][ns] = g;
+      }
+    }
+  }
+}
+
+// Fused SpMV of one step.  In the solve modes past the first vector pass,
+// CTA 0 books the step's scalars (above) while the other CTAs run the rows:
+// outputs are stored unscaled (y = A x for the stored, unnormalised x), with
+// ||y||^2 and the window dots <v_j, y> as per-CTA records (CTA 0's are zero).
 template <typename VT, typename XT, int LPR, bool MAT>
 __global__ void __launch_bounds__(kThreads, 2) spmv_fused_kernel(SpmvParams<VT, XT> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -288,123 +375,81 @@ __global__ void __launch_bounds__(kThreads, 2) spmv_fused_kernel(SpmvParams<VT, 
   __shared__ double tot[kPartStride];
   // a launch with too little shared memory does nothing (never writes out of bounds)
   if (dynamic_smem_bytes() < spmv_smem_bytes(LPR, sizeof(typename AccT<XT>::T))) return;
-  const bool cta0 = blockIdx.x == 0 && threadIdx.x == 0;
+  griddep_wait();
+  griddep_launch_dependents();
   int k = 0, lo = 1, nd = 0;
   const XT *x = p.x;
   XT *y = p.y;
   const XT *win = nullptr; int64_t wst = 0; int R = 1;
-  double xscale = 1.0;
   double *outpart = nullptr;
   bool reduce = true;
+  int rcta = blockIdx.x, ncta = gridDim.x;   // this CTA among the row CTAs
   if (p.mode == kModeApply) {
     reduce = false;
   } else {
-    stage_state(p.st, &sst);
-    if (sst.stop) return;
-    k = sst.k + 1;
+    if (__ldcg(&p.st->stop)) return;
+    k = __ldcg(&p.st->k) + 1;
     if (p.mode == kModeInitB) {
       y = p.wring + (size_t)ring_slot(1, p.RW) * p.wstride;
       outpart = p.part.b;
     } else if (p.mode == kModeInitBwd) {
-      reduce_partials(p.part.b, p.G_prev, 1, wsum, tot);
-      const double beta = sqrt(tot[0]);
-      if (cta0) {
-        SolveState *st = p.st;
-        st->beta0 = beta;
-        st->sig_w[ring_slot(1, p.RW)] = 1.0 / beta;
-        st->tol = (sst.noise_norm > 0.0) ? sst.eta * sst.noise_norm / beta : 0.0;
-        if (!(beta > 0.0)) st->stop = SFL_STOP_BREAKDOWN;
-        if (!isfinite(tot[0])) st->stop = kStopNonfinite;
-      }
-      if (!(beta > 0.0) || !isfinite(tot[0])) return;
       x = p.wring + (size_t)ring_slot(1, p.RW) * p.wstride;
-      xscale = 1.0 / beta;
       y = p.zraw;
       outpart = p.part.z;
     } else if (p.mode == kModeFwd) {
-      // alpha_k = ||p~_k|| from the z update; breakdown test; Gram row of p_k
-      const int lz = max(1, k - p.ell), ndz = k - lz;          // window of the z update
-      reduce_partials(p.part.p, p.G_prev, 1 + ndz, wsum, tot);
-      const double alpha = sqrt(tot[0]);
-      const bool bad = !(alpha > 1e-300) || !(alpha > 1e-14 * sqrt(sst.znorm_raw2)) || !isfinite(tot[0]);
-      if (cta0) {
-        SolveState *st = p.st;
-        if (bad) {
-          st->stop = isfinite(tot[0]) ? SFL_STOP_BREAKDOWN : kStopNonfinite;
-        } else {
-          const int ns = ring_slot(k, p.RP);
-          st->alpha = alpha;
-          st->sig_p[ns] = 1.0 / alpha;
-          p.sigZ[k - 1] = 1.0 / alpha;
-          for (int a = 0; a < ndz; ++a) {
-            const int sa = ring_slot(lz + a, p.RP);
-            const double g = tot[1 + a] * sst.sig_p[sa] / alpha;
-            st->gram_p[ns][sa] = g; st->gram_p[sa][ns] = g;
-          }
-        }
-      }
-      if (bad) return;
       x = p.Z + (size_t)(k - 1) * p.zstride;
-      xscale = 1.0 / alpha;
       y = p.wraw;
       lo = max(1, k - p.ell); nd = k - lo + 1;
       win = p.wring; wst = p.wstride; R = p.RW;
       outpart = p.part.w;
     } else {  // kModeBwd
-      // beta_{k+1} = ||w~_{k+1}|| from the w update; lucky-breakdown test; Gram row of w_{k+1}
-      const int lw = max(1, k - p.ell), ndw = k - lw + 1;      // window of the w update
-      reduce_partials(p.part.wn, p.G_prev, 1 + ndw, wsum, tot);
-      const double beta = sqrt(tot[0]);
-      const bool nonfinite = !isfinite(tot[0]);
-      const bool lucky = !(beta > 1e-300) || !(beta > 1e-14 * sqrt(sst.wnorm_raw2));
-      if (cta0) {
-        SolveState *st = p.st;
-        if (nonfinite) {
-          st->stop = kStopNonfinite;
-        } else if (lucky) {
-          st->lucky = 1;                 // step k is still solved; there is no w_{k+1}
-          st->betak = 0.0;
-        } else {
-          const int ns = ring_slot(k + 1, p.RW);
-          st->betak = beta;
-          st->sig_w[ns] = 1.0 / beta;
-          if (p.method == kSFLSMR) p.Hband[(size_t)(k - 1) * (p.ell + 2) + p.ell + 1] = beta;
-          for (int a = 0; a < ndw; ++a) {
-            const int sa = ring_slot(lw + a, p.RW);
-            const double g = tot[1 + a] * sst.sig_w[sa] / beta;
-            st->gram_w[ns][sa] = g; st->gram_w[sa][ns] = g;
-          }
-        }
-      }
-      if (nonfinite || lucky) return;
       x = p.wring + (size_t)ring_slot(k + 1, p.RW) * p.wstride;
-      xscale = 1.0 / beta;
       y = p.zraw;
       lo = max(1, k + 1 - p.ell); nd = k - lo + 1;
       win = p.pring; wst = p.pstride; R = p.RP;
       outpart = p.part.z;
     }
+    if (p.mode != kModeInitB) {
+      if (blockIdx.x == 0) {
+        if (threadIdx.x < kPartStride) outpart[(size_t)threadIdx.x * kPartCap] = 0.0;   // CTA 0's record
+        spmv_bookkeeping(p, k, &sst, tot);
+        return;
+      }
+      rcta = blockIdx.x - 1;
+      ncta = gridDim.x - 1;
+    }
   }
+  // this warp's rows: the products, then the window dots and the partial record
+  using ACC = typename AccT<XT>::T;
+  const int warp = threadIdx.x >> 5;
+  ACC *stash = reinterpret_cast<ACC *>(smem_raw) + warp * 32 * (LPR > 1 ? LPR : 1);
+  const int gw = rcta * kWarps + warp;
+  int64_t r0, r1;
+  if (p.wrow) { r0 = p.wrow[gw]; r1 = p.wrow[gw + 1]; }
+  else {
+    const int64_t W = (int64_t)ncta * kWarps;
+    r0 = (p.rows * gw) / W; r1 = (p.rows * (gw + 1)) / W;
+  }
+  const double nrm = spmv_rows<VT, XT, LPR, MAT>(p, r0, r1, x, y, stash);
+  if (!reduce) return;
   if (!MAT) {     // vector pass: no window dots
-    spmv_run<VT, XT, LPR, MAT, 0>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum);
+    spmv_finish<XT, 0>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum);
     return;
   }
-  switch (nd) {   // the window size is a compile-time constant inside the body
-    case 0: spmv_run<VT, XT, LPR, MAT, 0>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    case 1: spmv_run<VT, XT, LPR, MAT, 1>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    case 2: spmv_run<VT, XT, LPR, MAT, 2>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    case 3: spmv_run<VT, XT, LPR, MAT, 3>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    case 4: spmv_run<VT, XT, LPR, MAT, 4>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    case 5: spmv_run<VT, XT, LPR, MAT, 5>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    case 6: spmv_run<VT, XT, LPR, MAT, 6>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    case 7: spmv_run<VT, XT, LPR, MAT, 7>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    case 8: spmv_run<VT, XT, LPR, MAT, 8>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
-    default: spmv_run<VT, XT, LPR, MAT, 9>(p, x, y, xscale, win, wst, R, lo, outpart, reduce, smem_raw, wsum); break;
+  switch (nd) {   // the window size is a compile-time constant inside the tail
+    case 0: spmv_finish<XT, 0>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 1: spmv_finish<XT, 1>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 2: spmv_finish<XT, 2>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 3: spmv_finish<XT, 3>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 4: spmv_finish<XT, 4>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 5: spmv_finish<XT, 5>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 6: spmv_finish<XT, 6>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 7: spmv_finish<XT, 7>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 8: spmv_finish<XT, 8>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    default: spmv_finish<XT, 9>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
   }
 }
 
-// Row range of every warp so that each warp gets about the same number of
-// stored entries (rows are never split).  W warps, W + 1 boundaries.
 // Row cost for the warp partition of a product: the row's 4-load iterations
 // (ceil(len / unit), unit = 4 * lanes per row * load width) in quarter
 // iterations, plus one quarter for the row's share of the per-row work
@@ -485,7 +530,8 @@ struct SketchParams {
   double isz;                              // 1 / sqrt(zeta)
   SolveState *st;
   const double *v64;                       // kSkPlain / kSkInitB input
-  const XT *wraw, *zraw;                   // kSkStep / kSkInitBwd inputs
+  const XT *wraw, *zraw;                   // kSkStep / kSkInitBwd inputs (unscaled product outputs)
+  int RW, RP;                               // ring sizes (slots of the scales of wraw and zraw)
   const int32_t *rowM; const uint32_t *entM;   // m-side table (S_m)
   const int32_t *rowN; const uint32_t *entN;   // n-side table (S_n)
   double *SAZ, *SAtW, *rhs, *e, *sbm, *sk_out;
@@ -532,16 +578,22 @@ __global__ void __launch_bounds__(kSkWarps * 32) sketch_rows_kernel(SketchParams
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gr = blockIdx.x;
   if (gr >= rows_total) return;
+  griddep_wait();
+  griddep_launch_dependents();
   int k = 0;
-  double beta = 1.0;
+  double beta = 1.0, vscale = 1.0;
+  const int which = gr / p.s, r = gr % p.s;
   if (p.mode != kSkPlain) {
     const SolveState *st = p.st;
     if (__ldcg(&st->stop)) return;
     k = __ldcg(&st->k) + 1;
     if (p.mode == kSkStep && gr >= p.s && __ldcg(&st->lucky)) return;   // no z at a lucky breakdown
     if (p.mode == kSkInitBwd) beta = __ldcg(&st->beta0);
+    // scale of the unscaled product output: 1/alpha_k for A z_k, 1/beta_{k+1} for A^T w_{k+1}
+    if (p.mode == kSkInitBwd) vscale = __ldcg(&st->sig_w[ring_slot(1, p.RW)]);
+    else if (p.mode == kSkStep) vscale = which == 0 ? __ldcg(&st->sig_p[ring_slot(k, p.RP)])
+                                                    : __ldcg(&st->sig_w[ring_slot(k + 1, p.RW)]);
   }
-  const int which = gr / p.s, r = gr % p.s;
   const bool nside = (p.mode == kSkInitBwd) || (p.mode == kSkStep && which == 1);
   const int32_t *rowptr = nside ? p.rowN : p.rowM;
   const uint32_t *ent = nside ? p.entN : p.entM;
@@ -552,7 +604,7 @@ __global__ void __launch_bounds__(kSkWarps * 32) sketch_rows_kernel(SketchParams
   __syncthreads();
   if (threadIdx.x != 0) return;
   static_assert(kSkWarps == 4, "warp totals are added as a pair of pairs");
-  const double v = ((wpart[0] + wpart[1]) + (wpart[2] + wpart[3])) * p.isz;
+  const double v = ((wpart[0] + wpart[1]) + (wpart[2] + wpart[3])) * p.isz * vscale;
   if (p.mode == kSkPlain) {
     p.sk_out[r] = v;
   } else if (p.mode == kSkStep) {
@@ -572,6 +624,7 @@ __global__ void __launch_bounds__(kSkWarps * 32) sketch_rows_kernel(SketchParams
 
 template <typename XT>
 struct OrthParams {
+  int scale_ring;     // size of the ring whose scale of slot k applies to raw (w ring for z, p ring for w)
   SolveState *st;
   int side;            // 0: z side (p ring, tau, Z), 1: w side (w ring)
   int ell;
@@ -596,7 +649,8 @@ struct OrthParams {
 // for an unused window slot.
 template <typename XT, int ND>
 __device__ __forceinline__ void orth_run(const OrthParams<XT> &p, const SolveState &sst, int k, int lo, int newj,
-                                         const double *coefs, const double *s_c, bool reweight, double *wsum) {
+                                         const double *coefs, const double *s_c, bool reweight, double *wsum,
+                                         double rs) {
   double coef[ND > 0 ? ND : 1];
   const XT *vj[ND > 0 ? ND : 1];
 #pragma unroll
@@ -611,9 +665,13 @@ __device__ __forceinline__ void orth_run(const OrthParams<XT> &p, const SolveSta
   double acc[ND + 1];
 #pragma unroll
   for (int a = 0; a <= ND; ++a) acc[a] = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.len; i += stride) {
-    double v = (double)p.raw[i];
+  // one contiguous chunk of ceil(len / grid) elements per CTA: every CTA gets
+  // the same work (a grid-stride loop leaves CTAs idle when len < grid * block)
+  const int64_t chunk = (p.len + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * chunk;
+  const int64_t i1 = min(p.len, i0 + chunk);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double v = (double)p.raw[i] * rs;
     double old[ND > 0 ? ND : 1];
 #pragma unroll
     for (int a = 0; a < ND; ++a) { old[a] = (double)vj[a][i]; v -= coef[a] * old[a]; }
@@ -656,23 +714,37 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
   __shared__ double wsum[(kMaxWindow + 2) * kThreads];   // reduction scratch
   __shared__ double tot[kPartStride];
   __shared__ double coefs[kMaxWindow + 2];
+  griddep_wait();
+  griddep_launch_dependents();
   stage_state(p.st, &sst);
   if (sst.stop) return;
   const int k = sst.k + 1;
   if (dynamic_smem_bytes() < sizeof(double) * (size_t)k) return;
   const bool cta0 = blockIdx.x == 0 && threadIdx.x == 0;
+  // the product stored its output unscaled: raw * rs is the true vector
+  const double rs = p.side == 0 ? sst.sig_w[ring_slot(k, p.scale_ring)] : sst.sig_p[ring_slot(k, p.scale_ring)];
+  auto scale_dots = [&](int nq) {   // thread 0: products' records are of the unscaled output
+    tot[0] *= rs * rs;
+    for (int a = 1; a < nq; ++a) tot[a] *= rs;
+  };
   int lo, nd, newj;
   if (p.side == 0) {
     // coefficients of z against p_lo..p_{k-1} from the A^T w product's dots
     lo = max(1, k - p.ell); nd = k - lo; newj = k;
     reduce_partials(p.part.z, p.G_prev, 1 + nd, wsum, tot);
-    if (threadIdx.x == 0) mgs_coefficients(tot + 1, nd, lo, p.R, sst.sig_p, sst.gram_p, coefs);
+    if (threadIdx.x == 0) {
+      scale_dots(1 + nd);
+      mgs_coefficients(tot + 1, nd, lo, p.R, sst.sig_p, sst.gram_p, coefs);
+    }
     if (cta0) p.st->znorm_raw2 = tot[0];
   } else {
     // coefficients of w against w_lo..w_k (column k of H) from the A z_k product's dots
     lo = max(1, k - p.ell); nd = k - lo + 1; newj = k + 1;
     reduce_partials(p.part.w, p.G_prev, 1 + nd, wsum, tot);
-    if (threadIdx.x == 0) mgs_coefficients(tot + 1, nd, lo, p.R, sst.sig_w, sst.gram_w, coefs);
+    if (threadIdx.x == 0) {
+      scale_dots(1 + nd);
+      mgs_coefficients(tot + 1, nd, lo, p.R, sst.sig_w, sst.gram_w, coefs);
+    }
     if (cta0) {
       p.st->wnorm_raw2 = tot[0];
       for (int a = 0; a < nd; ++a) p.st->hw[a] = coefs[a];
@@ -689,16 +761,16 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
     for (int j = threadIdx.x; j < k - 1; j += blockDim.x) s_c[j] = p.sigZ[j] * p.y[j];
   __syncthreads();
   switch (nd) {
-    case 0: orth_run<XT, 0>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    case 1: orth_run<XT, 1>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    case 2: orth_run<XT, 2>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    case 3: orth_run<XT, 3>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    case 4: orth_run<XT, 4>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    case 5: orth_run<XT, 5>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    case 6: orth_run<XT, 6>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    case 7: orth_run<XT, 7>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    case 8: orth_run<XT, 8>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
-    default: orth_run<XT, 9>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum); break;
+    case 0: orth_run<XT, 0>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    case 1: orth_run<XT, 1>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    case 2: orth_run<XT, 2>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    case 3: orth_run<XT, 3>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    case 4: orth_run<XT, 4>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    case 5: orth_run<XT, 5>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    case 6: orth_run<XT, 6>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    case 7: orth_run<XT, 7>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    case 8: orth_run<XT, 8>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
+    default: orth_run<XT, 9>(p, sst, k, lo, newj, coefs, s_c, reweight, wsum, rs); break;
   }
 }
 
@@ -710,6 +782,7 @@ struct LsParams {
   SolveState *st;
   int method, s, maxit, ell, stop_rule;
   int stage_q;        // 1: each CTA copies its block of Q rows into shared memory first
+  int stage_saz;      // 1: each CTA copies its block of SAZ rows into shared memory (residual rule)
   double *Q;          // s x maxit, row-major: orthonormal basis of the sketched columns
   double *Rinv;       // maxit x maxit, row-major: inverse of the triangular factor
   double *y;          // maxit
@@ -727,15 +800,16 @@ struct LsParams {
 constexpr int kMaxCluster = 16;
 
 // Shared-memory plan of the least-squares step (in doubles), identical on the
-// host (launch size) and the device (guard): four vectors of maxit+2, three
-// row blocks, slice partials, and optionally the staged Q block with an odd
-// row stride (no bank conflicts between rows).
+// host (launch size) and the device (guard): six vectors of maxit+2, three
+// row blocks, slice partials, and optionally the staged Q and SAZ blocks with
+// an odd row stride (no bank conflicts between rows).
 __host__ __device__ inline int ls_rows_per_cta(int s, int cl) { return (s + cl - 1) / cl; }
 __host__ __device__ inline int ls_qld(int maxit) { return maxit | 1; }
-__host__ __device__ inline size_t ls_smem_doubles(int s, int maxit, int cl, int stage) {
+__host__ __device__ inline size_t ls_smem_doubles(int s, int maxit, int cl, int stage_q, int stage_saz) {
   const int RB = ls_rows_per_cta(s, cl);
-  size_t n = 4 * (size_t)(maxit + 2) + 3 * (size_t)RB + (size_t)(RB > kThreads ? RB : kThreads);
-  if (stage) n += (size_t)RB * ls_qld(maxit);
+  size_t n = 6 * (size_t)(maxit + 2) + 3 * (size_t)RB + (size_t)(RB > kThreads ? RB : kThreads);
+  if (stage_q) n += (size_t)RB * ls_qld(maxit);
+  if (stage_saz) n += (size_t)RB * ls_qld(maxit);
   return n;
 }
 
@@ -752,6 +826,8 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   SolveState *st = p.st;
+  griddep_wait();
+  griddep_launch_dependents();
   // Every CTA reads the flags before the first cluster barrier; rank 0 writes
   // them only after the last one, so all CTAs take the same branches.
   const int stop0 = st->stop, lucky = st->lucky;
@@ -764,25 +840,44 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
   const int RB = ls_rows_per_cta(s, CL);
   const int r0 = min(s, rank * RB), r1 = min(s, r0 + RB), nr = r1 - r0;
   const int KP = p.maxit + 2;
+  const bool resid_rule = p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL;
   // every CTA of the cluster got the same shared memory: all leave together
-  if (dynamic_smem_bytes() < sizeof(double) * ls_smem_doubles(s, p.maxit, CL, p.stage_q)) {
+  if (dynamic_smem_bytes() < sizeof(double) * ls_smem_doubles(s, p.maxit, CL, p.stage_q, p.stage_saz)) {
     if (rank == 0 && tid == 0 && p.use_cond) cudaGraphSetConditional(p.cond, 0u);
     return;
   }
 
+  // ---- prefetch, consumed in step 7: this warp's rows of R^{-1} (columns < kk) and of y
+  constexpr int kPR = 2, kPC = 8;   // rows per warp, values per lane per row held in registers
+  double rin[kPR][kPC], yold[kPR];
+#pragma unroll
+  for (int t = 0; t < kPR; ++t) {
+    const int i = rank * kWarps + warp + t * CL * kWarps;
+    yold[t] = (i < kk) ? p.y[i] : 0.0;
+#pragma unroll
+    for (int c = 0; c < kPC; ++c) {
+      const int j = i + lane + 32 * c;
+      rin[t][c] = (i < kk && j < kk) ? p.Rinv[(size_t)i * p.maxit + j] : 0.0;
+    }
+  }
+
   extern __shared__ __align__(16) double lsm[];
   double *part0 = lsm;              // [KP] partial vectors exchanged in the cluster (pass 1)
-  double *part1 = part0 + KP;       // [KP] (pass 2)
+  double *part1 = part0 + KP;       // [KP] (pass 2 and its two scalars)
   double *red = part1 + KP;         // [KP] cluster-reduced vector
   double *rr = red + KP;            // [KP] R column above the diagonal
-  double *crow = rr + KP;           // [RB] my rows of the working column
+  double *ys = rr + KP;             // [KP] entries of y_k computed by this CTA (read by peers)
+  double *yfull = ys + KP;          // [KP] y_k gathered from the cluster
+  double *crow = yfull + KP;        // [RB] my rows of the working column
   double *ecur = crow + RB;         // [RB] my rows of e
   double *upd = ecur + RB;          // [RB] my rows of a matrix-vector product
   double *tmp = upd + RB;           // [max(kThreads, RB)] slice partials
-  double *Qs = tmp + max(kThreads, RB);   // [RB x ldq] staged Q block
+  double *Qs = tmp + max(kThreads, RB);                        // [RB x ldq] staged Q block
+  double *Ss = Qs + (p.stage_q ? (size_t)RB * ls_qld(p.maxit) : 0);   // [RB x ldq] staged SAZ block
   const int H = max(1, kThreads / max(RB, 1));   // column slices per row
   __shared__ double s_sc[2][4];     // scalar partials exchanged in the cluster
   __shared__ double s_res[2][4];
+  __shared__ double s_r2n;
 
   // my block of Q rows: staged copy or the global rows
   const double *Qb = p.stage_q ? Qs : p.Q + (size_t)r0 * p.maxit;
@@ -870,7 +965,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
     __syncthreads();
   };
 
-  // ---- 0. the new column and e, my rows; the Q block
+  // ---- 0. the new column and e, my rows; the staged blocks
   for (int i = tid; i < nr; i += kThreads) {
     const int row = r0 + i;
     double c;
@@ -889,16 +984,24 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
     crow[i] = c;
     ecur[i] = p.e[row];
   }
-  if (p.stage_q && kk > 0) {
-    const int ldq = ls_qld(p.maxit);
+  const int ldq = ls_qld(p.maxit);
+  if (p.stage_q && kk > 0)
     for (int t = tid; t < nr * kk; t += kThreads) {
       const int i = t / kk, j = t - i * kk;
       Qs[(size_t)i * ldq + j] = p.Q[(size_t)(r0 + i) * p.maxit + j];
     }
-  }
+  if (p.stage_saz && resid_rule)
+    for (int t = tid; t < nr * k; t += kThreads) {
+      const int j = t / nr, i = t - j * nr;
+      Ss[(size_t)i * ldq + j] = p.SAZ[(size_t)j * s + r0 + i];
+    }
   __syncthreads();
 
-  // ---- 1-4. classical Gram-Schmidt twice against the first kk columns
+  // ---- 1-5. classical Gram-Schmidt twice against the first kk columns; the
+  // second pass also totals ||c'||^2 and <c', e>, so that
+  // rho^2 = ||c'||^2 - ||Q^T c'||^2 and <c'', e> = <c', e> - (Q^T c').(Q^T e),
+  // whose last term is a product of two rounding-level vectors and is dropped.
+  double rho2, ce, den;
   if (kk > 0) {
     qt_partial(part0);
     cluster_allreduce_vec(part0, kk, red);
@@ -907,27 +1010,48 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
     for (int i = tid; i < nr; i += kThreads) crow[i] -= upd[i];
     __syncthreads();
     qt_partial(part1);
-    cluster_allreduce_vec(part1, kk, red);
+    if (warp == kWarps - 1) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int i = lane; i < nr; i += 32) {
+        a0 += crow[i] * crow[i];
+        a1 += crow[i] * ecur[i];
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      if (lane == 0) { part1[kk] = a0; part1[kk + 1] = a1; }
+    }
+    cluster_allreduce_vec(part1, kk + 2, red);
     for (int j = tid; j < kk; j += kThreads) rr[j] += red[j];
-    rows_times_vec(Qb, qld, 1, red, kk, upd);
+    if (warp == 0) {
+      double a = 0.0;
+      for (int j = lane; j < kk; j += 32) a += red[j] * red[j];
+      a = warp_sum(a);
+      if (lane == 0) s_r2n = a;
+    }
+    rows_times_vec(Qb, qld, 1, red, kk, upd);   // synchronises: s_r2n is visible after it
     for (int i = tid; i < nr; i += kThreads) crow[i] -= upd[i];
-    __syncthreads();
-  }
-  // ---- 5. ||c||^2, <c, e> and (first step) the stop-ratio denominator:
-  // ||s_b|| (sFLSQR), ||S_m b|| (sFLSMR, residual rule) or ||s_{A^T b}||
-  // (sFLSMR, normal-equation rule)
-  {
-    const double *dv = (p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL) ? p.sbm : p.rhs;
+    rho2 = red[kk] - s_r2n;
+    ce = red[kk + 1];
+    den = st->stop_den;
+  } else {
+    // first step: ||c||^2, <c, e> and the stop-ratio denominator ||s_b||
+    // (sFLSQR), ||S_m b|| (sFLSMR, residual rule) or ||s_{A^T b}|| (sFLSMR,
+    // normal-equation rule)
+    const double *dv = resid_rule ? p.sbm : p.rhs;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     if (warp == 0)
       for (int i = lane; i < nr; i += 32) {
         a0 += crow[i] * crow[i];
         a1 += crow[i] * ecur[i];
-        if (k == 1) a2 += dv[r0 + i] * dv[r0 + i];
+        a2 += dv[r0 + i] * dv[r0 + i];
       }
-    cluster_allreduce_sc(a0, a1, a2, k == 1 ? 3 : 2, 0);
+    cluster_allreduce_sc(a0, a1, a2, 3, 0);
+    rho2 = s_res[0][0];
+    ce = s_res[0][1];
+    den = sqrt(s_res[0][2]);
   }
-  const double rho = sqrt(s_res[0][0]);
+  // rho^2 may round below zero for a dependent column (a breakdown); NaN stays NaN
+  const double rho = rho2 >= 0.0 ? sqrt(rho2) : (rho2 < 0.0 ? 0.0 : rho2);
   const double R11 = (k == 1) ? rho : st->R11;
   if (!(rho > 1e-300) || !(rho > 1e-14 * R11) || !isfinite(rho)) {
     cl.sync();   // no CTA leaves while a peer may still read its shared memory
@@ -937,10 +1061,10 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
     }
     return;
   }
-  const double den = (k == 1) ? sqrt(s_res[0][2]) : st->stop_den;
   // ---- 6. q_k = c / rho, gamma_k = <q_k, e>, e -= gamma_k q_k
   const double irho = 1.0 / rho;
-  const double gamma = s_res[0][1] * irho;
+  const double gamma = ce * irho;
+  __syncthreads();   // crow is final
   for (int i = tid; i < nr; i += kThreads) {
     const double q = crow[i] * irho;
     p.Q[(size_t)(r0 + i) * p.maxit + kk] = q;
@@ -949,29 +1073,57 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
     ecur[i] = ei;
   }
   // ---- 7. column kk of R^{-1} and y_k = [y_{k-1}; 0] + gamma_k R^{-1}[:, kk]
-  for (int i = rank * kWarps + warp; i < kk; i += CL * kWarps) {
-    double a = 0.0;
-    for (int j = i + lane; j < kk; j += 32) a += p.Rinv[(size_t)i * p.maxit + j] * rr[j];
+  auto rinv_row = [&](int i, double a, double y_prev) {
     a = warp_sum(a);
     if (lane == 0) {
       const double u = -a * irho;
+      const double yn = y_prev + gamma * u;
       p.Rinv[(size_t)i * p.maxit + kk] = u;
-      p.y[i] += gamma * u;
+      p.y[i] = yn;
+      ys[i] = yn;
     }
+  };
+#pragma unroll
+  for (int t = 0; t < kPR; ++t) {
+    const int i = rank * kWarps + warp + t * CL * kWarps;
+    if (i < kk) {
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int c = 0; c < kPC; ++c) {
+        const int j = i + lane + 32 * c;
+        if (j < kk) {
+          if (c & 1) a1 += rin[t][c] * rr[j];
+          else a0 += rin[t][c] * rr[j];
+        }
+      }
+      for (int j = i + lane + 32 * kPC; j < kk; j += 32) a0 += p.Rinv[(size_t)i * p.maxit + j] * rr[j];
+      rinv_row(i, a0 + a1, yold[t]);
+    }
+  }
+  for (int t = kPR;; ++t) {   // rows past the prefetched ones (kk > kPR * CL * kWarps)
+    const int i = rank * kWarps + warp + t * CL * kWarps;
+    if (i >= kk) break;
+    double a = 0.0;
+    for (int j = i + lane; j < kk; j += 32) a += p.Rinv[(size_t)i * p.maxit + j] * rr[j];
+    rinv_row(i, a, p.y[i]);
   }
   if (rank == 0 && tid == 0) {
     p.Rinv[(size_t)kk * p.maxit + kk] = irho;
     p.y[kk] = gamma * irho;
   }
-  __syncthreads();
   // ---- 8. residual of the stop test
-  if (p.method == kSFLSMR && p.stop_rule == SFL_STOP_RULE_RESIDUAL) {
-    // || S_m b - S_m A Z_k y_k ||, my rows; y is published in the cluster first
-    __threadfence();
+  if (resid_rule) {
+    // || S_m b - S_m A Z_k y_k ||, my rows; y_k is gathered from its owners'
+    // shared memory after a cluster barrier
     cl.sync();
-    for (int j = tid; j < k; j += kThreads) red[j] = __ldcg(p.y + j);
+    for (int j = tid; j < kk; j += kThreads) {
+      const int owner = (j % (CL * kWarps)) / kWarps;
+      yfull[j] = cl.map_shared_rank(ys, owner)[j];
+    }
+    if (tid == 0) yfull[kk] = gamma * irho;
     __syncthreads();
-    rows_times_vec(p.SAZ + r0, 1, s, red, k, upd);
+    if (p.stage_saz) rows_times_vec(Ss, ldq, 1, yfull, k, upd);
+    else rows_times_vec(p.SAZ + r0, 1, s, yfull, k, upd);
     double a0 = 0.0;
     if (warp == 0)
       for (int i = lane; i < nr; i += 32) {
@@ -980,6 +1132,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
       }
     cluster_allreduce_sc(a0, 0.0, 0.0, 1, 1);
   } else {
+    __syncthreads();   // ecur is final
     double a0 = 0.0;
     if (warp == 0)
       for (int i = lane; i < nr; i += 32) a0 += ecur[i] * ecur[i];

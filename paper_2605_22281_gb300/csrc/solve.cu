@@ -57,19 +57,24 @@ static void destroy_session(Plan &pl, Session &se) {
 // within this budget (it then serves the four Q products of a step).
 constexpr size_t kLsStageBudget = 160 * 1024;
 
-int ls_stage_q(int s, int maxit, int cluster) {
-  return sizeof(double) * ls_smem_doubles(s, maxit, cluster, 1) <= kLsStageBudget ? 1 : 0;
+// Staging plan: Q and SAZ blocks (SAZ only for the sFLSMR residual rule),
+// else Q only, else neither.  Returns bit 0 = Q, bit 1 = SAZ.
+int ls_stage_plan(int s, int maxit, int cluster, bool saz) {
+  if (saz && sizeof(double) * ls_smem_doubles(s, maxit, cluster, 1, 1) <= kLsStageBudget) return 3;
+  if (sizeof(double) * ls_smem_doubles(s, maxit, cluster, 1, 0) <= kLsStageBudget) return 1;
+  return 0;
 }
 
-size_t ls_smem_bytes(int s, int maxit, int cluster) {
-  return sizeof(double) * ls_smem_doubles(s, maxit, cluster, ls_stage_q(s, maxit, cluster));
+size_t ls_smem_bytes(int s, int maxit, int cluster, bool saz) {
+  const int st = ls_stage_plan(s, maxit, cluster, saz);
+  return sizeof(double) * ls_smem_doubles(s, maxit, cluster, st & 1, (st >> 1) & 1);
 }
 
-int ls_cluster_size(int s, int maxit) {
+int ls_cluster_size(int s, int maxit, bool saz) {
   cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   for (int cl : {16, 8, 4, 2, 1}) {
     static_assert(kMaxCluster == 16, "largest cluster tried");
-    const size_t smem = ls_smem_bytes(s, maxit, cl);
+    const size_t smem = ls_smem_bytes(s, maxit, cl, saz);
     if (cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
       cudaGetLastError();
       continue;
@@ -92,19 +97,21 @@ int ls_cluster_size(int s, int maxit) {
   return 0;
 }
 
-cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s) {
+cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s, bool pdl) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, ls_step_kernel, p);
 }
 
@@ -207,6 +214,7 @@ struct Engine {
     q.st = se.st;
     q.v64 = se.bbuf;
     q.wraw = (const XT *)se.wraw; q.zraw = (const XT *)se.zraw;
+    q.RW = se.RW; q.RP = se.RP;
     q.rowM = se.skM_row; q.entM = se.skM_ent; q.rowN = se.skN_row; q.entN = se.skN_ent;
     q.SAZ = se.SAZ; q.SAtW = se.SAtW; q.rhs = se.rhs; q.e = se.e; q.sbm = se.sbm;
     return q;
@@ -219,6 +227,7 @@ struct Engine {
     o.part = se.part;
     o.G_prev = side == 0 ? se.grid_spmv_T : se.grid_spmv_A;
     o.Hband = se.Hband;
+    o.scale_ring = side == 0 ? se.RW : se.RP;
     if (side == 0) {
       o.len = pl.A.cols; o.raw = (const XT *)se.zraw; o.ring = (XT *)se.pring; o.stride = pl.A.cols; o.R = se.RP;
       o.Z = (XT *)se.Z; o.zstride = pl.A.cols; o.sigZ = se.sigZ;
@@ -234,7 +243,8 @@ struct Engine {
     LsParams q{};
     q.st = se.st; q.method = se.key.method; q.s = se.key.s; q.maxit = se.key.maxit; q.ell = se.key.ell;
     q.stop_rule = se.key.stop_rule;
-    q.stage_q = se.ls_stage;
+    q.stage_q = se.ls_stage & 1;
+    q.stage_saz = (se.ls_stage >> 1) & 1;
     q.Q = se.Q; q.Rinv = se.Rinv; q.y = se.y; q.e = se.e;
     q.SAZ = se.SAZ; q.SAtW = se.SAtW; q.Hband = se.Hband; q.sbm = se.sbm; q.rhs = se.rhs;
     q.relres_hist = se.key.r_hist;
@@ -250,11 +260,11 @@ struct Engine {
     return f();
   }
 
-  static int k_sketch(const Session &se, int mode, int rows, cudaStream_t s) {
-    sketch_rows_kernel<XT><<<rows, kSkWarps * 32, 0, s>>>(sketch_params(se, mode), rows);
-    return cudaGetLastError() == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  static int k_sketch(const Session &se, int mode, int rows, cudaStream_t s, bool pdl = false) {
+    return launch_k(sketch_rows_kernel<XT>, dim3(rows), dim3(kSkWarps * 32), 0, s, pdl, sketch_params(se, mode),
+                    rows) == cudaSuccess ? SFL_OK : SFL_ECUDA;
   }
-  static int k_spmv(const Plan &pl, const Session &se, int mode, cudaStream_t s) {
+  static int k_spmv(const Plan &pl, const Session &se, int mode, cudaStream_t s, bool pdl = false) {
     const bool fwd = (mode == kModeFwd || mode == kModeInitB);
     const StoredCsr &M = fwd ? pl.A : pl.T;
     SpmvParams<VT, XT> p = base_params(pl, se, M, mode);
@@ -265,10 +275,11 @@ struct Engine {
     }
     const int grid = fwd ? se.grid_spmv_A : se.grid_spmv_T;
     const size_t smem = fwd ? se.smem_A : se.smem_T;
-    return O::spmv(p, M.lpr, true, grid, smem, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
+    return O::spmv(p, M.lpr, true, grid, smem, s, pdl) == cudaSuccess ? SFL_OK : SFL_ECUDA;
   }
-  static int k_orth(const Plan &pl, const Session &se, int side, cudaStream_t s) {
-    return O::orth(orth_params(pl, se, side), se.grid_vec, se.smem_orth, s) == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  static int k_orth(const Plan &pl, const Session &se, int side, cudaStream_t s, bool pdl = false) {
+    return O::orth(orth_params(pl, se, side), se.grid_vec, se.smem_orth, s, pdl) == cudaSuccess ? SFL_OK
+                                                                                                  : SFL_ECUDA;
   }
 
   using Timer = std::function<int(int, std::function<int()>)>;
@@ -286,18 +297,23 @@ struct Engine {
     return SFL_OK;
   }
 
+  // One step; pdl: kernels after the first depend programmatically on their
+  // predecessor (graph body only), except the sketch.
   static int enqueue_body(const Plan &pl, const Session &se, cudaStream_t s, int use_cond,
-                          cudaGraphConditionalHandle h, const Timer *tm = nullptr) {
+                          cudaGraphConditionalHandle h, const Timer *tm = nullptr, bool pdl = false) {
     int r;
     if ((r = launch_one(kKOrthZ, [&] { return k_orth(pl, se, 0, s); }, tm))) return r;
-    if ((r = launch_one(kKFwd, [&] { return k_spmv(pl, se, kModeFwd, s); }, tm))) return r;
-    if ((r = launch_one(kKOrthW, [&] { return k_orth(pl, se, 1, s); }, tm))) return r;
-    if ((r = launch_one(kKBwd, [&] { return k_spmv(pl, se, kModeBwd, s); }, tm))) return r;
+    if ((r = launch_one(kKFwd, [&] { return k_spmv(pl, se, kModeFwd, s, pdl); }, tm))) return r;
+    if ((r = launch_one(kKOrthW, [&] { return k_orth(pl, se, 1, s, pdl); }, tm))) return r;
+    if ((r = launch_one(kKBwd, [&] { return k_spmv(pl, se, kModeBwd, s, pdl); }, tm))) return r;
     const int gsk = se.key.s * (se.key.method == kSFLSMR ? 2 : 1);
+    // no programmatic edge into the sketch: its small CTAs, launched early,
+    // would pile onto the first SMs the product frees (measured 2x slower)
     if ((r = launch_one(kKSketch, [&] { return k_sketch(se, kSkStep, gsk, s); }, tm))) return r;
     if ((r = launch_one(kKLs, [&] {
-           return launch_ls(ls_params(se, use_cond, h), se.ls_cluster, se.smem_ls, s) == cudaSuccess ? SFL_OK
-                                                                                                       : SFL_ECUDA;
+           return launch_ls(ls_params(se, use_cond, h), se.ls_cluster, se.smem_ls, s, pdl) == cudaSuccess
+                      ? SFL_OK
+                      : SFL_ECUDA;
          }, tm)))
       return r;
     if (se.key.x_hist) {
@@ -317,6 +333,14 @@ struct Engine {
   }
 
   static int build_graph(const Plan &pl, Session &se) {
+    // programmatic edges inside the loop body first; plain edges if refused
+    const int r = build_graph_pdl(pl, se, true);
+    if (r != SFL_ECUDA) return r;
+    cudaGetLastError();
+    return build_graph_pdl(pl, se, false);
+  }
+
+  static int build_graph_pdl(const Plan &pl, Session &se, bool pdl) {
     cudaStream_t cs;
     SFL_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     int r = SFL_OK;
@@ -342,7 +366,7 @@ struct Engine {
       if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         r = SFL_ECUDA; break;
       }
-      r = enqueue_body(pl, se, cs, 1, h);
+      r = enqueue_body(pl, se, cs, 1, h, nullptr, pdl);
       cudaGraph_t body_out = body;
       if (cudaStreamEndCapture(cs, &body_out) != cudaSuccess || r) { r = r ? r : SFL_ECUDA; break; }
       // epilogue
@@ -421,26 +445,29 @@ struct Engine {
       if (occ > 8) occ = 8;
       return std::min(pl.num_sms * occ, kGroup * kMaxGroups);
     };
-    se->grid_spmv_A = grid_of(pl.A.lpr, true, se->smem_A);
-    se->grid_spmv_T = grid_of(pl.T.lpr, true, se->smem_T);
+    se->grid_spmv_A = std::max(2, grid_of(pl.A.lpr, true, se->smem_A));
+    se->grid_spmv_T = std::max(2, grid_of(pl.T.lpr, true, se->smem_T));
     se->grid_init = grid_of(1, false, se->smem_init);
     se->grid_vec = std::min(pl.num_sms * 2, kGroup * kMaxGroups);
     se->smem_orth = orth_smem_bytes(K);
     SFL_CU(O::set_orth_smem(se->smem_orth));
-    se->ls_cluster = ls_cluster_size(S, K);
+    const bool saz_rule = key.method == kSFLSMR && key.stop_rule == SFL_STOP_RULE_RESIDUAL;
+    se->ls_cluster = ls_cluster_size(S, K, saz_rule);
     if (se->ls_cluster < 1) { destroy_session(pl, *se); return SFL_EUNSUPPORTED; }
-    se->smem_ls = ls_smem_bytes(S, K, se->ls_cluster);
-    se->ls_stage = ls_stage_q(S, K, se->ls_cluster);
+    se->smem_ls = ls_smem_bytes(S, K, se->ls_cluster, saz_rule);
+    se->ls_stage = ls_stage_plan(S, K, se->ls_cluster, saz_rule);
     SFL_CU(cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se->smem_ls));
     const int gmax = std::max(std::max(se->grid_spmv_A, se->grid_spmv_T), std::max(se->grid_init, se->grid_vec));
-    const size_t pbytes = sizeof(double) * (size_t)gmax * kPartStride;
+    if (gmax > kPartCap) { destroy_session(pl, *se); return SFL_EUNSUPPORTED; }
+    const size_t pbytes = sizeof(double) * (size_t)kPartCap * kPartStride;
     SA(se->part.b, pbytes);
     SA(se->part.z, pbytes);
     SA(se->part.p, pbytes);
     SA(se->part.w, pbytes);
     SA(se->part.wn, pbytes);
-    // row range of every warp of the two products, balanced by row cost
-    const int WA = se->grid_spmv_A * kWarps, WT = se->grid_spmv_T * kWarps;
+    // row range of every warp of the two products, balanced by row cost; CTA 0
+    // of a product books the step's scalars and runs no rows
+    const int WA = (se->grid_spmv_A - 1) * kWarps, WT = (se->grid_spmv_T - 1) * kWarps;
     SA(se->wrowA, sizeof(int32_t) * (WA + 1));
     SA(se->wrowT, sizeof(int32_t) * (WT + 1));
 #undef SA
