@@ -106,7 +106,10 @@ typedef struct {
  *                  to x_history + (k-1)*n after every step (costs one n x k
  *                  product per step; for verification).
  *  relres_history: optional (may be NULL), device, maxit FP64: the stop-test
- *                  ratio of step k at index k-1. */
+ *                  ratio of step k at index k-1.
+ *  spmm_tile     : batched solves only: RHS per CTA column of the SpMMs (8, 16,
+ *                  32 or 64), or 0 to let the plan time the candidates.  The
+ *                  results are identical for every width. */
 typedef struct {
   int32_t s;
   int32_t zeta;
@@ -120,7 +123,7 @@ typedef struct {
   const double *diag_w;
   double irw_eps;
   int32_t vec_dtype;
-  int32_t reserved0;
+  int32_t spmm_tile;
   double *x_history;
   double *relres_history;
 } sfl_opts;
@@ -243,6 +246,34 @@ int sfl_sketch_apply(uint64_t seed, int32_t s, int32_t zeta, const double *v, in
  * order of summation (relative difference ~1e-16). */
 int sfl_sketch_apply_noalloc(uint64_t seed, int32_t s, int32_t zeta, const double *v, int64_t len,
                              double *sk, sfl_stream stream);
+
+/* ---- batched solves ------------------------------------------------------ */
+
+/* sFLSQR (Algorithm 1) for nrhs independent right-hand sides through the
+ * plan's operator, run together: every step does one SpMM with A and one with
+ * A^T (or B) for all right-hand sides still running, and a right-hand side
+ * stops on its own discrepancy test (eq. discrP: relative sketched residual
+ * below eta * noise_norms[r] / ||b_r||), after which it is masked out.
+ *   B           device, FP64, column-major m x nrhs (column r = b_r)
+ *   noise_norms host, nrhs values (<= 0: that column runs to opts->maxit)
+ *   opts        as for sflsqr_solve; opts->noise_norm is ignored; precond
+ *               must be identity or diagonal (reweighting is not batched)
+ *   X           device, FP64, column-major n x nrhs (output)
+ *   infos       host, nrhs entries (may be NULL: then the call does not wait)
+ * 1 <= nrhs <= 256.  Vectors are kept in the plan's vector precision (FP64 for
+ * an FP64 plan, FP32 otherwise); the small problems are FP64.  The plan keeps
+ * every basis vector of the solve: (2 maxit + 2) * max(m, n) * ld vectors of
+ * that precision (ld = next power of two >= max(nrhs, 4)) plus O(nrhs * s *
+ * maxit) doubles; SFL_ENOMEM if they do not fit.  Returns SFL_EINVAL for bad
+ * arguments, SFL_EUNSUPPORTED for the reweighting preconditioner or a full
+ * window. */
+int sflsqr_solve_batched(sfl_plan *plan, int32_t nrhs, const double *B, const double *noise_norms,
+                         const sfl_opts *opts, double *X, sfl_info *infos, sfl_stream stream);
+
+/* RHS tile width the SpMM tuner picked for the plan's most recent batch
+ * session: which = 0 for A, 1 for A^T / B.  0 if the plan has run no batch,
+ * -1 for bad arguments.  Results never depend on it. */
+int sfl_batched_tile(const sfl_plan *plan, int32_t which);
 
 /* ---- misc --------------------------------------------------------------- */
 

@@ -35,7 +35,7 @@ class Opts(ctypes.Structure):
                 ("window", ctypes.c_int32), ("maxit", ctypes.c_int32), ("noise_norm", ctypes.c_double),
                 ("eta", ctypes.c_double), ("precond", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("diag_w", ctypes.c_void_p), ("irw_eps", ctypes.c_double), ("vec_dtype", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("x_history", ctypes.c_void_p), ("relres_history", ctypes.c_void_p)]
+                ("spmm_tile", ctypes.c_int32), ("x_history", ctypes.c_void_p), ("relres_history", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -76,6 +76,8 @@ _SIGNATURES = {
     "sfl_sketch_apply": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P, _P]),
     "sfl_sketch_apply_noalloc": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64,
                                                 _P, _P]),
+    "sflsqr_solve_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.POINTER(Opts), _P, _P, _P]),
+    "sfl_batched_tile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "sfl_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sfl_last_cuda_error": (ctypes.c_char_p, []),
 }

@@ -174,6 +174,42 @@ class Plan:
         return x, SolveInfo(info.iters, info.status, info.relres, info.tol)
 
 
+def _batched_opts(plan, s, zeta, seed, window, maxit, eta, precond, diag_w, spmm_tile=0):
+    dw = diag_w.to(device=plan.device, dtype=torch.float64).contiguous() if diag_w is not None else None
+    vec = "f64" if plan.value_dtype == "f64" else "f32"
+    o = plan._opts(s, zeta, seed, window, maxit, 0.0, eta, precond, "residual", dw, 0.0, vec, None, None)
+    o.spmm_tile = int(spmm_tile)
+    return o, dw
+
+
+def solve_batched(plan: Plan, B: torch.Tensor, noise_norms, *, s: int, zeta: int = 8, seed: int = 0, window: int = 2,
+                  maxit: int = 100, eta: float = 1.01, precond: str = "identity", diag_w: torch.Tensor | None = None,
+                  spmm_tile: int = 0, out: torch.Tensor | None = None, sync: bool = True):
+    """Batched sFLSQR: B is (nrhs, m) (row r = b_r), noise_norms has nrhs entries.
+    spmm_tile: RHS per CTA column of the SpMMs (8/16/32/64) or 0 = tuned.
+    Returns (X (nrhs, n), [SolveInfo per RHS] or None when sync=False)."""
+    dev = plan.device
+    B = B.to(device=dev, dtype=torch.float64).contiguous()
+    R = int(B.shape[0])
+    X = out if out is not None else torch.empty((R, plan.n), dtype=torch.float64, device=dev)
+    noise = np.ascontiguousarray(np.broadcast_to(np.asarray(noise_norms, dtype=np.float64), (R,)))
+    o, dw = _batched_opts(plan, s, zeta, seed, window, maxit, eta, precond, diag_w, spmm_tile)
+    infos = (N.Info * R)() if sync else None
+    with torch.cuda.device(dev):
+        st = plan.lib.sflsqr_solve_batched(plan.handle, R, _ptr(B), noise.ctypes.data_as(ctypes.c_void_p),
+                                           ctypes.byref(o), _ptr(X), infos, _stream())
+    N.check(st, "sflsqr_solve_batched")
+    del dw
+    if not sync:
+        return X, None
+    return X, [SolveInfo(i.iters, i.status, i.relres, i.tol) for i in infos]
+
+
+def batched_tiles(plan: Plan):
+    """(A tile, A^T/B tile) the SpMM tuner picked for the last batch session."""
+    return plan.lib.sfl_batched_tile(plan.handle, 0), plan.lib.sfl_batched_tile(plan.handle, 1)
+
+
 def sflsqr(plan: Plan, b, **kw):
     """Algorithm 1 (sFLSQR) on the GPU; see Plan.solve."""
     return plan.solve("sflsqr", b, **kw)

@@ -62,6 +62,11 @@ struct Session {
   uint64_t bytes = 0;
 };
 
+// A batched-solve session (typed; freed with its plan).
+struct BatchSessionBase {
+  virtual ~BatchSessionBase() = default;
+};
+
 struct Plan {
   int device = 0;
   int num_sms = 0;
@@ -71,6 +76,7 @@ struct Plan {
   uint64_t bytes = 0, cap = 0;
   std::vector<void *> allocs;
   std::vector<std::unique_ptr<Session>> sessions;
+  std::vector<std::unique_ptr<BatchSessionBase>> batches;
   // scratch for sfl_plan_apply
   void *apply_x = nullptr, *apply_y = nullptr;
   RedScratch apply_red{};
@@ -112,8 +118,23 @@ struct Ops {
   static cudaError_t set_orth_smem(size_t smem);
 };
 
-cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s, bool pdl = false);
-int ls_cluster_size(int s, int maxit, bool saz);
+cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s, bool pdl = false, int nprob = 1);
+int ls_cluster_size(int s, int maxit, bool saz, int max_cluster = 16);
+cudaError_t ls_allow_max_smem();
+int wait_stream(cudaStream_t s);
+
+// Row range of each of W warps, balanced by 4 * ceil(len / unit) + 1 per row.
+int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s);
+
+// Row-major sparse-sign table (rows of S with their entries column | sign bit).
+struct SketchTableTmp {
+  uint32_t *kin = nullptr, *vin = nullptr, *kout = nullptr;
+  void *cub = nullptr;
+  size_t cub_bytes = 0;
+};
+int build_sketch_table(uint64_t seed, int s, int zeta, int64_t ncols, int32_t *rowptr, uint32_t *ent,
+                       SketchTableTmp &t, int *err, cudaStream_t st);
+size_t sketch_sort_bytes(int64_t nent, int s);
 size_t ls_smem_bytes(int s, int maxit, int cluster, bool saz);
 int ls_stage_plan(int s, int maxit, int cluster, bool saz);
 

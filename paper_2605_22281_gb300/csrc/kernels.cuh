@@ -795,6 +795,9 @@ struct LsParams {
   double *relres_hist;
   cudaGraphConditionalHandle cond;
   int use_cond;
+  // several independent problems (one cluster each, problem = cluster index):
+  // st is an array of states and every buffer above advances by its stride
+  int64_t bQ, bRinv, by, be, bSAZ, bSAtW, bHband, bvec, bhist;   // per-problem strides (0: one problem)
 };
 
 constexpr int kMaxCluster = 16;
@@ -821,10 +824,24 @@ __host__ __device__ inline size_t ls_smem_doubles(int s, int maxit, int cl, int 
 // reductions); partial vectors are exchanged through distributed shared
 // memory and every CTA adds the ranks' values as the same fixed tree, so all
 // CTAs hold bitwise identical totals and take the same branches.
-static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams p) {
+static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // this cluster's problem
+  const int64_t prob = blockIdx.x / CL;
+  LsParams p = pin;
+  p.st += prob;
+  p.Q += prob * p.bQ;
+  p.Rinv += prob * p.bRinv;
+  p.y += prob * p.by;
+  p.e += prob * p.be;
+  p.SAZ += prob * p.bSAZ;
+  if (p.SAtW) p.SAtW += prob * p.bSAtW;
+  if (p.Hband) p.Hband += prob * p.bHband;
+  if (p.sbm) p.sbm += prob * p.bvec;
+  p.rhs += prob * p.bvec;
+  if (p.relres_hist) p.relres_hist += prob * p.bhist;
   SolveState *st = p.st;
   griddep_wait();
   griddep_launch_dependents();

@@ -15,7 +15,7 @@ namespace sfl {
 static constexpr double kHostWaitSeconds = 1800.0;
 
 // Host wait with a wall-clock limit (cudaEventQuery polling).
-static int wait_stream(cudaStream_t s) {
+int wait_stream(cudaStream_t s) {
   cudaEvent_t ev;
   SFL_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   cudaError_t e = cudaEventRecord(ev, s);
@@ -70,15 +70,37 @@ size_t ls_smem_bytes(int s, int maxit, int cluster, bool saz) {
   return sizeof(double) * ls_smem_doubles(s, maxit, cluster, st & 1, (st >> 1) & 1);
 }
 
-int ls_cluster_size(int s, int maxit, bool saz) {
-  cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+// The dynamic shared memory limit of a kernel is one attribute shared by all
+// sessions: the small-LS kernel is allowed the device maximum once, so no
+// session can lower another's limit.
+static int ls_max_dynamic_smem() {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, ls_step_kernel) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return optin - (int)fa.sharedSizeBytes;   // the limit covers static plus dynamic shared memory
+}
+
+cudaError_t ls_allow_max_smem() {
+  const int lim = ls_max_dynamic_smem();
+  if (lim <= 0) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+int ls_cluster_size(int s, int maxit, bool saz, int max_cluster) {
+  if (ls_allow_max_smem() != cudaSuccess) { cudaGetLastError(); return 0; }
+  const int lim = ls_max_dynamic_smem();
   for (int cl : {16, 8, 4, 2, 1}) {
+    if (cl > max_cluster) continue;
     static_assert(kMaxCluster == 16, "largest cluster tried");
     const size_t smem = ls_smem_bytes(s, maxit, cl, saz);
-    if (cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
+    if (smem > (size_t)lim) continue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cl);
     cfg.blockDim = dim3(kThreads);
@@ -97,9 +119,9 @@ int ls_cluster_size(int s, int maxit, bool saz) {
   return 0;
 }
 
-cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s, bool pdl) {
+cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t s, bool pdl, int nprob) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cluster);
+  cfg.gridDim = dim3(cluster * nprob);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -116,11 +138,10 @@ cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t 
 }
 
 // Row range of each of W warps over the rows of M, balanced by row cost
-// (cost per row, exclusive scan, binary search per warp).  Temporaries are
-// freed before returning; the caller synchronises the stream.
-static int balance_rows(const StoredCsr &M, int P, int W, int32_t *wrow, cudaStream_t s) {
+// (4 * ceil(len / unit) + 1 per row, exclusive scan, binary search per warp).
+// Temporaries are freed before returning; the stream is synchronised.
+int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s) {
   const int64_t rows = M.rows;
-  const int unit = 4 * M.lpr * P;
   int64_t *cost = nullptr, *prefix = nullptr;
   void *tst = nullptr;
   size_t tb = 0;
@@ -153,13 +174,7 @@ static int balance_rows(const StoredCsr &M, int P, int W, int32_t *wrow, cudaStr
 // Row-major sparse-sign table for ncols columns: pairs (row, column|sign) in
 // column-major draw order, stably sorted by row, so every row lists its
 // columns in increasing order (deterministic).
-struct SketchTableTmp {
-  uint32_t *kin = nullptr, *vin = nullptr, *kout = nullptr;
-  void *cub = nullptr;
-  size_t cub_bytes = 0;
-};
-
-static int build_sketch_table(uint64_t seed, int s, int zeta, int64_t ncols, int32_t *rowptr, uint32_t *ent,
+int build_sketch_table(uint64_t seed, int s, int zeta, int64_t ncols, int32_t *rowptr, uint32_t *ent,
                               SketchTableTmp &t, int *err, cudaStream_t st) {
   const int64_t nent = ncols * zeta;
   sketch_pairs_kernel<<<(unsigned)((ncols + 255) / 256), 256, 0, st>>>(seed, s, zeta, ncols, t.kin, t.vin, err);
@@ -175,7 +190,7 @@ static int build_sketch_table(uint64_t seed, int s, int zeta, int64_t ncols, int
   return SFL_OK;
 }
 
-static size_t sketch_sort_bytes(int64_t nent, int s) {
+size_t sketch_sort_bytes(int64_t nent, int s) {
   int bits = 1;
   while ((1 << bits) < s) ++bits;
   size_t need = 0;
@@ -450,13 +465,13 @@ struct Engine {
     se->grid_init = grid_of(1, false, se->smem_init);
     se->grid_vec = std::min(pl.num_sms * 2, kGroup * kMaxGroups);
     se->smem_orth = orth_smem_bytes(K);
-    SFL_CU(O::set_orth_smem(se->smem_orth));
+    SFL_CU(O::set_orth_smem(orth_smem_bytes(kMaxIt)));   // one limit for every session
     const bool saz_rule = key.method == kSFLSMR && key.stop_rule == SFL_STOP_RULE_RESIDUAL;
     se->ls_cluster = ls_cluster_size(S, K, saz_rule);
     if (se->ls_cluster < 1) { destroy_session(pl, *se); return SFL_EUNSUPPORTED; }
     se->smem_ls = ls_smem_bytes(S, K, se->ls_cluster, saz_rule);
     se->ls_stage = ls_stage_plan(S, K, se->ls_cluster, saz_rule);
-    SFL_CU(cudaFuncSetAttribute(ls_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se->smem_ls));
+    SFL_CU(ls_allow_max_smem());
     const int gmax = std::max(std::max(se->grid_spmv_A, se->grid_spmv_T), std::max(se->grid_init, se->grid_vec));
     if (gmax > kPartCap) { destroy_session(pl, *se); return SFL_EUNSUPPORTED; }
     const size_t pbytes = sizeof(double) * (size_t)kPartCap * kPartStride;
@@ -472,7 +487,8 @@ struct Engine {
     SA(se->wrowT, sizeof(int32_t) * (WT + 1));
 #undef SA
     const int P = load_width(pl.vdt);
-    if ((r = balance_rows(pl.A, P, WA, se->wrowA, s)) || (r = balance_rows(pl.T, P, WT, se->wrowT, s))) {
+    if ((r = balance_rows(pl.A, 4 * pl.A.lpr * P, WA, se->wrowA, s)) ||
+        (r = balance_rows(pl.T, 4 * pl.T.lpr * P, WT, se->wrowT, s))) {
       destroy_session(pl, *se);
       return r;
     }
@@ -707,6 +723,7 @@ int sfl_plan_destroy(sfl_plan *plan) {
   cudaDeviceSynchronize();
   for (auto &se : pl.sessions) destroy_session(pl, *se);
   pl.sessions.clear();
+  pl.batches.clear();
   for (void *p : pl.allocs) cudaFree(p);
   pl.allocs.clear();
   delete plan;

@@ -1,0 +1,182 @@
+"""GPU parity of the batched sFLSQR (one SpMM per product for all right-hand
+sides, per-RHS discrepancy masks) against the FP64 oracle run per column.
+
+Bars: FP64 final iterates within the per-iteration bar of the single solve
+(relative 1e-10, widened only by the small problem's conditioning); stop
+iterations equal unless the stop ratio is within 1e-8 of the threshold;
+bitwise-identical results for every SpMM tile width; a right-hand side's
+result independent of the others in the batch.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+import torch  # noqa: E402
+
+from paper_2605_22281_gb300 import api as G  # noqa: E402
+
+
+@pytest.fixture(autouse=True)
+def _needs_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("GPU test selected but no CUDA device is available")
+
+
+U = np.finfo(np.float64).eps / 2
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def batch_problem(N=64, n_angles=60, R=5, seed=100, levels=None):
+    """R sinograms of ellipse phantoms through one 64x64 Siddon operator, noise
+    levels spread over [0.5%, 5%] so the columns stop at different steps."""
+    A = wl.siddon_projector(N, n_angles, wl.detector_bins(N))
+    levels = levels if levels is not None else np.geomspace(0.005, 0.05, R)
+    bs, en, xs = [], [], []
+    for j in range(R):
+        rng = np.random.default_rng(seed + j)
+        x = wl.ellipse_phantom(N, rng)
+        b, e = wl.add_noise(A.matvec(x), float(levels[j]), rng)
+        bs.append(b); en.append(e); xs.append(x)
+    return A, np.stack(bs), np.array(en), np.stack(xs)
+
+
+@pytest.fixture(scope="module")
+def ct64_batch():
+    A, B, en, X = batch_problem()
+    return A, B, en, X, G.Plan(A)
+
+
+def oracle_column(A, b, en, s, zeta, seed, ell, maxit, eta=1.01, tau=None):
+    S = O.SparseSign(seed, s, zeta, A.shape[0])
+    tol = O.discrepancy_tol(eta, en, np.linalg.norm(b)) if en > 0 else 0.0
+    r = O.sflsqr(A, b, S, maxit=maxit, tol=tol, ell=ell, tau=tau, keep_basis=True)
+    M = S.mat @ (A @ r.Z)
+    return r, tol, np.linalg.cond(M)
+
+
+def check_column(r, tol, cond, x_gpu, info):
+    if tol > 0 and abs(r.relres[-1] / tol - 1) <= 1e-8:
+        pytest.skip("stop ratio within 1e-8 of the threshold")
+    assert info.iters == r.iters, (info.iters, r.iters)
+    assert info.status == r.status
+    bar = max(1e-10, 32 * U * cond)
+    e = rel(x_gpu, r.x)
+    assert e <= bar, f"rel err {e:.3e} (bar {bar:.1e}, cond {cond:.1e})"
+
+
+def test_batched_columns_match_oracle(ct64_batch):
+    A, B, en, _, plan = ct64_batch
+    X, infos = G.solve_batched(plan, dev(B), en, s=200, zeta=8, seed=42, window=2, maxit=100)
+    Xh = X.cpu().numpy()
+    iters = [i.iters for i in infos]
+    assert len(set(iters)) > 1, "the columns should stop at different steps"
+    for j in range(B.shape[0]):
+        r, tol, cond = oracle_column(A.scipy(), B[j], en[j], 200, 8, 42, 2, 100)
+        check_column(r, tol, cond, Xh[j], infos[j])
+        assert abs(infos[j].tol - tol) <= 1e-15 * tol
+
+
+def test_batched_equals_single_solves(ct64_batch):
+    A, B, en, _, plan = ct64_batch
+    X, infos = G.solve_batched(plan, dev(B), en, s=200, zeta=8, seed=42, window=2, maxit=100)
+    for j in range(B.shape[0]):
+        x1, i1, _ = plan.solve("sflsqr", dev(B[j]), s=200, zeta=8, seed=42, window=2, maxit=100,
+                               noise_norm=en[j], eta=1.01)
+        assert i1.iters == infos[j].iters
+        assert rel(X[j].cpu().numpy(), x1.cpu().numpy()) <= 1e-10
+
+
+@pytest.mark.parametrize("R", [40, 64])
+def test_spmm_tile_width_never_changes_a_bit(R):
+    A, B, en, _ = batch_problem(R=R, seed=300)
+    plan = G.Plan(A)
+    outs = {}
+    for T in (8, 16, 32, 64):
+        X, infos = G.solve_batched(plan, dev(B), en, s=120, zeta=8, seed=5, window=2, maxit=40, spmm_tile=T)
+        outs[T] = (X.cpu().numpy(), [i.iters for i in infos])
+    for T in (16, 32, 64):
+        assert outs[T][1] == outs[8][1]
+        assert np.array_equal(outs[T][0], outs[8][0]), T
+    X, _ = G.solve_batched(plan, dev(B), en, s=120, zeta=8, seed=5, window=2, maxit=40)
+    assert np.array_equal(X.cpu().numpy(), outs[8][0])
+    ta, tt = G.batched_tiles(plan)
+    assert ta in (8, 16, 32, 64) and tt in (8, 16, 32, 64)
+    plan.close()
+
+
+def test_masked_column_is_independent_of_the_batch(ct64_batch):
+    """A column alone and inside a batch: the same steps and x up to the
+    grouping of the per-CTA partial sums."""
+    A, B, en, _, plan = ct64_batch
+    X, infos = G.solve_batched(plan, dev(B), en, s=200, zeta=8, seed=42, window=2, maxit=100)
+    for j in (0, B.shape[0] - 1):
+        X1, i1 = G.solve_batched(plan, dev(B[j:j + 1]), en[j:j + 1], s=200, zeta=8, seed=42, window=2, maxit=100)
+        assert i1[0].iters == infos[j].iters
+        assert rel(X1[0].cpu().numpy(), X[j].cpu().numpy()) <= 1e-12
+
+
+def test_zero_column_breaks_down_alone(ct64_batch):
+    A, B, en, _, plan = ct64_batch
+    B2 = B.copy()
+    B2[2] = 0.0
+    X, infos = G.solve_batched(plan, dev(B2), en, s=200, zeta=8, seed=42, window=2, maxit=100)
+    assert infos[2].status == O.STOP_BREAKDOWN and infos[2].iters == 0
+    assert np.all(X[2].cpu().numpy() == 0.0)
+    X0, i0 = G.solve_batched(plan, dev(B), en, s=200, zeta=8, seed=42, window=2, maxit=100)
+    for j in (0, 1, 3, 4):
+        assert infos[j].iters == i0[j].iters
+        assert rel(X[j].cpu().numpy(), X0[j].cpu().numpy()) <= 1e-12
+
+
+def test_batched_fixed_diagonal_operator(ct64_batch):
+    A, B, en, _, plan = ct64_batch
+    n = A.shape[1]
+    w = np.random.default_rng(47).uniform(0.5, 1.5, n)
+    X, infos = G.solve_batched(plan, dev(B[:3]), [0.0] * 3, s=61, zeta=8, seed=46, window=2, maxit=20,
+                               precond="diag", diag_w=dev(w))
+    for j in range(3):
+        r, tol, cond = oracle_column(A.scipy(), B[j], 0.0, 61, 8, 46, 2, 20, tau=O.FixedDiag(w))
+        check_column(r, tol, cond, X[j].cpu().numpy(), infos[j])
+
+
+def test_batched_fp32_error_against_fp64_oracle(ct64_batch):
+    """FP32 values and vectors (FP64 small problems): reconstruction error
+    against the FP64 oracle's x, stated here as the bar."""
+    A, B, en, Xtrue, _ = ct64_batch
+    plan32 = G.Plan(A, value_dtype="f32")
+    X, infos = G.solve_batched(plan32, dev(B), en, s=200, zeta=8, seed=42, window=2, maxit=100)
+    for j in range(B.shape[0]):
+        r, tol, cond = oracle_column(A.scipy(), B[j], en[j], 200, 8, 42, 2, 100)
+        assert abs(infos[j].iters - r.iters) <= 1
+        if infos[j].iters == r.iters:
+            assert rel(X[j].cpu().numpy(), r.x) <= 1e-4
+        # reconstruction error within 1% (relative) of the FP64 solve's
+        e32 = rel(X[j].cpu().numpy(), Xtrue[j])
+        e64 = rel(r.x, Xtrue[j])
+        assert abs(e32 - e64) <= 0.01 * e64
+    plan32.close()
+
+
+def test_batched_invalid_inputs(ct64_batch):
+    A, B, en, _, plan = ct64_batch
+    b = dev(B)
+    with pytest.raises(G.N.SflError):
+        G.solve_batched(plan, b, en, s=200, zeta=8, seed=42, window=2, maxit=100, precond="reweight")
+    with pytest.raises(G.N.SflError):
+        G.solve_batched(plan, b, en, s=50, zeta=8, seed=42, window=2, maxit=100)       # s < maxit + 1
+    with pytest.raises(G.N.SflError):
+        G.solve_batched(plan, b, en, s=200, zeta=8, seed=42, window=2, maxit=100, spmm_tile=12)
+    with pytest.raises(G.N.SflError):
+        G.solve_batched(plan, b, en, s=200, zeta=8, seed=42, window=-1, maxit=100)
