@@ -14,6 +14,8 @@
 
 namespace sfl {
 
+constexpr int kBMaxRowCtas = 2048;
+
 struct BatchKey {
   int R, s, zeta, ell, maxit, precond, keep_what, tile;   // tile: forced SpMM width, 0 = tuned
   bool operator==(const BatchKey &o) const {
@@ -251,7 +253,16 @@ struct BEngine {
     b.keep_what = key.keep_what;
     b.isz = 1.0 / std::sqrt((double)key.zeta);
     se->G_orth = pl.num_sms * 2;
-    se->G_rows = pl.num_sms * 2;
+    // row CTAs: as many as stay resident for every tile width (the records and
+    // the row partition depend on it, so it is one number per session)
+    int occ = 8;
+    for (auto f : {(const void *)bspmm_kernel<VT, XT, 8>, (const void *)bspmm_kernel<VT, XT, 16>,
+                   (const void *)bspmm_kernel<VT, XT, 32>, (const void *)bspmm_kernel<VT, XT, 64>}) {
+      int nb = 0;
+      SFL_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, 0));
+      occ = std::min(occ, std::max(nb, 1));
+    }
+    se->G_rows = std::min(pl.num_sms * occ, kBMaxRowCtas);
     se->bp.rcap = std::max(se->G_orth, se->G_rows);
     int r;
 #define BA(ptr, bytes) if ((r = alloc(*se, (void **)&(ptr), (bytes)))) return r;
@@ -288,15 +299,15 @@ struct BEngine {
     BA(se->kout, sizeof(uint32_t) * nent);
     se->cub_bytes = sketch_sort_bytes(nent, Sk) + 256;
     BA(se->cub, se->cub_bytes);
-    BA(se->wrowA, sizeof(int32_t) * (se->G_rows * kWarps + 1));
-    BA(se->wrowT, sizeof(int32_t) * (se->G_rows * kWarps + 1));
+    BA(se->wrowA, sizeof(int32_t) * (se->G_rows + 1));
+    BA(se->wrowT, sizeof(int32_t) * (se->G_rows + 1));
 #undef BA
     b.dw = se->dwbuf;
     b.skrow = se->skrow; b.skent = se->skent;
-    // SpMM rows per warp: one warp per row at a time, so a row costs its chunks
+    // SpMM rows per CTA (its warps interleave them): a row costs its chunks
     const int P = load_width(pl.vdt);
-    if ((r = balance_rows(pl.A, P, se->G_rows * kWarps, se->wrowA, s))) return r;
-    if ((r = balance_rows(pl.T, P, se->G_rows * kWarps, se->wrowT, s))) return r;
+    if ((r = balance_rows(pl.A, P, se->G_rows, se->wrowA, s))) return r;
+    if ((r = balance_rows(pl.T, P, se->G_rows, se->wrowT, s))) return r;
     // small problems: one cluster per RHS, as many SMs each as the batch leaves
     int maxc = 1;
     while (maxc * 2 * R <= pl.num_sms && maxc < 16) maxc <<= 1;

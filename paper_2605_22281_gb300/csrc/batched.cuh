@@ -271,7 +271,7 @@ struct BSpmmArgs {
   const int32_t *rowptr, *col;
   const void *val;
   int64_t rows;
-  const int32_t *wrow;       // row range of every warp (gridDim.x * kWarps + 1)
+  const int32_t *crow;       // row range of every CTA (gridDim.x + 1), balanced by cost
   int mode;
 };
 
@@ -280,24 +280,28 @@ template <> struct XT2<double> { using T = double2; };
 template <> struct XT2<float> { using T = float2; };
 
 // Y[row][r] = sum_e val[e] * X[col[e]][r] for the RHS of tile blockIdx.y (T of
-// them).  A warp owns one row at a time; lanes split the tile's RHS (T >= 32:
-// T/32 per lane) or, for T < 32, 32/T lane groups split the entries.  Every
+// them).  A CTA owns a contiguous range of rows and its warps take every
+// kWarps-th row, so they work on adjacent rows (neighbouring rays, or pixels)
+// at the same time and share the gathered lines in L1.  A warp owns one row at
+// a time; lanes split the tile's RHS (T >= 32: T/32 per lane) or, for T < 32,
+// 32/T lane groups split the entries.  Every
 // (row, RHS) sum is ((s0 + s1) + (s2 + s3)) with s_j the in-order sum of the
 // entries e = j (mod 4) of the row, whatever T is, so the tile width chosen by
 // the tuner never changes a result bit.  Window dots <v_a, y> and ||y||^2 per
 // RHS go to the records.
 template <typename VT, typename XT, int T>
-__global__ void __launch_bounds__(kThreads) bspmm_kernel(BParams<XT> p, BSpmmArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmmArgs a) {
   static_assert(T == 8 || T == 16 || T == 32 || T == 64, "tile widths");
   constexpr int PL = LoadWidth<VT>::P;
   constexpr int RPL = T >= 32 ? T / 32 : 1;       // RHS per lane
   constexpr int NG = T >= 32 ? 1 : 32 / T;        // lane groups splitting the entries
   using ACC = typename AccT<XT>::T;
-  __shared__ double scr[kWarps][kMaxWindow + 2][T];
+  __shared__ double scr[kWarps][T];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = *p.kstep + 1;
   const int tile0 = blockIdx.y * T;
   const int g = lane / (32 / NG), gl = lane % (32 / NG);   // group, lane within group
+  const bool owner = NG == 1 || g == 0;                    // lanes that hold the row results
   // this lane's RHS and their activity
   int rr[RPL];
   bool act[RPL];
@@ -326,15 +330,12 @@ __global__ void __launch_bounds__(kThreads) bspmm_kernel(BParams<XT> p, BSpmmArg
     win = p.P;
   }
   const int64_t wslot = (a.mode == kBSpmmFwd ? p.m : p.n) * p.ld;
-  double acc[kMaxWindow + 2][RPL];
+  const int64_t r0 = a.crow[blockIdx.x], r1 = a.crow[blockIdx.x + 1];
+  double nrm[RPL];
 #pragma unroll
-  for (int q = 0; q < kMaxWindow + 2; ++q)
-#pragma unroll
-    for (int j = 0; j < RPL; ++j) acc[q][j] = 0.0;
-  const int gw = blockIdx.x * kWarps + warp;
-  const int64_t r0 = a.wrow[gw], r1 = a.wrow[gw + 1];
+  for (int q = 0; q < RPL; ++q) nrm[q] = 0.0;
   if (tile_any) {
-    for (int64_t row = r0; row < r1; ++row) {
+    for (int64_t row = r0 + warp; row < r1; row += kWarps) {
       const int beg = a.rowptr[row], end = a.rowptr[row + 1];
       ACC s[4][RPL];
 #pragma unroll
@@ -376,35 +377,46 @@ __global__ void __launch_bounds__(kThreads) bspmm_kernel(BParams<XT> p, BSpmmArg
           s3 = __shfl_xor_sync(0xffffffffu, s[3][q], 24);
         }
         const ACC tot = (s0 + s1) + (s2 + s3);
-        if ((NG == 1 || g == 0) && act[q]) {
-          const size_t ei = (size_t)row * p.ld + rr[q];
-          y[ei] = (XT)tot;
+        if (owner && act[q]) {
+          y[(size_t)row * p.ld + rr[q]] = (XT)tot;
           const double yd = (double)(XT)tot;
-          acc[0][q] += yd * yd;
-#pragma unroll
-          for (int w = 0; w < kMaxWindow + 1; ++w)
-            if (w < nd) acc[1 + w][q] += yd * (double)win[(size_t)(lo + w - 1) * wslot + ei];
+          nrm[q] += yd * yd;
         }
       }
     }
   }
-  // records: per RHS of the tile, warps added in order
-  const int nq = 1 + nd;
+  // records: ||y||^2, then <v_w, y> one window vector at a time over the
+  // warp's own rows (each lane re-reads the outputs it stored); per RHS of the
+  // tile the warps are added in order
+  auto store = [&](const double (&v)[RPL], int q) {
 #pragma unroll
-  for (int q = 0; q < RPL; ++q)
-    if (NG == 1 || g == 0) {
-      const int slot = T >= 32 ? RPL * lane + q : gl;
-#pragma unroll
-      for (int w = 0; w < kMaxWindow + 2; ++w)
-        if (w < nq) scr[warp][w][slot] = acc[w][q];
+    for (int j = 0; j < RPL; ++j)
+      if (owner) scr[warp][T >= 32 ? RPL * lane + j : gl] = v[j];
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += kThreads) {
+      const int r = tile0 + t;
+      if (r >= p.R) continue;
+      double acc = 0.0;
+      for (int w = 0; w < kWarps; ++w) acc += scr[w][t];
+      b_rec(p.rec, p.R, p.rcap, q, r)[blockIdx.x] = acc;
     }
-  __syncthreads();
-  for (int t = threadIdx.x; t < nq * T; t += kThreads) {
-    const int w = t / T, slot = t % T, r = tile0 + slot;
-    if (r >= p.R) continue;
-    double v = 0.0;
-    for (int q = 0; q < kWarps; ++q) v += scr[q][w][slot];
-    b_rec(p.rec, p.R, p.rcap, w, r)[blockIdx.x] = v;
+    __syncthreads();
+  };
+  store(nrm, 0);
+  for (int w = 0; w < nd; ++w) {
+    const XT *wv = win + (size_t)(lo + w - 1) * wslot;
+    double d[RPL];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) d[q] = 0.0;
+    if (tile_any && owner)
+      for (int64_t row = r0 + warp; row < r1; row += kWarps)
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+          if (act[q]) {
+            const size_t ei = (size_t)row * p.ld + rr[q];
+            d[q] += (double)y[ei] * (double)wv[ei];
+          }
+    store(d, 1 + w);
   }
 }
 
