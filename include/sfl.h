@@ -275,6 +275,33 @@ int sflsqr_solve_batched(sfl_plan *plan, int32_t nrhs, const double *B, const do
  * -1 for bad arguments.  Results never depend on it. */
 int sfl_batched_tile(const sfl_plan *plan, int32_t which);
 
+/* ---- differentiation ------------------------------------------------------ */
+
+/* Fixed-k batched sFLSQR for differentiation: exactly opts->maxit steps of
+ * Algorithm 1 (no discrepancy test; a right-hand side stops early only on a
+ * breakdown), flexible operator identity or z = diag(diag_w) p, window <= 3.
+ * Arguments as sflsqr_solve_batched without the noise levels.  The plan keeps
+ * the whole forward state (every basis vector, A z_j, the coefficients and the
+ * small QR) for sflsqr_adjoint_batched until its next batched call with other
+ * sizes, or another fixed-k call. */
+int sflsqr_fixed_batched(sfl_plan *plan, int32_t nrhs, const double *B, const sfl_opts *opts, double *X,
+                         sfl_info *infos, sfl_stream stream);
+
+/* Reverse-mode adjoint of the plan's latest sflsqr_fixed_batched call: for a
+ * loss L(X), given Xbar = dL/dX (device, FP64, column-major n x nrhs) it writes
+ * Bbar = dL/dB (device, FP64, column-major m x nrhs) and, if dbar is not NULL,
+ * dbar = dL/d(diag_w) summed over the right-hand sides (device, FP64, n; at
+ * diag_w = 1 for an identity operator).  The derivative is that of the exact
+ * fixed-k map (modified Gram-Schmidt windows, normalisations, sketched QR
+ * solve, x = Z y), evaluated at the kept forward state.  SFL_EINVAL when the
+ * plan keeps no such forward or nrhs differs from it. */
+int sflsqr_adjoint_batched(sfl_plan *plan, int32_t nrhs, const double *Xbar, double *Bbar, double *dbar,
+                           sfl_stream stream);
+
+/* Number of sflsqr_fixed_batched calls made on the plan (a forward's identity
+ * for the adjoint that must follow it); -1 for a NULL plan. */
+int64_t sfl_fixed_calls(const sfl_plan *plan);
+
 /* ---- misc --------------------------------------------------------------- */
 
 const char *sfl_error_string(int status);

@@ -10,6 +10,8 @@ Modules:
             orthogonalization (eq. (FGK)), Householder small least squares,
             identity / fixed-diagonal / reweighting flexible operators, and the
             discrepancy stop of eq. (discrP).
+  adjoint - fixed-k sFLSQR with tau = diag(d) in plain PyTorch CPU FP64 ops,
+            differentiated by autograd (imported on demand: `oracle.adjoint`).
 """
 from .sketch import (DenseSketch, IdentitySketch, SparseSign, draw_hash, gaussian, sparse_sign_column,
                      sparse_sign_rows, splitmix64_stream)

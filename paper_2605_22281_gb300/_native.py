@@ -78,6 +78,9 @@ _SIGNATURES = {
                                                 _P, _P]),
     "sflsqr_solve_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.POINTER(Opts), _P, _P, _P]),
     "sfl_batched_tile": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "sflsqr_fixed_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(Opts), _P, _P, _P]),
+    "sflsqr_adjoint_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
+    "sfl_fixed_calls": (ctypes.c_int64, [_P]),
     "sfl_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sfl_last_cuda_error": (ctypes.c_char_p, []),
 }

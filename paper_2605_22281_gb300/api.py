@@ -210,6 +210,64 @@ def batched_tiles(plan: Plan):
     return plan.lib.sfl_batched_tile(plan.handle, 0), plan.lib.sfl_batched_tile(plan.handle, 1)
 
 
+def fixed_batched(plan: Plan, B: torch.Tensor, d: torch.Tensor | None = None, *, s: int, zeta: int = 8, seed: int = 0,
+                  window: int = 2, maxit: int = 30, out: torch.Tensor | None = None):
+    """Fixed-k batched sFLSQR (exactly maxit steps, no stop test) with
+    tau = diag(d) (identity when d is None).  B: (nrhs, m).  Returns
+    (X (nrhs, n), infos, forward id); the plan keeps the state for `adjoint`."""
+    dev = plan.device
+    B = B.detach().to(device=dev, dtype=torch.float64).contiguous()
+    R = int(B.shape[0])
+    X = out if out is not None else torch.empty((R, plan.n), dtype=torch.float64, device=dev)
+    o, dw = _batched_opts(plan, s, zeta, seed, window, maxit, 1.01, "diag" if d is not None else "identity",
+                          d.detach() if d is not None else None)
+    infos = (N.Info * R)()
+    with torch.cuda.device(dev):
+        st = plan.lib.sflsqr_fixed_batched(plan.handle, R, _ptr(B), ctypes.byref(o), _ptr(X), infos, _stream())
+    N.check(st, "sflsqr_fixed_batched")
+    del dw
+    return X, [SolveInfo(i.iters, i.status, i.relres, i.tol) for i in infos], plan.lib.sfl_fixed_calls(plan.handle)
+
+
+def adjoint(plan: Plan, Xbar: torch.Tensor, want_d: bool = True):
+    """Adjoint of the plan's latest fixed_batched call: (Bbar (nrhs, m), dbar (n) or None)."""
+    dev = plan.device
+    Xbar = Xbar.detach().to(device=dev, dtype=torch.float64).contiguous()
+    R = int(Xbar.shape[0])
+    Bbar = torch.empty((R, plan.m), dtype=torch.float64, device=dev)
+    dbar = torch.empty(plan.n, dtype=torch.float64, device=dev) if want_d else None
+    with torch.cuda.device(dev):
+        st = plan.lib.sflsqr_adjoint_batched(plan.handle, R, _ptr(Xbar), _ptr(Bbar), _ptr(dbar), _stream())
+    N.check(st, "sflsqr_adjoint_batched")
+    return Bbar, dbar
+
+
+class FixedKSolve(torch.autograd.Function):
+    """X = sFLSQR_k(B, d) on the GPU, differentiable in B and d through the
+    hand-written adjoint (the forward state, every basis vector included, is
+    kept by the plan between forward and backward)."""
+
+    @staticmethod
+    def forward(ctx, plan, B, d, kw):
+        X, infos, fid = fixed_batched(plan, B, d, **kw)
+        ctx.plan, ctx.fid, ctx.has_d = plan, fid, d is not None
+        ctx.infos = infos
+        return X
+
+    @staticmethod
+    def backward(ctx, Xbar):
+        plan = ctx.plan
+        if plan.lib.sfl_fixed_calls(plan.handle) != ctx.fid:
+            raise RuntimeError("the plan ran another fixed-k forward since this one; its state is gone")
+        Bbar, dbar = adjoint(plan, Xbar, want_d=ctx.has_d and ctx.needs_input_grad[2])
+        return None, Bbar if ctx.needs_input_grad[1] else None, dbar, None
+
+
+def sflsqr_fixed_k(plan: Plan, B: torch.Tensor, d: torch.Tensor | None = None, **kw) -> torch.Tensor:
+    """Differentiable fixed-k batched sFLSQR (see FixedKSolve); kw as fixed_batched."""
+    return FixedKSolve.apply(plan, B, d, kw)
+
+
 def sflsqr(plan: Plan, b, **kw):
     """Algorithm 1 (sFLSQR) on the GPU; see Plan.solve."""
     return plan.solve("sflsqr", b, **kw)

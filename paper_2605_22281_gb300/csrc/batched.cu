@@ -9,7 +9,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "batched.cuh"
+#include "adjoint.cuh"
 #include "engine.h"
 
 namespace sfl {
@@ -41,6 +41,14 @@ struct BatchSession : BatchSessionBase {
   int G_orth = 0, G_rows = 0, tileA = 32, tileT = 32, ls_cluster = 1, ls_stage = 0;
   size_t smem_ls = 0;
   float tune_ms[2][4] = {};
+  // adjoint workspace (allocated by the first adjoint call)
+  bool adj_ready = false;
+  XT *a_xbar = nullptr, *a_wbar = nullptr, *a_pbar = nullptr, *a_whatbar = nullptr, *a_tbar = nullptr, *a_u = nullptr,
+     *a_stm = nullptr, *a_tmpA = nullptr, *a_tmpB = nullptr;
+  double *a_dacc = nullptr, *a_rec = nullptr, *a_coef = nullptr, *a_ybar = nullptr, *a_sbar = nullptr,
+         *a_Mbar = nullptr, *a_ones = nullptr;
+  int *a_kr = nullptr;
+  const double *dw_in = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<void *> allocs;
@@ -357,7 +365,10 @@ struct BEngine {
     if (!se) {
       if (pl.batches.size() >= 2) {
         SFL_CU(cudaStreamSynchronize(s));
-        pl.batches.erase(pl.batches.begin());
+        size_t victim = 0;
+        if (pl.batches[0].get() == pl.last_fixed && !keep_what) victim = 1;   // keep a fixed forward for its adjoint
+        if (pl.batches[victim].get() == pl.last_fixed) pl.last_fixed = nullptr;
+        pl.batches.erase(pl.batches.begin() + victim);
       }
       if ((r = create(pl, key, s, &se))) return r;
     }
@@ -393,6 +404,212 @@ struct BEngine {
   }
 };
 
+// Reverse sweep of a fixed-k forward kept in a batch session (see adjoint.cuh).
+template <typename VT, typename XT>
+struct AEngine {
+  using S = BatchSession<VT, XT>;
+  using E = BEngine<VT, XT>;
+
+  static int workspace(S &se) {
+    if (se.adj_ready) return SFL_OK;
+    const int R = se.key.R, ld = se.ld, K = se.key.maxit, Sk = se.key.s, L = se.key.ell;
+    const int64_t m = se.bp.m, n = se.bp.n;
+    const size_t xs = sizeof(XT);
+    int r;
+#define AA(ptr, bytes) if ((r = E::alloc(se, (void **)&(ptr), (bytes)))) return r;
+    AA(se.a_xbar, xs * n * ld);
+    AA(se.a_wbar, xs * (size_t)(L + 2) * m * ld);
+    AA(se.a_pbar, xs * (size_t)(L + 1) * n * ld);
+    AA(se.a_whatbar, xs * m * ld);
+    AA(se.a_tbar, xs * n * ld);
+    AA(se.a_u, xs * n * ld);
+    AA(se.a_stm, xs * m * ld);
+    AA(se.a_tmpA, xs * m * ld);
+    AA(se.a_tmpB, xs * m * ld);
+    AA(se.a_dacc, sizeof(double) * n * ld);
+    AA(se.a_rec, sizeof(double) * (size_t)kAdjNQ * R * se.bp.rcap);
+    AA(se.a_coef, sizeof(double) * (size_t)R * kAdjNO * kAdjNV);
+    AA(se.a_ybar, sizeof(double) * (size_t)R * K);
+    AA(se.a_sbar, sizeof(double) * (size_t)R * Sk);
+    AA(se.a_Mbar, sizeof(double) * (size_t)R * K * Sk);
+    AA(se.a_ones, sizeof(double) * n);
+    AA(se.a_kr, sizeof(int) * R);
+#undef AA
+    se.adj_ready = true;
+    return SFL_OK;
+  }
+
+  static AVec vec(const void *p, const double *scale = nullptr, int64_t sstride = 0, int dmul = 0, int dbl = 0) {
+    AVec v;
+    v.p = p; v.dbl = dbl; v.scale = scale; v.sstride = sstride; v.dmul = dmul;
+    return v;
+  }
+
+  static AArgs args(const S &se, int64_t len, int j) {
+    AArgs a{};
+    a.R = se.key.R; a.ld = se.ld; a.len = len; a.kr = se.a_kr; a.jstep = j;
+    a.d = se.dwbuf ? se.dwbuf : se.a_ones;
+    a.coef = se.a_coef; a.rec = se.a_rec; a.rcap = se.bp.rcap;
+    return a;
+  }
+
+  static AScalArgs sargs(const S &se, int mode, int j, int nv) {
+    AScalArgs s{};
+    s.R = se.key.R; s.maxit = se.key.maxit; s.ell = se.key.ell; s.j = j; s.mode = mode; s.G = se.G_orth; s.nv = nv;
+    s.kr = se.a_kr; s.rec = se.a_rec; s.rcap = se.bp.rcap;
+    s.sigW = se.bp.sigW; s.sigP = se.bp.sigP; s.hband = se.bp.hband; s.tband = se.bp.tband; s.st = se.bp.st;
+    s.coef = se.a_coef; s.ybar = se.a_ybar;
+    return s;
+  }
+
+  static cudaError_t dots(const S &se, const AArgs &a, cudaStream_t s) {
+    adot_kernel<XT><<<se.G_orth, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t lin(const S &se, const AArgs &a, cudaStream_t s) {
+    alin_kernel<XT><<<se.G_orth, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t scal(const S &se, const AScalArgs &a, cudaStream_t s) {
+    ascal_adj_kernel<<<(se.key.R + kWarps - 1) / kWarps, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t spmm_x(const S &se, bool fwd, const XT *x, XT *y, int accumulate, int j, cudaStream_t s) {
+    const StoredCsr &M = fwd ? se.plan->A : se.plan->T;
+    BSpmmArgs a{M.rowptr, M.col, M.val, M.rows, fwd ? se.wrowA : se.wrowT, kBSpmmExplicit, x, y, accumulate,
+                se.a_kr, j};
+    dim3 grid(se.G_rows, (se.key.R + 63) / 64);
+    if (se.ld >= 64) { bspmm_kernel<VT, XT, 64><<<grid, kThreads, 0, s>>>(se.bp, a); }
+    else {
+      grid.y = (se.key.R + 7) / 8;
+      bspmm_kernel<VT, XT, 8><<<grid, kThreads, 0, s>>>(se.bp, a);
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t st_apply(const S &se, const double *V, int64_t vstride, int j, XT *out, cudaStream_t s) {
+    const int64_t tot = se.bp.m * se.ld;
+    ast_kernel<XT><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(se.key.R, se.ld, se.bp.m, se.key.zeta, se.bp.isz,
+                                                                 se.kin, se.vin, V, vstride, se.a_kr, j, out);
+    return cudaGetLastError();
+  }
+
+  static int run(S &se, const double *Xbar, double *Bbar, double *dbar, cudaStream_t s) {
+    int r;
+    if ((r = workspace(se))) return r;
+    const int R = se.key.R, ld = se.ld, K = se.key.maxit, Sk = se.key.s, L = se.key.ell;
+    const int64_t m = se.bp.m, n = se.bp.n;
+    const size_t xs = sizeof(XT);
+    // steps of every right-hand side
+    std::vector<SolveState> h(R);
+    SFL_CU(cudaMemcpyAsync(h.data(), se.bp.st, sizeof(SolveState) * R, cudaMemcpyDeviceToHost, s));
+    SFL_CU(cudaStreamSynchronize(s));
+    std::vector<int> kr(R);
+    int kmax = 0;
+    for (int q = 0; q < R; ++q) { kr[q] = h[q].k; kmax = std::max(kmax, kr[q]); }
+    SFL_CU(cudaMemcpyAsync(se.a_kr, kr.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+    if (!se.dwbuf) {
+      std::vector<double> one(n, 1.0);
+      SFL_CU(cudaMemcpyAsync(se.a_ones, one.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      SFL_CU(cudaStreamSynchronize(s));
+    }
+    dim3 tg((unsigned)((n + 31) / 32), (ld + 31) / 32), tb(32, 8);
+    binterleave_kernel<XT><<<tg, tb, 0, s>>>(Xbar, n, R, ld, se.a_xbar);
+    SFL_CU(cudaGetLastError());
+    SFL_CU(cudaMemsetAsync(se.a_wbar, 0, xs * (size_t)(L + 2) * m * ld, s));
+    SFL_CU(cudaMemsetAsync(se.a_pbar, 0, xs * (size_t)(L + 1) * n * ld, s));
+    SFL_CU(cudaMemsetAsync(se.a_dacc, 0, sizeof(double) * n * ld, s));
+    SFL_CU(cudaMemsetAsync(se.a_ybar, 0, sizeof(double) * (size_t)R * K, s));
+    const XT *Wb = se.bp.W, *Pb = se.bp.P, *Hb = se.bp.what;
+    auto wslot = [&](int j) { return Wb + (size_t)(j - 1) * m * ld; };     // w~_j
+    auto pslot = [&](int j) { return Pb + (size_t)(j - 1) * n * ld; };     // p~_j
+    auto hslot = [&](int j) { return Hb + (size_t)(j - 1) * m * ld; };     // A z~_j
+    auto wbar = [&](int j) { return se.a_wbar + (size_t)(j % (L + 2)) * m * ld; };
+    auto pbar = [&](int j) { return se.a_pbar + (size_t)(j % (L + 1)) * n * ld; };
+    const int64_t sW = K + 2, sP = K + 1;
+    // ybar_j = <z_j, xbar>, z_j = d * sigP_j p~_j (seven columns per pass)
+    for (int j0 = 1; j0 <= kmax; j0 += kAdjNV - 1) {
+      AArgs a = args(se, n, j0);
+      a.nv = 1 + std::min(kAdjNV - 1, kmax - j0 + 1);
+      a.v[0] = vec(se.a_xbar);
+      for (int l = 1; l < a.nv; ++l) a.v[l] = vec(pslot(j0 + l - 1), se.bp.sigP + (j0 + l - 1), sP, 1);
+      SFL_CU(dots(se, a, s));
+      SFL_CU(scal(se, sargs(se, kAScalYbar, j0, a.nv), s));
+    }
+    als_adj_kernel<<<R, kThreads, sizeof(double) * 2 * K, s>>>(R, Sk, K, se.a_kr, se.Q, se.Rinv, se.y, se.bp.e,
+                                                                 se.a_ybar, se.a_sbar, se.a_Mbar);
+    SFL_CU(cudaGetLastError());
+    for (int j = kmax; j >= 1; --j) {
+      // ---- m side
+      SFL_CU(st_apply(se, se.a_Mbar + (size_t)(j - 1) * Sk, (int64_t)K * Sk, j, se.a_stm, s));
+      const int lo = std::max(1, j - L), nw = j - lo + 1;
+      AArgs a = args(se, m, j);
+      a.nv = 2 + nw;
+      a.v[0] = vec(wbar(j + 1));
+      a.v[1] = vec(wslot(j + 1), se.bp.sigW + (j + 1), sW);
+      for (int t = 0; t < nw; ++t) a.v[2 + t] = vec(wslot(lo + t), se.bp.sigW + (lo + t), sW);
+      SFL_CU(dots(se, a, s));
+      SFL_CU(scal(se, sargs(se, kAScalM, j, a.nv), s));
+      a.v[2 + nw] = vec(hslot(j), se.bp.sigP + j, sP);
+      a.v[3 + nw] = vec(se.a_stm);
+      a.nv = 4 + nw;
+      a.no = 2 + nw;
+      a.o[0] = AOut{se.a_whatbar, 0, 0};
+      for (int t = 0; t < nw; ++t) a.o[1 + t] = AOut{wbar(lo + t), 0, 1};
+      a.o[1 + nw] = AOut{wbar(j + 1), 0, 0};
+      SFL_CU(lin(se, a, s));
+      // ---- u = A^T (adjoint of A z_j)
+      SFL_CU(spmm_x(se, false, se.a_whatbar, se.a_u, 0, j, s));
+      // ---- n side
+      AArgs pa = args(se, n, j);
+      pa.nv = 3;
+      pa.v[0] = vec(se.a_u);
+      pa.v[1] = vec(se.a_xbar, se.y + (j - 1), K);
+      pa.v[2] = vec(pslot(j), se.bp.sigP + j, sP);
+      pa.no = 2;
+      pa.o[0] = AOut{pbar(j), 0, 1};
+      pa.o[1] = AOut{se.a_dacc, 1, 1};
+      apre_kernel<XT><<<se.G_orth, kThreads, 0, s>>>(pa);
+      SFL_CU(cudaGetLastError());
+      const int np = j - lo;
+      AArgs b = args(se, n, j);
+      b.nv = 2 + np;
+      b.v[0] = vec(pbar(j));
+      b.v[1] = vec(pslot(j), se.bp.sigP + j, sP);
+      for (int t = 0; t < np; ++t) b.v[2 + t] = vec(pslot(lo + t), se.bp.sigP + (lo + t), sP);
+      SFL_CU(dots(se, b, s));
+      SFL_CU(scal(se, sargs(se, kAScalN, j, b.nv), s));
+      b.no = 2 + np;
+      b.o[0] = AOut{se.a_tbar, 0, 0};
+      for (int t = 0; t < np; ++t) b.o[1 + t] = AOut{pbar(lo + t), 0, 1};
+      b.o[1 + np] = AOut{pbar(j), 0, 0};
+      SFL_CU(lin(se, b, s));
+      // ---- wbar_j += A tbar_j
+      SFL_CU(spmm_x(se, true, se.a_tbar, wbar(j), 1, j, s));
+    }
+    // b-bar = S^T sbar + (wbar_1 - <w_1, wbar_1> w_1) / beta_0
+    SFL_CU(st_apply(se, se.a_sbar, Sk, 1, se.a_tmpA, s));
+    AArgs f = args(se, m, 1);
+    f.nv = 2;
+    f.v[0] = vec(wbar(1));
+    f.v[1] = vec(wslot(1), se.bp.sigW + 1, sW);
+    SFL_CU(dots(se, f, s));
+    SFL_CU(scal(se, sargs(se, kAScalFinal, 1, 2), s));
+    f.nv = 3;
+    f.v[2] = vec(se.a_tmpA);
+    f.no = 1;
+    f.o[0] = AOut{se.a_tmpB, 0, 0};
+    SFL_CU(lin(se, f, s));
+    dim3 tm((unsigned)((m + 31) / 32), (R + 31) / 32);
+    adeinterleave_kernel<XT><<<tm, tb, 0, s>>>(se.a_tmpB, m, R, ld, Bbar);
+    SFL_CU(cudaGetLastError());
+    if (dbar) {
+      adsum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(se.a_dacc, n, R, ld, dbar);
+      SFL_CU(cudaGetLastError());
+    }
+    return SFL_OK;
+  }
+};
+
 static int check_batched(const Plan &pl, int R, const sfl_opts *o) {
   if (!o || R < 1 || R > kBMaxRhs) return SFL_EINVAL;
   if (o->maxit < 1 || o->maxit > kMaxIt) return SFL_EINVAL;
@@ -411,7 +628,7 @@ static int check_batched(const Plan &pl, int R, const sfl_opts *o) {
 }
 
 int batched_solve(sfl_plan *plan, int32_t nrhs, const double *B, const double *noise_norms, const sfl_opts *opts,
-                  double *X, sfl_info *infos, sfl_stream stream, int keep_what) {
+                  double *X, sfl_info *infos, sfl_stream stream, int keep_what, BatchSessionBase **used = nullptr) {
   if (!plan || !B || !noise_norms || !X) return SFL_EINVAL;
   Plan &pl = plan->impl;
   int r = check_batched(pl, nrhs, opts);
@@ -419,9 +636,62 @@ int batched_solve(sfl_plan *plan, int32_t nrhs, const double *B, const double *n
   for (int j = 0; j < nrhs; ++j)
     if (noise_norms[j] > 0.0 && !(opts->eta > 0.0)) return SFL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (pl.vdt == SFL_F64) return BEngine<double, double>::solve(pl, nrhs, B, noise_norms, opts, X, infos, s, keep_what, nullptr);
-  if (pl.vdt == SFL_F32) return BEngine<float, float>::solve(pl, nrhs, B, noise_norms, opts, X, infos, s, keep_what, nullptr);
-  return BEngine<__nv_bfloat16, float>::solve(pl, nrhs, B, noise_norms, opts, X, infos, s, keep_what, nullptr);
+  if (pl.vdt == SFL_F64) {
+    BatchSession<double, double> *u = nullptr;
+    r = BEngine<double, double>::solve(pl, nrhs, B, noise_norms, opts, X, infos, s, keep_what, &u);
+    if (used) *used = u;
+    return r;
+  }
+  if (pl.vdt == SFL_F32) {
+    BatchSession<float, float> *u = nullptr;
+    r = BEngine<float, float>::solve(pl, nrhs, B, noise_norms, opts, X, infos, s, keep_what, &u);
+    if (used) *used = u;
+    return r;
+  }
+  BatchSession<__nv_bfloat16, float> *u = nullptr;
+  r = BEngine<__nv_bfloat16, float>::solve(pl, nrhs, B, noise_norms, opts, X, infos, s, keep_what, &u);
+  if (used) *used = u;
+  return r;
+}
+
+// Fixed-k forward for differentiation: no stop test, A z~_j kept.
+int fixed_batched(sfl_plan *plan, int32_t nrhs, const double *B, const sfl_opts *opts, double *X, sfl_info *infos,
+                  sfl_stream stream) {
+  if (!plan || !opts) return SFL_EINVAL;
+  if (opts->window > 3) return SFL_EUNSUPPORTED;   // the adjoint's combination kernels hold windows up to 3
+  if (nrhs < 1 || nrhs > kBMaxRhs) return SFL_EINVAL;
+  std::vector<double> zero(nrhs, 0.0);
+  Plan &pl = plan->impl;
+  pl.last_fixed = nullptr;
+  BatchSessionBase *u = nullptr;
+  const int r = batched_solve(plan, nrhs, B, zero.data(), opts, X, infos, stream, 1, &u);
+  if (r) return r;
+  pl.last_fixed = u;
+  pl.fixed_calls += 1;
+  return SFL_OK;
+}
+
+int adjoint_batched(sfl_plan *plan, int32_t nrhs, const double *Xbar, double *Bbar, double *dbar, sfl_stream stream) {
+  if (!plan || !Xbar || !Bbar) return SFL_EINVAL;
+  Plan &pl = plan->impl;
+  BatchSessionBase *b = pl.last_fixed;
+  bool live = false;
+  for (auto &p : pl.batches) live |= p.get() == b;
+  if (!b || !live) return SFL_EINVAL;   // no fixed-k forward kept by this plan
+  cudaStream_t s = (cudaStream_t)stream;
+  if (auto q = dynamic_cast<BatchSession<double, double> *>(b)) {
+    if (q->key.R != nrhs) return SFL_EINVAL;
+    return AEngine<double, double>::run(*q, Xbar, Bbar, dbar, s);
+  }
+  if (auto q = dynamic_cast<BatchSession<float, float> *>(b)) {
+    if (q->key.R != nrhs) return SFL_EINVAL;
+    return AEngine<float, float>::run(*q, Xbar, Bbar, dbar, s);
+  }
+  if (auto q = dynamic_cast<BatchSession<__nv_bfloat16, float> *>(b)) {
+    if (q->key.R != nrhs) return SFL_EINVAL;
+    return AEngine<__nv_bfloat16, float>::run(*q, Xbar, Bbar, dbar, s);
+  }
+  return SFL_EINVAL;
 }
 
 }  // namespace sfl
@@ -432,6 +702,18 @@ extern "C" int sflsqr_solve_batched(sfl_plan *plan, int32_t nrhs, const double *
                                     const sfl_opts *opts, double *X, sfl_info *infos, sfl_stream stream) {
   return batched_solve(plan, nrhs, B, noise_norms, opts, X, infos, stream, 0);
 }
+
+extern "C" int sflsqr_fixed_batched(sfl_plan *plan, int32_t nrhs, const double *B, const sfl_opts *opts, double *X,
+                                    sfl_info *infos, sfl_stream stream) {
+  return fixed_batched(plan, nrhs, B, opts, X, infos, stream);
+}
+
+extern "C" int sflsqr_adjoint_batched(sfl_plan *plan, int32_t nrhs, const double *Xbar, double *Bbar, double *dbar,
+                                      sfl_stream stream) {
+  return adjoint_batched(plan, nrhs, Xbar, Bbar, dbar, stream);
+}
+
+extern "C" int64_t sfl_fixed_calls(const sfl_plan *plan) { return plan ? plan->impl.fixed_calls : -1; }
 
 extern "C" int sfl_batched_tile(const sfl_plan *plan, int32_t which) {
   if (!plan || (which != 0 && which != 1)) return -1;

@@ -29,7 +29,7 @@ namespace sfl {
 constexpr int kBMaxRhs = 256;
 
 enum BScalMode : int { kBScalZ = 0, kBScalAlpha = 1, kBScalW = 2, kBScalBeta = 3 };
-enum BSpmmMode : int { kBSpmmInit = 0, kBSpmmFwd = 1, kBSpmmBwd = 2 };
+enum BSpmmMode : int { kBSpmmInit = 0, kBSpmmFwd = 1, kBSpmmBwd = 2, kBSpmmExplicit = 3 };
 
 template <typename XT>
 struct BParams {
@@ -273,6 +273,13 @@ struct BSpmmArgs {
   int64_t rows;
   const int32_t *crow;       // row range of every CTA (gridDim.x + 1), balanced by cost
   int mode;
+  // kBSpmmExplicit: y (=|+=) A x for the given interleaved vectors, no records;
+  // a right-hand side takes part iff jstep <= kr[r]
+  const void *xe;
+  void *ye;
+  int accumulate;
+  const int *kr;
+  int jstep;
 };
 
 template <typename XT> struct XT2;
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
     rr[q] = tile0 + (T >= 32 ? RPL * lane + q : gl);
-    act[q] = rr[q] < p.R && b_active(p.st, rr[q]);
+    act[q] = rr[q] < p.R && (a.mode == kBSpmmExplicit ? a.jstep <= a.kr[rr[q]] : b_active(p.st, rr[q]));
     any |= act[q];
   }
   const bool tile_any = __syncthreads_or(any);
@@ -318,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
   const XT *win = nullptr;
   int lo = 1, nd = 0;
   if (a.mode == kBSpmmInit) { x = p.W; y = p.zraw; }
+  else if (a.mode == kBSpmmExplicit) { x = (const XT *)a.xe; y = (XT *)a.ye; }
   else if (a.mode == kBSpmmFwd) {
     x = p.zbuf;
     y = p.what + (p.keep_what ? (size_t)(k - 1) * p.m * p.ld : 0);
@@ -378,7 +386,9 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
         }
         const ACC tot = (s0 + s1) + (s2 + s3);
         if (owner && act[q]) {
-          y[(size_t)row * p.ld + rr[q]] = (XT)tot;
+          XT *yo = y + (size_t)row * p.ld + rr[q];
+          if (a.accumulate) { *yo = (XT)((ACC)*yo + tot); continue; }
+          *yo = (XT)tot;
           const double yd = (double)(XT)tot;
           nrm[q] += yd * yd;
         }
@@ -402,6 +412,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
     }
     __syncthreads();
   };
+  if (a.mode == kBSpmmExplicit) return;
   store(nrm, 0);
   for (int w = 0; w < nd; ++w) {
     const XT *wv = win + (size_t)(lo + w - 1) * wslot;

@@ -77,6 +77,8 @@ struct Plan {
   std::vector<void *> allocs;
   std::vector<std::unique_ptr<Session>> sessions;
   std::vector<std::unique_ptr<BatchSessionBase>> batches;
+  BatchSessionBase *last_fixed = nullptr;   // session of the latest fixed-k forward (for its adjoint)
+  int64_t fixed_calls = 0;
   // scratch for sfl_plan_apply
   void *apply_x = nullptr, *apply_y = nullptr;
   RedScratch apply_red{};
