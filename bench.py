@@ -44,6 +44,10 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched multi-sinogram leg (64 x 512^2, FP32) and print its JSON")
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="run only the mixed-precision leg (1024^2, BF16 / FP32 values) and print its JSON")
+    ap.add_argument("--only-diff", action="store_true",
+                    help="run only the differentiable leg (16 x 256^2, fixed k, forward + adjoint) and print its JSON")
     ap.add_argument("--driver", default="graph", choices=["graph", "host_loop"],
                     help="graph: one CUDA graph per solve (the measured configuration); host_loop: the same "
                          "kernels launched one by one from the host, for profilers that cannot see inside "
@@ -266,6 +270,91 @@ def batched_variant(args, G, wl, np, torch):
             "speedup_vs_plain_fp64": value / fp64_solves}
 
 
+def mixed_variant(args, G, wl, np, torch):
+    """sFLSQR at scale: 1024x1024 image, 360 angles x 1449 bins (481M nonzeros),
+    1% noise, s = 600, window 4, maxit 300, with BF16 or FP32 operator values
+    (FP32 vectors and accumulation, FP64 small problem and coefficients), and
+    the FP64 path on the same problem for the error comparison."""
+    p = wl.make("ct1024_sflsqr")
+    st = p.settings
+    kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
+              noise_norm=float(p.noise_norm[0]), eta=st["eta"])
+    b = torch.as_tensor(p.b, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"m": p.A.shape[0], "n": p.A.shape[1], "nnz": int(p.A.nnz)}
+    xs = {}
+    for vdt in ("bf16", "f32", "f64"):
+        plan = G.Plan(p.A, value_dtype=vdt)
+        x, info, _ = plan.solve("sflsqr", b, **kw)
+        reps = max(1, min(args.steps, 3))
+        e0.record(stream)
+        for _ in range(reps):
+            plan.solve("sflsqr", b, out=x, sync=False, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        xh = x.cpu().numpy()
+        xs[vdt] = xh
+        leg = {"iters": info.iters, "stop": info.status_name, "time_to_stop_ms": ms,
+               "iters_per_s": info.iters / (ms / 1000),
+               "rel_error_vs_x_true": float(np.linalg.norm(xh - p.x_true) / np.linalg.norm(p.x_true))}
+        if vdt != "f64":
+            _, _, hp = plan.solve("sflsqr", b, driver="profiled", **kw)
+            kms, kl = hp["kernel_ms"], hp["kernel_launches"]
+            vb = 2 if vdt == "bf16" else 4
+            for name, nnz, rows, cols in (("spmv_fwd", p.A.nnz, p.A.shape[0], p.A.shape[1]),
+                                          ("spmv_bwd", p.A.nnz, p.A.shape[1], p.A.shape[0])):
+                avg = kms[name] / max(kl[name], 1)
+                nbytes = spmv_bytes(int(nnz), rows, cols, vb, 4, st["window"] + 1, 0)
+                leg[name] = {"avg_us": 1000 * avg, "bytes": nbytes, "gbs": nbytes / (avg * 1e-3) / 1e9,
+                             "hbm_frac_of_measured": nbytes / (avg * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]}
+        out[vdt] = leg
+        plan.close()
+    for vdt in ("bf16", "f32"):
+        out[vdt]["rel_diff_vs_fp64_path_x"] = float(np.linalg.norm(xs[vdt] - xs["f64"]) / np.linalg.norm(xs["f64"]))
+    out["value"] = out["bf16"]["iters_per_s"]
+    out["unit"] = "iters/s"
+    return out
+
+
+def diff_variant(args, G, wl, np, torch):
+    """The differentiable form: 16 sinograms of 256x256 phantoms, fixed k = 30
+    steps of sFLSQR with a diagonal weight (s = 61, window 2), FP32 values and
+    vectors; one forward plus one hand-written adjoint per timed step."""
+    p = wl.make("ct256_diff16")
+    st = p.settings
+    plan = G.Plan(p.A, value_dtype="f32")
+    B = torch.as_tensor(np.ascontiguousarray(p.b.T), device="cuda")
+    d = torch.as_tensor(st["weight"], device="cuda")
+    kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"])
+    Xbar = torch.randn((B.shape[0], p.A.shape[1]), dtype=torch.float64, device="cuda",
+                       generator=torch.Generator(device="cuda").manual_seed(0))
+    X, infos, _ = G.fixed_batched(plan, B, d, **kw)
+    G.adjoint(plan, Xbar)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    reps = max(1, min(args.steps, 5))
+    fwd = bwd = 0.0
+    for _ in range(reps):
+        e0.record(stream)
+        G.fixed_batched(plan, B, d, out=X, **kw)
+        e1.record(stream)
+        G.adjoint(plan, Xbar)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        fwd += e0.elapsed_time(e1)
+        bwd += e1.elapsed_time(e2)
+    fwd /= reps
+    bwd /= reps
+    R = B.shape[0]
+    plan.close()
+    return {"value": R / ((fwd + bwd) / 1000), "unit": "differentiated solves/s", "nrhs": R, "k": st["maxit"],
+            "forward_ms": fwd, "adjoint_ms": bwd, "values": "f32", "vectors": "f32",
+            "note": "gradients checked in tests (FP64 oracle autograd, finite differences)"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -274,10 +363,11 @@ def run_ours(args):
     import workloads as wl
     from paper_2605_22281_gb300 import api as G
 
-    if args.only_batched:
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        print(json.dumps(batched_variant(args, G, wl, np, torch)), flush=True)
-        return
+    for flag, leg in (("only_batched", batched_variant), ("only_mixed", mixed_variant), ("only_diff", diff_variant)):
+        if getattr(args, flag):
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            print(json.dumps(leg(args, G, wl, np, torch)), flush=True)
+            return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -411,6 +501,8 @@ def run_ours(args):
 
     if not args.no_variants:
         variants["batched_ct512_64rhs_f32"] = batched_variant(args, G, wl, np, torch)
+        variants["mixed_ct1024_sflsqr"] = mixed_variant(args, G, wl, np, torch)
+        variants["diff_ct256_16rhs_fixed_k"] = diff_variant(args, G, wl, np, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
