@@ -207,6 +207,40 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU leg
 
+def gather_rank_values(vals, world: int, device) -> list:
+    """Every rank's list of values (all_gather over the default process
+    group); with one rank, [vals]."""
+    if world <= 1:
+        return [list(vals)]
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    out = [torch.zeros_like(tt) for _ in range(world)]
+    dist.all_gather(out, tt)
+    return [[float(v) for v in o] for o in out]
+
+
+def aggregate(per_rank: list, steps: int) -> tuple:
+    """Weak scaling over independent problems: (max time over ranks in ms,
+    iterations of all ranks, whole-job iterations per second) from per-rank
+    (time ms, iterations per solve)."""
+    t_max = max(r[0] for r in per_rank)
+    total = sum(int(round(r[1])) * steps for r in per_rank)
+    return t_max, total, total / (t_max / 1000.0)
+
+
+def rank_problem(p, rank: int, wl, np):
+    """Rank r > 0 solves its own problem: the same operator and phantom, fresh
+    noise at the same level (seed 1000 + r)."""
+    if rank == 0:
+        return p
+    rng = np.random.default_rng(1000 + rank)
+    b_true = p.A.matvec(p.x_true)
+    p.b, en = wl.add_noise(b_true, float(p.noise_norm[0] / np.linalg.norm(b_true)), rng)
+    p.noise_norm = np.array([en])
+    return p
+
+
 def batched_variant(args, G, wl, np, torch):
     """The multi-sinogram form: 64 sinograms of 512x512 ellipse phantoms through
     one 360 x 725 Siddon operator (120M nonzeros), noise levels log-uniform in
@@ -382,14 +416,9 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    p = wl.make(args.workload)
+    p = rank_problem(wl.make(args.workload), rank, wl, np)
     st = p.settings
     method = st["method"]
-    if rank > 0:  # independent problem per rank: same operator, fresh noise
-        rng = np.random.default_rng(1000 + rank)
-        b_true = p.A.matvec(p.x_true)
-        p.b, en = wl.add_noise(b_true, float(p.noise_norm[0] / np.linalg.norm(b_true)), rng)
-        p.noise_norm = np.array([en])
     precond = {"identity": "identity", "irw": "reweight", "diag": "diag"}[st["precond"]]
     kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
               noise_norm=float(p.noise_norm[0]), eta=st["eta"], precond=precond, irw_eps=st.get("irw_eps", 1e-4))
@@ -423,17 +452,7 @@ def run_ours(args):
     t_ms = ev0.elapsed_time(ev1)
     _, info_chk, _ = plan.solve(method, b_dev, out=x_dev, **kw)
     assert info_chk.iters == iters, "solve is not deterministic"
-    t_all = [t_ms]
-    iters_all = [iters]
-    if world > 1:
-        tt = torch.tensor([t_ms, float(iters)], device="cuda", dtype=torch.float64)
-        gathered = [torch.zeros_like(tt) for _ in range(world)]
-        dist.all_gather(gathered, tt)
-        t_all = [float(g[0]) for g in gathered]
-        iters_all = [int(g[1]) for g in gathered]
-    t_max_ms = max(t_all)
-    total_iters = sum(i * args.steps for i in iters_all)
-    value = total_iters / (t_max_ms / 1000.0)
+    t_max_ms, total_iters, value = aggregate(gather_rank_values([t_ms, iters], world, "cuda"), args.steps)
     ms_per_step = t_max_ms / args.steps
 
     # per-kernel launch durations (CUDA events around every launch, same solve)
@@ -470,12 +489,7 @@ def run_ours(args):
         for _ in range(args.steps):
             _, info_h = plan.solve_host(method, b_host, x_out=x_host, **kw)
         t_e2e = time.perf_counter() - t0
-        e2e_all = [t_e2e]
-        if world > 1:
-            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            gathered = [torch.zeros_like(tt) for _ in range(world)]
-            dist.all_gather(gathered, tt)
-            e2e_all = [float(g[0]) for g in gathered]
+        e2e_all = [r[0] for r in gather_rank_values([t_e2e], world, "cuda")]
         e2e = {"value": total_iters / max(e2e_all), "unit": "iters/s", "h2d_bytes_per_step": 8 * m,
                "d2h_bytes_per_step": 8 * n}
 
