@@ -46,6 +46,9 @@ def parse_args():
                     help="run only the batched multi-sinogram leg (64 x 512^2, FP32) and print its JSON")
     ap.add_argument("--only-mixed", action="store_true",
                     help="run only the mixed-precision leg (1024^2, BF16 / FP32 values) and print its JSON")
+    ap.add_argument("--mixed-size", type=int, default=1024,
+                    help="image size of the mixed-precision leg (1024: the configured workload; smaller sizes keep "
+                         "its geometry recipe, for profiling)")
     ap.add_argument("--only-diff", action="store_true",
                     help="run only the differentiable leg (16 x 256^2, fixed k, forward + adjoint) and print its JSON")
     ap.add_argument("--driver", default="graph", choices=["graph", "host_loop"],
@@ -309,14 +312,15 @@ def mixed_variant(args, G, wl, np, torch):
     1% noise, s = 600, window 4, maxit 300, with BF16 or FP32 operator values
     (FP32 vectors and accumulation, FP64 small problem and coefficients), and
     the FP64 path on the same problem for the error comparison."""
-    p = wl.make("ct1024_sflsqr")
+    N = args.mixed_size
+    p = wl.make("ct1024_sflsqr") if N == 1024 else wl.make("ct1024_sflsqr", N=N, n_angles=max(1, 360 * N // 1024))
     st = p.settings
     kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
               noise_norm=float(p.noise_norm[0]), eta=st["eta"])
     b = torch.as_tensor(p.b, device="cuda")
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = {"m": p.A.shape[0], "n": p.A.shape[1], "nnz": int(p.A.nnz)}
+    out = {"image": f"{N}x{N}", "m": p.A.shape[0], "n": p.A.shape[1], "nnz": int(p.A.nnz)}
     xs = {}
     for vdt in ("bf16", "f32", "f64"):
         plan = G.Plan(p.A, value_dtype=vdt)

@@ -73,10 +73,14 @@ typedef struct sfl_plan sfl_plan;
 
 /* Plan options.  value_dtype is the precision the plan stores A (and its
  * transpose or B) in: SFL_F64, SFL_F32 or SFL_BF16 (round to nearest even).
- * max_device_bytes caps the plan's own allocations (0 = no cap). */
+ * lanes_per_row: lanes of a warp that share one row in the single-solve
+ * products (4, 8, 16 or 32), or 0 to choose it from the average row length.
+ * It fixes the summation order of every row, so results (not only speed)
+ * depend on it; a plan's choice never changes.  max_device_bytes caps the
+ * plan's own allocations (0 = no cap). */
 typedef struct {
   sfl_dtype value_dtype;
-  int32_t reserved0;
+  int32_t lanes_per_row;
   uint64_t max_device_bytes;
 } sfl_plan_opts;
 

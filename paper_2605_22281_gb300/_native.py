@@ -27,7 +27,7 @@ class Csr(ctypes.Structure):
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("value_dtype", ctypes.c_int), ("reserved0", ctypes.c_int32), ("max_device_bytes", ctypes.c_uint64)]
+    _fields_ = [("value_dtype", ctypes.c_int), ("lanes_per_row", ctypes.c_int32), ("max_device_bytes", ctypes.c_uint64)]
 
 
 class Opts(ctypes.Structure):

@@ -62,7 +62,8 @@ class Plan:
     """A sparse operator A (m x n, CSR) and its transposed copy, or an unmatched
     back-projector B (n x m), stored on the GPU in `value_dtype`."""
 
-    def __init__(self, A, B=None, value_dtype: str = "f64", device: str | int = 0, max_device_bytes: int = 0):
+    def __init__(self, A, B=None, value_dtype: str = "f64", device: str | int = 0, max_device_bytes: int = 0,
+                 lanes_per_row: int = 0):
         _require_cuda()
         self.lib = N.load()
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
@@ -71,7 +72,7 @@ class Plan:
             cb, keep_b = (None, None)
             if B is not None:
                 cb, keep_b = _dev_csr(B.rowptr, B.colidx, B.values, B.shape, self.device)
-            po = N.PlanOpts(N.DTYPE[value_dtype], 0, max_device_bytes)
+            po = N.PlanOpts(N.DTYPE[value_dtype], lanes_per_row, max_device_bytes)
             h = ctypes.c_void_p()
             st = N.check(self.lib.sfl_plan_create(ctypes.byref(h), ctypes.byref(ca),
                                                   ctypes.byref(cb) if cb is not None else None,

@@ -72,6 +72,7 @@ struct Plan {
   int num_sms = 0;
   sfl_dtype vdt = SFL_F64;
   bool unmatched = false;
+  int lpr_override = 0;      // lanes per row requested by the caller (0: from the row lengths)
   StoredCsr A, T;   // T: CSR of A^T (transposed copy) or of B
   uint64_t bytes = 0, cap = 0;
   std::vector<void *> allocs;

@@ -147,6 +147,14 @@ template <> struct Chunk<__nv_bfloat16, 8> {
 template <typename VT> struct LoadWidth { static constexpr int P = 4; };
 template <> struct LoadWidth<__nv_bfloat16> { static constexpr int P = 8; };
 
+// Loads in flight per lane and resident CTAs per SM of the SpMV, per value
+// type: 4 chunks (16 entries) per iteration for FP64 and FP32 values, 2 chunks
+// (16 entries) for BF16; 2 CTAs per SM for FP64 (FP64-pipe bound, registers
+// for the deeper pipeline), more for the reduced precisions (latency bound).
+template <typename VT> struct SpmvTune { static constexpr int NCH = 4, MINB = 2; };
+template <> struct SpmvTune<float> { static constexpr int NCH = 4, MINB = 3; };
+template <> struct SpmvTune<__nv_bfloat16> { static constexpr int NCH = 2, MINB = 3; };
+
 template <typename XT> struct AccT { using T = XT; };
 
 // Row sum of one row for a group of LPR lanes (lane gl of the group), P
@@ -167,6 +175,7 @@ template <typename VT, typename XT, int LPR>
 __device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT> &p, const XT *__restrict__ x,
                                                        int beg, int end, int gl) {
   constexpr int P = LoadWidth<VT>::P;
+  constexpr int NCH = SpmvTune<VT>::NCH;
   constexpr int STR = LPR * P;
   using ACC = typename AccT<XT>::T;
   ACC s0 = (ACC)0, s1 = (ACC)0;
@@ -177,26 +186,17 @@ __device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT>
   const int nslot = (end - beg + STR - 1) / STR;
   const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)nslot);
 #pragma unroll 1
-  for (int j = 0; j < nmax; j += 4) {
+  for (int j = 0; j < nmax; j += NCH) {
     const int off = beg + gl * P + j * STR;
-    Chunk<VT, P> c0, c1, c2, c3;
-    load_or_zero(c0, p.col, p.val, off, off < end);
-    load_or_zero(c1, p.col, p.val, off + STR, off + STR < end);
-    load_or_zero(c2, p.col, p.val, off + 2 * STR, off + 2 * STR < end);
-    load_or_zero(c3, p.col, p.val, off + 3 * STR, off + 3 * STR < end);
+    Chunk<VT, P> c[NCH];
 #pragma unroll
-    for (int q = 0; q < P; ++q) s0 += (ACC)c0.v[q] * (ACC)__ldg(x + c0.c[q]);
-    if (j + 1 < nmax) {
+    for (int h = 0; h < NCH; ++h) load_or_zero(c[h], p.col, p.val, off + h * STR, off + h * STR < end);
 #pragma unroll
-      for (int q = 0; q < P; ++q) s1 += (ACC)c1.v[q] * (ACC)__ldg(x + c1.c[q]);
-    }
-    if (j + 2 < nmax) {
+    for (int h = 0; h < NCH; ++h) {
+      if (h > 0 && j + h >= nmax) break;
+      ACC &s = (h & 1) ? s1 : s0;
 #pragma unroll
-      for (int q = 0; q < P; ++q) s0 += (ACC)c2.v[q] * (ACC)__ldg(x + c2.c[q]);
-    }
-    if (j + 3 < nmax) {
-#pragma unroll
-      for (int q = 0; q < P; ++q) s1 += (ACC)c3.v[q] * (ACC)__ldg(x + c3.c[q]);
+      for (int q = 0; q < P; ++q) s += (ACC)c[h].v[q] * (ACC)__ldg(x + c[h].c[q]);
     }
   }
   return s0 + s1;
@@ -368,7 +368,7 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
 // outputs are stored unscaled (y = A x for the stored, unnormalised x), with
 // ||y||^2 and the window dots <v_j, y> as per-CTA records (CTA 0's are zero).
 template <typename VT, typename XT, int LPR, bool MAT>
-__global__ void __launch_bounds__(kThreads, 2) spmv_fused_kernel(SpmvParams<VT, XT> p) {
+__global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kernel(SpmvParams<VT, XT> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SolveState sst;
   __shared__ double wsum[(kMaxWindow + 2) * kThreads];   // reduction scratch
