@@ -487,7 +487,8 @@ struct Engine {
     SA(se->wrowT, sizeof(int32_t) * (WT + 1));
 #undef SA
     const int P = load_width(pl.vdt);
-    const int nch = pl.vdt == SFL_BF16 ? SpmvTune<__nv_bfloat16>::NCH : SpmvTune<double>::NCH;
+    const int nch = pl.vdt == SFL_BF16 ? SpmvTune<__nv_bfloat16>::NCH
+                    : pl.vdt == SFL_F32 ? SpmvTune<float>::NCH : SpmvTune<double>::NCH;
     if ((r = balance_rows(pl.A, nch * pl.A.lpr * P, WA, se->wrowA, s)) ||
         (r = balance_rows(pl.T, nch * pl.T.lpr * P, WT, se->wrowT, s))) {
       destroy_session(pl, *se);
