@@ -342,3 +342,42 @@ def test_ct256_unmatched_full_size_matches_oracle():
                               irw_eps=st["irw_eps"])
     assert info2.iters == info.iters
     assert rel(x2.cpu().numpy(), r.x) <= RTOL_ITER
+
+
+# ---------------------------------------------------------------- reduced precision: solves
+
+def rounded(S, vdt):
+    if vdt == "f32":
+        return S.astype(np.float32).astype(np.float64)
+    R = S.copy()
+    R.data = torch.as_tensor(S.data).to(torch.bfloat16).to(torch.float64).numpy()
+    return R
+
+
+@pytest.mark.parametrize("vdt,bar_same_op,bar_fp64,bar_recon", [("f32", 2e-5, 2e-5, 0.01), ("bf16", 2e-5, 2e-2, 0.05)])
+def test_reduced_precision_solves_against_oracle(vdt, bar_same_op, bar_fp64, bar_recon, ct64):
+    """FP32/BF16 operator values with FP32 vectors and accumulation (FP64 small
+    problem).  Stated errors: against the FP64 oracle run on the same rounded
+    operator (what FP32 vectors cost), against the FP64 oracle on the exact
+    operator (what the value rounding costs), and the reconstruction error
+    within 1% (FP32) or 5% (BF16 values, about three significant digits) of
+    the FP64 solve's."""
+    p, _ = ct64
+    st = p.settings
+    S = p.A.scipy()
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    plan = G.Plan(p.A, value_dtype=vdt)
+    x, info, _ = plan.solve("sflsqr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                            maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"])
+    xg = x.cpu().numpy()
+    r_same = run_oracle_sflsqr(rounded(S, vdt), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
+    r_exact = run_oracle_sflsqr(S, p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
+    assert abs(info.iters - r_same.iters) <= 1
+    if info.iters == r_same.iters:
+        assert rel(xg, r_same.x) <= bar_same_op
+    if info.iters == r_exact.iters:
+        assert rel(xg, r_exact.x) <= bar_fp64
+    e_gpu = rel(xg, p.x_true)
+    e_fp64 = rel(r_exact.x, p.x_true)
+    assert abs(e_gpu - e_fp64) <= bar_recon * e_fp64
+    plan.close()
