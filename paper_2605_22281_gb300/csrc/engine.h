@@ -126,8 +126,9 @@ int ls_cluster_size(int s, int maxit, bool saz, int max_cluster = 16);
 cudaError_t ls_allow_max_smem();
 int wait_stream(cudaStream_t s);
 
-// Row range of each of W warps, balanced by 4 * ceil(len / unit) + 1 per row.
-int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s);
+// Row range of each of W warps, balanced by 4 * ceil(len / unit) + 1 per row,
+// plus 4 * ceil(len / slot) when slot > 0.
+int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s, int slot = 0);
 
 // Row-major sparse-sign table (rows of S with their entries column | sign bit).
 struct SketchTableTmp {

@@ -450,17 +450,21 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
   }
 }
 
-// Row cost for the warp partition of a product: the row's 4-load iterations
-// (ceil(len / unit), unit = 4 * lanes per row * load width) in quarter
-// iterations, plus one quarter for the row's share of the per-row work
-// (bounds, stash, output).  Warps over short rows run more iterations per
-// stored entry than warps over long rows, so entries alone do not balance.
-static __global__ void row_cost_kernel(const int32_t *rowptr, int64_t rows, int unit, int64_t *cost) {
+// Row cost for the warp partition of a product, in quarter iterations: the
+// row's load iterations (ceil(len / unit), unit = entries one iteration of its
+// lane group covers), plus, when slot > 0, its chunk slots (ceil(len / slot),
+// the FMA instructions it issues: on this GPU an FP64 instruction costs a full
+// issue slot whatever the number of active lanes), plus one quarter for the
+// row's share of the per-row work.  Warps over short rows run more iterations
+// per stored entry than warps over long rows, so entries alone do not balance.
+static __global__ void row_cost_kernel(const int32_t *rowptr, int64_t rows, int unit, int slot, int64_t *cost) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i > rows) return;
   if (i == rows) { cost[i] = 0; return; }
   const int len = rowptr[i + 1] - rowptr[i];
-  cost[i] = 4 * (int64_t)((len + unit - 1) / unit) + 1;
+  int64_t c = 4 * (int64_t)((len + unit - 1) / unit) + 1;
+  if (slot > 0) c += 4 * (int64_t)((len + slot - 1) / slot);
+  cost[i] = c;
 }
 
 // Row range of every warp: warp w starts at the first row whose cost prefix

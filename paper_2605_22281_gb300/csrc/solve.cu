@@ -140,7 +140,7 @@ cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t 
 // Row range of each of W warps over the rows of M, balanced by row cost
 // (4 * ceil(len / unit) + 1 per row, exclusive scan, binary search per warp).
 // Temporaries are freed before returning; the stream is synchronised.
-int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s) {
+int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s, int slot) {
   const int64_t rows = M.rows;
   int64_t *cost = nullptr, *prefix = nullptr;
   void *tst = nullptr;
@@ -155,7 +155,7 @@ int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_
   if (e == cudaSuccess) e = cudaMalloc(&prefix, sizeof(int64_t) * (rows + 1));
   if (e == cudaSuccess) e = cudaMalloc(&tst, tb ? tb : 16);
   if (e == cudaSuccess) {
-    row_cost_kernel<<<(unsigned)((rows + 256) / 256), 256, 0, s>>>(M.rowptr, rows, unit, cost);
+    row_cost_kernel<<<(unsigned)((rows + 256) / 256), 256, 0, s>>>(M.rowptr, rows, unit, slot, cost);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(tst, tb, cost, prefix, (int)(rows + 1), s);
@@ -489,8 +489,10 @@ struct Engine {
     const int P = load_width(pl.vdt);
     const int nch = pl.vdt == SFL_BF16 ? SpmvTune<__nv_bfloat16>::NCH
                     : pl.vdt == SFL_F32 ? SpmvTune<float>::NCH : SpmvTune<double>::NCH;
-    if ((r = balance_rows(pl.A, nch * pl.A.lpr * P, WA, se->wrowA, s)) ||
-        (r = balance_rows(pl.T, nch * pl.T.lpr * P, WT, se->wrowT, s))) {
+    // FP64 products are bound by FMA issue: their rows also pay for chunk slots
+    const bool fp64 = pl.vdt == SFL_F64;
+    if ((r = balance_rows(pl.A, nch * pl.A.lpr * P, WA, se->wrowA, s, fp64 ? pl.A.lpr * P : 0)) ||
+        (r = balance_rows(pl.T, nch * pl.T.lpr * P, WT, se->wrowT, s, fp64 ? pl.T.lpr * P : 0))) {
       destroy_session(pl, *se);
       return r;
     }
