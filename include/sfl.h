@@ -113,7 +113,13 @@ typedef struct {
  *                  ratio of step k at index k-1.
  *  spmm_tile     : batched solves only: RHS per CTA column of the SpMMs (8, 16,
  *                  32 or 64), or 0 to let the plan time the candidates.  The
- *                  results are identical for every width. */
+ *                  results are identical for every width.
+ *  orth_against_z: 0 (default): the new z is orthogonalized against the unit
+ *                  vectors p_j of the window, as eq. (FGK) states; 1: against
+ *                  the stored z_j = tau_j(p_j) themselves, as the window loop of
+ *                  Algorithms 1 and 2 is printed (z <- z - <z_j, z> z_j, in
+ *                  ascending j).  The two coincide for the identity operator.
+ *                  Single solves only (batched and fixed-k calls: 0). */
 typedef struct {
   int32_t s;
   int32_t zeta;
@@ -130,6 +136,7 @@ typedef struct {
   int32_t spmm_tile;
   double *x_history;
   double *relres_history;
+  int32_t orth_against_z;
 } sfl_opts;
 
 /* Result of a solve.  Filled when the call returns (the call then waits for

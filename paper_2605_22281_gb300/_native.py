@@ -35,7 +35,8 @@ class Opts(ctypes.Structure):
                 ("window", ctypes.c_int32), ("maxit", ctypes.c_int32), ("noise_norm", ctypes.c_double),
                 ("eta", ctypes.c_double), ("precond", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("diag_w", ctypes.c_void_p), ("irw_eps", ctypes.c_double), ("vec_dtype", ctypes.c_int32),
-                ("spmm_tile", ctypes.c_int32), ("x_history", ctypes.c_void_p), ("relres_history", ctypes.c_void_p)]
+                ("spmm_tile", ctypes.c_int32), ("x_history", ctypes.c_void_p), ("relres_history", ctypes.c_void_p),
+                ("orth_against_z", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -107,21 +107,26 @@ class Plan:
         return y
 
     def _opts(self, s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, diag_w, irw_eps,
-              vec_dtype, x_hist, r_hist):
+              vec_dtype, x_hist, r_hist, orth_against="p"):
+        if orth_against not in ("p", "z"):
+            raise ValueError(orth_against)
         return N.Opts(s, zeta, seed, window, maxit, float(noise_norm), float(eta), N.PRECOND[precond],
                       N.STOP_RULE[stop_rule], _ptr(diag_w), float(irw_eps), N.DTYPE[vec_dtype], 0,
-                      _ptr(x_hist), _ptr(r_hist))
+                      _ptr(x_hist), _ptr(r_hist), 1 if orth_against == "z" else 0)
 
     def solve(self, method: str, b: torch.Tensor, *, s: int, zeta: int = 8, seed: int = 0, window: int = 2,
               maxit: int = 100, noise_norm: float = 0.0, eta: float = 1.01, precond: str = "identity",
               stop_rule: str = "residual", diag_w: torch.Tensor | None = None, irw_eps: float = 1e-4,
               vec_dtype: str | None = None, x_history: bool = False, relres_history: bool = False,
-              driver: str = "graph", out: torch.Tensor | None = None, sync: bool = True):
+              driver: str = "graph", out: torch.Tensor | None = None, sync: bool = True,
+              orth_against: str = "p"):
         """Run sFLSQR (method='sflsqr', Algorithm 1) or sFLSMR ('sflsmr', Algorithm 2).
 
-        Returns (x, info, hist) where hist holds the optional per-step iterates
-        (maxit x n) and stop ratios.  With sync=False the call does not wait and
-        info is None."""
+        orth_against: 'p' orthogonalizes the new z against the window's unit
+        p_j (eq. (FGK)), 'z' against the stored z_j as the algorithms' loop is
+        printed.  Returns (x, info, hist) where hist holds the optional per-step
+        iterates (maxit x n) and stop ratios.  With sync=False the call does not
+        wait and info is None."""
         if vec_dtype is None:
             vec_dtype = "f64" if self.value_dtype == "f64" else "f32"
         dev = self.device
@@ -131,7 +136,7 @@ class Plan:
         xh = torch.zeros((maxit, self.n), dtype=torch.float64, device=dev) if x_history else None
         rh = torch.zeros(maxit, dtype=torch.float64, device=dev) if relres_history else None
         o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
-                       xh, rh)
+                       xh, rh, orth_against)
         info = N.Info()
         pinfo = ctypes.byref(info) if sync else None
         with torch.cuda.device(dev):
@@ -157,7 +162,7 @@ class Plan:
     def solve_host(self, method: str, b: np.ndarray, *, s: int, zeta: int = 8, seed: int = 0, window: int = 2,
                    maxit: int = 100, noise_norm: float = 0.0, eta: float = 1.01, precond: str = "identity",
                    stop_rule: str = "residual", diag_w: torch.Tensor | None = None, irw_eps: float = 1e-4,
-                   vec_dtype: str | None = None, x_out: np.ndarray | None = None):
+                   vec_dtype: str | None = None, x_out: np.ndarray | None = None, orth_against: str = "p"):
         """Same solve with host FP64 b and x (copies inside the call)."""
         if vec_dtype is None:
             vec_dtype = "f64" if self.value_dtype == "f64" else "f32"
@@ -165,7 +170,7 @@ class Plan:
         x = x_out if x_out is not None else np.empty(self.n, dtype=np.float64)
         dw = diag_w.to(device=self.device, dtype=torch.float64).contiguous() if diag_w is not None else None
         o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
-                       None, None)
+                       None, None, orth_against)
         info = N.Info()
         fn = self.lib.sflsqr_solve_host if method == "sflsqr" else self.lib.sflsmr_solve_host
         with torch.cuda.device(self.device):

@@ -43,7 +43,7 @@ struct SolveState {
   double znorm_raw2, wnorm_raw2;  // squared norms before orthogonalization
   double alpha, betak;
   double sig_w[kRing], sig_p[kRing];            // scales by ring slot
-  double gram_w[kRing][kRing], gram_p[kRing][kRing];  // <v_i, v_j> of unit vectors, by slot
+  double gram_w[kRing][kRing], gram_p[kRing][kRing];  // <v_i, v_j> by slot: unit w and p (z_j when orth_z)
   double cz[kMaxWindow + 2];   // MGS coefficients of z against the p window
   double hw[kMaxWindow + 2];   // MGS coefficients of w against the w window (column of H)
 };

@@ -25,10 +25,11 @@ struct StoredCsr {
 struct SessionKey {
   int method, s, zeta, ell, maxit, precond, stop_rule, vdt;
   double *x_hist, *r_hist;
+  int orth_z;        // 1: the z window is the stored z_j (sfl_opts.orth_against_z)
   bool operator==(const SessionKey &o) const {
     return method == o.method && s == o.s && zeta == o.zeta && ell == o.ell && maxit == o.maxit &&
            precond == o.precond && stop_rule == o.stop_rule && vdt == o.vdt && x_hist == o.x_hist &&
-           r_hist == o.r_hist;
+           r_hist == o.r_hist && orth_z == o.orth_z;
   }
 };
 

@@ -100,6 +100,7 @@ struct SpmvParams {
   XT *pring; int64_t pstride; int RP;   // ring of p~ (n-vectors)
   XT *Z; int64_t zstride;               // z~_j columns
   double *sigZ;
+  int orth_z;                           // 1: the z window is Z's columns, not the p ring
   XT *wraw;                             // w = A z_k
   XT *zraw;                             // z = A^T w
   double *Hband;                        // sFLSMR: columns of H, (ell+2) entries per column
@@ -214,6 +215,10 @@ __device__ __forceinline__ void mgs_coefficients(const double *dots, int nd, int
   }
 }
 
+// Storage slot of window vector j: its ring slot, or (R == 0) column j - 1 of
+// a matrix that keeps every vector (Z).
+__device__ __forceinline__ int window_slot(int j, int R) { return R > 0 ? ring_slot(j, R) : j - 1; }
+
 // Rows [r0, r1) of one warp, in 32-row blocks: groups of LPR lanes run one row
 // each in LPR substeps; per-lane partial sums are stashed in shared memory and
 // lane r adds its row's partials in order, so the output and ||y||^2 run with
@@ -270,7 +275,7 @@ __device__ __forceinline__ void spmv_window_dots(int64_t r0, int64_t r1, const X
   const int lane = threadIdx.x & 31;
   const XT *wv[ND > 0 ? ND : 1];
 #pragma unroll
-  for (int a = 0; a < ND; ++a) wv[a] = win + (size_t)ring_slot(lo + a, R) * wst;
+  for (int a = 0; a < ND; ++a) wv[a] = win + (size_t)window_slot(lo + a, R) * wst;
   for (int64_t row0 = r0; row0 < r1; row0 += 32) {
     const int64_t row = row0 + lane;
     if (row < r1) {
@@ -317,7 +322,7 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
     if (!(beta > 0.0)) st->stop = SFL_STOP_BREAKDOWN;
     if (!isfinite(tot[0])) st->stop = kStopNonfinite;
   } else if (p.mode == kModeFwd) {
-    // alpha_k = ||p~_k|| from the z update; breakdown test; Gram row of p_k
+    // alpha_k = ||p~_k|| from the z update; breakdown test; Gram row of p_k (of z_k when the z window is Z)
     const int lz = max(1, k - p.ell), ndz = k - lz;          // window of the z update
     reduce_partials(p.part.p, p.G_prev, 1 + ndz, nullptr, tot);
     if (!t0) return;
@@ -406,7 +411,8 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
       x = p.wring + (size_t)ring_slot(k + 1, p.RW) * p.wstride;
       y = p.zraw;
       lo = max(1, k + 1 - p.ell); nd = k - lo + 1;
-      win = p.pring; wst = p.pstride; R = p.RP;
+      if (p.orth_z) { win = p.Z; wst = p.zstride; R = 0; }   // column j - 1 holds z~_j
+      else { win = p.pring; wst = p.pstride; R = p.RP; }
       outpart = p.part.z;
     }
     if (p.mode != kModeInitB) {
@@ -631,6 +637,7 @@ struct OrthParams {
   int scale_ring;     // size of the ring whose scale of slot k applies to raw (w ring for z, p ring for w)
   SolveState *st;
   int side;            // 0: z side (p ring, tau, Z), 1: w side (w ring)
+  int orth_z;          // z side: the window is the stored z~_j (Z columns) instead of the p ring
   int ell;
   int method;
   int G_prev;          // CTAs of the product kernel whose partials this one reduces
@@ -646,9 +653,11 @@ struct OrthParams {
   Partials part;
 };
 
-// z side: p~_k = z - sum_{j=lo}^{k-1} c_j p_j, z~_k = tau_k(p~_k);
+// z side: p~_k = z - sum_{j=lo}^{k-1} c_j v_j, z~_k = tau_k(p~_k), with v_j = p_j
+// (or z_j when orth_z);
 // w side: w~_{k+1} = w - sum_{j=lo}^{k} h_j w_j.
-// Stores this CTA's ||new||^2 and <new, v~_j> over the window.  ND (the
+// Stores this CTA's ||new||^2 and <new, v~_j> over the window (<z~_k, z~_j>
+// when orth_z: the Gram row the next steps' coefficients need).  ND (the
 // window size) is a compile-time constant, so no FP64 instruction is issued
 // for an unused window slot.
 template <typename XT, int ND>
@@ -660,9 +669,9 @@ __device__ __forceinline__ void orth_run(const OrthParams<XT> &p, const SolveSta
 #pragma unroll
   for (int a = 0; a < ND; ++a) {
     const int slot = ring_slot(lo + a, p.R);
-    const double sg = (p.side == 0) ? sst.sig_p[slot] : sst.sig_w[slot];
+    const double sg = (p.side == 0) ? sst.sig_p[slot] : sst.sig_w[slot];   // z~_j shares p~_j's scale
     coef[a] = coefs[a] * sg;
-    vj[a] = p.ring + (size_t)slot * p.stride;
+    vj[a] = (p.side == 0 && p.orth_z) ? p.Z + (size_t)(lo + a - 1) * p.zstride : p.ring + (size_t)slot * p.stride;
   }
   XT *out = p.ring + (size_t)ring_slot(newj, p.R) * p.stride;
   XT *zout = (p.side == 0) ? p.Z + (size_t)(k - 1) * p.zstride : nullptr;
@@ -683,8 +692,10 @@ __device__ __forceinline__ void orth_run(const OrthParams<XT> &p, const SolveSta
     out[i] = vx;
     const double vd = (double)vx;
     acc[0] += vd * vd;
+    if (!(p.side == 0 && p.orth_z)) {
 #pragma unroll
-    for (int a = 0; a < ND; ++a) acc[1 + a] += vd * old[a];
+      for (int a = 0; a < ND; ++a) acc[1 + a] += vd * old[a];
+    }
     if (p.side == 0) {
       double zt = vd;
       if (p.precond == SFL_PRECOND_DIAG) {
@@ -704,7 +715,13 @@ __device__ __forceinline__ void orth_run(const OrthParams<XT> &p, const SolveSta
         const double xv = (a0 + a1) + (a2 + a3);
         zt = sqrt(sqrt(xv * xv + sst.irw_eps)) * vd;
       }
-      zout[i] = (XT)zt;
+      const XT zx = (XT)zt;
+      zout[i] = zx;
+      if (p.orth_z) {
+        const double zd = (double)zx;
+#pragma unroll
+        for (int a = 0; a < ND; ++a) acc[1 + a] += zd * old[a];
+      }
     }
   }
   __syncthreads();

@@ -212,6 +212,7 @@ struct Engine {
     p.ell = se.key.ell;
     p.st = se.st;
     p.part = se.part;
+    p.orth_z = se.key.orth_z;
     if (mode == kModeFwd) { p.wrow = se.wrowA; p.G_prev = se.grid_vec; }
     else if (mode == kModeBwd) { p.wrow = se.wrowT; p.G_prev = se.grid_vec; }
     else if (mode == kModeInitBwd) { p.wrow = se.wrowT; p.G_prev = se.grid_init; }
@@ -237,7 +238,7 @@ struct Engine {
 
   static OrthParams<XT> orth_params(const Plan &pl, const Session &se, int side) {
     OrthParams<XT> o{};
-    o.st = se.st; o.side = side; o.ell = se.key.ell;
+    o.st = se.st; o.side = side; o.ell = se.key.ell; o.orth_z = se.key.orth_z;
     o.method = se.key.method;
     o.part = se.part;
     o.G_prev = side == 0 ? se.grid_spmv_T : se.grid_spmv_A;
@@ -617,6 +618,7 @@ static int check_opts(const Plan &pl, int method, const sfl_opts *o) {
   if (o->vec_dtype == SFL_F64 && pl.vdt != SFL_F64) return SFL_EINVAL;
   if (o->vec_dtype == SFL_F32 && pl.vdt == SFL_F64) return SFL_EUNSUPPORTED;
   if (o->vec_dtype != SFL_F64 && o->vec_dtype != SFL_F32) return SFL_EINVAL;
+  if (o->orth_against_z != 0 && o->orth_against_z != 1) return SFL_EINVAL;
   (void)method;
   return SFL_OK;
 }
@@ -626,7 +628,8 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
   using E = Engine<VT, XT>;
   const sfl_opts *o = q.o;
   SessionKey key{q.method, o->s, o->zeta, o->window, o->maxit, o->precond,
-                 q.method == kSFLSMR ? o->stop_rule : 0, o->vec_dtype, o->x_history, o->relres_history};
+                 q.method == kSFLSMR ? o->stop_rule : 0, o->vec_dtype, o->x_history, o->relres_history,
+                 o->orth_against_z};
   Session *se = nullptr;
   for (auto &p : pl.sessions)
     if (p->key == key) { se = p.get(); break; }

@@ -5,6 +5,7 @@ Bars: bit-exact for the sketch's integer draws; FP64 iterates within relative
 order differs); reduced-precision products against the oracle run on the same
 rounded operator.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -138,18 +139,20 @@ def test_spmv_reduced_precision_on_rounded_operator(vdt, tol, ct64):
 U = 2.0 ** -53   # FP64 unit roundoff
 
 
-def run_oracle_sflsqr(A, b, s, zeta, seed, maxit, tol, ell, tau=None, AT=None):
+def run_oracle_sflsqr(A, b, s, zeta, seed, maxit, tol, ell, tau=None, AT=None, orth_against="p"):
     S = O.SparseSign(seed, s, zeta, A.shape[0])
-    r = O.sflsqr(A, b, S, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, record_x=True, keep_basis=True)
+    r = O.sflsqr(A, b, S, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, record_x=True, keep_basis=True,
+                 orth_against=orth_against)
     r.M = S.mat @ (A @ r.Z)                                  # sketched LS matrix S A Z (eq. (sFLSQR))
     return r
 
 
-def run_oracle_sflsmr(A, b, s, zeta, seed, maxit, tol, ell, tau=None, AT=None, stop_rule="residual"):
+def run_oracle_sflsmr(A, b, s, zeta, seed, maxit, tol, ell, tau=None, AT=None, stop_rule="residual",
+                      orth_against="p"):
     Sn = O.SparseSign(seed, s, zeta, A.shape[1])
     Sm = O.SparseSign(seed + 1, s, zeta, A.shape[0])
     r = O.sflsmr(A, b, Sn, S_stop=Sm, maxit=maxit, tol=tol, ell=ell, tau=tau, AT=AT, stop_rule=stop_rule,
-                 record_x=True, keep_basis=True)
+                 record_x=True, keep_basis=True, orth_against=orth_against)
     BT = A.T if AT is None else AT
     r.M = Sn.mat @ (BT @ (A @ r.Z))                          # S A^T A Z (eq. (sFLSMR))
     return r
@@ -242,6 +245,51 @@ def test_sflsmr_normal_equation_stop_rule(ct64):
     x, info, h = plan.solve("sflsmr", dev(p.b), s=81, zeta=4, seed=5, window=2, maxit=25, stop_rule="normal",
                             x_history=True, relres_history=True)
     assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
+
+
+@pytest.mark.parametrize("precond,window", [("diag", 2), ("reweight", 2), ("diag", 5)])
+def test_sflsqr_literal_z_window(ct64, precond, window):
+    """The z window taken as the stored z_j = tau(p_j) (the window loop of
+    Algorithm 1 as printed) against the oracle's literal reading."""
+    p, plan = ct64
+    n = p.A.shape[1]
+    w = np.random.default_rng(47).uniform(0.5, 1.5, n)
+    tau = O.FixedDiag(w) if precond == "diag" else O.Reweighting(1e-4)
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, 61, 8, 46, 20, 0.0, window, tau=tau, orth_against="z")
+    r_p = run_oracle_sflsqr(p.A.scipy(), p.b, 61, 8, 46, 20, 0.0, window, tau=tau)
+    assert rel(r.x, r_p.x) > 1e-6, "the two readings should differ when tau is not the identity"
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=61, zeta=8, seed=46, window=window, maxit=20, precond=precond,
+                            diag_w=dev(w) if precond == "diag" else None, irw_eps=1e-4, x_history=True,
+                            relres_history=True, orth_against="z")
+    assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
+
+
+def test_sflsmr_unmatched_literal_z_window(ct64_unmatched):
+    A, B, x_true, b, en, plan = ct64_unmatched
+    tol = O.discrepancy_tol(1.01, en, np.linalg.norm(b))
+    r = run_oracle_sflsmr(A.scipy(), b, 201, 8, 43, 150, tol, 2, tau=O.Reweighting(1e-4), AT=B.scipy(),
+                          orth_against="z")
+    x, info, h = plan.solve("sflsmr", dev(b), s=201, zeta=8, seed=43, window=2, maxit=150, noise_norm=en, eta=1.01,
+                            precond="reweight", irw_eps=1e-4, x_history=True, relres_history=True,
+                            orth_against="z")
+    assert info.status == r.status
+    assert_iterates_match(r, h["x"], h["relres"], info, tol)
+
+
+def test_literal_z_window_is_the_default_for_identity(ct64):
+    """For tau = id the stored z~_j are the p~_j bit for bit, so both readings
+    run the same arithmetic."""
+    p, plan = ct64
+    kw = dict(s=101, zeta=8, seed=42, window=3, maxit=30)
+    x1, i1, _ = plan.solve("sflsqr", dev(p.b), **kw)
+    x2, i2, _ = plan.solve("sflsqr", dev(p.b), orth_against="z", **kw)
+    assert i1.iters == i2.iters and torch.equal(x1, x2)
+    o = plan._opts(101, 8, 42, 2, 30, 0.0, 1.01, "identity", "residual", None, 1e-4, "f64", None, None)
+    o.orth_against_z = 2
+    info = G.N.Info()
+    st = plan.lib.sflsqr_solve(plan.handle, G._ptr(dev(p.b)), ctypes.byref(o), G._ptr(x1), ctypes.byref(info),
+                               G._stream())
+    assert st == G.N.SFL_EINVAL
 
 
 # ---------------------------------------------------------------- determinism and drivers
