@@ -119,7 +119,17 @@ typedef struct {
  *                  the stored z_j = tau_j(p_j) themselves, as the window loop of
  *                  Algorithms 1 and 2 is printed (z <- z - <z_j, z> z_j, in
  *                  ascending j).  The two coincide for the identity operator.
- *                  Single solves only (batched and fixed-k calls: 0). */
+ *                  Single solves only (batched and fixed-k calls: 0).
+ *  sketch_dense  : NULL for the sparse-sign sketch above, or a device FP64
+ *                  s x len matrix (row-major, caller-owned, read by every
+ *                  sketch application of the call) used as S itself, as
+ *                  given: len = m for sFLSQR, n for sFLSMR (its S_n).  zeta and
+ *                  seed are then ignored.  For dense sketches (Gaussian, the
+ *                  identity when s = len) and tests; every application reads
+ *                  all of S.  Single solves only.
+ *  sketch_dense_stop: with sketch_dense in sFLSMR, the s x m matrix of its
+ *                  m-side sketch S_m (discrepancy test); required there, NULL
+ *                  otherwise. */
 typedef struct {
   int32_t s;
   int32_t zeta;
@@ -137,6 +147,8 @@ typedef struct {
   double *x_history;
   double *relres_history;
   int32_t orth_against_z;
+  const double *sketch_dense;
+  const double *sketch_dense_stop;
 } sfl_opts;
 
 /* Result of a solve.  Filled when the call returns (the call then waits for

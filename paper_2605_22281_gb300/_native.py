@@ -36,7 +36,8 @@ class Opts(ctypes.Structure):
                 ("eta", ctypes.c_double), ("precond", ctypes.c_int32), ("stop_rule", ctypes.c_int32),
                 ("diag_w", ctypes.c_void_p), ("irw_eps", ctypes.c_double), ("vec_dtype", ctypes.c_int32),
                 ("spmm_tile", ctypes.c_int32), ("x_history", ctypes.c_void_p), ("relres_history", ctypes.c_void_p),
-                ("orth_against_z", ctypes.c_int32)]
+                ("orth_against_z", ctypes.c_int32), ("sketch_dense", ctypes.c_void_p),
+                ("sketch_dense_stop", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):

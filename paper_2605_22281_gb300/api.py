@@ -107,26 +107,38 @@ class Plan:
         return y
 
     def _opts(self, s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, diag_w, irw_eps,
-              vec_dtype, x_hist, r_hist, orth_against="p"):
+              vec_dtype, x_hist, r_hist, orth_against="p", sk=None, sk_stop=None):
         if orth_against not in ("p", "z"):
             raise ValueError(orth_against)
         return N.Opts(s, zeta, seed, window, maxit, float(noise_norm), float(eta), N.PRECOND[precond],
                       N.STOP_RULE[stop_rule], _ptr(diag_w), float(irw_eps), N.DTYPE[vec_dtype], 0,
-                      _ptr(x_hist), _ptr(r_hist), 1 if orth_against == "z" else 0)
+                      _ptr(x_hist), _ptr(r_hist), 1 if orth_against == "z" else 0, _ptr(sk), _ptr(sk_stop))
+
+    def _dense_sketch(self, S, rows, cols):
+        if S is None:
+            return None
+        S = S.to(device=self.device, dtype=torch.float64).contiguous()
+        if tuple(S.shape) != (rows, cols):
+            raise ValueError(f"sketch matrix of shape {tuple(S.shape)}, expected {(rows, cols)}")
+        return S
 
     def solve(self, method: str, b: torch.Tensor, *, s: int, zeta: int = 8, seed: int = 0, window: int = 2,
               maxit: int = 100, noise_norm: float = 0.0, eta: float = 1.01, precond: str = "identity",
               stop_rule: str = "residual", diag_w: torch.Tensor | None = None, irw_eps: float = 1e-4,
               vec_dtype: str | None = None, x_history: bool = False, relres_history: bool = False,
               driver: str = "graph", out: torch.Tensor | None = None, sync: bool = True,
-              orth_against: str = "p"):
+              orth_against: str = "p", sketch_matrix: torch.Tensor | None = None,
+              sketch_matrix_stop: torch.Tensor | None = None):
         """Run sFLSQR (method='sflsqr', Algorithm 1) or sFLSMR ('sflsmr', Algorithm 2).
 
         orth_against: 'p' orthogonalizes the new z against the window's unit
         p_j (eq. (FGK)), 'z' against the stored z_j as the algorithms' loop is
-        printed.  Returns (x, info, hist) where hist holds the optional per-step
-        iterates (maxit x n) and stop ratios.  With sync=False the call does not
-        wait and info is None."""
+        printed.  sketch_matrix: an explicit s x m (sFLSQR) or s x n (sFLSMR)
+        sketch used instead of the sparse-sign one, with sketch_matrix_stop the
+        s x m stop sketch of sFLSMR (kept alive by the caller until the solve
+        has run when sync=False).  Returns (x, info, hist) where hist holds the
+        optional per-step iterates (maxit x n) and stop ratios.  With sync=False
+        the call does not wait and info is None."""
         if vec_dtype is None:
             vec_dtype = "f64" if self.value_dtype == "f64" else "f32"
         dev = self.device
@@ -135,8 +147,10 @@ class Plan:
         dw = diag_w.to(device=dev, dtype=torch.float64).contiguous() if diag_w is not None else None
         xh = torch.zeros((maxit, self.n), dtype=torch.float64, device=dev) if x_history else None
         rh = torch.zeros(maxit, dtype=torch.float64, device=dev) if relres_history else None
+        sk = self._dense_sketch(sketch_matrix, s, self.m if method == "sflsqr" else self.n)
+        sks = self._dense_sketch(sketch_matrix_stop, s, self.m)
         o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
-                       xh, rh, orth_against)
+                       xh, rh, orth_against, sk, sks)
         info = N.Info()
         pinfo = ctypes.byref(info) if sync else None
         with torch.cuda.device(dev):

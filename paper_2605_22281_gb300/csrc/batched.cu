@@ -622,6 +622,7 @@ static int check_batched(const Plan &pl, int R, const sfl_opts *o) {
   if (o->precond != SFL_PRECOND_IDENTITY && o->precond != SFL_PRECOND_DIAG) return SFL_EINVAL;
   if (o->precond == SFL_PRECOND_DIAG && !o->diag_w) return SFL_EINVAL;
   if (o->orth_against_z != 0) return o->orth_against_z == 1 ? SFL_EUNSUPPORTED : SFL_EINVAL;
+  if (o->sketch_dense || o->sketch_dense_stop) return SFL_EUNSUPPORTED;
   if (o->spmm_tile != 0 && o->spmm_tile != 8 && o->spmm_tile != 16 && o->spmm_tile != 32 && o->spmm_tile != 64)
     return SFL_EINVAL;
   (void)pl;

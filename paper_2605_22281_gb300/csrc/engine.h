@@ -26,15 +26,17 @@ struct SessionKey {
   int method, s, zeta, ell, maxit, precond, stop_rule, vdt;
   double *x_hist, *r_hist;
   int orth_z;        // 1: the z window is the stored z_j (sfl_opts.orth_against_z)
+  const double *dense_S, *dense_Sm;   // explicit sketches (sfl_opts.sketch_dense, sketch_dense_stop)
   bool operator==(const SessionKey &o) const {
     return method == o.method && s == o.s && zeta == o.zeta && ell == o.ell && maxit == o.maxit &&
            precond == o.precond && stop_rule == o.stop_rule && vdt == o.vdt && x_hist == o.x_hist &&
-           r_hist == o.r_hist && orth_z == o.orth_z;
+           r_hist == o.r_hist && orth_z == o.orth_z && dense_S == o.dense_S && dense_Sm == o.dense_Sm;
   }
 };
 
 struct Session {
   SessionKey key{};
+  int64_t m = 0, n = 0;                // the plan's operator shape
   int RW = 0, RP = 0;
   SolveState *st = nullptr;
   void *wring = nullptr, *pring = nullptr, *wraw = nullptr, *zraw = nullptr, *Z = nullptr;

@@ -544,6 +544,8 @@ struct SketchParams {
   int RW, RP;                               // ring sizes (slots of the scales of wraw and zraw)
   const int32_t *rowM; const uint32_t *entM;   // m-side table (S_m)
   const int32_t *rowN; const uint32_t *entN;   // n-side table (S_n)
+  const double *dM, *dN;                       // explicit sketches (row-major s x m, s x n) instead of the tables
+  int64_t lenM, lenN;
   double *SAZ, *SAtW, *rhs, *e, *sbm, *sk_out;
 };
 
@@ -582,6 +584,23 @@ __device__ __forceinline__ T sketch_row_sum(const int32_t *rowptr, const uint32_
   return warp_sum((a0 + a1) + (a2 + a3));
 }
 
+// Row r of an explicit sketch times v: the row's len entries, threads
+// strided, four independent accumulators, then a warp butterfly.
+template <typename T, typename VT>
+__device__ __forceinline__ T dense_row_sum(const double *Srow, const VT *v, int64_t len) {
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  constexpr int B = kSkWarps * 32;
+  int64_t i = threadIdx.x;
+  for (; i + 3 * B < len; i += 4 * B) {
+    a0 += (T)Srow[i] * (T)v[i];
+    a1 += (T)Srow[i + B] * (T)v[i + B];
+    a2 += (T)Srow[i + 2 * B] * (T)v[i + 2 * B];
+    a3 += (T)Srow[i + 3 * B] * (T)v[i + 3 * B];
+  }
+  for (; i < len; i += B) a0 += (T)Srow[i] * (T)v[i];
+  return warp_sum((a0 + a1) + (a2 + a3));
+}
+
 template <typename XT>
 __global__ void __launch_bounds__(kSkWarps * 32) sketch_rows_kernel(SketchParams<XT> p, int rows_total) {
   __shared__ double wpart[kSkWarps];
@@ -608,8 +627,17 @@ __global__ void __launch_bounds__(kSkWarps * 32) sketch_rows_kernel(SketchParams
   const int32_t *rowptr = nside ? p.rowN : p.rowM;
   const uint32_t *ent = nside ? p.entN : p.entM;
   double t;
-  if (p.mode == kSkPlain || p.mode == kSkInitB) t = sketch_row_sum<double>(rowptr, ent, p.v64, r);
-  else t = (double)sketch_row_sum<typename AccT<XT>::T>(rowptr, ent, nside ? p.zraw : p.wraw, r);
+  const double *dmat = nside ? p.dN : p.dM;
+  if (dmat) {
+    const int64_t len = nside ? p.lenN : p.lenM;
+    const double *Srow = dmat + (size_t)r * len;
+    if (p.mode == kSkInitB) t = dense_row_sum<double>(Srow, p.v64, len);
+    else t = (double)dense_row_sum<typename AccT<XT>::T>(Srow, nside ? p.zraw : p.wraw, len);
+  } else if (p.mode == kSkPlain || p.mode == kSkInitB) {
+    t = sketch_row_sum<double>(rowptr, ent, p.v64, r);
+  } else {
+    t = (double)sketch_row_sum<typename AccT<XT>::T>(rowptr, ent, nside ? p.zraw : p.wraw, r);
+  }
   if (lane == 0) wpart[warp] = t;
   __syncthreads();
   if (threadIdx.x != 0) return;

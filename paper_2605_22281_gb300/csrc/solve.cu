@@ -227,6 +227,12 @@ struct Engine {
   static SketchParams<XT> sketch_params(const Session &se, int mode) {
     SketchParams<XT> q{};
     q.mode = mode; q.method = se.key.method; q.s = se.key.s; q.isz = 1.0 / std::sqrt((double)se.key.zeta);
+    if (se.key.dense_S) {      // an explicit sketch is applied as given
+      q.isz = 1.0;
+      q.dM = se.key.method == kSFLSQR ? se.key.dense_S : se.key.dense_Sm;
+      q.dN = se.key.method == kSFLSMR ? se.key.dense_S : nullptr;
+      q.lenM = se.m; q.lenN = se.n;
+    }
     q.st = se.st;
     q.v64 = se.bbuf;
     q.wraw = (const XT *)se.wraw; q.zraw = (const XT *)se.zraw;
@@ -410,6 +416,7 @@ struct Engine {
     auto se = std::make_unique<Session>();
     se->key = key;
     const int64_t m = pl.A.rows, n = pl.A.cols;
+    se->m = m; se->n = n;
     const int S = key.s, K = key.maxit, ell = key.ell, Z = key.zeta;
     const size_t xs = sizeof(XT);
     se->RW = ell + 2;
@@ -508,6 +515,7 @@ struct Engine {
 
   // Row-major sketch tables for `seed` (kept until the seed changes).
   static int ensure_tables(const Plan &pl, Session &se, uint64_t seed, cudaStream_t s) {
+    if (se.key.dense_S) return SFL_OK;      // explicit sketch: no draws
     if (se.tab_valid && se.tab_seed == seed) return SFL_OK;
     SketchTableTmp t;
     t.kin = se.sk_kin; t.vin = se.sk_vin; t.kout = se.sk_kout; t.cub = se.sk_cub; t.cub_bytes = se.sk_cub_bytes;
@@ -606,8 +614,11 @@ struct SolveRequest {
 static int check_opts(const Plan &pl, int method, const sfl_opts *o) {
   if (!o) return SFL_EINVAL;
   if (o->maxit < 1 || o->maxit > kMaxIt) return SFL_EINVAL;
-  if (o->zeta < 1 || o->zeta > kMaxZeta) return SFL_EINVAL;
-  if (o->s < o->maxit + 1 || o->s < o->zeta || o->s > kMaxS) return SFL_EINVAL;
+  const bool dense = o->sketch_dense != nullptr;
+  if (!dense && (o->zeta < 1 || o->zeta > kMaxZeta)) return SFL_EINVAL;
+  if (o->s < o->maxit + 1 || (!dense && o->s < o->zeta) || o->s > kMaxS) return SFL_EINVAL;
+  if (dense && method == kSFLSMR && !o->sketch_dense_stop) return SFL_EINVAL;
+  if (o->sketch_dense_stop && (!dense || method != kSFLSMR)) return SFL_EINVAL;
   if (o->window < 0) return SFL_EUNSUPPORTED;   // full orthogonalization: not on the GPU path
   if (o->window > kMaxWindow) return SFL_EINVAL;
   if (o->noise_norm > 0.0 && !(o->eta > 0.0)) return SFL_EINVAL;
@@ -619,7 +630,6 @@ static int check_opts(const Plan &pl, int method, const sfl_opts *o) {
   if (o->vec_dtype == SFL_F32 && pl.vdt == SFL_F64) return SFL_EUNSUPPORTED;
   if (o->vec_dtype != SFL_F64 && o->vec_dtype != SFL_F32) return SFL_EINVAL;
   if (o->orth_against_z != 0 && o->orth_against_z != 1) return SFL_EINVAL;
-  (void)method;
   return SFL_OK;
 }
 
@@ -629,7 +639,8 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
   const sfl_opts *o = q.o;
   SessionKey key{q.method, o->s, o->zeta, o->window, o->maxit, o->precond,
                  q.method == kSFLSMR ? o->stop_rule : 0, o->vec_dtype, o->x_history, o->relres_history,
-                 o->orth_against_z};
+                 o->orth_against_z, o->sketch_dense, o->sketch_dense_stop};
+  if (key.dense_S) key.zeta = 1;   // the draws are not used: one session per explicit sketch
   Session *se = nullptr;
   for (auto &p : pl.sessions)
     if (p->key == key) { se = p.get(); break; }

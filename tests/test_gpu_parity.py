@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 import oracle as O
 import workloads as wl
@@ -290,6 +291,83 @@ def test_literal_z_window_is_the_default_for_identity(ct64):
     st = plan.lib.sflsqr_solve(plan.handle, G._ptr(dev(p.b)), ctypes.byref(o), G._ptr(x1), ctypes.byref(info),
                                G._stream())
     assert st == G.N.SFL_EINVAL
+
+
+@pytest.fixture(scope="module")
+def ct24():
+    """24x24 image, 30 angles x 34 bins (m = 1020, n = 576): small enough for
+    an identity sketch on either side (s = m or s = n <= 2048)."""
+    A = wl.siddon_projector(24, 30, wl.detector_bins(24))
+    rng = np.random.default_rng(11)
+    x = wl.ellipse_phantom(24, rng)
+    b, en = wl.add_noise(A.matvec(x), 0.01, rng)
+    return A, b, G.Plan(A)
+
+
+def test_identity_sketch_with_full_window_is_textbook_lsqr(ct24):
+    """S = I, tau = id and a window covering every earlier vector (ell = 8,
+    k <= 9): x_k is the LSQR iterate, checked against SciPy's lsqr run for k
+    iterations with no stopping tolerance (the pin on textbook LSQR, on the GPU
+    path itself)."""
+    A, b, plan = ct24
+    m = A.shape[0]
+    eye = torch.eye(m, dtype=torch.float64, device="cuda")
+    x, info, h = plan.solve("sflsqr", dev(b), s=m, window=8, maxit=9, x_history=True, sketch_matrix=eye)
+    assert info.iters == 9
+    S = A.scipy()
+    for k in range(1, 10):
+        xk = spla.lsqr(S, b, atol=0.0, btol=0.0, conlim=0.0, iter_lim=k)[0]
+        assert rel(h["x"][k - 1].cpu().numpy(), xk) <= 1e-8, k
+
+
+def test_identity_sketches_with_full_window_are_textbook_lsmr(ct24):
+    A, b, plan = ct24
+    m, n = A.shape
+    eye_n = torch.eye(n, dtype=torch.float64, device="cuda")
+    # the m-side sketch only feeds the discrepancy estimate (no stop here); it has s = n rows
+    stop = dev(np.random.default_rng(3).standard_normal((n, m)))
+    x, info, h = plan.solve("sflsmr", dev(b), s=n, window=8, maxit=9, x_history=True, sketch_matrix=eye_n,
+                            sketch_matrix_stop=stop)
+    assert info.iters == 9
+    S = A.scipy()
+    for k in range(1, 10):
+        xk = spla.lsmr(S, b, atol=0.0, btol=0.0, conlim=0.0, maxiter=k)[0]
+        assert rel(h["x"][k - 1].cpu().numpy(), xk) <= 1e-8, k
+
+
+@pytest.mark.parametrize("method", ["sflsqr", "sflsmr"])
+def test_gaussian_sketch_matches_oracle(ct64, method):
+    """An explicit Gaussian sketch (N(0,1) entries, unscaled as in Corollary
+    1), the same matrices given to the oracle's dense sketch."""
+    p, plan = ct64
+    A = p.A.scipy()
+    m, n = A.shape
+    s, maxit = 61, 25
+    rng = np.random.default_rng(2024)
+    if method == "sflsqr":
+        Sm = rng.standard_normal((s, m))
+        r = O.sflsqr(A, p.b, O.DenseSketch(Sm), maxit=maxit, tol=0.0, ell=2, record_x=True, keep_basis=True)
+        r.M = Sm @ (A @ r.Z)
+        x, info, h = plan.solve("sflsqr", dev(p.b), s=s, window=2, maxit=maxit, x_history=True,
+                                relres_history=True, sketch_matrix=dev(Sm))
+    else:
+        Sn, Sm = rng.standard_normal((s, n)), rng.standard_normal((s, m))
+        r = O.sflsmr(A, p.b, O.DenseSketch(Sn), S_stop=O.DenseSketch(Sm), maxit=maxit, tol=0.0, ell=2,
+                     record_x=True, keep_basis=True)
+        r.M = Sn @ (A.T @ (A @ r.Z))
+        x, info, h = plan.solve("sflsmr", dev(p.b), s=s, window=2, maxit=maxit, x_history=True,
+                                relres_history=True, sketch_matrix=dev(Sn), sketch_matrix_stop=dev(Sm))
+    assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
+
+
+def test_dense_sketch_argument_checks(ct64):
+    p, plan = ct64
+    m, n = p.A.shape
+    Sn = torch.zeros((61, n), dtype=torch.float64, device="cuda")
+    with pytest.raises(G.N.SflError):           # sFLSMR needs its m-side stop sketch too
+        plan.solve("sflsmr", dev(p.b), s=61, window=2, maxit=10, sketch_matrix=Sn)
+    with pytest.raises(ValueError):
+        plan.solve("sflsqr", dev(p.b), s=61, window=2, maxit=10, sketch_matrix=Sn)   # wrong width
 
 
 # ---------------------------------------------------------------- determinism and drivers
