@@ -42,6 +42,8 @@ def parse_args():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-tiles", action="store_true",
+                    help="store the rows of A^T / B in natural order instead of 16x16 pixel tiles")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched multi-sinogram leg (64 x 512^2, FP32) and print its JSON")
     ap.add_argument("--only-mixed", action="store_true",
@@ -114,6 +116,11 @@ class ClockSampler:
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def img(args, p):
+    """The n-side image shape of a CT workload (pixel tiles for A^T / B), unless --no-tiles."""
+    return None if getattr(args, "no_tiles", False) else (p.N, p.N)
 
 
 def kernel_source_hash() -> str:
@@ -255,7 +262,7 @@ def batched_variant(args, G, wl, np, torch):
     R = p.b.shape[1]
     kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"], eta=st["eta"])
     B = torch.as_tensor(np.ascontiguousarray(p.b.T), device="cuda")
-    plan32 = G.Plan(p.A, value_dtype="f32")
+    plan32 = G.Plan(p.A, value_dtype="f32", image_shape=img(args, p))
     t0 = time.perf_counter()
     X, infos = G.solve_batched(plan32, B, p.noise_norm, **kw)       # builds and tunes the session
     torch.cuda.synchronize()
@@ -276,7 +283,7 @@ def batched_variant(args, G, wl, np, torch):
     tiles = G.batched_tiles(plan32)
     plan32.close()
     # plain FP64 path, one solve per right-hand side, on a sample of columns
-    plan64 = G.Plan(p.A, value_dtype="f64")
+    plan64 = G.Plan(p.A, value_dtype="f64", image_shape=img(args, p))
     sample = list(range(0, R, 16))
     for j in sample[:1]:
         plan64.solve("sflsqr", torch.as_tensor(p.b[:, j], device="cuda"), noise_norm=float(p.noise_norm[j]), **kw)
@@ -323,7 +330,7 @@ def mixed_variant(args, G, wl, np, torch):
     out = {"image": f"{N}x{N}", "m": p.A.shape[0], "n": p.A.shape[1], "nnz": int(p.A.nnz)}
     xs = {}
     for vdt in ("bf16", "f32", "f64"):
-        plan = G.Plan(p.A, value_dtype=vdt)
+        plan = G.Plan(p.A, value_dtype=vdt, image_shape=img(args, p))
         x, info, _ = plan.solve("sflsqr", b, **kw)
         reps = max(1, min(args.steps, 3))
         e0.record(stream)
@@ -362,7 +369,7 @@ def diff_variant(args, G, wl, np, torch):
     vectors; one forward plus one hand-written adjoint per timed step."""
     p = wl.make("ct256_diff16")
     st = p.settings
-    plan = G.Plan(p.A, value_dtype="f32")
+    plan = G.Plan(p.A, value_dtype="f32", image_shape=img(args, p))
     B = torch.as_tensor(np.ascontiguousarray(p.b.T), device="cuda")
     d = torch.as_tensor(st["weight"], device="cuda")
     kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"])
@@ -427,7 +434,7 @@ def run_ours(args):
     kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
               noise_norm=float(p.noise_norm[0]), eta=st["eta"], precond=precond, irw_eps=st.get("irw_eps", 1e-4))
     t_plan = time.perf_counter()
-    plan = G.Plan(p.A, p.B, value_dtype="f64")
+    plan = G.Plan(p.A, p.B, value_dtype="f64", image_shape=img(args, p))
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t_plan
     stats = plan.stats()
@@ -500,7 +507,7 @@ def run_ours(args):
     variants = {}
     if not args.no_variants:
         # FP32 values and vectors (FP64 coefficients and small QR), same workload
-        plan32 = G.Plan(p.A, p.B, value_dtype="f32")
+        plan32 = G.Plan(p.A, p.B, value_dtype="f32", image_shape=img(args, p))
         for _ in range(3):
             x32, i32, _ = plan32.solve(method, b_dev, **kw)
         torch.cuda.synchronize()

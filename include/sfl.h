@@ -77,11 +77,17 @@ typedef struct sfl_plan sfl_plan;
  * products (4, 8, 16 or 32), or 0 to choose it from the average row length.
  * It fixes the summation order of every row, so results (not only speed)
  * depend on it; a plan's choice never changes.  max_device_bytes caps the
- * plan's own allocations (0 = no cap). */
+ * plan's own allocations (0 = no cap).  image_rows, image_cols: 0, or the
+ * shape of the n-side as an image (n = image_rows * image_cols, column index
+ * = row * image_cols + col).  When given, the plan stores the rows of A^T (or
+ * B) in 16 x 16 pixel tiles, so that the rays one tile's rows gather stay in
+ * the L1 cache; outputs still go to each row's own index, and every row's
+ * sum is formed exactly as without tiles (bit-identical products). */
 typedef struct {
   sfl_dtype value_dtype;
   int32_t lanes_per_row;
   uint64_t max_device_bytes;
+  int32_t image_rows, image_cols;
 } sfl_plan_opts;
 
 /* Solve options (the Require lines of Algorithms 1 and 2).
@@ -168,6 +174,7 @@ typedef struct {
   int32_t value_dtype;
   int32_t unmatched;                     /* 1 if B was given */
   uint64_t device_bytes;                 /* bytes the plan holds */
+  int32_t tiled_At;                      /* 1 if A^T / B rows are stored in pixel tiles */
 } sfl_plan_stats;
 
 /* ---- plans ------------------------------------------------------------- */

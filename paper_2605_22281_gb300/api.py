@@ -60,10 +60,13 @@ class SolveInfo:
 
 class Plan:
     """A sparse operator A (m x n, CSR) and its transposed copy, or an unmatched
-    back-projector B (n x m), stored on the GPU in `value_dtype`."""
+    back-projector B (n x m), stored on the GPU in `value_dtype`.  image_shape
+    (rows, cols) with rows * cols = n declares the n-side an image (column
+    index row * cols + col): the plan then stores the rows of A^T / B in pixel
+    tiles (same products bit for bit, better cache reuse)."""
 
     def __init__(self, A, B=None, value_dtype: str = "f64", device: str | int = 0, max_device_bytes: int = 0,
-                 lanes_per_row: int = 0):
+                 lanes_per_row: int = 0, image_shape: tuple | None = None):
         _require_cuda()
         self.lib = N.load()
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
@@ -72,7 +75,8 @@ class Plan:
             cb, keep_b = (None, None)
             if B is not None:
                 cb, keep_b = _dev_csr(B.rowptr, B.colidx, B.values, B.shape, self.device)
-            po = N.PlanOpts(N.DTYPE[value_dtype], lanes_per_row, max_device_bytes)
+            ir, ic = (int(image_shape[0]), int(image_shape[1])) if image_shape is not None else (0, 0)
+            po = N.PlanOpts(N.DTYPE[value_dtype], lanes_per_row, max_device_bytes, ir, ic)
             h = ctypes.c_void_p()
             st = N.check(self.lib.sfl_plan_create(ctypes.byref(h), ctypes.byref(ca),
                                                   ctypes.byref(cb) if cb is not None else None,

@@ -280,6 +280,7 @@ struct BSpmmArgs {
   int accumulate;
   const int *kr;
   int jstep;
+  const int32_t *orig;       // stored row i is operator row orig[i] (nullptr: identity)
 };
 
 template <typename XT> struct XT2;
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
         }
         const ACC tot = (s0 + s1) + (s2 + s3);
         if (owner && act[q]) {
-          XT *yo = y + (size_t)row * p.ld + rr[q];
+          XT *yo = y + (size_t)(a.orig ? a.orig[row] : row) * p.ld + rr[q];
           if (a.accumulate) { *yo = (XT)((ACC)*yo + tot); continue; }
           *yo = (XT)tot;
           const double yd = (double)(XT)tot;
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
 #pragma unroll
         for (int q = 0; q < RPL; ++q)
           if (act[q]) {
-            const size_t ei = (size_t)row * p.ld + rr[q];
+            const size_t ei = (size_t)(a.orig ? a.orig[row] : row) * p.ld + rr[q];
             d[q] += (double)y[ei] * (double)wv[ei];
           }
     store(d, 1 + w);

@@ -18,6 +18,7 @@ struct StoredCsr {
   int32_t *rowptr = nullptr;
   int32_t *col = nullptr;
   void *val = nullptr;
+  int32_t *orig = nullptr;   // stored row i is row orig[i] of the operator (nullptr: the identity)
   int64_t rows = 0, cols = 0, nnz = 0, pnnz = 0;
   int lpr = 32;
 };
@@ -76,6 +77,7 @@ struct Plan {
   sfl_dtype vdt = SFL_F64;
   bool unmatched = false;
   int lpr_override = 0;      // lanes per row requested by the caller (0: from the row lengths)
+  int img_rows = 0, img_cols = 0;   // n-side image shape: A^T / B rows stored in pixel tiles
   StoredCsr A, T;   // T: CSR of A^T (transposed copy) or of B
   uint64_t bytes = 0, cap = 0;
   std::vector<void *> allocs;
@@ -132,6 +134,7 @@ int wait_stream(cudaStream_t s);
 // Row range of each of W warps, balanced by 4 * ceil(len / unit) + 1 per row,
 // plus 4 * ceil(len / slot) when slot > 0.
 int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s, int slot = 0);
+bool interleave_rows(const StoredCsr &M, int row_ctas);
 
 // Row-major sparse-sign table (rows of S with their entries column | sign bit).
 struct SketchTableTmp {

@@ -88,6 +88,8 @@ struct SpmvParams {
   const VT *val;
   int64_t rows;
   const int32_t *wrow;      // row range of every warp (nnz balanced), gridDim*kWarps + 1 entries
+  const int32_t *orig;      // stored row i is operator row orig[i] (nullptr: identity); outputs go there
+  int interleave;           // 1: the warps of a CTA take its 32-row blocks in turn (tiled operators)
   int mode;
   int method;
   int ell;
@@ -219,27 +221,35 @@ __device__ __forceinline__ void mgs_coefficients(const double *dots, int nd, int
 // a matrix that keeps every vector (Z).
 __device__ __forceinline__ int window_slot(int j, int R) { return R > 0 ? ring_slot(j, R) : j - 1; }
 
-// Rows [r0, r1) of one warp, in 32-row blocks: groups of LPR lanes run one row
-// each in LPR substeps; per-lane partial sums are stashed in shared memory and
-// lane r adds its row's partials in order, so the output and ||y||^2 run with
-// lane r owning row r and every FP64 instruction on a full warp.  LPR = 1 is
-// the vector pass (no matrix; the row value is b_r).
+// The 32-row blocks of one warp: row0 = first, first + stride, ... below
+// end; a block holds rows [row0, min(row0 + 32, end)).
+struct RowBlocks {
+  int64_t first, stride, end;
+};
+
+// A warp's rows, in 32-row blocks: groups of LPR lanes run one row each in
+// LPR substeps; per-lane partial sums are stashed in shared memory and lane r
+// adds its row's partials in order, so the output and ||y||^2 run with lane r
+// owning row r and every FP64 instruction on a full warp.  Stored row r goes
+// to output index orig[r] (when the rows are stored in another order).  LPR = 1
+// is the vector pass (no matrix; the row value is b_r).
 template <typename VT, typename XT, int LPR, bool MAT>
-__device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, int64_t r0, int64_t r1,
+__device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, RowBlocks rb,
                                             const XT *__restrict__ x, XT *y, typename AccT<XT>::T *stash) {
   constexpr int G = 32 / LPR;
   using ACC = typename AccT<XT>::T;
   const int lane = threadIdx.x & 31;
   const int gl = lane % LPR, grp = lane / LPR;
   double nrm = 0.0;
-  for (int64_t row0 = r0; row0 < r1; row0 += 32) {
+  for (int64_t row0 = rb.first; row0 < rb.end; row0 += rb.stride) {
+    const int64_t r1 = min(row0 + 32, rb.end);
     const int64_t row = row0 + lane;
     const bool valid = row < r1;
     ACC yv = (ACC)0;
     if (MAT) {
-      // lane r holds rowptr[row0 + r]; rows past r1 read rowptr[r1] (empty ranges)
+      // lane r holds rowptr[row0 + r]; rows past the block read rowptr[r1] (empty ranges)
       const int rp = p.rowptr[valid ? row : r1];
-      const int rp_last = p.rowptr[(row0 + 32) < r1 ? (row0 + 32) : r1];
+      const int rp_last = p.rowptr[r1];
       int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
       if (lane == 31) rp_next = rp_last;
 #pragma unroll 1
@@ -259,7 +269,7 @@ __device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, int64_t
     } else {
       if (valid) yv = (ACC)p.b[row];
     }
-    if (valid) y[row] = (XT)yv;
+    if (valid) y[(MAT && p.orig) ? p.orig[row] : row] = (XT)yv;
     const double yd = valid ? (double)yv : 0.0;
     nrm += yd * yd;
   }
@@ -270,30 +280,31 @@ __device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, int64_t
 // re-reads the output of row r it stored itself, so the row loop above keeps
 // no per-window registers.
 template <typename XT, int ND>
-__device__ __forceinline__ void spmv_window_dots(int64_t r0, int64_t r1, const XT *y, const XT *win, int64_t wst,
-                                                 int R, int lo, double (&acc)[ND + 1]) {
+__device__ __forceinline__ void spmv_window_dots(RowBlocks rb, const int32_t *orig, const XT *y, const XT *win,
+                                                 int64_t wst, int R, int lo, double (&acc)[ND + 1]) {
   const int lane = threadIdx.x & 31;
   const XT *wv[ND > 0 ? ND : 1];
 #pragma unroll
   for (int a = 0; a < ND; ++a) wv[a] = win + (size_t)window_slot(lo + a, R) * wst;
-  for (int64_t row0 = r0; row0 < r1; row0 += 32) {
+  for (int64_t row0 = rb.first; row0 < rb.end; row0 += rb.stride) {
     const int64_t row = row0 + lane;
-    if (row < r1) {
-      const double yd = (double)y[row];
+    if (row < min(row0 + 32, rb.end)) {
+      const int64_t o = orig ? orig[row] : row;
+      const double yd = (double)y[o];
 #pragma unroll
-      for (int a = 0; a < ND; ++a) acc[1 + a] += (double)wv[a][row] * yd;
+      for (int a = 0; a < ND; ++a) acc[1 + a] += (double)wv[a][o] * yd;
     }
   }
 }
 
 template <typename XT, int ND>
-__device__ __forceinline__ void spmv_finish(int64_t r0, int64_t r1, const XT *y, const XT *win, int64_t wst, int R,
-                                            int lo, double nrm, double *outpart, double *wsum) {
+__device__ __forceinline__ void spmv_finish(RowBlocks rb, const int32_t *orig, const XT *y, const XT *win,
+                                            int64_t wst, int R, int lo, double nrm, double *outpart, double *wsum) {
   double acc[ND + 1];
   acc[0] = nrm;
 #pragma unroll
   for (int a = 1; a <= ND; ++a) acc[a] = 0.0;
-  spmv_window_dots<XT, ND>(r0, r1, y, win, wst, R, lo, acc);
+  spmv_window_dots<XT, ND>(rb, orig, y, win, wst, R, lo, acc);
   __syncthreads();
   store_partials<ND + 1>(acc, wsum, outpart);
 }
@@ -429,30 +440,40 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
   using ACC = typename AccT<XT>::T;
   const int warp = threadIdx.x >> 5;
   ACC *stash = reinterpret_cast<ACC *>(smem_raw) + warp * 32 * (LPR > 1 ? LPR : 1);
+  // this warp's blocks: its own balanced range, or (tiled operators) every
+  // kWarps-th block of the CTA's range, so the CTA's warps work on one tile
   const int gw = rcta * kWarps + warp;
-  int64_t r0, r1;
-  if (p.wrow) { r0 = p.wrow[gw]; r1 = p.wrow[gw + 1]; }
-  else {
-    const int64_t W = (int64_t)ncta * kWarps;
-    r0 = (p.rows * gw) / W; r1 = (p.rows * (gw + 1)) / W;
+  auto bound = [&](int64_t w) {
+    return p.wrow ? (int64_t)p.wrow[w] : (p.rows * w) / ((int64_t)ncta * kWarps);
+  };
+  RowBlocks rb;
+  if (p.interleave) {
+    rb.first = bound((int64_t)rcta * kWarps) + 32 * warp;
+    rb.stride = 32 * kWarps;
+    rb.end = bound((int64_t)(rcta + 1) * kWarps);
+  } else {
+    rb.first = bound(gw);
+    rb.stride = 32;
+    rb.end = bound(gw + 1);
   }
-  const double nrm = spmv_rows<VT, XT, LPR, MAT>(p, r0, r1, x, y, stash);
+  const double nrm = spmv_rows<VT, XT, LPR, MAT>(p, rb, x, y, stash);
   if (!reduce) return;
+  const int32_t *og = MAT ? p.orig : nullptr;
   if (!MAT) {     // vector pass: no window dots
-    spmv_finish<XT, 0>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum);
+    spmv_finish<XT, 0>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum);
     return;
   }
   switch (nd) {   // the window size is a compile-time constant inside the tail
-    case 0: spmv_finish<XT, 0>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 1: spmv_finish<XT, 1>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 2: spmv_finish<XT, 2>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 3: spmv_finish<XT, 3>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 4: spmv_finish<XT, 4>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 5: spmv_finish<XT, 5>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 6: spmv_finish<XT, 6>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 7: spmv_finish<XT, 7>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 8: spmv_finish<XT, 8>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    default: spmv_finish<XT, 9>(r0, r1, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 0: spmv_finish<XT, 0>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 1: spmv_finish<XT, 1>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 2: spmv_finish<XT, 2>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 3: spmv_finish<XT, 3>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 4: spmv_finish<XT, 4>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 5: spmv_finish<XT, 5>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 6: spmv_finish<XT, 6>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 7: spmv_finish<XT, 7>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 8: spmv_finish<XT, 8>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    default: spmv_finish<XT, 9>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
   }
 }
 

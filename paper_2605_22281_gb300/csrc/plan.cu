@@ -2,9 +2,11 @@
 // of A (one-time set-up; the per-step kernels are in kernels.cuh).
 #include <cub/cub.cuh>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "engine.h"
 
@@ -66,25 +68,30 @@ __global__ void convert_values_kernel(const void *in, int dt, OT *out, int64_t n
   }
 }
 
-__global__ void padded_len_kernel(const int32_t *rowptr, int64_t rows, int P, int32_t *plen) {
+// Padded length of stored row i, which is row order[i] of the input (order
+// nullptr: row i).
+__global__ void padded_len_kernel(const int32_t *rowptr, int64_t rows, int P, const int32_t *order, int32_t *plen) {
   const int64_t st = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= rows; i += st) {
     if (i == rows) { plen[i] = 0; continue; }
-    const int len = rowptr[i + 1] - rowptr[i];
+    const int64_t src = order ? order[i] : i;
+    const int len = rowptr[src + 1] - rowptr[src];
     plen[i] = (len + P - 1) / P * P;
   }
 }
 
-// One warp per row: copy the row into its padded slot.  Padding entries take
-// the row's last column (or 0 for an empty row) and value 0.
+// One warp per stored row: copy input row order[r] (or r) into its padded
+// slot.  Padding entries take the row's last column (or 0 for an empty row)
+// and value 0.
 template <typename OT>
 __global__ void fill_padded_kernel(const int32_t *rowptr, const int32_t *col, const OT *val, int64_t rows,
-                                   const int32_t *prow, int32_t *pcol, OT *pval) {
+                                   const int32_t *order, const int32_t *prow, int32_t *pcol, OT *pval) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w0; r < rows; r += nw) {
-    const int b = rowptr[r], e = rowptr[r + 1], pb = prow[r], pe = prow[r + 1];
+    const int64_t src = order ? order[r] : r;
+    const int b = rowptr[src], e = rowptr[src + 1], pb = prow[r], pe = prow[r + 1];
     const int last = e > b ? col[e - 1] : 0;
     for (int i = lane; i < pe - pb; i += 32) {
       if (b + i < e) { pcol[pb + i] = col[b + i]; pval[pb + i] = val[b + i]; }
@@ -186,18 +193,39 @@ static int choose_lpr(int64_t pnnz, int64_t rows, int P) {
   return avg >= 12.0 * P * 16 ? 16 : 8;
 }
 
-// Pad (rowptr, col, val[OT]) into plan-owned storage.
+// Row order of 16 x 16 pixel tiles (tiles and the pixels inside one in
+// row-major order) for an image_rows x image_cols n-side.
+static std::vector<int32_t> tile_order(int rows, int cols) {
+  constexpr int kTile = 16;
+  std::vector<int32_t> o;
+  o.reserve((size_t)rows * cols);
+  for (int ty = 0; ty < rows; ty += kTile)
+    for (int tx = 0; tx < cols; tx += kTile)
+      for (int iy = ty; iy < std::min(rows, ty + kTile); ++iy)
+        for (int ix = tx; ix < std::min(cols, tx + kTile); ++ix) o.push_back(iy * cols + ix);
+  return o;
+}
+
+// Pad (rowptr, col, val[OT]) into plan-owned storage, rows in the plan's
+// tile order when `tiled` (the n-side image shape is known).
 template <typename OT>
 static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const int32_t *col, const OT *val,
-                        int64_t rows, int64_t cols, int64_t nnz, cudaStream_t s) {
+                        int64_t rows, int64_t cols, int64_t nnz, cudaStream_t s, bool tiled = false) {
   const int P = load_width(pl.vdt);
   TmpAlloc tmp;
+  int r;
+  if (tiled) {
+    const std::vector<int32_t> o = tile_order(pl.img_rows, pl.img_cols);
+    if ((int64_t)o.size() != rows) return SFL_EINVAL;
+    if ((r = plan_alloc(pl, (void **)&out.orig, sizeof(int32_t) * rows))) return r;
+    SFL_CU(cudaMemcpyAsync(out.orig, o.data(), sizeof(int32_t) * rows, cudaMemcpyHostToDevice, s));
+    SFL_CU(cudaStreamSynchronize(s));
+  }
   int32_t *plen = nullptr;
   SFL_CU(tmp.get(&plen, sizeof(int32_t) * (rows + 1)));
-  padded_len_kernel<<<1024, 256, 0, s>>>(rowptr, rows, P, plen);
+  padded_len_kernel<<<1024, 256, 0, s>>>(rowptr, rows, P, out.orig, plen);
   SFL_CU(cudaGetLastError());
-  int r = plan_alloc(pl, (void **)&out.rowptr, sizeof(int32_t) * (rows + 1));
-  if (r) return r;
+  if ((r = plan_alloc(pl, (void **)&out.rowptr, sizeof(int32_t) * (rows + 1)))) return r;
   size_t tb = 0;
   SFL_CU(cub::DeviceScan::ExclusiveSum(nullptr, tb, plen, out.rowptr, (int)(rows + 1), s));
   void *tst = nullptr;
@@ -211,7 +239,8 @@ static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const i
   if ((r = plan_alloc(pl, (void **)&out.col, sizeof(int32_t) * (pnnz + 8)))) return r;
   if ((r = plan_alloc(pl, (void **)&out.val, sizeof(OT) * (pnnz + 8)))) return r;
   if (rows > 0) {
-    fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.rowptr, out.col, (OT *)out.val);
+    fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.orig, out.rowptr, out.col,
+                                                 (OT *)out.val);
     SFL_CU(cudaGetLastError());
   }
   out.rows = rows; out.cols = cols; out.nnz = nnz; out.pnnz = pnnz;
@@ -237,7 +266,7 @@ static int build_plan(Plan &pl, const sfl_csr *A, const sfl_csr *B, cudaStream_t
       convert_values_kernel<OT><<<2048, 256, 0, s>>>(B->values, B->dtype, bval, B->nnz);
       SFL_CU(cudaGetLastError());
     }
-    r = store_padded<OT>(pl, pl.T, B->rowptr, B->colidx, bval, B->rows, B->cols, B->nnz, s);
+    r = store_padded<OT>(pl, pl.T, B->rowptr, B->colidx, bval, B->rows, B->cols, B->nnz, s, pl.img_rows > 0);
     SFL_CU(cudaStreamSynchronize(s));
     return r;
   }
@@ -270,7 +299,7 @@ static int build_plan(Plan &pl, const sfl_csr *A, const sfl_csr *B, cudaStream_t
   }
   bounds_kernel<<<1024, 256, 0, s>>>(keys_out, nnz, A->cols, trow);
   SFL_CU(cudaGetLastError());
-  r = store_padded<OT>(pl, pl.T, trow, tcol, tval, A->cols, A->rows, nnz, s);
+  r = store_padded<OT>(pl, pl.T, trow, tcol, tval, A->cols, A->rows, nnz, s, pl.img_rows > 0);
   SFL_CU(cudaStreamSynchronize(s));
   return r;
 }
@@ -311,6 +340,9 @@ int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const s
   if (vdt != SFL_F64 && vdt != SFL_F32 && vdt != SFL_BF16) return SFL_EINVAL;
   const int lpr = popts ? popts->lanes_per_row : 0;
   if (lpr != 0 && lpr != 4 && lpr != 8 && lpr != 16 && lpr != 32) return SFL_EINVAL;
+  const int img_r = popts ? popts->image_rows : 0, img_c = popts ? popts->image_cols : 0;
+  if (img_r < 0 || img_c < 0 || (img_r == 0) != (img_c == 0)) return SFL_EINVAL;
+  if (img_r > 0 && (int64_t)img_r * img_c != A->cols) return SFL_EINVAL;
   sfl_plan *p = new sfl_plan();
   Plan &pl = p->impl;
   cudaGetDevice(&pl.device);
@@ -318,6 +350,7 @@ int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const s
   pl.vdt = vdt;
   pl.unmatched = B != nullptr;
   pl.lpr_override = lpr;
+  pl.img_rows = img_r; pl.img_cols = img_c;
   pl.cap = popts ? popts->max_device_bytes : 0;
   if (vdt == SFL_F64) r = build_plan<double>(pl, A, B, s);
   else if (vdt == SFL_F32) r = build_plan<float>(pl, A, B, s);
@@ -339,6 +372,7 @@ int sfl_plan_get_stats(const sfl_plan *plan, sfl_plan_stats *st) {
   st->lanes_A = pl.A.lpr; st->lanes_At = pl.T.lpr;
   st->value_dtype = pl.vdt; st->unmatched = pl.unmatched ? 1 : 0;
   st->device_bytes = pl.bytes;
+  st->tiled_At = pl.T.orig != nullptr ? 1 : 0;
   return SFL_OK;
 }
 

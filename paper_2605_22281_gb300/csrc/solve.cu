@@ -137,6 +137,15 @@ cudaError_t launch_ls(const LsParams &p, int cluster, size_t smem, cudaStream_t 
   return cudaLaunchKernelEx(&cfg, ls_step_kernel, p);
 }
 
+// Whether the warps of a product CTA take the CTA's 32-row blocks in turn
+// (instead of one balanced range each): for pixel-tiled operators whose CTAs
+// own at least eight 16 x 16 tiles, so the eight warps share one tile's
+// gathers; below that a CTA's rows fit in about a tile anyway, and splitting
+// a few blocks among eight warps would leave some idle.
+bool interleave_rows(const StoredCsr &M, int row_ctas) {
+  return M.orig != nullptr && row_ctas > 0 && M.rows / row_ctas >= 8 * 256;
+}
+
 // Row range of each of W warps over the rows of M, balanced by row cost
 // (4 * ceil(len / unit) + 1 per row, exclusive scan, binary search per warp).
 // Temporaries are freed before returning; the stream is synchronised.
@@ -207,6 +216,7 @@ struct Engine {
   static SpmvParams<VT, XT> base_params(const Plan &pl, const Session &se, const StoredCsr &M, int mode) {
     SpmvParams<VT, XT> p{};
     p.rowptr = M.rowptr; p.col = M.col; p.val = (const VT *)M.val; p.rows = M.rows;
+    p.orig = M.orig;
     p.mode = mode;
     p.method = se.key.method;
     p.ell = se.key.ell;
@@ -297,6 +307,7 @@ struct Engine {
     }
     const int grid = fwd ? se.grid_spmv_A : se.grid_spmv_T;
     const size_t smem = fwd ? se.smem_A : se.smem_T;
+    p.interleave = interleave_rows(M, grid - 1);
     return O::spmv(p, M.lpr, true, grid, smem, s, pdl) == cudaSuccess ? SFL_OK : SFL_ECUDA;
   }
   static int k_orth(const Plan &pl, const Session &se, int side, cudaStream_t s, bool pdl = false) {
@@ -706,8 +717,10 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
   const StoredCsr &M = which == 0 ? pl.A : pl.T;
   SpmvParams<VT, XT> p{};
   p.rowptr = M.rowptr; p.col = M.col; p.val = (const VT *)M.val; p.rows = M.rows;
+  p.orig = M.orig;
   p.mode = kModeApply;
   const int grid = pl.num_sms * 2;
+  p.interleave = interleave_rows(M, grid);
   const size_t smem = spmv_smem_bytes(M.lpr, sizeof(typename AccT<XT>::T));
   SFL_CU(Ops<VT, XT>::set_smem(M.lpr, true, smem));
   if (std::is_same<XT, double>::value) {

@@ -370,6 +370,72 @@ def test_dense_sketch_argument_checks(ct64):
         plan.solve("sflsqr", dev(p.b), s=61, window=2, maxit=10, sketch_matrix=Sn)   # wrong width
 
 
+# ---------------------------------------------------------------- pixel-tiled A^T / B
+
+@pytest.mark.parametrize("vdt", ["f64", "f32", "bf16"])
+def test_tiled_transpose_products_are_bit_identical(ct64, ct64_unmatched, vdt):
+    """Rows of A^T (or B) stored in 16x16 pixel tiles: every row is summed in
+    the same order as in natural order, so the products agree bit for bit."""
+    p, _ = ct64
+    N = int(round(math.sqrt(p.A.shape[1])))
+    rng = np.random.default_rng(5)
+    for A, B in ((p.A, None), (ct64_unmatched[0], ct64_unmatched[1])):
+        plain = G.Plan(A, B, value_dtype=vdt)
+        tiled = G.Plan(A, B, value_dtype=vdt, image_shape=(N, N))
+        assert tiled.stats()["tiled_At"] == 1 and plain.stats()["tiled_At"] == 0
+        w = dev(rng.standard_normal(A.shape[0]))
+        z = dev(rng.standard_normal(A.shape[1]))
+        assert torch.equal(plain.apply(w, transpose=True), tiled.apply(w, transpose=True))
+        assert torch.equal(plain.apply(z), tiled.apply(z))
+        plain.close(); tiled.close()
+
+
+@pytest.mark.slow
+def test_tiled_transpose_with_interleaved_warps_is_bit_identical():
+    """1024x1024 operator (481M entries, BF16 values): A^T has 2^20 rows, so a
+    tiled plan's CTAs own many tiles and their warps take the blocks in turn;
+    every row is still summed exactly as in natural order."""
+    A = wl.siddon_projector(1024, 360, wl.detector_bins(1024))
+    plain = G.Plan(A, value_dtype="bf16")
+    tiled = G.Plan(A, value_dtype="bf16", image_shape=(1024, 1024))
+    w = dev(np.random.default_rng(9).standard_normal(A.shape[0]))
+    assert torch.equal(plain.apply(w, transpose=True), tiled.apply(w, transpose=True))
+    plain.close(); tiled.close()
+
+
+def test_tiled_plan_solves_match_oracle(ct64, ct64_unmatched):
+    p, _ = ct64
+    N = int(round(math.sqrt(p.A.shape[1])))
+    st = p.settings
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    plan = G.Plan(p.A, image_shape=(N, N))
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                            maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], x_history=True,
+                            relres_history=True)
+    assert info.status == r.status
+    assert_iterates_match(r, h["x"], h["relres"], info, tol)
+    plan.close()
+    A, B, x_true, b, en, _ = ct64_unmatched
+    plan = G.Plan(A, B, image_shape=(N, N))
+    tol = O.discrepancy_tol(1.01, en, np.linalg.norm(b))
+    r = run_oracle_sflsmr(A.scipy(), b, 201, 8, 43, 150, tol, 2, tau=O.Reweighting(1e-4), AT=B.scipy())
+    x, info, h = plan.solve("sflsmr", dev(b), s=201, zeta=8, seed=43, window=2, maxit=150, noise_norm=en, eta=1.01,
+                            precond="reweight", irw_eps=1e-4, x_history=True, relres_history=True)
+    assert info.status == r.status
+    assert_iterates_match(r, h["x"], h["relres"], info, tol)
+    plan.close()
+
+
+def test_image_shape_must_match_the_columns(ct64):
+    p, _ = ct64
+    N = int(round(math.sqrt(p.A.shape[1])))
+    with pytest.raises(G.N.SflError):
+        G.Plan(p.A, image_shape=(N - 1, N))
+    with pytest.raises(G.N.SflError):
+        G.Plan(p.A, image_shape=(0, N))
+
+
 # ---------------------------------------------------------------- determinism and drivers
 
 def test_bitwise_reproducible_and_drivers_agree(ct64_unmatched):
