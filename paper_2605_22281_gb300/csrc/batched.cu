@@ -85,6 +85,7 @@ struct BEngine {
   static cudaError_t spmm_t(const S &se, const StoredCsr &M, const int32_t *wrow, int mode, cudaStream_t s) {
     BSpmmArgs a{M.rowptr, M.col, M.val, M.rows, wrow, mode};
     a.orig = M.orig;
+    a.slot = M.lpr * load_width(se.plan->vdt);
     dim3 grid(se.G_rows, (se.key.R + T - 1) / T);
     bspmm_kernel<VT, XT, T><<<grid, kThreads, 0, s>>>(se.bp, a);
     return cudaGetLastError();
@@ -480,6 +481,7 @@ struct AEngine {
     BSpmmArgs a{M.rowptr, M.col, M.val, M.rows, fwd ? se.wrowA : se.wrowT, kBSpmmExplicit, x, y, accumulate,
                 se.a_kr, j};
     a.orig = M.orig;
+    a.slot = M.lpr * load_width(se.plan->vdt);
     dim3 grid(se.G_rows, (se.key.R + 63) / 64);
     if (se.ld >= 64) { bspmm_kernel<VT, XT, 64><<<grid, kThreads, 0, s>>>(se.bp, a); }
     else {

@@ -82,10 +82,15 @@ __global__ void padded_len_kernel(const int32_t *rowptr, int64_t rows, int P, co
 
 // One warp per stored row: copy input row order[r] (or r) into its padded
 // slot.  Padding entries take the row's last column (or 0 for an empty row)
-// and value 0.
+// and value 0.  Inside every chunk slot of str = lanes * P entries (the last
+// one holding A = its length / P lanes' chunks) entry w goes to position
+// (w mod A) * P + w / A: lane g's P-entry chunk holds entries g, g + A, ...
+// of the slot, so the lanes of one gather instruction read consecutive
+// entries of the row (neighbouring pixels along a ray share cache sectors).
 template <typename OT>
 __global__ void fill_padded_kernel(const int32_t *rowptr, const int32_t *col, const OT *val, int64_t rows,
-                                   const int32_t *order, const int32_t *prow, int32_t *pcol, OT *pval) {
+                                   const int32_t *order, const int32_t *prow, int P, int str, int32_t *pcol,
+                                   OT *pval) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -93,9 +98,13 @@ __global__ void fill_padded_kernel(const int32_t *rowptr, const int32_t *col, co
     const int64_t src = order ? order[r] : r;
     const int b = rowptr[src], e = rowptr[src + 1], pb = prow[r], pe = prow[r + 1];
     const int last = e > b ? col[e - 1] : 0;
-    for (int i = lane; i < pe - pb; i += 32) {
-      if (b + i < e) { pcol[pb + i] = col[b + i]; pval[pb + i] = val[b + i]; }
-      else { pcol[pb + i] = last; pval[pb + i] = cvt<OT>(0.0); }
+    const int plen = pe - pb;
+    for (int i = lane; i < plen; i += 32) {
+      const int slot0 = i / str * str, w = i - slot0;
+      const int A = min(str, plen - slot0) / P;
+      const int d = pb + slot0 + (w % A) * P + w / A;
+      if (b + i < e) { pcol[d] = col[b + i]; pval[d] = val[b + i]; }
+      else { pcol[d] = last; pval[d] = cvt<OT>(0.0); }
     }
   }
 }
@@ -238,13 +247,13 @@ static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const i
   if (pnnz < nnz) return SFL_EINVAL;   // padded count overflowed int32
   if ((r = plan_alloc(pl, (void **)&out.col, sizeof(int32_t) * (pnnz + 8)))) return r;
   if ((r = plan_alloc(pl, (void **)&out.val, sizeof(OT) * (pnnz + 8)))) return r;
-  if (rows > 0) {
-    fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.orig, out.rowptr, out.col,
-                                                 (OT *)out.val);
-    SFL_CU(cudaGetLastError());
-  }
   out.rows = rows; out.cols = cols; out.nnz = nnz; out.pnnz = pnnz;
   out.lpr = pl.lpr_override ? pl.lpr_override : choose_lpr(pnnz, rows, P);
+  if (rows > 0) {
+    fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.orig, out.rowptr, P, out.lpr * P,
+                                                 out.col, (OT *)out.val);
+    SFL_CU(cudaGetLastError());
+  }
   return SFL_OK;
 }
 
