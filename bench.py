@@ -262,7 +262,8 @@ def batched_variant(args, G, wl, np, torch):
     R = p.b.shape[1]
     kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"], eta=st["eta"])
     B = torch.as_tensor(np.ascontiguousarray(p.b.T), device="cuda")
-    plan32 = G.Plan(p.A, value_dtype="f32", image_shape=img(args, p))
+    # batched solves: rows in the operator's entry order, no pixel tiles (the SpMM walks one row per warp)
+    plan32 = G.Plan(p.A, value_dtype="f32", slot_layout="operator")
     t0 = time.perf_counter()
     X, infos = G.solve_batched(plan32, B, p.noise_norm, **kw)       # builds and tunes the session
     torch.cuda.synchronize()
@@ -331,11 +332,11 @@ def mixed_variant(args, G, wl, np, torch):
     xs = {}
     for vdt in ("bf16", "f32", "f64"):
         plan = G.Plan(p.A, value_dtype=vdt, image_shape=img(args, p))
-        x, info, _ = plan.solve("sflsqr", b, **kw)
+        x, info, _ = plan.solve("sflsqr", b, driver=args.driver, **kw)
         reps = max(1, min(args.steps, 3))
         e0.record(stream)
         for _ in range(reps):
-            plan.solve("sflsqr", b, out=x, sync=False, **kw)
+            plan.solve("sflsqr", b, out=x, sync=False, driver=args.driver, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps

@@ -82,12 +82,19 @@ typedef struct sfl_plan sfl_plan;
  * = row * image_cols + col).  When given, the plan stores the rows of A^T (or
  * B) in 16 x 16 pixel tiles, so that the rays one tile's rows gather stay in
  * the L1 cache; outputs still go to each row's own index, and every row's
- * sum is formed exactly as without tiles (bit-identical products). */
+ * sum is formed exactly as without tiles (bit-identical products).
+ * slot_layout: 0 (default) stores every chunk slot of a row (lanes_per_row x
+ * load-width entries) lane-interleaved, so the lanes of one gather read
+ * neighbouring entries (faster single-solve products on ray-ordered rows);
+ * 1 keeps each row in the caller's entry order (faster batched SpMMs, which
+ * walk a row one entry at a time).  Results depend on it only through the
+ * summation order. */
 typedef struct {
   sfl_dtype value_dtype;
   int32_t lanes_per_row;
   uint64_t max_device_bytes;
   int32_t image_rows, image_cols;
+  int32_t slot_layout;
 } sfl_plan_opts;
 
 /* Solve options (the Require lines of Algorithms 1 and 2).

@@ -28,7 +28,7 @@ class Csr(ctypes.Structure):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("value_dtype", ctypes.c_int), ("lanes_per_row", ctypes.c_int32), ("max_device_bytes", ctypes.c_uint64),
-                ("image_rows", ctypes.c_int32), ("image_cols", ctypes.c_int32)]
+                ("image_rows", ctypes.c_int32), ("image_cols", ctypes.c_int32), ("slot_layout", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):

@@ -63,10 +63,12 @@ class Plan:
     back-projector B (n x m), stored on the GPU in `value_dtype`.  image_shape
     (rows, cols) with rows * cols = n declares the n-side an image (column
     index row * cols + col): the plan then stores the rows of A^T / B in pixel
-    tiles (same products bit for bit, better cache reuse)."""
+    tiles (same products bit for bit, better cache reuse).  slot_layout:
+    'interleaved' (single solves) or 'operator' (batched solves) entry order
+    inside each row's chunk slots."""
 
     def __init__(self, A, B=None, value_dtype: str = "f64", device: str | int = 0, max_device_bytes: int = 0,
-                 lanes_per_row: int = 0, image_shape: tuple | None = None):
+                 lanes_per_row: int = 0, image_shape: tuple | None = None, slot_layout: str = "interleaved"):
         _require_cuda()
         self.lib = N.load()
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
@@ -76,7 +78,10 @@ class Plan:
             if B is not None:
                 cb, keep_b = _dev_csr(B.rowptr, B.colidx, B.values, B.shape, self.device)
             ir, ic = (int(image_shape[0]), int(image_shape[1])) if image_shape is not None else (0, 0)
-            po = N.PlanOpts(N.DTYPE[value_dtype], lanes_per_row, max_device_bytes, ir, ic)
+            if slot_layout not in ("interleaved", "operator"):
+                raise ValueError(slot_layout)
+            po = N.PlanOpts(N.DTYPE[value_dtype], lanes_per_row, max_device_bytes, ir, ic,
+                            0 if slot_layout == "interleaved" else 1)
             h = ctypes.c_void_p()
             st = N.check(self.lib.sfl_plan_create(ctypes.byref(h), ctypes.byref(ca),
                                                   ctypes.byref(cb) if cb is not None else None,

@@ -82,12 +82,33 @@ struct BEngine {
   }
 
   template <int T>
-  static cudaError_t spmm_t(const S &se, const StoredCsr &M, const int32_t *wrow, int mode, cudaStream_t s) {
-    BSpmmArgs a{M.rowptr, M.col, M.val, M.rows, wrow, mode};
+  static const void *spmm_fn_t(bool orig, bool ilv) {
+    if (orig && ilv) return (const void *)bspmm_kernel<VT, XT, T, true, true>;
+    if (orig) return (const void *)bspmm_kernel<VT, XT, T, true, false>;
+    if (ilv) return (const void *)bspmm_kernel<VT, XT, T, false, true>;
+    return (const void *)bspmm_kernel<VT, XT, T, false, false>;
+  }
+  static const void *spmm_fn(int T, bool orig, bool ilv) {
+    return T == 8 ? spmm_fn_t<8>(orig, ilv) : T == 16 ? spmm_fn_t<16>(orig, ilv)
+                  : T == 32 ? spmm_fn_t<32>(orig, ilv) : spmm_fn_t<64>(orig, ilv);
+  }
+
+  // the instance for the plan's row order (ORIG) and slot layout (ILV)
+  template <int T>
+  static void launch_spmm(const S &se, const StoredCsr &M, BSpmmArgs &a, dim3 grid, cudaStream_t s) {
     a.orig = M.orig;
     a.slot = M.lpr * load_width(se.plan->vdt);
+    if (M.orig && M.interleaved) bspmm_kernel<VT, XT, T, true, true><<<grid, kThreads, 0, s>>>(se.bp, a);
+    else if (M.orig) bspmm_kernel<VT, XT, T, true, false><<<grid, kThreads, 0, s>>>(se.bp, a);
+    else if (M.interleaved) bspmm_kernel<VT, XT, T, false, true><<<grid, kThreads, 0, s>>>(se.bp, a);
+    else bspmm_kernel<VT, XT, T, false, false><<<grid, kThreads, 0, s>>>(se.bp, a);
+  }
+
+  template <int T>
+  static cudaError_t spmm_t(const S &se, const StoredCsr &M, const int32_t *wrow, int mode, cudaStream_t s) {
+    BSpmmArgs a{M.rowptr, M.col, M.val, M.rows, wrow, mode};
     dim3 grid(se.G_rows, (se.key.R + T - 1) / T);
-    bspmm_kernel<VT, XT, T><<<grid, kThreads, 0, s>>>(se.bp, a);
+    launch_spmm<T>(se, M, a, grid, s);
     return cudaGetLastError();
   }
   static cudaError_t spmm(const S &se, int mode, cudaStream_t s) {
@@ -266,12 +287,13 @@ struct BEngine {
     // row CTAs: as many as stay resident for every tile width (the records and
     // the row partition depend on it, so it is one number per session)
     int occ = 8;
-    for (auto f : {(const void *)bspmm_kernel<VT, XT, 8>, (const void *)bspmm_kernel<VT, XT, 16>,
-                   (const void *)bspmm_kernel<VT, XT, 32>, (const void *)bspmm_kernel<VT, XT, 64>}) {
-      int nb = 0;
-      SFL_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, 0));
-      occ = std::min(occ, std::max(nb, 1));
-    }
+    for (const StoredCsr *M : {&pl.A, &pl.T})
+      for (int T : {8, 16, 32, 64}) {
+        int nb = 0;
+        SFL_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmm_fn(T, M->orig != nullptr, M->interleaved),
+                                                             kThreads, 0));
+        occ = std::min(occ, std::max(nb, 1));
+      }
     se->G_rows = std::min(pl.num_sms * occ, kBMaxRowCtas);
     se->bp.rcap = std::max(se->G_orth, se->G_rows);
     int r;
@@ -480,13 +502,12 @@ struct AEngine {
     const StoredCsr &M = fwd ? se.plan->A : se.plan->T;
     BSpmmArgs a{M.rowptr, M.col, M.val, M.rows, fwd ? se.wrowA : se.wrowT, kBSpmmExplicit, x, y, accumulate,
                 se.a_kr, j};
-    a.orig = M.orig;
-    a.slot = M.lpr * load_width(se.plan->vdt);
     dim3 grid(se.G_rows, (se.key.R + 63) / 64);
-    if (se.ld >= 64) { bspmm_kernel<VT, XT, 64><<<grid, kThreads, 0, s>>>(se.bp, a); }
-    else {
+    if (se.ld >= 64) {
+      BEngine<VT, XT>::template launch_spmm<64>(se, M, a, grid, s);
+    } else {
       grid.y = (se.key.R + 7) / 8;
-      bspmm_kernel<VT, XT, 8><<<grid, kThreads, 0, s>>>(se.bp, a);
+      BEngine<VT, XT>::template launch_spmm<8>(se, M, a, grid, s);
     }
     return cudaGetLastError();
   }

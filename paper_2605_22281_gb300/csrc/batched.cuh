@@ -280,9 +280,10 @@ struct BSpmmArgs {
   int accumulate;
   const int *kr;
   int jstep;
-  const int32_t *orig;       // stored row i is operator row orig[i] (nullptr: identity)
-  int slot;                  // entries per chunk slot of the stored rows (lanes per row x load width)
+  const int32_t *orig;       // stored row i is operator row orig[i] (used by the ORIG instances)
+  int slot;                  // entries per lane-interleaved chunk slot (used by the ILV instances)
 };
+
 
 // Largest chunk slot of a stored row (32 lanes x 8 entries).
 constexpr int kMaxSlot = 256;
@@ -295,16 +296,20 @@ template <> struct XT2<float> { using T = float2; };
 // them).  A CTA owns a contiguous range of rows and its warps take every
 // kWarps-th row, so they work on adjacent rows (neighbouring rays, or pixels)
 // at the same time and share the gathered lines in L1.  A warp owns one row at
-// a time and walks its entries in the operator's own order (the plan stores
-// each chunk slot lane-interleaved for the single-solve products: entry
-// q * A + c of a slot of A chunks sits at c * P + q), so neighbouring warps
-// gather the same X rows at about the same time; lanes split the tile's RHS
+// a time and walks its stored entries in order; lanes split the tile's RHS
 // (T >= 32: T/32 per lane) or, for T < 32, 32/T lane groups split the entries.
 // Every (row, RHS) sum is ((s0 + s1) + (s2 + s3)) with s_j the in-order sum of
-// the entries e = j (mod 4) of the row, whatever T is, so the tile width chosen
-// by the tuner never changes a result bit.  Window dots <v_a, y> and ||y||^2
-// per RHS go to the records.
-template <typename VT, typename XT, int T>
+// the stored entries e = j (mod 4) of the row, whatever T is, so the tile
+// width chosen by the tuner never changes a result bit.  Window dots
+// <v_a, y> and ||y||^2 per RHS go to the records.  ORIG: stored row i is
+// operator row orig[i] (pixel-tiled plans); a compile-time flag, because the
+// dependent index load costs the untiled loops 13%.  ILV: the plan stores
+// every chunk slot lane-interleaved (entry q * A + c of a slot of A chunks at
+// c * PL + q); the warp's lanes then load the slot's chunks at once (vector
+// loads spread over the lanes) and the warp reads it back in operator order
+// through shared memory, so the streams, and every bit, are those of an
+// operator-order plan's walk.
+template <typename VT, typename XT, int T, bool ORIG, bool ILV>
 __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmmArgs a) {
   static_assert(T == 8 || T == 16 || T == 32 || T == 64, "tile widths");
   constexpr int PL = LoadWidth<VT>::P;
@@ -312,8 +317,6 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
   constexpr int NG = T >= 32 ? 1 : 32 / T;        // lane groups splitting the entries
   using ACC = typename AccT<XT>::T;
   __shared__ double scr[kWarps][T];
-  __shared__ int s_col[kWarps][kMaxSlot];        // one slot of the warp's row, operator order
-  __shared__ typename AccT<XT>::T s_val[kWarps][kMaxSlot];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = *p.kstep + 1;
   const int tile0 = blockIdx.y * T;
@@ -360,42 +363,67 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
       for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int q = 0; q < RPL; ++q) s[j][q] = (ACC)0;
-      // the row's entries in operator order, slot by slot: lane c loads chunk
-      // c of the slot (PL indices and values, vector loads) and writes entry
-      // e = q * A + c (stored at c * PL + q) to the warp's buffer at e; the
-      // warp then reads PL entries at a time (broadcast) in order.  Group g
-      // takes the entries e = j (mod 4) with j = g (mod NG).
-      int *bc = s_col[warp];
-      ACC *bv = s_val[warp];
-      for (int slot0 = 0; slot0 < end - beg; slot0 += a.slot) {
-        const int A = min(a.slot, end - beg - slot0) / PL;
-        __syncwarp();
-        if (lane < A) {
-          Chunk<VT, PL> ch;
-          ch.load(a.col, (const VT *)a.val, beg + slot0 + lane * PL);
+      if constexpr (ILV) {
+        // slot by slot: lane c < A loads chunk c and writes entry q * A + c to
+        // the warp's buffer; the warp reads PL entries at a time in order
+        // (slot0 and e0 are multiples of 4: entry e0 + u is in stream u mod 4)
+        __shared__ int s_col[kWarps][kMaxSlot];
+        __shared__ ACC s_val[kWarps][kMaxSlot];
+        int *bc = s_col[warp];
+        ACC *bv = s_val[warp];
+        for (int slot0 = 0; slot0 < end - beg; slot0 += a.slot) {
+          const int A = min(a.slot, end - beg - slot0) / PL;
+          __syncwarp();
+          if (lane < A) {
+            Chunk<VT, PL> ch;
+            ch.load(a.col, (const VT *)a.val, beg + slot0 + lane * PL);
 #pragma unroll
-          for (int q = 0; q < PL; ++q) {
-            bc[q * A + lane] = ch.c[q];
-            bv[q * A + lane] = (ACC)ch.v[q];
+            for (int q = 0; q < PL; ++q) {
+              bc[q * A + lane] = ch.c[q];
+              bv[q * A + lane] = (ACC)ch.v[q];
+            }
+          }
+          __syncwarp();
+          for (int e0 = 0; e0 < A * PL; e0 += PL) {
+#pragma unroll
+            for (int u = 0; u < PL; ++u) {
+              const int j = u & 3;
+              if (NG > 1 && (j % NG) != g) continue;
+              const XT *xr = x + (size_t)bc[e0 + u] * p.ld + tile0;
+              const ACC v = bv[e0 + u];
+              if (RPL == 2) {
+                if (act[0] || act[1]) {
+                  const typename XT2<XT>::T xv = *reinterpret_cast<const typename XT2<XT>::T *>(xr + 2 * lane);
+                  s[j][0] += v * (ACC)xv.x;
+                  s[j][RPL - 1] += v * (ACC)xv.y;
+                }
+              } else if (act[0]) {
+                s[j][0] += v * (ACC)xr[T >= 32 ? lane : gl];
+              }
+            }
           }
         }
-        __syncwarp();
-        const int L = A * PL;
-        for (int e0 = 0; e0 < L; e0 += PL) {
+      } else {
+        // chunks of PL entries (rows start at multiples of PL), every lane
+        // loads the same chunk (broadcast); group g takes the entries
+        // e = j (mod 4) with j = g (mod NG)
+#pragma unroll 2
+        for (int off = beg; off < end; off += PL) {
+          Chunk<VT, PL> c;
+          c.load(a.col, (const VT *)a.val, off);
 #pragma unroll
-          for (int u = 0; u < PL; ++u) {
-            const int j = u & 3;                // e0 is a multiple of PL (>= 4): e = j (mod 4)
+          for (int e = 0; e < PL; ++e) {
+            const int j = e & 3;
             if (NG > 1 && (j % NG) != g) continue;
-            const XT *xr = x + (size_t)bc[e0 + u] * p.ld + tile0;
-            const ACC v = bv[e0 + u];
+            const XT *xr = x + (size_t)c.c[e] * p.ld + tile0;
             if (RPL == 2) {
               if (act[0] || act[1]) {
                 const typename XT2<XT>::T xv = *reinterpret_cast<const typename XT2<XT>::T *>(xr + 2 * lane);
-                s[j][0] += v * (ACC)xv.x;
-                s[j][RPL - 1] += v * (ACC)xv.y;
+                s[j][0] += (ACC)c.v[e] * (ACC)xv.x;
+                s[j][RPL - 1] += (ACC)c.v[e] * (ACC)xv.y;
               }
             } else if (act[0]) {
-              s[j][0] += v * (ACC)xr[T >= 32 ? lane : gl];
+              s[j][0] += (ACC)c.v[e] * (ACC)xr[T >= 32 ? lane : gl];
             }
           }
         }
@@ -414,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
         }
         const ACC tot = (s0 + s1) + (s2 + s3);
         if (owner && act[q]) {
-          XT *yo = y + (size_t)(a.orig ? a.orig[row] : row) * p.ld + rr[q];
+          XT *yo = y + (size_t)(ORIG ? a.orig[row] : row) * p.ld + rr[q];
           if (a.accumulate) { *yo = (XT)((ACC)*yo + tot); continue; }
           *yo = (XT)tot;
           const double yd = (double)(XT)tot;
@@ -452,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
 #pragma unroll
         for (int q = 0; q < RPL; ++q)
           if (act[q]) {
-            const size_t ei = (size_t)(a.orig ? a.orig[row] : row) * p.ld + rr[q];
+            const size_t ei = (size_t)(ORIG ? a.orig[row] : row) * p.ld + rr[q];
             d[q] += (double)y[ei] * (double)wv[ei];
           }
     store(d, 1 + w);

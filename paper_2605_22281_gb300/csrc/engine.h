@@ -19,6 +19,7 @@ struct StoredCsr {
   int32_t *col = nullptr;
   void *val = nullptr;
   int32_t *orig = nullptr;   // stored row i is row orig[i] of the operator (nullptr: the identity)
+  bool interleaved = false;  // chunk slots stored lane-interleaved (else the caller's entry order)
   int64_t rows = 0, cols = 0, nnz = 0, pnnz = 0;
   int lpr = 32;
 };
@@ -78,6 +79,7 @@ struct Plan {
   bool unmatched = false;
   int lpr_override = 0;      // lanes per row requested by the caller (0: from the row lengths)
   int img_rows = 0, img_cols = 0;   // n-side image shape: A^T / B rows stored in pixel tiles
+  int slot_layout = 0;              // 0: lane-interleaved chunk slots, 1: the caller's entry order
   StoredCsr A, T;   // T: CSR of A^T (transposed copy) or of B
   uint64_t bytes = 0, cap = 0;
   std::vector<void *> allocs;

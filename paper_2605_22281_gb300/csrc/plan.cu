@@ -87,6 +87,7 @@ __global__ void padded_len_kernel(const int32_t *rowptr, int64_t rows, int P, co
 // (w mod A) * P + w / A: lane g's P-entry chunk holds entries g, g + A, ...
 // of the slot, so the lanes of one gather instruction read consecutive
 // entries of the row (neighbouring pixels along a ray share cache sectors).
+// str = 0 keeps the caller's order.
 template <typename OT>
 __global__ void fill_padded_kernel(const int32_t *rowptr, const int32_t *col, const OT *val, int64_t rows,
                                    const int32_t *order, const int32_t *prow, int P, int str, int32_t *pcol,
@@ -100,9 +101,12 @@ __global__ void fill_padded_kernel(const int32_t *rowptr, const int32_t *col, co
     const int last = e > b ? col[e - 1] : 0;
     const int plen = pe - pb;
     for (int i = lane; i < plen; i += 32) {
-      const int slot0 = i / str * str, w = i - slot0;
-      const int A = min(str, plen - slot0) / P;
-      const int d = pb + slot0 + (w % A) * P + w / A;
+      int d = pb + i;                       // str == 0: the caller's order
+      if (str > 0) {
+        const int slot0 = i / str * str, w = i - slot0;
+        const int A = min(str, plen - slot0) / P;
+        d = pb + slot0 + (w % A) * P + w / A;
+      }
       if (b + i < e) { pcol[d] = col[b + i]; pval[d] = val[b + i]; }
       else { pcol[d] = last; pval[d] = cvt<OT>(0.0); }
     }
@@ -250,8 +254,9 @@ static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const i
   out.rows = rows; out.cols = cols; out.nnz = nnz; out.pnnz = pnnz;
   out.lpr = pl.lpr_override ? pl.lpr_override : choose_lpr(pnnz, rows, P);
   if (rows > 0) {
-    fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.orig, out.rowptr, P, out.lpr * P,
-                                                 out.col, (OT *)out.val);
+    out.interleaved = pl.slot_layout == 0;
+    fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.orig, out.rowptr, P,
+                                                 out.interleaved ? out.lpr * P : 0, out.col, (OT *)out.val);
     SFL_CU(cudaGetLastError());
   }
   return SFL_OK;
@@ -352,6 +357,8 @@ int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const s
   const int img_r = popts ? popts->image_rows : 0, img_c = popts ? popts->image_cols : 0;
   if (img_r < 0 || img_c < 0 || (img_r == 0) != (img_c == 0)) return SFL_EINVAL;
   if (img_r > 0 && (int64_t)img_r * img_c != A->cols) return SFL_EINVAL;
+  const int layout = popts ? popts->slot_layout : 0;
+  if (layout != 0 && layout != 1) return SFL_EINVAL;
   sfl_plan *p = new sfl_plan();
   Plan &pl = p->impl;
   cudaGetDevice(&pl.device);
@@ -360,6 +367,7 @@ int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const s
   pl.unmatched = B != nullptr;
   pl.lpr_override = lpr;
   pl.img_rows = img_r; pl.img_cols = img_c;
+  pl.slot_layout = layout;
   pl.cap = popts ? popts->max_device_bytes : 0;
   if (vdt == SFL_F64) r = build_plan<double>(pl, A, B, s);
   else if (vdt == SFL_F32) r = build_plan<float>(pl, A, B, s);

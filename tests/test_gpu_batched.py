@@ -193,3 +193,17 @@ def test_tiled_plan_batched_matches_natural_order(ct64_batch):
         assert i0[j].iters == i1[j].iters
         assert rel(X1[j].cpu().numpy(), X0[j].cpu().numpy()) <= 1e-12
     tiled.close()
+
+
+def test_slot_layouts_give_the_same_batched_results(ct64_batch):
+    """A plan whose rows keep the caller's entry order: the SpMM sums every row
+    in another order, nothing else changes."""
+    A, B, en, _, plan = ct64_batch
+    op = G.Plan(A, slot_layout="operator")
+    X0, i0 = G.solve_batched(plan, dev(B), en, s=200, zeta=8, seed=42, window=2, maxit=100)
+    X1, i1 = G.solve_batched(op, dev(B), en, s=200, zeta=8, seed=42, window=2, maxit=100)
+    assert [i.iters for i in i0] == [i.iters for i in i1]
+    for j in range(B.shape[0]):
+        assert rel(X1[j].cpu().numpy(), X0[j].cpu().numpy()) <= 1e-12
+    op.close()
+

@@ -427,6 +427,24 @@ def test_tiled_plan_solves_match_oracle(ct64, ct64_unmatched):
     plan.close()
 
 
+def test_operator_order_plan_matches_oracle(ct64):
+    """Rows kept in the caller's entry order (no lane-interleaved slots): the
+    single-solve products still cover every entry once."""
+    p, _ = ct64
+    st = p.settings
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    plan = G.Plan(p.A, slot_layout="operator")
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                            maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], x_history=True,
+                            relres_history=True)
+    assert_iterates_match(r, h["x"], h["relres"], info, tol)
+    w = dev(np.random.default_rng(4).standard_normal(p.A.shape[0]))
+    ref = p.A.scipy().T @ w.cpu().numpy()
+    assert rel(plan.apply(w, transpose=True).cpu().numpy(), ref) <= 1e-14
+    plan.close()
+
+
 def test_image_shape_must_match_the_columns(ct64):
     p, _ = ct64
     N = int(round(math.sqrt(p.A.shape[1])))
