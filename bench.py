@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-tiles", action="store_true",
                     help="store the rows of A^T / B in natural order instead of 16x16 pixel tiles")
+    ap.add_argument("--slot-layout", default="interleaved", choices=["interleaved", "operator"],
+                    help="entry order inside the chunk slots of the single-solve plans (main and mixed legs)")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched multi-sinogram leg (64 x 512^2, FP32) and print its JSON")
     ap.add_argument("--only-mixed", action="store_true",
@@ -331,7 +333,7 @@ def mixed_variant(args, G, wl, np, torch):
     out = {"image": f"{N}x{N}", "m": p.A.shape[0], "n": p.A.shape[1], "nnz": int(p.A.nnz)}
     xs = {}
     for vdt in ("bf16", "f32", "f64"):
-        plan = G.Plan(p.A, value_dtype=vdt, image_shape=img(args, p))
+        plan = G.Plan(p.A, value_dtype=vdt, image_shape=img(args, p), slot_layout=args.slot_layout)
         x, info, _ = plan.solve("sflsqr", b, driver=args.driver, **kw)
         reps = max(1, min(args.steps, 3))
         e0.record(stream)
@@ -435,7 +437,7 @@ def run_ours(args):
     kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
               noise_norm=float(p.noise_norm[0]), eta=st["eta"], precond=precond, irw_eps=st.get("irw_eps", 1e-4))
     t_plan = time.perf_counter()
-    plan = G.Plan(p.A, p.B, value_dtype="f64", image_shape=img(args, p))
+    plan = G.Plan(p.A, p.B, value_dtype="f64", image_shape=img(args, p), slot_layout=args.slot_layout)
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t_plan
     stats = plan.stats()
