@@ -522,9 +522,19 @@ def run_ours(args):
         torch.cuda.synchronize()
         t32 = e0.elapsed_time(e1)
         err32 = float(np.linalg.norm(x32.cpu().numpy() - p.x_true) / np.linalg.norm(p.x_true))
+        # per-product launch times of the same solve (profiled driver), against the measured HBM peak
+        _, _, hp32 = plan32.solve(method, b_dev, driver="profiled", **kw)
+        k32 = {}
+        for name, nnz, rows, cols, nd in (("spmv_fwd", stats["nnz_A"], m, n, ell + 1),
+                                          ("spmv_bwd", stats["nnz_At"], n, m, ell)):
+            avg_ms = hp32["kernel_ms"][name] / max(hp32["kernel_launches"][name], 1)
+            nbytes = spmv_bytes(nnz, rows, cols, 4, 4, nd, 0)
+            k32[name] = {"avg_us": 1000 * avg_ms, "bytes": nbytes,
+                         "hbm_frac_of_measured": nbytes / (avg_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
         variants["f32_values_vectors"] = {"value": i32.iters * args.steps / (t32 / 1000), "unit": "iters/s",
                                           "ms_per_step": t32 / args.steps, "iters": i32.iters,
-                                          "rel_error_vs_x_true": err32, "fp64_rel_error_vs_x_true": err}
+                                          "rel_error_vs_x_true": err32, "fp64_rel_error_vs_x_true": err,
+                                          "kernels": k32}
         plan32.close()
 
     if not args.no_variants:
