@@ -13,30 +13,38 @@ template <typename XT> __global__ void convert_out_kernel(const XT *x, double *y
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += st) y[i] = (double)x[i];
 }
 
+// The product kernel for lanes per row `lpr`: the vector pass (mat false),
+// the matrix form, or the matrix form writing through an original-row map
+// (orig: pixel-tiled A^T / B rows).
+template <typename VT, typename XT, bool ORIG>
+static void (*spmv_mat_fn(int lpr))(SpmvParams<VT, XT>) {
+  constexpr int M = ORIG ? kSpmvMatOrig : kSpmvMat;
+  if (lpr == 4) return spmv_fused_kernel<VT, XT, 4, M>;
+  if (lpr == 8) return spmv_fused_kernel<VT, XT, 8, M>;
+  if (lpr == 16) return spmv_fused_kernel<VT, XT, 16, M>;
+  return spmv_fused_kernel<VT, XT, 32, M>;
+}
 template <typename VT, typename XT>
-static const void *spmv_fn(int lpr, bool mat) {
-  if (!mat) return (const void *)spmv_fused_kernel<VT, XT, 1, false>;
-  if (lpr == 4) return (const void *)spmv_fused_kernel<VT, XT, 4, true>;
-  if (lpr == 8) return (const void *)spmv_fused_kernel<VT, XT, 8, true>;
-  if (lpr == 16) return (const void *)spmv_fused_kernel<VT, XT, 16, true>;
-  return (const void *)spmv_fused_kernel<VT, XT, 32, true>;
+static void (*spmv_fn(int lpr, bool mat, bool orig))(SpmvParams<VT, XT>) {
+  if (!mat) return spmv_fused_kernel<VT, XT, 1, kSpmvVec>;
+  return orig ? spmv_mat_fn<VT, XT, true>(lpr) : spmv_mat_fn<VT, XT, false>(lpr);
 }
 
 template <typename VT, typename XT>
 cudaError_t Ops<VT, XT>::spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, int grid, size_t smem, cudaStream_t s,
                               bool pdl) {
-  void (*kern)(SpmvParams<VT, XT>);
-  if (!mat) kern = spmv_fused_kernel<VT, XT, 1, false>;
-  else if (lpr == 4) kern = spmv_fused_kernel<VT, XT, 4, true>;
-  else if (lpr == 8) kern = spmv_fused_kernel<VT, XT, 8, true>;
-  else if (lpr == 16) kern = spmv_fused_kernel<VT, XT, 16, true>;
-  else kern = spmv_fused_kernel<VT, XT, 32, true>;
-  return launch_k(kern, dim3(grid), dim3(kThreads), smem, s, pdl, p);
+  return launch_k(spmv_fn<VT, XT>(lpr, mat, mat && p.orig != nullptr), dim3(grid), dim3(kThreads), smem, s, pdl, p);
 }
 
+// Both matrix forms (with and without the row map) get the same limit.
 template <typename VT, typename XT>
 cudaError_t Ops<VT, XT>::set_smem(int lpr, bool mat, size_t smem) {
-  return cudaFuncSetAttribute(spmv_fn<VT, XT>(lpr, mat), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute((const void *)spmv_fn<VT, XT>(lpr, mat, false),
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && mat)
+    e = cudaFuncSetAttribute((const void *)spmv_fn<VT, XT>(lpr, mat, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  return e;
 }
 
 template <typename VT, typename XT>
@@ -45,12 +53,18 @@ cudaError_t Ops<VT, XT>::set_orth_smem(size_t smem) {
                               (int)smem);
 }
 
+// Resident CTAs per SM of the product kernel (the smaller of the two matrix forms).
 template <typename VT, typename XT>
 int Ops<VT, XT>::spmv_occupancy(int lpr, bool mat, size_t smem) {
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_fn<VT, XT>(lpr, mat), kThreads, smem) != cudaSuccess)
-    return 0;
-  return nb;
+  int best = 1 << 20;
+  for (int orig = 0; orig <= (mat ? 1 : 0); ++orig) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)spmv_fn<VT, XT>(lpr, mat, orig != 0),
+                                                      kThreads, smem) != cudaSuccess)
+      return 0;
+    best = std::min(best, nb);
+  }
+  return best;
 }
 
 template <typename VT, typename XT>

@@ -233,7 +233,7 @@ struct RowBlocks {
 // owning row r and every FP64 instruction on a full warp.  Stored row r goes
 // to output index orig[r] (when the rows are stored in another order).  LPR = 1
 // is the vector pass (no matrix; the row value is b_r).
-template <typename VT, typename XT, int LPR, bool MAT>
+template <typename VT, typename XT, int LPR, bool MAT, bool ORIG>
 __device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, RowBlocks rb,
                                             const XT *__restrict__ x, XT *y, typename AccT<XT>::T *stash) {
   constexpr int G = 32 / LPR;
@@ -269,7 +269,7 @@ __device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, RowBloc
     } else {
       if (valid) yv = (ACC)p.b[row];
     }
-    if (valid) y[(MAT && p.orig) ? p.orig[row] : row] = (XT)yv;
+    if (valid) y[ORIG ? p.orig[row] : row] = (XT)yv;
     const double yd = valid ? (double)yv : 0.0;
     nrm += yd * yd;
   }
@@ -279,7 +279,7 @@ __device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, RowBloc
 // Window dots <v_j, y> over the warp's rows, after the products: lane r
 // re-reads the output of row r it stored itself, so the row loop above keeps
 // no per-window registers.
-template <typename XT, int ND>
+template <typename XT, int ND, bool ORIG>
 __device__ __forceinline__ void spmv_window_dots(RowBlocks rb, const int32_t *orig, const XT *y, const XT *win,
                                                  int64_t wst, int R, int lo, double (&acc)[ND + 1]) {
   const int lane = threadIdx.x & 31;
@@ -289,7 +289,7 @@ __device__ __forceinline__ void spmv_window_dots(RowBlocks rb, const int32_t *or
   for (int64_t row0 = rb.first; row0 < rb.end; row0 += rb.stride) {
     const int64_t row = row0 + lane;
     if (row < min(row0 + 32, rb.end)) {
-      const int64_t o = orig ? orig[row] : row;
+      const int64_t o = ORIG ? orig[row] : row;
       const double yd = (double)y[o];
 #pragma unroll
       for (int a = 0; a < ND; ++a) acc[1 + a] += (double)wv[a][o] * yd;
@@ -297,14 +297,14 @@ __device__ __forceinline__ void spmv_window_dots(RowBlocks rb, const int32_t *or
   }
 }
 
-template <typename XT, int ND>
+template <typename XT, int ND, bool ORIG>
 __device__ __forceinline__ void spmv_finish(RowBlocks rb, const int32_t *orig, const XT *y, const XT *win,
                                             int64_t wst, int R, int lo, double nrm, double *outpart, double *wsum) {
   double acc[ND + 1];
   acc[0] = nrm;
 #pragma unroll
   for (int a = 1; a <= ND; ++a) acc[a] = 0.0;
-  spmv_window_dots<XT, ND>(rb, orig, y, win, wst, R, lo, acc);
+  spmv_window_dots<XT, ND, ORIG>(rb, orig, y, win, wst, R, lo, acc);
   __syncthreads();
   store_partials<ND + 1>(acc, wsum, outpart);
 }
@@ -379,12 +379,18 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
   }
 }
 
+// Forms of the product kernel: the vector pass (y = b), the matrix form, and
+// the matrix form writing through an original-row map (pixel-tiled rows; a
+// compile-time form, so untiled operators carry no dependent index load).
+enum : int { kSpmvVec = 0, kSpmvMat = 1, kSpmvMatOrig = 2 };
+
 // Fused SpMV of one step.  In the solve modes past the first vector pass,
 // CTA 0 books the step's scalars (above) while the other CTAs run the rows:
 // outputs are stored unscaled (y = A x for the stored, unnormalised x), with
 // ||y||^2 and the window dots <v_j, y> as per-CTA records (CTA 0's are zero).
-template <typename VT, typename XT, int LPR, bool MAT>
+template <typename VT, typename XT, int LPR, int FORM>
 __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kernel(SpmvParams<VT, XT> p) {
+  constexpr bool MAT = FORM != kSpmvVec, ORIG = FORM == kSpmvMatOrig;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SolveState sst;
   __shared__ double wsum[(kMaxWindow + 2) * kThreads];   // reduction scratch
@@ -456,24 +462,24 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
     rb.stride = 32;
     rb.end = bound(gw + 1);
   }
-  const double nrm = spmv_rows<VT, XT, LPR, MAT>(p, rb, x, y, stash);
+  const double nrm = spmv_rows<VT, XT, LPR, MAT, ORIG>(p, rb, x, y, stash);
   if (!reduce) return;
-  const int32_t *og = MAT ? p.orig : nullptr;
+  const int32_t *og = p.orig;
   if (!MAT) {     // vector pass: no window dots
-    spmv_finish<XT, 0>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum);
+    spmv_finish<XT, 0, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum);
     return;
   }
   switch (nd) {   // the window size is a compile-time constant inside the tail
-    case 0: spmv_finish<XT, 0>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 1: spmv_finish<XT, 1>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 2: spmv_finish<XT, 2>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 3: spmv_finish<XT, 3>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 4: spmv_finish<XT, 4>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 5: spmv_finish<XT, 5>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 6: spmv_finish<XT, 6>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 7: spmv_finish<XT, 7>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    case 8: spmv_finish<XT, 8>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
-    default: spmv_finish<XT, 9>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 0: spmv_finish<XT, 0, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 1: spmv_finish<XT, 1, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 2: spmv_finish<XT, 2, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 3: spmv_finish<XT, 3, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 4: spmv_finish<XT, 4, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 5: spmv_finish<XT, 5, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 6: spmv_finish<XT, 6, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 7: spmv_finish<XT, 7, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    case 8: spmv_finish<XT, 8, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
+    default: spmv_finish<XT, 9, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
   }
 }
 
