@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--mixed-size", type=int, default=1024,
                     help="image size of the mixed-precision leg (1024: the configured workload; smaller sizes keep "
                          "its geometry recipe, for profiling)")
+    ap.add_argument("--only-decay", action="store_true",
+                    help="run only the residual-size study (dense 1024 x 512, Gaussian sketches) and print its JSON")
     ap.add_argument("--only-diff", action="store_true",
                     help="run only the differentiable leg (16 x 256^2, fixed k, forward + adjoint) and print its JSON")
     ap.add_argument("--driver", default="graph", choices=["graph", "host_loop"],
@@ -403,6 +405,40 @@ def diff_variant(args, G, wl, np, torch):
             "note": "gradients checked in tests (FP64 oracle autograd, finite differences)"}
 
 
+def decay_variant(args, G, wl, np, torch):
+    """The paper's residual-size study through the GPU path: A (1024 x 512) with
+    singular values rho^(1-i), x_true = ones, ||b_true|| = 1, 10% noise; 20 steps of
+    sLSQR and sLSMR with Gaussian sketches of s = 2k + 1 = 41 rows (explicit dense
+    sketch matrices, identity operator, window 8), against the optimal residual of
+    the same Krylov space (LSQR: SciPy's lsqr, 20 iterations, on the host).  Per rho:
+    LSQR's ||A x - b|| / ||b|| and the sketched residuals relative to it, averaged
+    over 5 sketches."""
+    import scipy.sparse.linalg as spla
+    k, s, m, n, draws = 20, 41, 1024, 512, 5
+    Sm = torch.empty((s, m), dtype=torch.float64, device="cuda")
+    Sn = torch.empty((s, n), dtype=torch.float64, device="cuda")
+    out = {"m": m, "n": n, "k": k, "s": s, "noise": 0.10, "sketches": draws, "window": 8, "rho": {}}
+    for rho in (1.01, 1.03, 1.05, 1.08, 1.10, 1.15):
+        A, b, _, _ = wl.decaying(m, n, rho, 70, 0.10)
+        x_opt = spla.lsqr(A, b, atol=0.0, btol=0.0, conlim=0.0, iter_lim=k)[0]
+        r_opt = float(np.linalg.norm(A @ x_opt - b))
+        plan = G.Plan(wl.dense_csr(A))
+        bd = torch.as_tensor(b, device="cuda")
+        rq, rm = [], []
+        for t in range(draws):
+            g = np.random.default_rng(500 + t)
+            Sm.copy_(torch.as_tensor(g.standard_normal((s, m))))
+            Sn.copy_(torch.as_tensor(g.standard_normal((s, n))))
+            xq, _, _ = plan.solve("sflsqr", bd, s=s, window=8, maxit=k, sketch_matrix=Sm)
+            xm, _, _ = plan.solve("sflsmr", bd, s=s, window=8, maxit=k, sketch_matrix=Sn, sketch_matrix_stop=Sm)
+            rq.append(float(np.linalg.norm(A @ xq.cpu().numpy() - b)) / r_opt)
+            rm.append(float(np.linalg.norm(A @ xm.cpu().numpy() - b)) / r_opt)
+        plan.close()
+        out["rho"][f"{rho:.2f}"] = {"lsqr_rel_residual": r_opt / float(np.linalg.norm(b)),
+                                    "slsqr_over_lsqr": statistics.mean(rq), "slsmr_over_lsqr": statistics.mean(rm)}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -411,7 +447,8 @@ def run_ours(args):
     import workloads as wl
     from paper_2605_22281_gb300 import api as G
 
-    for flag, leg in (("only_batched", batched_variant), ("only_mixed", mixed_variant), ("only_diff", diff_variant)):
+    for flag, leg in (("only_batched", batched_variant), ("only_mixed", mixed_variant), ("only_diff", diff_variant),
+                      ("only_decay", decay_variant)):
         if getattr(args, flag):
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             print(json.dumps(leg(args, G, wl, np, torch)), flush=True)
@@ -541,6 +578,7 @@ def run_ours(args):
         variants["batched_ct512_64rhs_f32"] = batched_variant(args, G, wl, np, torch)
         variants["mixed_ct1024_sflsqr"] = mixed_variant(args, G, wl, np, torch)
         variants["diff_ct256_16rhs_fixed_k"] = diff_variant(args, G, wl, np, torch)
+        variants["decay_study_gaussian"] = decay_variant(args, G, wl, np, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

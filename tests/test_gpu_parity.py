@@ -360,6 +360,59 @@ def test_gaussian_sketch_matches_oracle(ct64, method):
     assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
 
 
+@pytest.fixture(scope="module")
+def decay105():
+    """The residual-size study's problem at rho = 1.05: dense 1024 x 512, 10% noise."""
+    A, b, _, _ = wl.decaying(1024, 512, 1.05, 70, 0.10)
+    return A, b, G.Plan(wl.dense_csr(A))
+
+
+@pytest.mark.parametrize("method", ["sflsqr", "sflsmr"])
+def test_decaying_dense_operator_with_gaussian_sketch_matches_oracle(decay105, method):
+    """20 steps, window 8, Gaussian s = 2k + 1 = 41: per-iteration parity on a
+    dense operator stored as CSR."""
+    A, b, plan = decay105
+    m, n = A.shape
+    k, s = 20, 41
+    g = np.random.default_rng(500)
+    Sm, Sn = g.standard_normal((s, m)), g.standard_normal((s, n))
+    if method == "sflsqr":
+        r = O.sflsqr(A, b, O.DenseSketch(Sm), maxit=k, tol=0.0, ell=8, record_x=True, keep_basis=True)
+        r.M = Sm @ (A @ r.Z)
+        x, info, h = plan.solve("sflsqr", dev(b), s=s, window=8, maxit=k, x_history=True, relres_history=True,
+                                sketch_matrix=dev(Sm))
+    else:
+        r = O.sflsmr(A, b, O.DenseSketch(Sn), S_stop=O.DenseSketch(Sm), maxit=k, tol=0.0, ell=8, record_x=True,
+                     keep_basis=True)
+        r.M = Sn @ (A.T @ (A @ r.Z))
+        x, info, h = plan.solve("sflsmr", dev(b), s=s, window=8, maxit=k, x_history=True, relres_history=True,
+                                sketch_matrix=dev(Sn), sketch_matrix_stop=dev(Sm))
+    assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
+
+
+def test_residual_size_study_ordering():
+    """The paper's residual-size study (rho = 1.01, 10% noise, 20 steps,
+    Gaussian s = 41), on the GPU path: sLSQR's residual ends well above LSQR's
+    (about 30% in the paper), and sLSMR's stays the closer of the two to it
+    (means over three sketches)."""
+    A, b, _, _ = wl.decaying(1024, 512, 1.01, 70, 0.10)
+    m, n = A.shape
+    k, s = 20, 41
+    r_opt = np.linalg.norm(A @ spla.lsqr(A, b, atol=0.0, btol=0.0, conlim=0.0, iter_lim=k)[0] - b)
+    plan = G.Plan(wl.dense_csr(A))
+    rq, rm = [], []
+    for t in range(3):
+        g = np.random.default_rng(500 + t)
+        Sm, Sn = dev(g.standard_normal((s, m))), dev(g.standard_normal((s, n)))
+        xq, _, _ = plan.solve("sflsqr", dev(b), s=s, window=8, maxit=k, sketch_matrix=Sm)
+        xm, _, _ = plan.solve("sflsmr", dev(b), s=s, window=8, maxit=k, sketch_matrix=Sn, sketch_matrix_stop=Sm)
+        rq.append(np.linalg.norm(A @ xq.cpu().numpy() - b) / r_opt)
+        rm.append(np.linalg.norm(A @ xm.cpu().numpy() - b) / r_opt)
+    plan.close()
+    assert 1.05 < np.mean(rq) < 1.8
+    assert abs(np.mean(rm) - 1.0) < abs(np.mean(rq) - 1.0)
+
+
 def test_dense_sketch_argument_checks(ct64):
     p, plan = ct64
     m, n = p.A.shape

@@ -165,6 +165,30 @@ def add_noise(b_true: np.ndarray, level: float, rng: np.random.Generator) -> tup
     return b_true + e, float(np.linalg.norm(e))
 
 
+def dense_csr(M: np.ndarray) -> CSR:
+    """A dense matrix stored as CSR (every entry kept)."""
+    m, n = M.shape
+    rowptr = np.arange(0, (m + 1) * n, n, dtype=np.int64)
+    colidx = np.tile(np.arange(n, dtype=np.int32), m)
+    return CSR((m, n), rowptr, colidx, np.ascontiguousarray(M, dtype=np.float64).ravel())
+
+
+def decaying(m: int, n: int, rho: float, seed: int, level: float) -> tuple:
+    """The artificial problem of the paper's residual-size study: A = U diag(rho^(1-i)) V^T
+    with seeded random orthogonal U (m x n) and V (n x n), x_true = ones, A scaled so
+    that ||b_true|| = 1, and b = b_true + e with ||e|| = level.  Returns
+    (A dense, b, b_true, ||e||)."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sv = rho ** (1.0 - np.arange(1, n + 1))
+    A = (U * sv) @ V.T
+    A /= np.linalg.norm(A @ np.ones(n))
+    b_true = A @ np.ones(n)
+    b, en = add_noise(b_true, level, rng)
+    return A, b, b_true, en
+
+
 @dataclass
 class Problem:
     """One synthetic CT problem: operator(s), phantoms, data and solver settings."""
