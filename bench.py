@@ -127,6 +127,17 @@ def img(args, p):
     return None if getattr(args, "no_tiles", False) else (p.N, p.N)
 
 
+def adjoint_mismatch(p, np):
+    """|y^T A x - x^T B y| for seeded random unit x, y: how far an unmatched
+    back-projector B is from A^T (None when the plan uses A^T itself)."""
+    if p.B is None:
+        return None
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(p.A.shape[1]); x /= np.linalg.norm(x)
+    y = rng.standard_normal(p.A.shape[0]); y /= np.linalg.norm(y)
+    return float(abs(y @ (p.A.scipy() @ x) - x @ (p.B.scipy() @ y)))
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for name in ("kernels.cuh", "common.cuh"):
@@ -177,9 +188,10 @@ def oracle_solve(workload: str, maxit_cap: int | None, problem=None):
     return r, time.perf_counter() - t0
 
 
-def cpu_baseline_subprocess(workload: str, maxit_cap: int | None) -> dict:
-    """Time the oracle in a child process pinned to one BLAS/OpenMP thread."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def cpu_baseline_subprocess(workload: str, maxit_cap: int | None, threads: int = 1) -> dict:
+    """Time the oracle in a child process with `threads` BLAS/OpenMP threads."""
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     cmd = [sys.executable, os.path.abspath(__file__), "--workload", workload, "--oracle-sample",
            str(maxit_cap if maxit_cap else -1)]
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1200)
@@ -584,9 +596,15 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res = cpu_baseline_subprocess(args.workload, None)
         if "iters" in res:
+            host = os.cpu_count() or 1
             cpu = {"value": res["iters"] / res["seconds"], "unit": "iters/s", "cores": 1, "kind": "oracle",
                    "sample": f"one full oracle solve of {args.workload} ({res['iters']} steps, "
-                             f"{res['seconds']:.1f} s, FP64, 1 thread)"}
+                             f"{res['seconds']:.1f} s, FP64, 1 thread)", "host_cores": host}
+            # the same solve with every host core for BLAS (the sparse products stay single-threaded)
+            res_all = cpu_baseline_subprocess(args.workload, None, host)
+            if "iters" in res_all:
+                cpu["all_cores"] = {"value": res_all["iters"] / res_all["seconds"], "cores": host,
+                                    "seconds": res_all["seconds"]}
         else:
             cpu = {"value": None, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": res.get("error", "")}
 
@@ -604,7 +622,7 @@ def run_ours(args):
                            "rel_error_vs_x_true": err, "plan_build_s": t_plan,
                            "l2": "inputs larger than L2 (operators 464 MB > 129 MB); no flush",
                            "parallelism": f"replicas x{world} (independent problems)",
-                           "driver": args.driver},
+                           "driver": args.driver, "unmatched_adjoint_mismatch": adjoint_mismatch(p, np)},
                 "roofline": roof, "kernels": kern, "kernel_breakdown": breakdown, "clocks": clocks,
                 "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps,
