@@ -88,7 +88,7 @@ struct SpmvParams {
   const VT *val;
   int64_t rows;
   const int32_t *wrow;      // row range of every warp (nnz balanced), gridDim*kWarps + 1 entries
-  const int32_t *orig;      // stored row i is operator row orig[i] (nullptr: identity); outputs go there
+  const int32_t *orig;      // stored row i is operator row orig[i] (read by the kSpmvMatOrig form)
   int interleave;           // 1: the warps of a CTA take its 32-row blocks in turn (tiled operators)
   int mode;
   int method;
@@ -161,9 +161,12 @@ template <> struct SpmvTune<__nv_bfloat16> { static constexpr int NCH = 2, MINB 
 template <typename XT> struct AccT { using T = XT; };
 
 // Row sum of one row for a group of LPR lanes (lane gl of the group), P
-// entries per lane per load.  Every iteration issues four loads per lane
-// (those past the row end are predicated off and contribute zero), so a row
-// costs ceil(loads / 4) memory round trips instead of one per leftover load.
+// entries per lane per chunk load.  Every iteration issues NCH chunk loads per
+// lane (those past the row end are predicated off and contribute zero), so a
+// row costs ceil(chunks / NCH) memory round trips instead of one per leftover
+// chunk.  With the plan's default slot layout every slot of LPR chunks is
+// stored lane-interleaved, so the gathers of one q across the group's lanes
+// read consecutive entries of the row.
 template <typename VT, int P>
 __device__ __forceinline__ void load_or_zero(Chunk<VT, P> &c, const int32_t *col, const VT *val, int off, bool ok) {
   if (ok) {
