@@ -6,7 +6,8 @@
  * of "Randomized Flexible LSQR and LSMR with applications to inverse problems":
  * a flexible Golub-Kahan process with window-ell partial orthogonalization
  * (eq. (FGK)), a flexible right operator z_k = tau_k(p_k) (eq. (modbasis)),
- * an s-row sparse-sign sketch of every new basis vector (Section 2.7), a small
+ * an s-row sketch of every new basis vector (sparse-sign, Section 2.7, or an
+ * explicit dense matrix such as a Gaussian one), a small
  * FP64 sketched least-squares solve per step, and the discrepancy-principle
  * stop of eq. (discrP) in Section 1.1.
  *
@@ -211,8 +212,10 @@ int sfl_plan_apply(sfl_plan *plan, int which, const double *x, double *y, sfl_st
 /* Algorithm 1, sFLSQR.  b: device FP64, length m.  x: device FP64, length n,
  * receives x_k = Z_k y_k at the stop step.  info: host, may be NULL; when
  * given, the call waits for the stream and fills it.  The first call for a new
- * (s, zeta, window, maxit, precond, vec_dtype, histories) combination
- * allocates a workspace and builds a CUDA graph that later calls reuse. */
+ * (s, zeta, window, maxit, precond, stop rule, vec_dtype, histories,
+ * orth_against_z, explicit sketch pointers) combination allocates a workspace
+ * and builds a CUDA graph that later calls reuse (the graph reads the
+ * explicit sketches' contents at run time). */
 int sflsqr_solve(sfl_plan *plan, const double *b, const sfl_opts *opts, double *x,
                  sfl_info *info, sfl_stream stream);
 
@@ -302,8 +305,8 @@ int sfl_sketch_apply_noalloc(uint64_t seed, int32_t s, int32_t zeta, const doubl
  * every basis vector of the solve: (2 maxit + 2) * max(m, n) * ld vectors of
  * that precision (ld = next power of two >= max(nrhs, 4)) plus O(nrhs * s *
  * maxit) doubles; SFL_ENOMEM if they do not fit.  Returns SFL_EINVAL for bad
- * arguments, SFL_EUNSUPPORTED for the reweighting preconditioner or a full
- * window. */
+ * arguments, SFL_EUNSUPPORTED for the reweighting preconditioner, a full
+ * window, orth_against_z = 1 or an explicit sketch. */
 int sflsqr_solve_batched(sfl_plan *plan, int32_t nrhs, const double *B, const double *noise_norms,
                          const sfl_opts *opts, double *X, sfl_info *infos, sfl_stream stream);
 
