@@ -498,18 +498,24 @@ struct AEngine {
     ascal_adj_kernel<<<(se.key.R + kWarps - 1) / kWarps, kThreads, 0, s>>>(a);
     return cudaGetLastError();
   }
+  template <int T>
+  static cudaError_t spmm_xt(const S &se, const StoredCsr &M, BSpmmArgs &a, cudaStream_t s) {
+    dim3 grid(se.G_rows, (se.key.R + T - 1) / T);
+    BEngine<VT, XT>::template launch_spmm<T>(se, M, a, grid, s);
+    return cudaGetLastError();
+  }
+  // y (=|+=) A x or A^T x with the session's tile width for that product (the
+  // forward's tuned or requested width; results do not depend on it)
   static cudaError_t spmm_x(const S &se, bool fwd, const XT *x, XT *y, int accumulate, int j, cudaStream_t s) {
     const StoredCsr &M = fwd ? se.plan->A : se.plan->T;
     BSpmmArgs a{M.rowptr, M.col, M.val, M.rows, fwd ? se.wrowA : se.wrowT, kBSpmmExplicit, x, y, accumulate,
                 se.a_kr, j};
-    dim3 grid(se.G_rows, (se.key.R + 63) / 64);
-    if (se.ld >= 64) {
-      BEngine<VT, XT>::template launch_spmm<64>(se, M, a, grid, s);
-    } else {
-      grid.y = (se.key.R + 7) / 8;
-      BEngine<VT, XT>::template launch_spmm<8>(se, M, a, grid, s);
+    switch (fwd ? se.tileA : se.tileT) {
+      case 8: return spmm_xt<8>(se, M, a, s);
+      case 16: return spmm_xt<16>(se, M, a, s);
+      case 32: return spmm_xt<32>(se, M, a, s);
+      default: return spmm_xt<64>(se, M, a, s);
     }
-    return cudaGetLastError();
   }
   static cudaError_t st_apply(const S &se, const double *V, int64_t vstride, int j, XT *out, cudaStream_t s) {
     const int64_t tot = se.bp.m * se.ld;
