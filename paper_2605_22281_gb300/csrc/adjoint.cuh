@@ -54,11 +54,15 @@ struct AArgs {
   int rcap;
 };
 
-template <typename XT>
-__device__ __forceinline__ double a_load(const AVec &v, size_t e, int r, int64_t i, const double *d) {
-  double x = v.dbl ? ((const double *)v.p)[e] : (double)((const XT *)v.p)[e];
-  if (v.scale) x *= v.scale[(size_t)r * v.sstride];
-  if (v.dmul) x *= d[i];
+// Element arithmetic of the passes runs in AT = AccT<XT>::T: FP64 for FP64
+// vectors, FP32 for FP32 vectors (whose entries are FP32-rounded anyway).  On
+// this GPU an FP64 instruction costs about 64 times an FP32 one, which made
+// the FP32 passes FP64-bound.  Sums across threads stay FP64.
+template <typename XT, typename AT = typename AccT<XT>::T>
+__device__ __forceinline__ AT a_load(const AVec &v, size_t e, int r, int64_t i, const double *d) {
+  AT x = v.dbl ? (AT)((const double *)v.p)[e] : (AT)((const XT *)v.p)[e];
+  if (v.scale) x *= (AT)v.scale[(size_t)r * v.sstride];
+  if (v.dmul) x *= (AT)d[i];
   return x;
 }
 
@@ -69,22 +73,23 @@ __device__ __forceinline__ bool a_active(const AArgs &a, int r) { return r < a.R
 // contiguous chunk of rows per CTA.
 template <typename XT>
 __global__ void __launch_bounds__(kThreads) adot_kernel(AArgs a) {
+  using AT = typename AccT<XT>::T;
   __shared__ double scr[kThreads];
   const int tid = threadIdx.x, per = kThreads / a.ld, r = tid % a.ld;
   const bool act = a_active(a, r);
-  double acc[kAdjNV][kAdjNV];
+  AT acc[kAdjNV][kAdjNV];
 #pragma unroll
   for (int x = 0; x < kAdjNV; ++x)
 #pragma unroll
-    for (int y = 0; y < kAdjNV; ++y) acc[x][y] = 0.0;
+    for (int y = 0; y < kAdjNV; ++y) acc[x][y] = (AT)0;
   const int64_t chunk = (a.len + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(a.len, i0 + chunk);
   if (act)
     for (int64_t i = i0 + tid / a.ld; i < i1; i += per) {
       const size_t e = (size_t)i * a.ld + r;
-      double val[kAdjNV];
+      AT val[kAdjNV];
 #pragma unroll
-      for (int x = 0; x < kAdjNV; ++x) val[x] = x < a.nv ? a_load<XT>(a.v[x], e, r, i, a.d) : 0.0;
+      for (int x = 0; x < kAdjNV; ++x) val[x] = x < a.nv ? a_load<XT>(a.v[x], e, r, i, a.d) : (AT)0;
 #pragma unroll
       for (int x = 0; x < kAdjNV; ++x)
 #pragma unroll
@@ -97,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) adot_kernel(AArgs a) {
 #pragma unroll
     for (int y = x; y < kAdjNV; ++y) {
       if (y >= a.nv) continue;
-      scr[tid] = acc[x][y];
+      scr[tid] = (double)acc[x][y];
       __syncthreads();
       if (tid < a.ld && tid < a.R) {
         double s = 0.0;
@@ -111,33 +116,34 @@ __global__ void __launch_bounds__(kThreads) adot_kernel(AArgs a) {
 // out_o (=|+=) sum_l coef[r][o][l] * v_l for every running right-hand side.
 template <typename XT>
 __global__ void __launch_bounds__(kThreads) alin_kernel(AArgs a) {
+  using AT = typename AccT<XT>::T;
   const int tid = threadIdx.x, per = kThreads / a.ld, r = tid % a.ld;
   if (!a_active(a, r)) return;
-  double c[kAdjNO][kAdjNV];
+  AT c[kAdjNO][kAdjNV];
 #pragma unroll
   for (int o = 0; o < kAdjNO; ++o)
 #pragma unroll
     for (int l = 0; l < kAdjNV; ++l)
-      c[o][l] = (o < a.no && l < a.nv) ? a.coef[((size_t)r * kAdjNO + o) * kAdjNV + l] : 0.0;
+      c[o][l] = (o < a.no && l < a.nv) ? (AT)a.coef[((size_t)r * kAdjNO + o) * kAdjNV + l] : (AT)0;
   const int64_t chunk = (a.len + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(a.len, i0 + chunk);
   for (int64_t i = i0 + tid / a.ld; i < i1; i += per) {
     const size_t e = (size_t)i * a.ld + r;
-    double val[kAdjNV];
+    AT val[kAdjNV];
 #pragma unroll
-    for (int l = 0; l < kAdjNV; ++l) val[l] = l < a.nv ? a_load<XT>(a.v[l], e, r, i, a.d) : 0.0;
+    for (int l = 0; l < kAdjNV; ++l) val[l] = l < a.nv ? a_load<XT>(a.v[l], e, r, i, a.d) : (AT)0;
 #pragma unroll
     for (int o = 0; o < kAdjNO; ++o) {
       if (o >= a.no) continue;
-      double s = 0.0;
+      AT s = (AT)0;
 #pragma unroll
       for (int l = 0; l < kAdjNV; ++l) s += c[o][l] * val[l];
       if (a.o[o].dbl) {
         double *q = (double *)a.o[o].p + e;
-        *q = a.o[o].accumulate ? *q + s : s;
+        *q = a.o[o].accumulate ? *q + (double)s : (double)s;
       } else {
         XT *q = (XT *)a.o[o].p + e;
-        *q = a.o[o].accumulate ? (XT)((double)*q + s) : (XT)s;
+        *q = a.o[o].accumulate ? (XT)((AT)*q + s) : (XT)s;
       }
     }
   }
@@ -148,34 +154,52 @@ __global__ void __launch_bounds__(kThreads) alin_kernel(AArgs a) {
 // (scale sigP_j); o[0] = pbar_j, o[1] = dbar accumulator (FP64).
 template <typename XT>
 __global__ void __launch_bounds__(kThreads) apre_kernel(AArgs a) {
+  using AT = typename AccT<XT>::T;
   const int tid = threadIdx.x, per = kThreads / a.ld, r = tid % a.ld;
   if (!a_active(a, r)) return;
   const int64_t chunk = (a.len + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(a.len, i0 + chunk);
   for (int64_t i = i0 + tid / a.ld; i < i1; i += per) {
     const size_t e = (size_t)i * a.ld + r;
-    const double zb = a_load<XT>(a.v[0], e, r, i, a.d) + a_load<XT>(a.v[1], e, r, i, a.d);
-    const double pj = a_load<XT>(a.v[2], e, r, i, a.d);
+    const AT zb = a_load<XT>(a.v[0], e, r, i, a.d) + a_load<XT>(a.v[1], e, r, i, a.d);
+    const AT pj = a_load<XT>(a.v[2], e, r, i, a.d);
     XT *pb = (XT *)a.o[0].p + e;
-    *pb = (XT)((double)*pb + a.d[i] * zb);
-    double *db = (double *)a.o[1].p + e;
-    *db += pj * zb;
+    *pb = (XT)((AT)*pb + (AT)a.d[i] * zb);
+    double *db = (double *)a.o[1].p + e;   // the d-bar accumulator stays FP64
+    *db += (double)(pj * zb);
   }
 }
 
-// Totals of dot pass records for one right-hand side: tot[a * 8 + b] for the
-// pairs a <= b < nv (one warp, lanes over the producer's CTAs).
-__device__ __forceinline__ void a_totals(const double *rec, int R, int rcap, int r, int G, int nv, int lane,
-                                         double (&tot)[kAdjNV][kAdjNV]) {
-  for (int x = 0; x < nv; ++x)
-    for (int y = x; y < nv; ++y) {
-      const double *rq = rec + ((size_t)(x * kAdjNV + y) * R + r) * rcap;
-      double s = 0.0;
-      for (int b = lane; b < G; b += 32) s += rq[b];
-      s = warp_sum(s);
-      tot[x][y] = s;
-      tot[y][x] = s;
+// Totals of dot pass records for one right-hand side: tot[x][y] for the
+// pairs x <= y < nv (and the mirrored entries).  Warp w sums the pairs w,
+// w + kWarps, ...: each lane issues its kRedLoads record loads at once (lanes
+// over the producer's CTAs), adds them as a fixed tree, then the lanes fold
+// with a butterfly.  tot: shared memory.  All threads call.
+__device__ __forceinline__ void a_totals(const double *rec, int R, int rcap, int r, int G, int nv,
+                                         double (*tot)[kAdjNV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int npair = nv * (nv + 1) / 2;
+  for (int q = warp; q < npair; q += kWarps) {
+    int x = 0, rem = q;   // pair q in row-major order of the upper triangle
+    while (rem >= nv - x) { rem -= nv - x; ++x; }
+    const int y = x + rem;
+    const double *rq = rec + ((size_t)(x * kAdjNV + y) * R + r) * rcap;
+    double v[kRedLoads];
+#pragma unroll
+    for (int u = 0; u < kRedLoads; ++u) {
+      const int b = lane + 32 * u;
+      v[u] = b < G ? rq[b] : 0.0;
     }
+#pragma unroll
+    for (int w = kRedLoads / 2; w >= 1; w >>= 1)
+#pragma unroll
+      for (int u = 0; u < w; ++u) v[u] += v[u + w];
+    double s = v[0];
+    for (int b = lane + 32 * kRedLoads; b < G; b += 32) s += rq[b];
+    s = warp_sum(s);
+    if (lane == 0) { tot[x][y] = s; tot[y][x] = s; }
+  }
+  __syncthreads();
 }
 
 enum AScalMode : int { kAScalM = 0, kAScalN = 1, kAScalFinal = 2, kAScalYbar = 3 };
@@ -192,7 +216,8 @@ struct AScalArgs {
   double *ybar;                  // [R][maxit] (kAScalYbar: columns j0..j0+nv-2)
 };
 
-// Per-RHS algebra of a reverse step (one warp per right-hand side).
+// Per-RHS algebra of a reverse step (one CTA per right-hand side: the
+// record totals use every warp, the algebra runs in thread 0).
 //  m side (vectors 0: wbar_{j+1}, 1: w_{j+1}, 2..: w_lo..w_j):
 //    s = <w_{j+1}, wbar>; q0 = (wbar - s w_{j+1}) / beta_{j+1};
 //    hbar_i = -(<w_i, q0> + sum_{i' > i} hbar_i' <w_i, w_i'>), i descending;
@@ -209,15 +234,14 @@ struct AScalArgs {
 //             o(1+np) = 0 into pbar_j's slot
 //  final (vectors 0: wbar_1, 1: w_1): o0 = (wbar_1 - <w_1, wbar_1> w_1) / beta_0
 //  ybar (vectors 0: xbar, 1..: z_j0 ...): ybar_{j0 + l - 1} = <xbar, z_{j0 + l - 1}>
-__global__ void ascal_adj_kernel(AScalArgs a) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r = blockIdx.x * (blockDim.x / 32) + warp;
+__global__ void __launch_bounds__(kThreads) ascal_adj_kernel(AScalArgs a) {
+  __shared__ double tot[kAdjNV][kAdjNV];
+  const int r = blockIdx.x;
   if (r >= a.R) return;
   const int j = a.j;
   if (a.mode != kAScalFinal && a.mode != kAScalYbar && j > a.kr[r]) return;
-  double tot[kAdjNV][kAdjNV];
-  a_totals(a.rec, a.R, a.rcap, r, a.G, a.nv, lane, tot);
-  if (lane != 0) return;
+  a_totals(a.rec, a.R, a.rcap, r, a.G, a.nv, tot);
+  if (threadIdx.x != 0) return;
   double *c = a.coef + (size_t)r * kAdjNO * kAdjNV;
   for (int q = 0; q < kAdjNO * kAdjNV; ++q) c[q] = 0.0;
   auto C = [&](int o, int l) -> double & { return c[o * kAdjNV + l]; };

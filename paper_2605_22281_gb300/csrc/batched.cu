@@ -495,7 +495,7 @@ struct AEngine {
     return cudaGetLastError();
   }
   static cudaError_t scal(const S &se, const AScalArgs &a, cudaStream_t s) {
-    ascal_adj_kernel<<<(se.key.R + kWarps - 1) / kWarps, kThreads, 0, s>>>(a);
+    ascal_adj_kernel<<<se.key.R, kThreads, 0, s>>>(a);
     return cudaGetLastError();
   }
   template <int T>
