@@ -308,7 +308,9 @@ template <> struct XT2<float> { using T = float2; };
 // c * PL + q); the warp's lanes then load the slot's chunks at once (vector
 // loads spread over the lanes) and the warp reads it back in operator order
 // through shared memory, so the streams, and every bit, are those of an
-// operator-order plan's walk.
+// operator-order plan's walk.  Both walks are unrolled 8 deep, so a warp has up
+// to 8 chunks' gathers in flight (the SpMM is bound by gather latency and L2
+// bandwidth, not by the matrix stream).
 template <typename VT, typename XT, int T, bool ORIG, bool ILV>
 __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmmArgs a) {
   static_assert(T == 8 || T == 16 || T == 32 || T == 64, "tile widths");
@@ -384,6 +386,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
             }
           }
           __syncwarp();
+#pragma unroll 8
           for (int e0 = 0; e0 < A * PL; e0 += PL) {
 #pragma unroll
             for (int u = 0; u < PL; ++u) {
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
         // chunks of PL entries (rows start at multiples of PL), every lane
         // loads the same chunk (broadcast); group g takes the entries
         // e = j (mod 4) with j = g (mod NG)
-#pragma unroll 2
+#pragma unroll 8
         for (int off = beg; off < end; off += PL) {
           Chunk<VT, PL> c;
           c.load(a.col, (const VT *)a.val, off);
