@@ -248,6 +248,38 @@ def test_sflsmr_normal_equation_stop_rule(ct64):
     assert_iterates_match(r, h["x"], h["relres"], info, 0.0)
 
 
+def ls_smem_doubles(s, maxit, cl, stage_q, stage_saz):
+    """The small least-squares kernel's shared-memory plan (doubles), restated:
+    six vectors of maxit + 2, three row blocks, slice partials, and the staged
+    Q / S_m A Z blocks with an odd row stride."""
+    rb = -(-s // cl)
+    n = 6 * (maxit + 2) + 3 * rb + max(rb, 256)
+    return n + (stage_q + stage_saz) * rb * (maxit | 1)
+
+
+@pytest.mark.parametrize("method", ["sflsqr", "sflsmr"])
+def test_largest_sketch_runs_the_unstaged_small_problem(ct64, method):
+    """s = 2048 (the largest sketch) with maxit = 300: a CTA's block of Q (and,
+    under sFLSMR's residual rule, of S_m A Z) no longer fits the kernel's
+    160 KB staging budget, so the small least-squares step reads them from
+    global memory.  Staging depends on s and maxit only; the discrepancy stop
+    ends the solve after a few well-conditioned steps."""
+    assert ls_smem_doubles(2048, 300, 16, 1, 0) * 8 > 160 * 1024
+    p, plan = ct64
+    st = p.settings
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    kw = dict(s=2048, zeta=8, seed=st["seed"], window=2, maxit=300, noise_norm=p.noise_norm[0], eta=st["eta"],
+              x_history=True, relres_history=True)
+    if method == "sflsqr":
+        r = run_oracle_sflsqr(p.A.scipy(), p.b, 2048, 8, st["seed"], 300, tol, 2)
+    else:
+        r = run_oracle_sflsmr(p.A.scipy(), p.b, 2048, 8, st["seed"], 300, tol, 2)
+    x, info, h = plan.solve(method, dev(p.b), **kw)
+    assert info.status == O.STOP_DISCREPANCY == r.status
+    assert 2 <= info.iters <= 40
+    assert_iterates_match(r, h["x"], h["relres"], info, tol)
+
+
 @pytest.mark.parametrize("precond,window", [("diag", 2), ("reweight", 2), ("diag", 5)])
 def test_sflsqr_literal_z_window(ct64, precond, window):
     """The z window taken as the stored z_j = tau(p_j) (the window loop of
