@@ -132,7 +132,7 @@ struct BEngine {
   }
   static cudaError_t sketch(const S &se, int mode, cudaStream_t s) {
     dim3 grid(se.key.s, (se.key.R + 31) / 32);
-    bsketch_kernel<XT><<<grid, kSkWarps * 32, 0, s>>>(se.bp, mode, se.B);
+    bsketch_kernel<XT><<<grid, kBSkWarps * 32, 0, s>>>(se.bp, mode, se.B);
     return cudaGetLastError();
   }
   static LsParams ls_params(const S &se) {

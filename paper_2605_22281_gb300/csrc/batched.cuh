@@ -494,45 +494,79 @@ __global__ void __launch_bounds__(kThreads, 4) bspmm_kernel(BParams<XT> p, BSpmm
 
 // Column k of S_m A Z for every running RHS (mode 0), or S_m b (mode 1, from
 // the FP64 column-major right-hand sides).  CTA (sketch row, 32-RHS chunk),
-// kSkWarps warps split the row's entries, lane = RHS.
+// lane = RHS.  A row holds zeta * m / s entries (thousands when s is small),
+// so kBSkWarps warps split them (warp w takes the entries w, w + kBSkWarps,
+// ...) and each warp keeps kBSkBatch table loads, then kBSkBatch gathers, in
+// flight: the walk is a chain of L2 round trips, not a bandwidth stream.
+// Entry u of a warp's batch goes to accumulator u mod 2; the warps' partial
+// sums are added as a fixed tree.
+constexpr int kBSkWarps = 16;
+constexpr int kBSkBatch = 8;
+
 template <typename XT>
-__global__ void __launch_bounds__(kSkWarps * 32) bsketch_kernel(BParams<XT> p, int mode, const double *B) {
-  __shared__ double part[kSkWarps][32];
+__global__ void __launch_bounds__(kBSkWarps * 32) bsketch_kernel(BParams<XT> p, int mode, const double *B) {
+  __shared__ double part[kBSkWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int row = blockIdx.x, r = blockIdx.y * 32 + lane;
   const bool act = r < p.R && b_active(p.st, r);
   const int k = *p.kstep + 1;
   const int b0 = p.skrow[row], b1 = p.skrow[row + 1];
-  double a0 = 0.0, a1 = 0.0;
+  constexpr int STEP = kBSkWarps * kBSkBatch;
+  double a = 0.0;
   if (act) {
     if (mode == 0) {
       const XT *v = p.what + (p.keep_what ? (size_t)(k - 1) * p.m * p.ld : 0) + r;
       using ACC = typename AccT<XT>::T;
-      ACC c0 = 0, c1 = 0;
-      int i = b0 + warp;
-      for (; i + kSkWarps < b1; i += 2 * kSkWarps) {
-        const uint32_t e0 = __ldg(p.skent + i), e1 = __ldg(p.skent + i + kSkWarps);
-        c0 += flip_sign((ACC)v[(size_t)(e0 & 0x7FFFFFFFu) * p.ld], e0);
-        c1 += flip_sign((ACC)v[(size_t)(e1 & 0x7FFFFFFFu) * p.ld], e1);
+      ACC c[2] = {(ACC)0, (ACC)0};
+      for (int i0 = b0 + warp; i0 < b1; i0 += STEP) {
+        uint32_t e[kBSkBatch];
+#pragma unroll
+        for (int u = 0; u < kBSkBatch; ++u) {
+          const int i = i0 + u * kBSkWarps;
+          e[u] = i < b1 ? __ldg(p.skent + i) : 0u;
+        }
+        ACC x[kBSkBatch];
+#pragma unroll
+        for (int u = 0; u < kBSkBatch; ++u)
+          x[u] = i0 + u * kBSkWarps < b1 ? flip_sign((ACC)v[(size_t)(e[u] & 0x7FFFFFFFu) * p.ld], e[u]) : (ACC)0;
+#pragma unroll
+        for (int u = 0; u < kBSkBatch; ++u)
+          if (i0 + u * kBSkWarps < b1) c[u & 1] += x[u];
       }
-      if (i < b1) {
-        const uint32_t e0 = __ldg(p.skent + i);
-        c0 += flip_sign((ACC)v[(size_t)(e0 & 0x7FFFFFFFu) * p.ld], e0);
-      }
-      a0 = (double)(c0 + c1);
+      a = (double)(c[0] + c[1]);
     } else {
       const double *v = B + (size_t)r * p.m;
-      for (int i = b0 + warp; i < b1; i += kSkWarps) {
-        const uint32_t e0 = __ldg(p.skent + i);
-        a0 += flip_sign(v[e0 & 0x7FFFFFFFu], e0);
+      double c[2] = {0.0, 0.0};
+      for (int i0 = b0 + warp; i0 < b1; i0 += STEP) {
+        uint32_t e[kBSkBatch];
+#pragma unroll
+        for (int u = 0; u < kBSkBatch; ++u) {
+          const int i = i0 + u * kBSkWarps;
+          e[u] = i < b1 ? __ldg(p.skent + i) : 0u;
+        }
+        double x[kBSkBatch];
+#pragma unroll
+        for (int u = 0; u < kBSkBatch; ++u)
+          x[u] = i0 + u * kBSkWarps < b1 ? flip_sign(v[e[u] & 0x7FFFFFFFu], e[u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < kBSkBatch; ++u)
+          if (i0 + u * kBSkWarps < b1) c[u & 1] += x[u];
       }
+      a = c[0] + c[1];
     }
   }
-  part[warp][lane] = a0 + a1;
+  part[warp][lane] = a;
   __syncthreads();
   if (warp != 0 || !act) return;
-  static_assert(kSkWarps == 4, "warp totals are added as a pair of pairs");
-  const double t = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
+  static_assert(kBSkWarps == 16, "warp totals are added as a 4-level tree");
+  double w[kBSkWarps];
+#pragma unroll
+  for (int q = 0; q < kBSkWarps; ++q) w[q] = part[q][lane];
+#pragma unroll
+  for (int h = kBSkWarps / 2; h >= 1; h >>= 1)
+#pragma unroll
+    for (int q = 0; q < h; ++q) w[q] += w[q + h];
+  const double t = w[0];
   if (mode == 0) {
     const double sc = p.isz * p.sigP[(size_t)r * (p.maxit + 1) + k];
     p.SAZ[((size_t)r * p.maxit + (k - 1)) * p.s + row] = t * sc;
