@@ -58,11 +58,33 @@ struct AArgs {
 // vectors, FP32 for FP32 vectors (whose entries are FP32-rounded anyway).  On
 // this GPU an FP64 instruction costs about 64 times an FP32 one, which made
 // the FP32 passes FP64-bound.  Sums across threads stay FP64.
-template <typename XT, typename AT = typename AccT<XT>::T>
-__device__ __forceinline__ AT a_load(const AVec &v, size_t e, int r, int64_t i, const double *d) {
+// The per-RHS scale of every input is loaded and converted once per thread
+// (a thread keeps one RHS); d[i] once per element.
+template <typename AT>
+struct AFactors {
+  AT sc[kAdjNV];   // scale[r * sstride], or 1
+  bool needd;      // some input is multiplied by d[i]
+};
+
+template <typename AT>
+__device__ __forceinline__ AFactors<AT> a_factors(const AArgs &a, int r) {
+  AFactors<AT> f;
+  f.needd = false;
+#pragma unroll
+  for (int l = 0; l < kAdjNV; ++l) {
+    const bool on = l < a.nv;
+    f.sc[l] = (on && a.v[l].scale) ? (AT)a.v[l].scale[(size_t)r * a.v[l].sstride] : (AT)1;
+    f.needd |= on && a.v[l].dmul;
+  }
+  return f;
+}
+
+// Element e of input v: (value * scale) * d[i], the factors precomputed.
+template <typename XT, typename AT>
+__device__ __forceinline__ AT a_elem(const AVec &v, size_t e, AT sc, AT di) {
   AT x = v.dbl ? (AT)((const double *)v.p)[e] : (AT)((const XT *)v.p)[e];
-  if (v.scale) x *= (AT)v.scale[(size_t)r * v.sstride];
-  if (v.dmul) x *= (AT)d[i];
+  if (v.scale) x *= sc;
+  if (v.dmul) x *= di;
   return x;
 }
 
@@ -84,18 +106,21 @@ __global__ void __launch_bounds__(kThreads) adot_kernel(AArgs a) {
     for (int y = 0; y < kAdjNV; ++y) acc[x][y] = (AT)0;
   const int64_t chunk = (a.len + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(a.len, i0 + chunk);
-  if (act)
+  if (act) {
+    const AFactors<AT> f = a_factors<AT>(a, r);
     for (int64_t i = i0 + tid / a.ld; i < i1; i += per) {
       const size_t e = (size_t)i * a.ld + r;
+      const AT di = f.needd ? (AT)a.d[i] : (AT)1;
       AT val[kAdjNV];
 #pragma unroll
-      for (int x = 0; x < kAdjNV; ++x) val[x] = x < a.nv ? a_load<XT>(a.v[x], e, r, i, a.d) : (AT)0;
+      for (int x = 0; x < kAdjNV; ++x) val[x] = x < a.nv ? a_elem<XT, AT>(a.v[x], e, f.sc[x], di) : (AT)0;
 #pragma unroll
       for (int x = 0; x < kAdjNV; ++x)
 #pragma unroll
         for (int y = x; y < kAdjNV; ++y)
           if (y < a.nv) acc[x][y] += val[x] * val[y];
     }
+  }
   // records, one pair at a time (threads sharing r added in order)
 #pragma unroll
   for (int x = 0; x < kAdjNV; ++x)
@@ -125,13 +150,15 @@ __global__ void __launch_bounds__(kThreads) alin_kernel(AArgs a) {
 #pragma unroll
     for (int l = 0; l < kAdjNV; ++l)
       c[o][l] = (o < a.no && l < a.nv) ? (AT)a.coef[((size_t)r * kAdjNO + o) * kAdjNV + l] : (AT)0;
+  const AFactors<AT> f = a_factors<AT>(a, r);
   const int64_t chunk = (a.len + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(a.len, i0 + chunk);
   for (int64_t i = i0 + tid / a.ld; i < i1; i += per) {
     const size_t e = (size_t)i * a.ld + r;
+    const AT di = f.needd ? (AT)a.d[i] : (AT)1;
     AT val[kAdjNV];
 #pragma unroll
-    for (int l = 0; l < kAdjNV; ++l) val[l] = l < a.nv ? a_load<XT>(a.v[l], e, r, i, a.d) : (AT)0;
+    for (int l = 0; l < kAdjNV; ++l) val[l] = l < a.nv ? a_elem<XT, AT>(a.v[l], e, f.sc[l], di) : (AT)0;
 #pragma unroll
     for (int o = 0; o < kAdjNO; ++o) {
       if (o >= a.no) continue;
@@ -159,12 +186,14 @@ __global__ void __launch_bounds__(kThreads) apre_kernel(AArgs a) {
   if (!a_active(a, r)) return;
   const int64_t chunk = (a.len + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(a.len, i0 + chunk);
+  const AFactors<AT> f = a_factors<AT>(a, r);
   for (int64_t i = i0 + tid / a.ld; i < i1; i += per) {
     const size_t e = (size_t)i * a.ld + r;
-    const AT zb = a_load<XT>(a.v[0], e, r, i, a.d) + a_load<XT>(a.v[1], e, r, i, a.d);
-    const AT pj = a_load<XT>(a.v[2], e, r, i, a.d);
+    const AT di = (AT)a.d[i];
+    const AT zb = a_elem<XT, AT>(a.v[0], e, f.sc[0], di) + a_elem<XT, AT>(a.v[1], e, f.sc[1], di);
+    const AT pj = a_elem<XT, AT>(a.v[2], e, f.sc[2], di);
     XT *pb = (XT *)a.o[0].p + e;
-    *pb = (XT)((AT)*pb + (AT)a.d[i] * zb);
+    *pb = (XT)((AT)*pb + di * zb);
     double *db = (double *)a.o[1].p + e;   // the d-bar accumulator stays FP64
     *db += (double)(pj * zb);
   }
