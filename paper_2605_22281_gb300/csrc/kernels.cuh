@@ -932,6 +932,10 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     return;
   }
   const int k = st->k + 1, kk = k - 1;
+  // state that only this kernel's final block writes, read here so that no
+  // later phase waits on a global load: the first diagonal of R (k > 1), the
+  // stop-ratio denominator (k > 1) and the stop tolerance
+  const double R11_prev = st->R11, den_prev = st->stop_den, tol = st->tol;
   const int s = p.s;
   const int RB = ls_rows_per_cta(s, CL);
   const int r0 = min(s, rank * RB), r1 = min(s, r0 + RB), nr = r1 - r0;
@@ -1128,7 +1132,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     for (int i = tid; i < nr; i += kThreads) crow[i] -= upd[i];
     rho2 = red[kk] - s_r2n;
     ce = red[kk + 1];
-    den = st->stop_den;
+    den = den_prev;
   } else {
     // first step: ||c||^2, <c, e> and the stop-ratio denominator ||s_b||
     // (sFLSQR), ||S_m b|| (sFLSMR, residual rule) or ||s_{A^T b}|| (sFLSMR,
@@ -1148,7 +1152,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
   }
   // rho^2 may round below zero for a dependent column (a breakdown); NaN stays NaN
   const double rho = rho2 >= 0.0 ? sqrt(rho2) : (rho2 < 0.0 ? 0.0 : rho2);
-  const double R11 = (k == 1) ? rho : st->R11;
+  const double R11 = (k == 1) ? rho : R11_prev;
   if (!(rho > 1e-300) || !(rho > 1e-14 * R11) || !isfinite(rho)) {
     cl.sync();   // no CTA leaves while a peer may still read its shared memory
     if (rank == 0 && tid == 0) {
@@ -1245,7 +1249,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     st->k = k;
     st->hist_pending = 1;
     int stop = 0;
-    if (rel < st->tol) stop = SFL_STOP_DISCREPANCY;
+    if (rel < tol) stop = SFL_STOP_DISCREPANCY;
     else if (lucky) stop = SFL_STOP_BREAKDOWN;
     else if (k >= p.maxit) stop = SFL_STOP_MAXIT;
     if (!isfinite(rel)) stop = kStopNonfinite;
