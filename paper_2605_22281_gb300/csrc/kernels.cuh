@@ -936,6 +936,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
   // later phase waits on a global load: the first diagonal of R (k > 1), the
   // stop-ratio denominator (k > 1) and the stop tolerance
   const double R11_prev = st->R11, den_prev = st->stop_den, tol = st->tol;
+  const double inv_den_prev = 1.0 / den_prev;   // used at the stop test (k > 1)
   const int s = p.s;
   const int RB = ls_rows_per_cta(s, CL);
   const int r0 = min(s, rank * RB), r1 = min(s, r0 + RB), nr = r1 - r0;
@@ -1101,7 +1102,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
   // second pass also totals ||c'||^2 and <c', e>, so that
   // rho^2 = ||c'||^2 - ||Q^T c'||^2 and <c'', e> = <c', e> - (Q^T c').(Q^T e),
   // whose last term is a product of two rounding-level vectors and is dropped.
-  double rho2, ce, den;
+  double rho2, ce, den, inv_den;
   if (kk > 0) {
     qt_partial(part0);
     cluster_allreduce_vec(part0, kk, red);
@@ -1133,6 +1134,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     rho2 = red[kk] - s_r2n;
     ce = red[kk + 1];
     den = den_prev;
+    inv_den = inv_den_prev;
   } else {
     // first step: ||c||^2, <c, e> and the stop-ratio denominator ||s_b||
     // (sFLSQR), ||S_m b|| (sFLSMR, residual rule) or ||s_{A^T b}|| (sFLSMR,
@@ -1149,9 +1151,18 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     rho2 = s_res[0][0];
     ce = s_res[0][1];
     den = sqrt(s_res[0][2]);
+    inv_den = 1.0 / den;
   }
-  // rho^2 may round below zero for a dependent column (a breakdown); NaN stays NaN
-  const double rho = rho2 >= 0.0 ? sqrt(rho2) : (rho2 < 0.0 ? 0.0 : rho2);
+  // rho^2 may round below zero for a dependent column (a breakdown); NaN stays
+  // NaN (and +inf becomes NaN: 0 * inf).  1/rho is one reciprocal square root
+  // and rho = rho^2 / rho, instead of a square root followed by a division.
+  double rho, irho = 0.0;
+  if (rho2 > 0.0) {
+    irho = rsqrt(rho2);
+    rho = rho2 * irho;
+  } else {
+    rho = rho2 < 0.0 ? 0.0 : rho2;
+  }
   const double R11 = (k == 1) ? rho : R11_prev;
   if (!(rho > 1e-300) || !(rho > 1e-14 * R11) || !isfinite(rho)) {
     cl.sync();   // no CTA leaves while a peer may still read its shared memory
@@ -1162,7 +1173,6 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     return;
   }
   // ---- 6. q_k = c / rho, gamma_k = <q_k, e>, e -= gamma_k q_k
-  const double irho = 1.0 / rho;
   const double gamma = ce * irho;
   __syncthreads();   // crow is final
   for (int i = tid; i < nr; i += kThreads) {
@@ -1242,7 +1252,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
   cl.sync();   // no CTA leaves while a peer may still read its shared memory
   if (rank == 0 && tid == 0) {
     if (k == 1) st->stop_den = den;
-    const double rel = sqrt(res2) / den;
+    const double rel = sqrt(res2) * inv_den;
     st->relres = rel;
     if (p.relres_hist) p.relres_hist[kk] = rel;
     if (k == 1) st->R11 = rho;
