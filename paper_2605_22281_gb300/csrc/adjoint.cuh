@@ -21,6 +21,7 @@ namespace sfl {
 constexpr int kAdjNV = 8;     // vectors per dot pass / inputs per combination
 constexpr int kAdjNO = 6;     // outputs per combination
 constexpr int kAdjNQ = kAdjNV * kAdjNV;   // record slots of a dot pass (pairs a <= b, slot a * 8 + b)
+constexpr int kAdjRG = 8;                 // dot pairs reduced per round of the records
 
 // One interleaved vector of a pass: element e = i * ld + r of `p` (XT, or
 // FP64 when dbl), times scale[r * sstride] when scale is set, times d[i] when
@@ -96,7 +97,7 @@ __device__ __forceinline__ bool a_active(const AArgs &a, int r) { return r < a.R
 template <typename XT>
 __global__ void __launch_bounds__(kThreads) adot_kernel(AArgs a) {
   using AT = typename AccT<XT>::T;
-  __shared__ double scr[kThreads];
+  __shared__ double scr[kAdjRG * kThreads];
   const int tid = threadIdx.x, per = kThreads / a.ld, r = tid % a.ld;
   const bool act = a_active(a, r);
   AT acc[kAdjNV][kAdjNV];
@@ -121,21 +122,42 @@ __global__ void __launch_bounds__(kThreads) adot_kernel(AArgs a) {
           if (y < a.nv) acc[x][y] += val[x] * val[y];
     }
   }
-  // records, one pair at a time (threads sharing r added in order)
+  // records, kAdjRG pairs per round: every thread parks its values of the
+  // round's pairs, then thread (pair, r) adds the per threads sharing r with
+  // four interleaved partial sums (g mod 4), combined as a fixed tree
+  const int npair = a.nv * (a.nv + 1) / 2;
+  for (int p0 = 0; p0 < npair; p0 += kAdjRG) {
+    int q = 0;
 #pragma unroll
-  for (int x = 0; x < kAdjNV; ++x)
+    for (int x = 0; x < kAdjNV; ++x)
 #pragma unroll
-    for (int y = x; y < kAdjNV; ++y) {
-      if (y >= a.nv) continue;
-      scr[tid] = (double)acc[x][y];
-      __syncthreads();
-      if (tid < a.ld && tid < a.R) {
-        double s = 0.0;
-        for (int g = 0; g < per; ++g) s += scr[g * a.ld + tid];
-        a.rec[((size_t)(x * kAdjNV + y) * a.R + tid) * a.rcap + blockIdx.x] = s;
+      for (int y = x; y < kAdjNV; ++y) {
+        if (y < a.nv) {
+          if (q >= p0 && q < p0 + kAdjRG) scr[(q - p0) * kThreads + tid] = (double)acc[x][y];
+          ++q;
+        }
       }
-      __syncthreads();
+    __syncthreads();
+    const int nq = min(kAdjRG, npair - p0);
+    for (int t = tid; t < nq * a.ld; t += kThreads) {
+      const int qq = t / a.ld, rr = t - qq * a.ld;
+      if (rr >= a.R) continue;
+      const double *sv = scr + qq * kThreads + rr;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      for (int g = 0; g < per; g += 4) {
+        s0 += sv[g * a.ld];
+        if (g + 1 < per) s1 += sv[(g + 1) * a.ld];
+        if (g + 2 < per) s2 += sv[(g + 2) * a.ld];
+        if (g + 3 < per) s3 += sv[(g + 3) * a.ld];
+      }
+      const double s = (s0 + s1) + (s2 + s3);
+      // pair index p0 + qq -> (x, y), row-major over the upper triangle
+      int x = 0, rem = p0 + qq;
+      while (rem >= a.nv - x) { rem -= a.nv - x; ++x; }
+      a.rec[((size_t)(x * kAdjNV + x + rem) * a.R + rr) * a.rcap + blockIdx.x] = s;
     }
+    __syncthreads();
+  }
 }
 
 // out_o (=|+=) sum_l coef[r][o][l] * v_l for every running right-hand side.
