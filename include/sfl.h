@@ -43,7 +43,7 @@ typedef enum {
   SFL_ECUDA = 3,         /* a CUDA runtime call failed */
   SFL_ENONFINITE = 4,    /* NaN or Inf in the matrix values or in b */
   SFL_ETIMEOUT = 5,      /* host wait exceeded its wall-clock limit */
-  SFL_EUNSUPPORTED = 6   /* valid request this build does not implement */
+  SFL_EUNSUPPORTED = 6   /* valid request the library does not implement */
 } sfl_status;
 
 typedef enum { SFL_F64 = 0, SFL_F32 = 1, SFL_BF16 = 2 } sfl_dtype;

@@ -332,7 +332,7 @@ const char *sfl_error_string(int status) {
     case SFL_ECUDA: return "CUDA runtime error";
     case SFL_ENONFINITE: return "NaN or Inf in the input";
     case SFL_ETIMEOUT: return "host wait timed out";
-    case SFL_EUNSUPPORTED: return "unsupported by this build";
+    case SFL_EUNSUPPORTED: return "unsupported by the library";
     default: return "unknown status";
   }
 }
