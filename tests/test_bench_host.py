@@ -1,0 +1,57 @@
+"""Host logic of bench.py that decides whether a recorded ncu measurement
+still describes the kernels: the source hash ignores comments and blank
+lines, changes with any code edit, and the recorded DRAM traffic is only
+returned while it matches."""
+import json
+import os
+import shutil
+
+import pytest
+
+import bench
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2605_22281_gb300", "csrc")
+
+
+@pytest.fixture
+def tree(tmp_path, monkeypatch):
+    src = tmp_path / "paper_2605_22281_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for name in ("kernels.cuh", "common.cuh"):
+        shutil.copy(os.path.join(CSRC, name), src / name)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    return tmp_path
+
+
+def test_hash_ignores_comments_and_blank_lines(tree):
+    h0 = bench.kernel_source_hash()
+    p = tree / "paper_2605_22281_gb300" / "csrc" / "kernels.cuh"
+    text = p.read_text()
+    p.write_text("// a new leading comment\n\n" + text.replace("\n", "  // trailing note\n", 3) + "\n\n")
+    assert bench.kernel_source_hash() == h0
+
+
+def test_hash_changes_with_code(tree):
+    h0 = bench.kernel_source_hash()
+    p = tree / "paper_2605_22281_gb300" / "csrc" / "common.cuh"
+    p.write_text(p.read_text() + "\nstatic const int kUnusedForTest = 1;\n")
+    assert bench.kernel_source_hash() != h0
+
+
+def test_recorded_traffic_only_while_the_hash_matches(tree):
+    h = bench.kernel_source_hash()
+    rec = {"w": {"spmv_bwd": {"bytes_per_launch": 123, "kernel_source_sha": h}}}
+    (tree / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("spmv_bwd", "w") == 123
+    assert bench.recorded_traffic("spmv_fwd", "w") is None
+    assert bench.recorded_traffic("spmv_bwd", "other") is None
+    rec["w"]["spmv_bwd"]["kernel_source_sha"] = "0" * 16
+    (tree / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("spmv_bwd", "w") is None
+
+
+def test_spmv_bytes_closed_form():
+    # 10 entries of 8-byte values and 4-byte indices, 3 rows, 5 columns,
+    # 8-byte vectors, 2 window dots, no table
+    assert bench.spmv_bytes(10, 3, 5, 8, 8, 2, 0) == 10 * 12 + 4 * 4 + 8 * (5 + 3) + 8 * 3 * 2
