@@ -55,3 +55,33 @@ def test_spmv_bytes_closed_form():
     # 10 entries of 8-byte values and 4-byte indices, 3 rows, 5 columns,
     # 8-byte vectors, 2 window dots, no table
     assert bench.spmv_bytes(10, 3, 5, 8, 8, 2, 0) == 10 * 12 + 4 * 4 + 8 * (5 + 3) + 8 * 3 * 2
+
+
+class _DoneProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_parses_clocks_and_reasons(tmp_path):
+    csv = tmp_path / "clocks.csv"
+    csv.write_text(
+        "0, 2070, 2070, 400.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 2040, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, 2070, 2070, 410.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "garbled line\n"
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = bench.ClockSampler(0)
+    s.proc, s.path = _DoneProc(), str(csv)
+    out = s.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert not csv.exists()
+
+
+def test_clock_sampler_without_nvidia_smi():
+    s = bench.ClockSampler(0)
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
