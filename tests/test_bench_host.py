@@ -85,3 +85,30 @@ def test_clock_sampler_parses_clocks_and_reasons(tmp_path):
 def test_clock_sampler_without_nvidia_smi():
     s = bench.ClockSampler(0)
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def _run_bench(args, env_extra=None):
+    import subprocess
+    import sys
+    env = dict(os.environ, **(env_extra or {}))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], env=env, capture_output=True,
+                          text=True, timeout=600)
+
+
+def test_reference_arm_prints_the_contract_line():
+    out = _run_bench(["--impl", "reference", "--workload", "ct64_sflsqr", "--steps", "1", "--warmup", "0"])
+    assert out.returncode == 0, out.stderr[-400:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "iters/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "iters/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    out = _run_bench(["--impl", "reference", "--workload", "ct64_sflsqr", "--steps", "1", "--warmup", "0"],
+                     {"RANK": "1"})
+    assert out.returncode == 0, out.stderr[-400:]
+    assert out.stdout.strip() == ""
