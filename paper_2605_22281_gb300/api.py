@@ -203,35 +203,40 @@ class Plan:
         return x, SolveInfo(info.iters, info.status, info.relres, info.tol)
 
 
-def _batched_opts(plan, s, zeta, seed, window, maxit, eta, precond, diag_w, spmm_tile=0):
+def _batched_opts(plan, s, zeta, seed, window, maxit, eta, precond, diag_w, spmm_tile=0, x_hist=None):
     dw = diag_w.to(device=plan.device, dtype=torch.float64).contiguous() if diag_w is not None else None
     vec = "f64" if plan.value_dtype == "f64" else "f32"
-    o = plan._opts(s, zeta, seed, window, maxit, 0.0, eta, precond, "residual", dw, 0.0, vec, None, None)
+    o = plan._opts(s, zeta, seed, window, maxit, 0.0, eta, precond, "residual", dw, 0.0, vec, x_hist, None)
     o.spmm_tile = int(spmm_tile)
     return o, dw
 
 
 def solve_batched(plan: Plan, B: torch.Tensor, noise_norms, *, s: int, zeta: int = 8, seed: int = 0, window: int = 2,
                   maxit: int = 100, eta: float = 1.01, precond: str = "identity", diag_w: torch.Tensor | None = None,
-                  spmm_tile: int = 0, out: torch.Tensor | None = None, sync: bool = True):
+                  spmm_tile: int = 0, out: torch.Tensor | None = None, sync: bool = True,
+                  x_history: bool = False):
     """Batched sFLSQR: B is (nrhs, m) (row r = b_r), noise_norms has nrhs entries.
     spmm_tile: RHS per CTA column of the SpMMs (8/16/32/64) or 0 = tuned.
-    Returns (X (nrhs, n), [SolveInfo per RHS] or None when sync=False)."""
+    x_history: also return every right-hand side's iterate after every step,
+    a (maxit, nrhs, n) tensor whose [k - 1, r] row is x_k of column r for
+    k <= its stop step (zeros after it).
+    Returns (X (nrhs, n), [SolveInfo per RHS] or None when sync=False), plus
+    the history as a third item when x_history is set."""
     dev = plan.device
     B = B.to(device=dev, dtype=torch.float64).contiguous()
     R = int(B.shape[0])
     X = out if out is not None else torch.empty((R, plan.n), dtype=torch.float64, device=dev)
     noise = np.ascontiguousarray(np.broadcast_to(np.asarray(noise_norms, dtype=np.float64), (R,)))
-    o, dw = _batched_opts(plan, s, zeta, seed, window, maxit, eta, precond, diag_w, spmm_tile)
+    xh = torch.zeros((maxit, R, plan.n), dtype=torch.float64, device=dev) if x_history else None
+    o, dw = _batched_opts(plan, s, zeta, seed, window, maxit, eta, precond, diag_w, spmm_tile, xh)
     infos = (N.Info * R)() if sync else None
     with torch.cuda.device(dev):
         st = plan.lib.sflsqr_solve_batched(plan.handle, R, _ptr(B), noise.ctypes.data_as(ctypes.c_void_p),
                                            ctypes.byref(o), _ptr(X), infos, _stream())
     N.check(st, "sflsqr_solve_batched")
     del dw
-    if not sync:
-        return X, None
-    return X, [SolveInfo(i.iters, i.status, i.relres, i.tol) for i in infos]
+    infos = [SolveInfo(i.iters, i.status, i.relres, i.tol) for i in infos] if sync else None
+    return (X, infos, xh) if x_history else (X, infos)
 
 
 def batched_tiles(plan: Plan):
@@ -330,12 +335,32 @@ def sketch_apply(seed: int, s: int, zeta: int, v: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def check_noalloc_args(s: int, v, out) -> None:
+    """Argument checks of sketch_apply_noalloc, made before anything is
+    launched: v must be a contiguous CUDA float64 vector, and out, when given,
+    a contiguous CUDA float64 tensor on v's device with at least s elements
+    (the kernel writes s doubles through its pointer).  Raises ValueError."""
+    if not getattr(v, "is_cuda", False) or v.dtype != torch.float64 or not v.is_contiguous() or v.dim() != 1:
+        raise ValueError("v must be a contiguous 1-D CUDA float64 tensor")
+    if out is not None:
+        if not getattr(out, "is_cuda", False) or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CUDA float64 tensor")
+        if out.device != v.device:
+            raise ValueError(f"out is on {out.device}, v on {v.device}")
+        if out.numel() < s:
+            raise ValueError(f"out holds {out.numel()} elements, the sketch has s = {s} rows")
+
+
 def sketch_apply_noalloc(seed: int, s: int, zeta: int, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-    """S v through the allocation-free entry point (s <= 1024).  For callers
-    that may not allocate device memory; pass a preallocated `out`."""
+    """S v through the allocation-free entry point (s <= 1024), for callers
+    that may not allocate device memory.  v must already be a contiguous CUDA
+    float64 vector (no conversion is made).  The C entry point allocates
+    nothing; this wrapper allocates only when `out` is omitted (the result
+    tensor, through PyTorch's caching allocator), so pass a preallocated out
+    for a call that allocates nothing at all."""
+    check_noalloc_args(s, v, out)
     _require_cuda()
     lib = N.load()
-    v = v.to(dtype=torch.float64).contiguous()
     if out is None:
         out = torch.empty(s, dtype=torch.float64, device=v.device)
     with torch.cuda.device(v.device):

@@ -18,9 +18,10 @@ constexpr int kBMaxRowCtas = 2048;
 
 struct BatchKey {
   int R, s, zeta, ell, maxit, precond, keep_what, tile;   // tile: forced SpMM width, 0 = tuned
+  double *x_hist;                                          // x_k of every RHS after every step, or null
   bool operator==(const BatchKey &o) const {
     return R == o.R && s == o.s && zeta == o.zeta && ell == o.ell && maxit == o.maxit && precond == o.precond &&
-           keep_what == o.keep_what && tile == o.tile;
+           keep_what == o.keep_what && tile == o.tile && x_hist == o.x_hist;
   }
 };
 
@@ -175,6 +176,11 @@ struct BEngine {
     SFL_CU(spmm(se, kBSpmmBwd, s));
     SFL_CU(sketch(se, 0, s));
     SFL_CU(launch_ls(ls_params(se), se.ls_cluster, se.smem_ls, s, false, se.key.R));
+    if (se.key.x_hist) {   // x_k of the right-hand sides that completed step k (before the step counter moves)
+      dim3 tg((unsigned)((se.bp.n + 31) / 32), (se.key.R + 31) / 32), tb(32, 8);
+      bsolution_kernel<XT><<<tg, tb, 0, s>>>(se.bp, se.y, se.key.x_hist, 1);
+      SFL_CU(cudaGetLastError());
+    }
     bcond_kernel<XT><<<1, 256, 0, s>>>(se.bp, h, use_cond);
     SFL_CU(cudaGetLastError());
     return SFL_OK;
@@ -182,7 +188,7 @@ struct BEngine {
 
   static int enqueue_epilogue(const S &se, cudaStream_t s) {
     dim3 tg((unsigned)((se.bp.n + 31) / 32), (se.key.R + 31) / 32), tb(32, 8);
-    bsolution_kernel<XT><<<tg, tb, 0, s>>>(se.bp, se.y, se.X);
+    bsolution_kernel<XT><<<tg, tb, 0, s>>>(se.bp, se.y, se.X, 0);
     SFL_CU(cudaGetLastError());
     return SFL_OK;
   }
@@ -379,7 +385,8 @@ struct BEngine {
 
   static int solve(Plan &pl, int R, const double *B, const double *noise, const sfl_opts *o, double *X, sfl_info *infos,
                    cudaStream_t s, int keep_what, S **used) {
-    BatchKey key{R, o->s, o->zeta, o->window, o->maxit, o->precond, keep_what, o->spmm_tile};
+    BatchKey key{R, o->s, o->zeta, o->window, o->maxit, o->precond, keep_what, o->spmm_tile,
+                 keep_what ? nullptr : o->x_history};
     S *se = nullptr;
     for (auto &p : pl.batches) {
       S *q = dynamic_cast<S *>(p.get());

@@ -659,12 +659,20 @@ __global__ void binterleave_kernel(const double *src, int64_t len, int R, int ld
 // x_r = tau(sum_{j <= k_r} p~_j sigP_j y_j) written column-major FP64 (tiles
 // of 32 rows x 32 RHS; the sum over j runs in FP64).
 template <typename XT>
-__global__ void bsolution_kernel(BParams<XT> p, const double *Y, double *X) {
+__global__ void bsolution_kernel(BParams<XT> p, const double *Y, double *X, int hist) {
   __shared__ double t[32][33];
   const int64_t i0 = (int64_t)blockIdx.x * 32;
   const int r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   const int r = r0 + tx;
+  // hist: inside the loop, after the small problems of step k = kstep + 1;
+  // X points at the history and only right-hand sides that completed step k
+  // write their iterate, to X + (k - 1) * R * n
+  int kh = 0;
+  if (hist) {
+    kh = __ldcg(p.kstep) + 1;
+    X += (size_t)(kh - 1) * p.R * p.n;
+  }
   int kr = 0;
   if (r < p.R) kr = __ldcg(&p.st[r].k);
   for (int j = ty; j < 32; j += 8) {
@@ -682,7 +690,7 @@ __global__ void bsolution_kernel(BParams<XT> p, const double *Y, double *X) {
   for (int j = ty; j < 32; j += 8) {
     const int rr = r0 + j;
     const int64_t i = i0 + tx;
-    if (rr < p.R && i < p.n) X[(size_t)rr * p.n + i] = t[tx][j];
+    if (rr < p.R && i < p.n && (!hist || __ldcg(&p.st[rr].k) == kh)) X[(size_t)rr * p.n + i] = t[tx][j];
   }
 }
 

@@ -21,6 +21,7 @@ constexpr int kNoAllocGrid = 256;                          // most CTAs a launch
 constexpr int kNoAllocStride = kNoAllocMaxS + 16;          // doubles per CTA partial
 constexpr int kNoAllocGroups = kNoAllocGrid / kGroup;      // first-level reduction groups
 constexpr size_t kNoAllocDoubles = (size_t)(kNoAllocGrid + kNoAllocGroups) * kNoAllocStride;
+constexpr uint16_t kNoAllocUnused = 0xFFFFu;                 // marks a draw slot that holds no row
 
 // Shared by every call on a device; a call leaves its partial sums behind.
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocDoubles];
@@ -59,6 +60,9 @@ __global__ void __launch_bounds__(kThreads) sketch_apply_inline_kernel(uint64_t 
         stage[warp][lane][cnt] = (uint16_t)(r | ((int)(h & 1ull) << 15));
         ++cnt;
       }
+      // a column whose draws hit the cap holds fewer than zeta rows (never
+      // expected): its missing entries are marked and skipped below
+      for (int q = cnt; q < zeta; ++q) stage[warp][lane][q] = kNoAllocUnused;
     }
     __syncwarp();
     const int nrow = (len - rb * 32) < 32 ? (int)(len - rb * 32) : 32;
@@ -66,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) sketch_apply_inline_kernel(uint64_t 
       const double x = __shfl_sync(0xffffffffu, vc, L);
       if (lane < zeta) {
         const uint16_t ent = stage[warp][L][lane];
-        myacc[ent & 0x7FFF] += (ent & 0x8000) ? -x : x;
+        if (ent != kNoAllocUnused) myacc[ent & 0x7FFF] += (ent & 0x8000) ? -x : x;
       }
       __syncwarp();
     }

@@ -70,3 +70,36 @@ def test_ctypes_layout_matches_c():
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def _fake_tensor(is_cuda=True, dtype="f64", contiguous=True, dim=1, device="cuda:0", numel=100):
+    """An object with the tensor attributes the no-alloc argument check reads
+    (no CUDA device is needed to build it)."""
+    import types
+
+    import torch
+    dt = {"f64": torch.float64, "f32": torch.float32}[dtype]
+    return types.SimpleNamespace(is_cuda=is_cuda, dtype=dt, is_contiguous=lambda: contiguous, dim=lambda: dim,
+                                 device=device, numel=lambda: numel)
+
+
+def test_noalloc_arguments_are_rejected_before_any_launch():
+    """A wrong v or out raises ValueError on the host, before the library is
+    loaded or any kernel could write s doubles through a bad pointer."""
+    from paper_2605_22281_gb300 import api as G
+    ok_v = _fake_tensor()
+    G.check_noalloc_args(64, ok_v, None)
+    G.check_noalloc_args(64, ok_v, _fake_tensor(numel=64))
+    bad = [
+        (_fake_tensor(is_cuda=False), None),                 # v on the host
+        (_fake_tensor(dtype="f32"), None),                   # v not FP64 (no silent conversion)
+        (_fake_tensor(contiguous=False), None),              # v strided
+        (ok_v, _fake_tensor(dtype="f32", numel=64)),         # out FP32
+        (ok_v, _fake_tensor(numel=63)),                      # out shorter than s
+        (ok_v, _fake_tensor(contiguous=False, numel=64)),    # out strided
+        (ok_v, _fake_tensor(is_cuda=False, numel=64)),       # out on the host
+        (ok_v, _fake_tensor(device="cuda:1", numel=64)),     # out on another device
+    ]
+    for v, out in bad:
+        with pytest.raises(ValueError):
+            G.check_noalloc_args(64, v, out)

@@ -34,6 +34,21 @@ def test_noalloc_matches_allocating_entry_point_on_consecutive_calls():
         assert np.array_equal(got1, got2)
 
 
+def test_noalloc_writes_into_a_preallocated_output():
+    """With `out` given, neither the C entry point nor the wrapper allocates;
+    the result lands in the caller's buffer (longer than s is allowed), on two
+    calls in a row."""
+    seed, s, zeta, n = 5, 333, 8, 20011
+    v = torch.as_tensor(np.random.default_rng(6).standard_normal(n), device="cuda")
+    want = G.sketch_apply(seed, s, zeta, v).cpu().numpy()
+    out = torch.full((s + 7,), 7.0, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        got = G.sketch_apply_noalloc(seed, s, zeta, v, out=out)
+        assert got.data_ptr() == out.data_ptr()
+        assert _rel(out[:s].cpu().numpy(), want) <= 1e-14
+    assert torch.all(out[s:] == 7.0)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     v = torch.ones(100, dtype=torch.float64, device="cuda")
     with pytest.raises(G.N.SflError) as e:
