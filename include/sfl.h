@@ -107,7 +107,13 @@ typedef struct {
  *                  sketches n-vectors with `seed` and keeps an m-side sketch
  *                  drawn from `seed + 1` for its discrepancy test.
  *                  Requires 1 <= zeta <= 16, maxit + 1 <= s <= 2048.
- *  window        : ell, the orthogonalization window, 0 <= ell <= 8.
+ *  window        : ell, the orthogonalization window, 0 <= ell <= 8, or any
+ *                  negative value for full orthogonalization (every earlier
+ *                  vector, eq. (FGK) with the band filled): the new z and w are
+ *                  orthogonalized against the whole stored basis by block
+ *                  classical Gram-Schmidt applied twice, and the plan keeps all
+ *                  p_j and w_j (n*maxit + m*(maxit+1) more vector entries).
+ *                  Not with orth_against_z = 1.
  *  maxit         : 1 <= maxit <= 1024.
  *  noise_norm    : ||e||_2 of the data noise; <= 0 disables the discrepancy stop.
  *  eta           : discrepancy safety factor (eta > 1, typically 1.01).
@@ -122,7 +128,10 @@ typedef struct {
  *                  small QR and y are FP64 in both.
  *  x_history     : optional (may be NULL), device, maxit*n FP64: x_k is written
  *                  to x_history + (k-1)*n after every step (costs one n x k
- *                  product per step; for verification).
+ *                  product per step; for verification).  Batched solves:
+ *                  maxit*nrhs*n FP64, x_k of right-hand side r at
+ *                  x_history + ((k-1)*nrhs + r)*n for every step k it completes
+ *                  (rows of later steps are left as they were).
  *  relres_history: optional (may be NULL), device, maxit FP64: the stop-test
  *                  ratio of step k at index k-1.
  *  spmm_tile     : batched solves only: RHS per CTA column of the SpMMs (8, 16,
@@ -225,6 +234,20 @@ int sflsqr_solve(sfl_plan *plan, const double *b, const sfl_opts *opts, double *
 int sflsmr_solve(sfl_plan *plan, const double *b, const sfl_opts *opts, double *x,
                  sfl_info *info, sfl_stream stream);
 
+/* FLSQR, the unsketched flexible LSQR the paper compares against (Section 2.2,
+ * eq. (FLSQR); timings in Section 4): full orthogonalization of both bases
+ * (opts->window must be negative) and, at every step, the exact projected
+ * problem min_y || beta e_1 - H_{k+1,k} y ||, which equals min || b - A Z_k y ||
+ * while W_{k+1} is orthonormal.  Its relative residual is the stop ratio, tested
+ * against eta*||e||/||b|| (eq. (discrP)).  s, zeta, seed, stop_rule and the
+ * sketch pointers are ignored (SFL_EINVAL for an explicit sketch); maxit <=
+ * 1024.  Same arguments and outputs as sflsqr_solve. */
+int flsqr_solve(sfl_plan *plan, const double *b, const sfl_opts *opts, double *x, sfl_info *info,
+                sfl_stream stream);
+/* flsqr_solve with HOST b and x (as sflsqr_solve_host). */
+int flsqr_solve_host(sfl_plan *plan, const double *b, const sfl_opts *opts, double *x, sfl_info *info,
+                     sfl_stream stream);
+
 /* Same solves with HOST FP64 b and x (b: m doubles, x: n doubles, ordinary or
  * pinned host memory).  The host-to-device copy of b and the device-to-host
  * copy of x are part of the call, which returns when x is written. */
@@ -233,7 +256,7 @@ int sflsqr_solve_host(sfl_plan *plan, const double *b_host, const sfl_opts *opts
 int sflsmr_solve_host(sfl_plan *plan, const double *b_host, const sfl_opts *opts, double *x_host,
                       sfl_info *info, sfl_stream stream);
 
-/* Same as sflsqr_solve (method 0) / sflsmr_solve (method 1) but driven by a
+/* Same as sflsqr_solve (method 0) / sflsmr_solve (method 1) / flsqr_solve (method 2) but driven by a
  * host loop over the same per-step kernels instead of the CUDA graph's
  * device-side WHILE node: one stream synchronisation per step.  Results are
  * bitwise identical to the graph driver; meant for verification. */
@@ -243,9 +266,10 @@ int sfl_solve_host_loop(sfl_plan *plan, int method, const double *b, const sfl_o
 /* Per-kernel device time of one solve.  Index: 0 initial sketches (S b, and
  * S A^T b for sFLSMR), 1 init ||b||, 2 init A^T w_1, 3 z orthogonalization +
  * tau, 4 fused A z_k SpMV, 5 w orthogonalization, 6 fused A^T w / B w SpMV,
- * 7 small least squares, 8 x = Z y, 9 per-step sketches.  ms: total
+ * 7 small least squares, 8 x = Z y, 9 per-step sketches, 10 block CGS2 of full
+ * orthogonalization (five kernels per side, counted as one launch).  ms: total
  * milliseconds over the launches that did work; launches: their number. */
-#define SFL_NUM_KERNEL_CLASSES 10
+#define SFL_NUM_KERNEL_CLASSES 11
 typedef struct {
   double ms[SFL_NUM_KERNEL_CLASSES];
   int32_t launches[SFL_NUM_KERNEL_CLASSES];

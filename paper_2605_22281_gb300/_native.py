@@ -47,11 +47,11 @@ class Info(ctypes.Structure):
 
 
 class KernelTimes(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 10), ("launches", ctypes.c_int32 * 10)]
+    _fields_ = [("ms", ctypes.c_double * 11), ("launches", ctypes.c_int32 * 11)]
 
 
 KERNEL_CLASSES = ["sketch_init", "init_b", "init_bwd", "orth_z", "spmv_fwd", "orth_w", "spmv_bwd", "small_ls",
-                  "solution", "sketch"]
+                  "solution", "sketch", "orth_full"]
 
 
 class PlanStats(ctypes.Structure):
@@ -72,6 +72,8 @@ _SIGNATURES = {
     "sflsmr_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(Info), _P]),
     "sflsqr_solve_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(Info), _P]),
     "sflsmr_solve_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(Info), _P]),
+    "flsqr_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(Info), _P]),
+    "flsqr_solve_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(Info), _P]),
     "sfl_solve_host_loop": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(Info), _P]),
     "sfl_solve_profiled": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(Info),
                                           ctypes.POINTER(KernelTimes), _P]),

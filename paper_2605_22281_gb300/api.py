@@ -46,6 +46,9 @@ def _dev_csr(rowptr, colidx, values, shape, device):
     return c, (rp, ci, va)
 
 
+METHODS = {"sflsqr": 0, "sflsmr": 1, "flsqr": 2}
+
+
 @dataclass
 class SolveInfo:
     iters: int
@@ -138,7 +141,10 @@ class Plan:
               driver: str = "graph", out: torch.Tensor | None = None, sync: bool = True,
               orth_against: str = "p", sketch_matrix: torch.Tensor | None = None,
               sketch_matrix_stop: torch.Tensor | None = None):
-        """Run sFLSQR (method='sflsqr', Algorithm 1) or sFLSMR ('sflsmr', Algorithm 2).
+        """Run sFLSQR (method='sflsqr', Algorithm 1), sFLSMR ('sflsmr', Algorithm
+        2) or the unsketched FLSQR ('flsqr', eq. (FLSQR); needs window < 0).
+        window < 0: full orthogonalization (block CGS2 against every earlier
+        vector).
 
         orth_against: 'p' orthogonalizes the new z against the window's unit
         p_j (eq. (FGK)), 'z' against the stored z_j as the algorithms' loop is
@@ -163,15 +169,16 @@ class Plan:
         info = N.Info()
         pinfo = ctypes.byref(info) if sync else None
         with torch.cuda.device(dev):
+            mid = METHODS[method]
             if driver == "graph":
-                fn = self.lib.sflsqr_solve if method == "sflsqr" else self.lib.sflsmr_solve
+                fn = (self.lib.sflsqr_solve, self.lib.sflsmr_solve, self.lib.flsqr_solve)[mid]
                 st = fn(self.handle, _ptr(b), ctypes.byref(o), _ptr(x), pinfo, _stream())
             elif driver == "profiled":
                 kt = N.KernelTimes()
-                st = self.lib.sfl_solve_profiled(self.handle, 0 if method == "sflsqr" else 1, _ptr(b), ctypes.byref(o),
+                st = self.lib.sfl_solve_profiled(self.handle, mid, _ptr(b), ctypes.byref(o),
                                                  _ptr(x), pinfo, ctypes.byref(kt), _stream())
             elif driver == "host_loop":
-                st = self.lib.sfl_solve_host_loop(self.handle, 0 if method == "sflsqr" else 1, _ptr(b),
+                st = self.lib.sfl_solve_host_loop(self.handle, mid, _ptr(b),
                                                   ctypes.byref(o), _ptr(x), pinfo, _stream())
             else:
                 raise ValueError(driver)
@@ -195,7 +202,7 @@ class Plan:
         o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
                        None, None, orth_against)
         info = N.Info()
-        fn = self.lib.sflsqr_solve_host if method == "sflsqr" else self.lib.sflsmr_solve_host
+        fn = (self.lib.sflsqr_solve_host, self.lib.sflsmr_solve_host, self.lib.flsqr_solve_host)[METHODS[method]]
         with torch.cuda.device(self.device):
             st = fn(self.handle, b.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o), x.ctypes.data_as(ctypes.c_void_p),
                     ctypes.byref(info), _stream())

@@ -23,7 +23,9 @@ constexpr int kRedExtra = 2 * kRing + 4;  // scalar slots in a reduction besides
 // Internal stop codes beyond sfl_stop.
 constexpr int kStopNonfinite = 100;
 
-enum Method : int { kSFLSQR = 0, kSFLSMR = 1 };
+// kFLSQR: full orthogonalization with the exact projected problem min || beta e_1 - H y ||
+// (no sketch), solved by the small least-squares kernel in its sFLSMR form with identity columns.
+enum Method : int { kSFLSQR = 0, kSFLSMR = 1, kFLSQR = 2 };
 
 // Device-resident state of one solve.  Vectors of the partially orthogonal
 // bases are stored unnormalised (w~, p~) with their scales sig = 1/||.|| so

@@ -54,6 +54,12 @@ struct Session {
   double *Q = nullptr, *Rinv = nullptr, *y = nullptr, *e = nullptr, *rhs = nullptr;
   double *SAZ = nullptr, *SAtW = nullptr, *Hband = nullptr, *sbm = nullptr;
   double *bbuf = nullptr, *xbuf = nullptr, *dw = nullptr;
+  // full orthogonalization (window < 0): every basis vector, the w scales, CGS2 scratch
+  bool full = false;
+  int hb_ell = 0;                      // H band width minus 2 (ell, or maxit when full)
+  void *Pfull = nullptr, *Wfull = nullptr;
+  double *sigWall = nullptr, *cgs_rec = nullptr, *cgs_coef = nullptr;
+  int grid_cgs = 0;
   int *err = nullptr;
   Partials part{};                     // per-CTA partial sums of the reducing kernels
   int32_t *wrowA = nullptr, *wrowT = nullptr;   // nnz-balanced row range of every warp

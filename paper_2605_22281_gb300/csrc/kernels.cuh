@@ -105,7 +105,12 @@ struct SpmvParams {
   int orth_z;                           // 1: the z window is Z's columns, not the p ring
   XT *wraw;                             // w = A z_k
   XT *zraw;                             // z = A^T w
-  double *Hband;                        // sFLSMR: columns of H, (ell+2) entries per column
+  double *Hband;                        // columns of H, (hb_ell+2) entries per column (when want_h)
+  int want_h;                           // H is recorded (sFLSMR, FLSQR)
+  int hb_ell;                           // band width of Hband columns minus 2 (ell, or maxit when full)
+  int full;                             // full orthogonalization: no window dots (block CGS2 kernels do it)
+  XT *wfull;                            // full: every w~_j (column j - 1); the vector pass writes w~_1
+  double *sigWall;                      // full: 1/||w~_j|| at index j - 1
   Partials part;
 };
 
@@ -272,7 +277,10 @@ __device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, RowBloc
     } else {
       if (valid) yv = (ACC)p.b[row];
     }
-    if (valid) y[ORIG ? p.orig[row] : row] = (XT)yv;
+    if (valid) {
+      y[ORIG ? p.orig[row] : row] = (XT)yv;
+      if (!MAT && p.wfull) p.wfull[row] = (XT)yv;
+    }
     const double yd = valid ? (double)yv : 0.0;
     nrm += yd * yd;
   }
@@ -332,12 +340,13 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
     const double beta = sqrt(tot[0]);
     st->beta0 = beta;
     st->sig_w[ring_slot(1, p.RW)] = 1.0 / beta;
+    if (p.sigWall) p.sigWall[0] = 1.0 / beta;
     st->tol = (sst->noise_norm > 0.0) ? sst->eta * sst->noise_norm / beta : 0.0;
     if (!(beta > 0.0)) st->stop = SFL_STOP_BREAKDOWN;
     if (!isfinite(tot[0])) st->stop = kStopNonfinite;
   } else if (p.mode == kModeFwd) {
     // alpha_k = ||p~_k|| from the z update; breakdown test; Gram row of p_k (of z_k when the z window is Z)
-    const int lz = max(1, k - p.ell), ndz = k - lz;          // window of the z update
+    const int lz = max(1, k - p.ell), ndz = p.full ? 0 : k - lz;   // window of the z update
     reduce_partials(p.part.p, p.G_prev, 1 + ndz, nullptr, tot);
     if (!t0) return;
     const double alpha = sqrt(tot[0]);
@@ -358,7 +367,7 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
     }
   } else {   // kModeBwd
     // beta_{k+1} = ||w~_{k+1}|| from the w update; lucky-breakdown test; Gram row of w_{k+1}
-    const int lw = max(1, k - p.ell), ndw = k - lw + 1;      // window of the w update
+    const int lw = max(1, k - p.ell), ndw = p.full ? 0 : k - lw + 1;   // window of the w update
     reduce_partials(p.part.wn, p.G_prev, 1 + ndw, nullptr, tot);
     if (!t0) return;
     const double beta = sqrt(tot[0]);
@@ -372,7 +381,8 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
       const int ns = ring_slot(k + 1, p.RW);
       st->betak = beta;
       st->sig_w[ns] = ib;
-      if (p.method == kSFLSMR) p.Hband[(size_t)(k - 1) * (p.ell + 2) + p.ell + 1] = beta;
+      if (p.want_h) p.Hband[(size_t)(k - 1) * (p.hb_ell + 2) + p.hb_ell + 1] = beta;
+      if (p.sigWall) p.sigWall[k] = ib;
       for (int a = 0; a < ndw; ++a) {
         const int sa = ring_slot(lw + a, p.RW);
         const double g = tot[1 + a] * sst->sig_w[sa] * ib;
@@ -424,13 +434,13 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
     } else if (p.mode == kModeFwd) {
       x = p.Z + (size_t)(k - 1) * p.zstride;
       y = p.wraw;
-      lo = max(1, k - p.ell); nd = k - lo + 1;
+      lo = max(1, k - p.ell); nd = p.full ? 0 : k - lo + 1;
       win = p.wring; wst = p.wstride; R = p.RW;
       outpart = p.part.w;
     } else {  // kModeBwd
       x = p.wring + (size_t)ring_slot(k + 1, p.RW) * p.wstride;
       y = p.zraw;
-      lo = max(1, k + 1 - p.ell); nd = k - lo + 1;
+      lo = max(1, k + 1 - p.ell); nd = p.full ? 0 : k - lo + 1;
       if (p.orth_z) { win = p.Z; wst = p.zstride; R = 0; }   // column j - 1 holds z~_j
       else { win = p.pring; wst = p.pstride; R = p.RP; }
       outpart = p.part.z;
@@ -707,7 +717,10 @@ struct OrthParams {
   int precond;
   const double *diag_w;     // SFL_PRECOND_DIAG
   const double *y;          // LS solution y_{k-1} (SFL_PRECOND_REWEIGHT)
-  double *Hband;            // sFLSMR: column k of H (rows lo..k)
+  double *Hband;            // column k of H (rows lo..k) when want_h
+  int want_h;               // H is recorded (sFLSMR, FLSQR)
+  int full;                 // full orthogonalization: the block CGS2 kernels already orthogonalized raw
+  XT *vfull;                // full: every new vector is also stored at column newj - 1
   Partials part;
 };
 
@@ -732,6 +745,7 @@ __device__ __forceinline__ void orth_run(const OrthParams<XT> &p, const SolveSta
     vj[a] = (p.side == 0 && p.orth_z) ? p.Z + (size_t)(lo + a - 1) * p.zstride : p.ring + (size_t)slot * p.stride;
   }
   XT *out = p.ring + (size_t)ring_slot(newj, p.R) * p.stride;
+  XT *fout = p.vfull ? p.vfull + (size_t)(newj - 1) * p.stride : nullptr;
   XT *zout = (p.side == 0) ? p.Z + (size_t)(k - 1) * p.zstride : nullptr;
   double acc[ND + 1];
 #pragma unroll
@@ -748,6 +762,7 @@ __device__ __forceinline__ void orth_run(const OrthParams<XT> &p, const SolveSta
     for (int a = 0; a < ND; ++a) { old[a] = (double)vj[a][i]; v -= coef[a] * old[a]; }
     const XT vx = (XT)v;
     out[i] = vx;
+    if (fout) fout[i] = vx;
     const double vd = (double)vx;
     acc[0] += vd * vd;
     if (!(p.side == 0 && p.orth_z)) {
@@ -809,7 +824,7 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
   int lo, nd, newj;
   if (p.side == 0) {
     // coefficients of z against p_lo..p_{k-1} from the A^T w product's dots
-    lo = max(1, k - p.ell); nd = k - lo; newj = k;
+    lo = max(1, k - p.ell); nd = p.full ? 0 : k - lo; newj = k;
     reduce_partials(p.part.z, p.G_prev, 1 + nd, wsum, tot);
     if (threadIdx.x == 0) {
       scale_dots(1 + nd);
@@ -818,7 +833,7 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
     if (cta0) p.st->znorm_raw2 = tot[0];
   } else {
     // coefficients of w against w_lo..w_k (column k of H) from the A z_k product's dots
-    lo = max(1, k - p.ell); nd = k - lo + 1; newj = k + 1;
+    lo = max(1, k - p.ell); nd = p.full ? 0 : k - lo + 1; newj = k + 1;
     reduce_partials(p.part.w, p.G_prev, 1 + nd, wsum, tot);
     if (threadIdx.x == 0) {
       scale_dots(1 + nd);
@@ -827,7 +842,7 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
     if (cta0) {
       p.st->wnorm_raw2 = tot[0];
       for (int a = 0; a < nd; ++a) p.st->hw[a] = coefs[a];
-      if (p.method == kSFLSMR) {
+      if (p.want_h && !p.full) {   // full: the block CGS2 kernels wrote the column
         double *hb = p.Hband + (size_t)(k - 1) * (p.ell + 2);
         for (int q = 0; q < p.ell + 2; ++q) hb[q] = 0.0;
         for (int a = 0; a < nd; ++a) hb[(lo + a) - k + p.ell] = coefs[a];
@@ -1266,6 +1281,162 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     st->stop = stop;
     if (p.use_cond) cudaGraphSetConditional(p.cond, stop ? 0u : 1u);
   }
+}
+
+// ---------------------------------------------------------------- full orthogonalization (window < 0)
+
+// With window ell < 0 (full orthogonalization, eq. (FGK) with the band filled:
+// FLSQR / FLSMR and their sketched forms) the product output is orthogonalized
+// against every earlier basis vector by block classical Gram-Schmidt applied
+// twice (CGS2) before the ordinary update kernel normalises it:
+//   pass 1: c1 = V^T x;  x <- x - V c1;   pass 2: c2 = V^T x;  x <- x - V c2,
+// with V the unit basis (p_1..p_{k-1} for z at step k, w_1..w_k for w), stored
+// unnormalised with its scales.  Each pass is a tall-skinny product with the
+// stored basis: one DFMA per basis entry, the basis streamed from HBM.  The
+// coefficients are in the units of the raw (unscaled) product output; for the
+// w side the column of H is rs (c1 + c2), rs the product's scale sig_p(k).
+constexpr int kCgsChunk = 4096;   // most vector entries one CTA of the dot kernels holds in shared memory
+
+template <typename XT>
+struct CgsParams {
+  SolveState *st;
+  int side;                    // 0: z against p_1..p_{k-1}; 1: w against w_1..w_k
+  int want_h;                  // w side: write column k of H
+  int64_t len;
+  XT *x;                       // the raw product output, orthogonalized in place
+  const XT *V; int64_t vstride;   // column j - 1: v~_j
+  const double *sigV;          // 1/||v~_j|| at index j - 1
+  const double *sigP;          // sig_p(k) at index k - 1 (the scale of the raw w)
+  double *rec;                 // per-CTA dots, rec[(j - 1) * cap + cta]
+  int cap;                     // record stride (>= the dot kernels' grid)
+  double *coef;                // [2][kMaxIt + 2]: unit-basis coefficients of passes 1 and 2
+  double *Hband; int hb_ell;   // H columns, hb_ell + 2 entries each
+};
+
+template <typename XT>
+__device__ __forceinline__ int cgs_nbasis(const CgsParams<XT> &p, int &k) {
+  if (__ldcg(&p.st->stop)) return 0;
+  k = __ldcg(&p.st->k) + 1;
+  return p.side == 0 ? k - 1 : k;
+}
+
+// Per-CTA dots <v~_j, x> over one contiguous chunk of the entries.  pass 2
+// first applies pass 1's update to the chunk (x <- x - V c1, written back) and
+// takes the dots of the updated entries.  The chunk sits in shared memory;
+// warp w sums the columns j = w, w + 8, ... with coalesced loads.
+template <typename XT>
+__global__ void __launch_bounds__(kThreads) cgs_dots_kernel(CgsParams<XT> p, int pass) {
+  __shared__ double xs[kCgsChunk];
+  __shared__ double cs[kMaxIt + 2];
+  int k = 0;
+  const int kv = cgs_nbasis(p, k);
+  if (kv <= 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t chunk = (p.len + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * chunk;
+  const int nloc = (int)max((int64_t)0, min(p.len, i0 + chunk) - i0);
+  if (chunk > kCgsChunk) return;   // the host sizes the grid so this never happens
+  if (pass == 2)
+    for (int j = tid; j < kv; j += kThreads) cs[j] = __ldcg(p.coef + j) * p.sigV[j];
+  __syncthreads();
+  for (int i = tid; i < nloc; i += kThreads) {
+    double v = (double)p.x[i0 + i];
+    if (pass == 2) {
+      const XT *vi = p.V + i0 + i;
+      double a0 = 0.0, a1 = 0.0;
+      int j = 0;
+      for (; j + 1 < kv; j += 2) {
+        a0 += (double)vi[(size_t)j * p.vstride] * cs[j];
+        a1 += (double)vi[(size_t)(j + 1) * p.vstride] * cs[j + 1];
+      }
+      if (j < kv) a0 += (double)vi[(size_t)j * p.vstride] * cs[j];
+      const XT nx = (XT)(v - (a0 + a1));
+      p.x[i0 + i] = nx;
+      v = (double)nx;
+    }
+    xs[i] = v;
+  }
+  __syncthreads();
+  for (int j = warp; j < kv; j += kWarps) {
+    const XT *vj = p.V + (size_t)j * p.vstride + i0;
+    double a0 = 0.0, a1 = 0.0;
+    int i = lane;
+    for (; i + 32 < nloc; i += 64) {
+      a0 += (double)vj[i] * xs[i];
+      a1 += (double)vj[i + 32] * xs[i + 32];
+    }
+    if (i < nloc) a0 += (double)vj[i] * xs[i];
+    const double t = warp_sum(a0 + a1);
+    if (lane == 0) p.rec[(size_t)j * p.cap + blockIdx.x] = t;
+  }
+}
+
+// Coefficients of one pass: warp per basis vector, the G per-CTA records
+// summed in a fixed order, times the vector's scale.  After pass 2 of the w
+// side, column k of H (rows 1..k) when it is recorded.
+template <typename XT>
+__global__ void __launch_bounds__(kThreads) cgs_reduce_kernel(CgsParams<XT> p, int pass, int G) {
+  int k = 0;
+  const int kv = cgs_nbasis(p, k);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * kWarps + warp;
+  if (j >= kv) return;
+  const double *r = p.rec + (size_t)j * p.cap;
+  double a0 = 0.0, a1 = 0.0;
+  int b = lane;
+  for (; b + 32 < G; b += 64) { a0 += __ldcg(r + b); a1 += __ldcg(r + b + 32); }
+  if (b < G) a0 += __ldcg(r + b);
+  const double t = warp_sum(a0 + a1);
+  if (lane != 0) return;
+  const double c = t * p.sigV[j];
+  p.coef[(pass - 1) * (kMaxIt + 2) + j] = c;
+  if (pass == 2 && p.side == 1 && p.want_h) {
+    const double rs = p.sigP[k - 1];
+    // row j + 1 of column k: index (j + 1) - k + hb_ell in the band
+    p.Hband[(size_t)(k - 1) * (p.hb_ell + 2) + (j + 1) - k + p.hb_ell] = rs * (__ldcg(p.coef + j) + c);
+  }
+}
+
+// Pass 2's update: x <- x - V c2 (entries strided over the grid).
+template <typename XT>
+__global__ void __launch_bounds__(kThreads) cgs_update_kernel(CgsParams<XT> p) {
+  __shared__ double cs[kMaxIt + 2];
+  int k = 0;
+  const int kv = cgs_nbasis(p, k);
+  if (kv <= 0) return;
+  for (int j = threadIdx.x; j < kv; j += kThreads) cs[j] = __ldcg(p.coef + (kMaxIt + 2) + j) * p.sigV[j];
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.len; i += stride) {
+    const XT *vi = p.V + i;
+    double a0 = 0.0, a1 = 0.0;
+    int j = 0;
+    for (; j + 1 < kv; j += 2) {
+      a0 += (double)vi[(size_t)j * p.vstride] * cs[j];
+      a1 += (double)vi[(size_t)(j + 1) * p.vstride] * cs[j + 1];
+    }
+    if (j < kv) a0 += (double)vi[(size_t)j * p.vstride] * cs[j];
+    p.x[i] = (XT)((double)p.x[i] - (a0 + a1));
+  }
+}
+
+// FLSQR's small problem is min || beta e_1 - H_{k+1,k} y ||: right-hand side
+// and initial residual beta e_1 (beta = ||b|| from the initial pass).
+static __global__ void flsqr_rhs_kernel(const SolveState *st, double *rhs, double *e, int s) {
+  const double beta = __ldcg(&st->beta0);
+  for (int r = threadIdx.x; r < s; r += blockDim.x) {
+    const double v = r == 0 ? beta : 0.0;
+    rhs[r] = v;
+    e[r] = v;
+  }
+}
+
+// Columns 0..ncol-1 of the s x ncol identity, column-major (FLSQR's stand-in
+// for the sketched columns S A^T W, so that [I] H is H itself).
+static __global__ void identity_cols_kernel(double *M, int s, int ncol) {
+  const int64_t tot = (int64_t)s * ncol;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    M[t] = (t / s == t % s) ? 1.0 : 0.0;
 }
 
 // ---------------------------------------------------------------- x = Z y

@@ -231,6 +231,14 @@ struct Engine {
     p.Z = (XT *)se.Z; p.zstride = pl.A.cols; p.sigZ = se.sigZ;
     p.wraw = (XT *)se.wraw; p.zraw = (XT *)se.zraw;
     p.Hband = se.Hband;
+    p.want_h = se.key.method != kSFLSQR;
+    p.hb_ell = se.hb_ell;
+    p.full = se.full;
+    if (se.full) {
+      p.ell = 0;                        // the rings and scalars run as for window 0, with no window dots
+      p.wfull = mode == kModeInitB ? (XT *)se.Wfull : nullptr;
+      p.sigWall = se.sigWall;
+    }
     return p;
   }
 
@@ -259,6 +267,12 @@ struct Engine {
     o.part = se.part;
     o.G_prev = side == 0 ? se.grid_spmv_T : se.grid_spmv_A;
     o.Hband = se.Hband;
+    o.want_h = se.key.method != kSFLSQR;
+    o.full = se.full;
+    if (se.full) {
+      o.ell = 0;
+      o.vfull = (XT *)(side == 0 ? se.Pfull : se.Wfull);
+    }
     o.scale_ring = side == 0 ? se.RW : se.RP;
     if (side == 0) {
       o.len = pl.A.cols; o.raw = (const XT *)se.zraw; o.ring = (XT *)se.pring; o.stride = pl.A.cols; o.R = se.RP;
@@ -273,8 +287,10 @@ struct Engine {
 
   static LsParams ls_params(const Session &se, int use_cond, cudaGraphConditionalHandle h) {
     LsParams q{};
-    q.st = se.st; q.method = se.key.method; q.s = se.key.s; q.maxit = se.key.maxit; q.ell = se.key.ell;
-    q.stop_rule = se.key.stop_rule;
+    // FLSQR runs the sFLSMR form of the small problem with identity columns
+    q.st = se.st; q.method = se.key.method == kFLSQR ? kSFLSMR : se.key.method; q.s = se.key.s;
+    q.maxit = se.key.maxit; q.ell = se.hb_ell;
+    q.stop_rule = se.key.method == kFLSQR ? SFL_STOP_RULE_NORMAL : se.key.stop_rule;
     q.stage_q = se.ls_stage & 1;
     q.stage_saz = (se.ls_stage >> 1) & 1;
     q.Q = se.Q; q.Rinv = se.Rinv; q.y = se.y; q.e = se.e;
@@ -285,7 +301,33 @@ struct Engine {
   }
 
   // Kernel classes of the profiled driver (sfl_kernel_times index).
-  enum { kKSketchInit = 0, kKInitB, kKInitBwd, kKOrthZ, kKFwd, kKOrthW, kKBwd, kKLs, kKSolution, kKSketch };
+  enum { kKSketchInit = 0, kKInitB, kKInitBwd, kKOrthZ, kKFwd, kKOrthW, kKBwd, kKLs, kKSolution, kKSketch, kKOrthFull };
+
+  static CgsParams<XT> cgs_params(const Plan &pl, const Session &se, int side) {
+    CgsParams<XT> c{};
+    c.st = se.st; c.side = side; c.want_h = se.key.method != kSFLSQR;
+    c.len = side == 0 ? pl.A.cols : pl.A.rows;
+    c.x = (XT *)(side == 0 ? se.zraw : se.wraw);
+    c.V = (const XT *)(side == 0 ? se.Pfull : se.Wfull);
+    c.vstride = c.len;
+    c.sigV = side == 0 ? se.sigZ : se.sigWall;
+    c.sigP = se.sigZ;
+    c.rec = se.cgs_rec; c.cap = se.grid_cgs;
+    c.coef = se.cgs_coef;
+    c.Hband = se.Hband; c.hb_ell = se.hb_ell;
+    return c;
+  }
+  // Block CGS2 of the raw product output against the whole stored basis (five launches).
+  static int k_cgs(const Plan &pl, const Session &se, int side, cudaStream_t s) {
+    const CgsParams<XT> c = cgs_params(pl, se, side);
+    const int gred = (se.key.maxit + 1 + kWarps - 1) / kWarps;
+    cgs_dots_kernel<XT><<<se.grid_cgs, kThreads, 0, s>>>(c, 1);
+    cgs_reduce_kernel<XT><<<gred, kThreads, 0, s>>>(c, 1, se.grid_cgs);
+    cgs_dots_kernel<XT><<<se.grid_cgs, kThreads, 0, s>>>(c, 2);
+    cgs_reduce_kernel<XT><<<gred, kThreads, 0, s>>>(c, 2, se.grid_cgs);
+    cgs_update_kernel<XT><<<se.grid_vec, kThreads, 0, s>>>(c);
+    return cudaGetLastError() == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  }
 
   template <typename F> static int launch_one(int cls, F &&f, const std::function<int(int, std::function<int()>)> *tm) {
     if (tm) return (*tm)(cls, std::function<int()>(f));
@@ -321,6 +363,11 @@ struct Engine {
     int r;
     if ((r = launch_one(kKInitB, [&] { return k_spmv(pl, se, kModeInitB, s); }, tm))) return r;
     if ((r = launch_one(kKInitBwd, [&] { return k_spmv(pl, se, kModeInitBwd, s); }, tm))) return r;
+    if (se.key.method == kFLSQR) {   // no sketch: the small problem's right-hand side is beta e_1
+      flsqr_rhs_kernel<<<1, kThreads, 0, s>>>(se.st, se.rhs, se.e, se.key.s);
+      SFL_CU(cudaGetLastError());
+      return SFL_OK;
+    }
     if ((r = launch_one(kKSketchInit, [&] {
            int q = k_sketch(se, kSkInitB, se.key.s, s);
            if (!q && se.key.method == kSFLSMR) q = k_sketch(se, kSkInitBwd, se.key.s, s);
@@ -335,14 +382,17 @@ struct Engine {
   static int enqueue_body(const Plan &pl, const Session &se, cudaStream_t s, int use_cond,
                           cudaGraphConditionalHandle h, const Timer *tm = nullptr, bool pdl = false) {
     int r;
+    if (se.full && (r = launch_one(kKOrthFull, [&] { return k_cgs(pl, se, 0, s); }, tm))) return r;
     if ((r = launch_one(kKOrthZ, [&] { return k_orth(pl, se, 0, s); }, tm))) return r;
     if ((r = launch_one(kKFwd, [&] { return k_spmv(pl, se, kModeFwd, s, pdl); }, tm))) return r;
+    if (se.full && (r = launch_one(kKOrthFull, [&] { return k_cgs(pl, se, 1, s); }, tm))) return r;
     if ((r = launch_one(kKOrthW, [&] { return k_orth(pl, se, 1, s, pdl); }, tm))) return r;
     if ((r = launch_one(kKBwd, [&] { return k_spmv(pl, se, kModeBwd, s, pdl); }, tm))) return r;
     const int gsk = se.key.s * (se.key.method == kSFLSMR ? 2 : 1);
     // no programmatic edge into the sketch: its small CTAs, launched early,
     // would pile onto the first SMs the product frees (measured 2x slower)
-    if ((r = launch_one(kKSketch, [&] { return k_sketch(se, kSkStep, gsk, s); }, tm))) return r;
+    if (se.key.method != kFLSQR && (r = launch_one(kKSketch, [&] { return k_sketch(se, kSkStep, gsk, s); }, tm)))
+      return r;
     if ((r = launch_one(kKLs, [&] {
            return launch_ls(ls_params(se, use_cond, h), se.ls_cluster, se.smem_ls, s, pdl) == cudaSuccess
                       ? SFL_OK
@@ -428,8 +478,11 @@ struct Engine {
     se->key = key;
     const int64_t m = pl.A.rows, n = pl.A.cols;
     se->m = m; se->n = n;
-    const int S = key.s, K = key.maxit, ell = key.ell, Z = key.zeta;
+    const int S = key.s, K = key.maxit, Z = key.zeta;
     const size_t xs = sizeof(XT);
+    se->full = key.ell < 0;
+    const int ell = se->full ? 0 : key.ell;        // window of the ring machinery
+    se->hb_ell = se->full ? K : ell;
     se->RW = ell + 2;
     se->RP = ell + 1;
     int r;
@@ -441,6 +494,14 @@ struct Engine {
     SA(se->zraw, xs * n);
     SA(se->Z, xs * (size_t)n * K);
     SA(se->sigZ, sizeof(double) * K);
+    if (se->full) {
+      SA(se->Pfull, xs * (size_t)n * K);
+      SA(se->Wfull, xs * (size_t)m * (K + 1));
+      SA(se->sigWall, sizeof(double) * (K + 2));
+      se->grid_cgs = (int)std::max<int64_t>(pl.num_sms * 2, (std::max(m, n) + kCgsChunk - 1) / kCgsChunk);
+      SA(se->cgs_rec, sizeof(double) * (size_t)(K + 2) * se->grid_cgs);
+      SA(se->cgs_coef, sizeof(double) * 2 * (kMaxIt + 2));
+    }
     SA(se->skM_row, sizeof(int32_t) * (S + 1));
     SA(se->skM_ent, sizeof(uint32_t) * (size_t)Z * m);
     if (key.method == kSFLSMR) {
@@ -460,7 +521,7 @@ struct Engine {
     SA(se->rhs, sizeof(double) * S);
     SA(se->SAZ, sizeof(double) * (size_t)S * K);
     SA(se->SAtW, sizeof(double) * (size_t)S * (K + 1));
-    SA(se->Hband, sizeof(double) * (size_t)K * (ell + 2));
+    SA(se->Hband, sizeof(double) * (size_t)K * (se->hb_ell + 2));
     SA(se->sbm, sizeof(double) * S);
     SA(se->bbuf, sizeof(double) * m);
     SA(se->xbuf, sizeof(double) * n);
@@ -485,7 +546,7 @@ struct Engine {
     se->grid_vec = std::min(pl.num_sms * 2, kGroup * kMaxGroups);
     se->smem_orth = orth_smem_bytes(K);
     SFL_CU(O::set_orth_smem(orth_smem_bytes(kMaxIt)));   // one limit for every session
-    const bool saz_rule = key.method == kSFLSMR && key.stop_rule == SFL_STOP_RULE_RESIDUAL;
+    const bool saz_rule = key.method == kSFLSMR && key.stop_rule == SFL_STOP_RULE_RESIDUAL;   // FLSQR: normal rule
     se->ls_cluster = ls_cluster_size(S, K, saz_rule);
     if (se->ls_cluster < 1) { destroy_session(pl, *se); return SFL_EUNSUPPORTED; }
     se->smem_ls = ls_smem_bytes(S, K, se->ls_cluster, saz_rule);
@@ -516,7 +577,11 @@ struct Engine {
       return r;
     }
     SFL_CU(cudaMemsetAsync(se->err, 0, sizeof(int), s));
-    SFL_CU(cudaMemsetAsync(se->Hband, 0, sizeof(double) * (size_t)K * (ell + 2), s));
+    SFL_CU(cudaMemsetAsync(se->Hband, 0, sizeof(double) * (size_t)K * (se->hb_ell + 2), s));
+    if (key.method == kFLSQR) {   // [I] H = H: identity columns in place of the sketched S A^T W
+      identity_cols_kernel<<<64, kThreads, 0, s>>>(se->SAtW, S, K + 1);
+      SFL_CU(cudaGetLastError());
+    }
     SFL_CU(cudaStreamSynchronize(s));
     if ((r = build_graph(pl, *se))) { destroy_session(pl, *se); return r; }
     *out = se.get();
@@ -526,7 +591,7 @@ struct Engine {
 
   // Row-major sketch tables for `seed` (kept until the seed changes).
   static int ensure_tables(const Plan &pl, Session &se, uint64_t seed, cudaStream_t s) {
-    if (se.key.dense_S) return SFL_OK;      // explicit sketch: no draws
+    if (se.key.dense_S || se.key.method == kFLSQR) return SFL_OK;      // explicit sketch or none: no draws
     if (se.tab_valid && se.tab_seed == seed) return SFL_OK;
     SketchTableTmp t;
     t.kin = se.sk_kin; t.vin = se.sk_vin; t.kout = se.sk_kout; t.cub = se.sk_cub; t.cub_bytes = se.sk_cub_bytes;
@@ -626,12 +691,13 @@ static int check_opts(const Plan &pl, int method, const sfl_opts *o) {
   if (!o) return SFL_EINVAL;
   if (o->maxit < 1 || o->maxit > kMaxIt) return SFL_EINVAL;
   const bool dense = o->sketch_dense != nullptr;
-  if (!dense && (o->zeta < 1 || o->zeta > kMaxZeta)) return SFL_EINVAL;
-  if (o->s < o->maxit + 1 || (!dense && o->s < o->zeta) || o->s > kMaxS) return SFL_EINVAL;
+  if (!dense && method != kFLSQR && (o->zeta < 1 || o->zeta > kMaxZeta)) return SFL_EINVAL;
+  if (method != kFLSQR && (o->s < o->maxit + 1 || (!dense && o->s < o->zeta) || o->s > kMaxS)) return SFL_EINVAL;
   if (dense && method == kSFLSMR && !o->sketch_dense_stop) return SFL_EINVAL;
   if (o->sketch_dense_stop && (!dense || method != kSFLSMR)) return SFL_EINVAL;
-  if (o->window < 0) return SFL_EUNSUPPORTED;   // full orthogonalization: not on the GPU path
   if (o->window > kMaxWindow) return SFL_EINVAL;
+  if (o->window < 0 && o->orth_against_z) return SFL_EUNSUPPORTED;   // the literal z_j loop is not a projection
+  if (method == kFLSQR && (o->window >= 0 || dense)) return SFL_EINVAL;
   if (o->noise_norm > 0.0 && !(o->eta > 0.0)) return SFL_EINVAL;
   if (o->precond < 0 || o->precond > 2) return SFL_EINVAL;
   if (o->precond == SFL_PRECOND_DIAG && !o->diag_w) return SFL_EINVAL;
@@ -652,6 +718,13 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
                  q.method == kSFLSMR ? o->stop_rule : 0, o->vec_dtype, o->x_history, o->relres_history,
                  o->orth_against_z, o->sketch_dense, o->sketch_dense_stop};
   if (key.dense_S) key.zeta = 1;   // the draws are not used: one session per explicit sketch
+  if (q.method == kFLSQR) {         // no sketch: the small problem has maxit + 1 rows
+    key.s = o->maxit + 1;
+    key.zeta = 1;
+    key.stop_rule = SFL_STOP_RULE_NORMAL;
+    key.ell = -1;
+  }
+  if (key.ell < 0) key.ell = -1;
   Session *se = nullptr;
   for (auto &p : pl.sessions)
     if (p->key == key) { se = p.get(); break; }
@@ -784,18 +857,25 @@ int sflsmr_solve_host(sfl_plan *plan, const double *b, const sfl_opts *opts, dou
                       sfl_stream stream) {
   return solve(plan, SolveRequest{kSFLSMR, b, true, opts, x, true, info, (cudaStream_t)stream, false});
 }
+int flsqr_solve(sfl_plan *plan, const double *b, const sfl_opts *opts, double *x, sfl_info *info, sfl_stream stream) {
+  return solve(plan, SolveRequest{kFLSQR, b, false, opts, x, false, info, (cudaStream_t)stream, false});
+}
+int flsqr_solve_host(sfl_plan *plan, const double *b, const sfl_opts *opts, double *x, sfl_info *info,
+                     sfl_stream stream) {
+  return solve(plan, SolveRequest{kFLSQR, b, true, opts, x, true, info, (cudaStream_t)stream, false});
+}
 
 // Same solve driven by a host loop instead of the graph's WHILE node (one
 // stream synchronisation per step); used to check that both drivers agree.
 int sfl_solve_host_loop(sfl_plan *plan, int method, const double *b, const sfl_opts *opts, double *x, sfl_info *info,
                         sfl_stream stream) {
-  if (method != kSFLSQR && method != kSFLSMR) return SFL_EINVAL;
+  if (method != kSFLSQR && method != kSFLSMR && method != kFLSQR) return SFL_EINVAL;
   return solve(plan, SolveRequest{method, b, false, opts, x, false, info, (cudaStream_t)stream, true});
 }
 
 int sfl_solve_profiled(sfl_plan *plan, int method, const double *b, const sfl_opts *opts, double *x, sfl_info *info,
                        sfl_kernel_times *times, sfl_stream stream) {
-  if (method != kSFLSQR && method != kSFLSMR) return SFL_EINVAL;
+  if (method != kSFLSQR && method != kSFLSMR && method != kFLSQR) return SFL_EINVAL;
   if (!times) return SFL_EINVAL;
   SolveRequest q{method, b, false, opts, x, false, info, (cudaStream_t)stream, true};
   q.times = times;

@@ -634,8 +634,8 @@ def test_invalid_inputs_are_rejected(ct64):
         plan.solve("sflsqr", b, s=10, maxit=10)            # needs s >= maxit + 1
     assert e.value.status == G.N.SFL_EINVAL
     with pytest.raises(G.N.SflError) as e:
-        plan.solve("sflsqr", b, s=50, maxit=10, window=-1)  # full orthogonalization: oracle only
-    assert e.value.status == G.N.SFL_EUNSUPPORTED
+        plan.solve("sflsqr", b, s=50, maxit=10, window=9)   # windows above 8 (negative: full orthogonalization)
+    assert e.value.status == G.N.SFL_EINVAL
     bad = to_csr(sp.eye(5, format="csr"))
     bad.colidx = bad.colidx.copy(); bad.colidx[2] = 7
     with pytest.raises(G.N.SflError) as e:
