@@ -59,6 +59,8 @@ def parse_args():
                          "its geometry recipe, for profiling)")
     ap.add_argument("--only-decay", action="store_true",
                     help="run only the residual-size study (dense 1024 x 512, Gaussian sketches) and print its JSON")
+    ap.add_argument("--only-flsqr", action="store_true",
+                    help="only the FLSQR / sFLSQR comparison at equal step counts (1024x1024, FP64)")
     ap.add_argument("--only-diff", action="store_true",
                     help="run only the differentiable leg (16 x 256^2, fixed k, forward + adjoint) and print its JSON")
     ap.add_argument("--driver", default="graph", choices=["graph", "host_loop"],
@@ -394,6 +396,41 @@ def mixed_variant(args, G, wl, np, torch, x_fp64=None):
     return out
 
 
+def flsqr_variant(args, G, wl, np, torch, steps: int = 100):
+    """The paper's FLSQR-against-sFLSQR timing comparison, on the GPU at
+    1024x1024 (FP64, 481M nonzeros), at equal step counts: FLSQR (full
+    orthogonalization by block CGS2, exact projected problem through H, no
+    sketch) and sFLSQR (window 4, sparse-sign sketch s = 600), both run for
+    `steps` steps with the discrepancy stop off, plus sFLSMR with a full window.
+    Also the relative residual each reaches at the last step."""
+    p = wl.make("ct1024_sflsqr")
+    st = p.settings
+    plan = G.Plan(p.A, value_dtype="f64", image_shape=img(args, p), slot_layout=args.slot_layout)
+    b = torch.as_tensor(p.b, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"image": "1024x1024", "steps": steps, "values": "f64"}
+    legs = {"flsqr_full": ("flsqr", dict(s=0, window=-1)),
+            "sflsqr_window4": ("sflsqr", dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"])),
+            "sflsqr_full": ("sflsqr", dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=-1))}
+    for name, (method, kw) in legs.items():
+        x, info, _ = plan.solve(method, b, maxit=steps, **kw)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        plan.solve(method, b, maxit=steps, out=x, sync=False, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        xh = x.cpu().numpy()
+        res = float(np.linalg.norm(p.A.matvec(xh) - p.b) / np.linalg.norm(p.b))
+        out[name] = {"iters": info.iters, "stop": info.status_name, "ms": ms, "ms_per_step": ms / max(info.iters, 1),
+                     "rel_residual": res,
+                     "rel_error_vs_x_true": float(np.linalg.norm(xh - p.x_true) / np.linalg.norm(p.x_true))}
+    plan.close()
+    out["flsqr_over_sflsqr_time"] = out["flsqr_full"]["ms"] / out["sflsqr_window4"]["ms"]
+    return out
+
+
 def diff_variant(args, G, wl, np, torch):
     """The differentiable form: 16 sinograms of 256x256 phantoms, fixed k = 30
     steps of sFLSQR with a diagonal weight (s = 61, window 2), FP32 values and
@@ -610,7 +647,7 @@ def run_ours(args):
     from paper_2605_22281_gb300 import api as G
 
     for flag, leg in (("only_batched", batched_variant), ("only_mixed", mixed_variant), ("only_diff", diff_variant),
-                      ("only_decay", decay_variant)):
+                      ("only_decay", decay_variant), ("only_flsqr", flsqr_variant)):
         if getattr(args, flag):
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             print(json.dumps(leg(args, G, wl, np, torch)), flush=True)
@@ -648,6 +685,7 @@ def run_ours(args):
     if not args.no_variants:
         if args.workload == "ct1024_sflsqr":
             variants["mixed_ct1024_sflsqr"] = mixed_variant(args, G, wl, np, torch, x_fp64=leg["x"])
+            variants["flsqr_vs_sflsqr_ct1024_100_steps"] = flsqr_variant(args, G, wl, np, torch)
         if args.workload != "ct256_sflsmr_unmatched":
             variants["ct256_sflsmr_unmatched"] = ct256_variants(args, G, wl, np, torch)
         variants["batched_ct512_64rhs_f32"] = batched_variant(args, G, wl, np, torch)
