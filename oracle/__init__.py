@@ -10,6 +10,9 @@ Modules:
             orthogonalization (eq. (FGK)), Householder small least squares,
             identity / fixed-diagonal / reweighting flexible operators, and the
             discrepancy stop of eq. (discrP).
+  lowrank - the rank-r truncation operator of Section 1.2 (truncated SVD of
+            the basis vector reshaped to an image) and its randomized-SVD form
+            (the -RND variants of Section 4.1).
   adjoint - fixed-k sFLSQR with tau = diag(d) in plain PyTorch CPU FP64 ops,
             differentiated by autograd (imported on demand: `oracle.adjoint`).
 """
@@ -17,3 +20,4 @@ from .sketch import (DenseSketch, IdentitySketch, SparseSign, draw_hash, gaussia
                      sparse_sign_rows, splitmix64_stream)
 from .sfl import (STOP_BREAKDOWN, STOP_DISCREPANCY, STOP_MAXIT, FixedDiag, Identity, Reweighting,
                   discrepancy_tol, householder_lstsq, sflsmr, sflsqr, sketches_for)
+from .lowrank import LowRank, LowRankRandomized, randomized_svd_truncation, truncated_svd
