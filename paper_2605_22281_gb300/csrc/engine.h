@@ -58,6 +58,7 @@ struct Session {
   bool full = false;
   int hb_ell = 0;                      // H band width minus 2 (ell, or maxit when full)
   void *Pfull = nullptr, *Wfull = nullptr;
+  void *zcgs = nullptr, *wcgs = nullptr;   // orthogonalized product outputs (the raw ones stay for the sketch)
   double *sigWall = nullptr, *cgs_rec = nullptr, *cgs_coef = nullptr;
   int grid_cgs = 0;
   int *err = nullptr;

@@ -1303,7 +1303,8 @@ struct CgsParams {
   int side;                    // 0: z against p_1..p_{k-1}; 1: w against w_1..w_k
   int want_h;                  // w side: write column k of H
   int64_t len;
-  XT *x;                       // the raw product output, orthogonalized in place
+  const XT *x;                 // the raw product output (left as it is: the sketch still reads it)
+  XT *xo;                      // the orthogonalized vector
   const XT *V; int64_t vstride;   // column j - 1: v~_j
   const double *sigV;          // 1/||v~_j|| at index j - 1
   const double *sigP;          // sig_p(k) at index k - 1 (the scale of the raw w)
@@ -1321,8 +1322,8 @@ __device__ __forceinline__ int cgs_nbasis(const CgsParams<XT> &p, int &k) {
 }
 
 // Per-CTA dots <v~_j, x> over one contiguous chunk of the entries.  pass 2
-// first applies pass 1's update to the chunk (x <- x - V c1, written back) and
-// takes the dots of the updated entries.  The chunk sits in shared memory;
+// first applies pass 1's update to the chunk (xo = x - V c1) and takes the
+// dots of the updated entries.  The chunk sits in shared memory;
 // warp w sums the columns j = w, w + 8, ... with coalesced loads.
 template <typename XT>
 __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(CgsParams<XT> p, int pass) {
@@ -1351,7 +1352,7 @@ __global__ void __launch_bounds__(kThreads) cgs_dots_kernel(CgsParams<XT> p, int
       }
       if (j < kv) a0 += (double)vi[(size_t)j * p.vstride] * cs[j];
       const XT nx = (XT)(v - (a0 + a1));
-      p.x[i0 + i] = nx;
+      p.xo[i0 + i] = nx;
       v = (double)nx;
     }
     xs[i] = v;
@@ -1397,16 +1398,19 @@ __global__ void __launch_bounds__(kThreads) cgs_reduce_kernel(CgsParams<XT> p, i
   }
 }
 
-// Pass 2's update: x <- x - V c2 (entries strided over the grid).
+// Pass 2's update: xo <- xo - V c2 (entries strided over the grid).
 template <typename XT>
 __global__ void __launch_bounds__(kThreads) cgs_update_kernel(CgsParams<XT> p) {
   __shared__ double cs[kMaxIt + 2];
   int k = 0;
   const int kv = cgs_nbasis(p, k);
-  if (kv <= 0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (kv <= 0) {   // no basis yet (z at step 1): the vector passes through
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.len; i += stride) p.xo[i] = p.x[i];
+    return;
+  }
   for (int j = threadIdx.x; j < kv; j += kThreads) cs[j] = __ldcg(p.coef + (kMaxIt + 2) + j) * p.sigV[j];
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.len; i += stride) {
     const XT *vi = p.V + i;
     double a0 = 0.0, a1 = 0.0;
@@ -1416,7 +1420,7 @@ __global__ void __launch_bounds__(kThreads) cgs_update_kernel(CgsParams<XT> p) {
       a1 += (double)vi[(size_t)(j + 1) * p.vstride] * cs[j + 1];
     }
     if (j < kv) a0 += (double)vi[(size_t)j * p.vstride] * cs[j];
-    p.x[i] = (XT)((double)p.x[i] - (a0 + a1));
+    p.xo[i] = (XT)((double)p.xo[i] - (a0 + a1));
   }
 }
 

@@ -269,10 +269,6 @@ struct Engine {
     o.Hband = se.Hband;
     o.want_h = se.key.method != kSFLSQR;
     o.full = se.full;
-    if (se.full) {
-      o.ell = 0;
-      o.vfull = (XT *)(side == 0 ? se.Pfull : se.Wfull);
-    }
     o.scale_ring = side == 0 ? se.RW : se.RP;
     if (side == 0) {
       o.len = pl.A.cols; o.raw = (const XT *)se.zraw; o.ring = (XT *)se.pring; o.stride = pl.A.cols; o.R = se.RP;
@@ -281,6 +277,11 @@ struct Engine {
     } else {
       o.len = pl.A.rows; o.raw = (const XT *)se.wraw; o.ring = (XT *)se.wring; o.stride = pl.A.rows; o.R = se.RW;
       o.sigZ = se.sigZ;
+    }
+    if (se.full) {
+      o.ell = 0;
+      o.vfull = (XT *)(side == 0 ? se.Pfull : se.Wfull);
+      o.raw = (const XT *)(side == 0 ? se.zcgs : se.wcgs);   // block CGS2 output
     }
     return o;
   }
@@ -307,7 +308,8 @@ struct Engine {
     CgsParams<XT> c{};
     c.st = se.st; c.side = side; c.want_h = se.key.method != kSFLSQR;
     c.len = side == 0 ? pl.A.cols : pl.A.rows;
-    c.x = (XT *)(side == 0 ? se.zraw : se.wraw);
+    c.x = (const XT *)(side == 0 ? se.zraw : se.wraw);
+    c.xo = (XT *)(side == 0 ? se.zcgs : se.wcgs);
     c.V = (const XT *)(side == 0 ? se.Pfull : se.Wfull);
     c.vstride = c.len;
     c.sigV = side == 0 ? se.sigZ : se.sigWall;
@@ -498,6 +500,8 @@ struct Engine {
       SA(se->Pfull, xs * (size_t)n * K);
       SA(se->Wfull, xs * (size_t)m * (K + 1));
       SA(se->sigWall, sizeof(double) * (K + 2));
+      SA(se->zcgs, xs * n);
+      SA(se->wcgs, xs * m);
       se->grid_cgs = (int)std::max<int64_t>(pl.num_sms * 2, (std::max(m, n) + kCgsChunk - 1) / kCgsChunk);
       SA(se->cgs_rec, sizeof(double) * (size_t)(K + 2) * se->grid_cgs);
       SA(se->cgs_coef, sizeof(double) * 2 * (kMaxIt + 2));
