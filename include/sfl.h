@@ -56,7 +56,10 @@ typedef enum {
   SFL_STOP_BREAKDOWN = 3      /* ||z|| or ||w|| or |R_kk| vanished; the last completed iterate is returned */
 } sfl_stop;
 
-typedef enum { SFL_PRECOND_IDENTITY = 0, SFL_PRECOND_DIAG = 1, SFL_PRECOND_REWEIGHT = 2 } sfl_precond;
+typedef enum {
+  SFL_PRECOND_IDENTITY = 0, SFL_PRECOND_DIAG = 1, SFL_PRECOND_REWEIGHT = 2,
+  SFL_PRECOND_LOWRANK = 3     /* rank-r truncation by the randomized SVD (see sfl_opts.lowrank_*) */
+} sfl_precond;
 typedef enum { SFL_STOP_RULE_RESIDUAL = 0, SFL_STOP_RULE_NORMAL = 1 } sfl_stop_rule;
 
 /* A CSR matrix.  rowptr has rows+1 entries with rowptr[0] = 0, nondecreasing,
@@ -119,7 +122,17 @@ typedef struct {
  *  eta           : discrepancy safety factor (eta > 1, typically 1.01).
  *  precond       : tau_k.  IDENTITY; DIAG (z = diag(diag_w) p, diag_w FP64 of
  *                  length n); REWEIGHT (z = diag((x_{k-1}^2 + irw_eps)^(1/4)) p,
- *                  x_0 = 0), the iteratively reweighted operator of Section 1.2.
+ *                  x_0 = 0), the iteratively reweighted operator of Section 1.2;
+ *                  LOWRANK (single solves; needs a plan with image_rows x
+ *                  image_cols = n): z = vec(C_r), C the new p reshaped to the
+ *                  image, C_r the rank-r approximation of the randomized SVD
+ *                  (Halko, Martinsson & Tropp 2011: range finder with
+ *                  lowrank_power steps of subspace iteration, then the SVD of
+ *                  the projected matrix, truncated to rank r), the -RND form of
+ *                  the truncation operator of Section 1.2 used in Section 4.1.
+ *                  Computed in FP32 (the small l x l problems in one CTA); if
+ *                  a Cholesky factorization inside it fails, that step keeps
+ *                  z = p.
  *  stop_rule     : sFLSMR only.  RESIDUAL tests ||S_m (b - A x_k)|| against
  *                  eta*||e|| relative to ||S_m b||; NORMAL tests the residual of
  *                  the sketched normal equations that sFLSMR minimises.
@@ -172,6 +185,15 @@ typedef struct {
   int32_t orth_against_z;
   const double *sketch_dense;
   const double *sketch_dense_stop;
+  /* SFL_PRECOND_LOWRANK: rank r (>= 1), oversampling p (l = r + p <= 64 and
+   * l <= min(image_rows, image_cols)), subspace-iteration steps q (0..4), and
+   * the Gaussian test matrix Omega: device FP64, image_cols x l, row-major,
+   * caller-owned, read at the start of every solve (the same Omega serves
+   * every step).  Ignored for the other operators. */
+  int32_t lowrank_rank;
+  int32_t lowrank_oversample;
+  int32_t lowrank_power;
+  const double *lowrank_omega;
 } sfl_opts;
 
 /* Result of a solve.  Filled when the call returns (the call then waits for
@@ -267,9 +289,11 @@ int sfl_solve_host_loop(sfl_plan *plan, int method, const double *b, const sfl_o
  * S A^T b for sFLSMR), 1 init ||b||, 2 init A^T w_1, 3 z orthogonalization +
  * tau, 4 fused A z_k SpMV, 5 w orthogonalization, 6 fused A^T w / B w SpMV,
  * 7 small least squares, 8 x = Z y, 9 per-step sketches, 10 block CGS2 of full
- * orthogonalization (five kernels per side, counted as one launch).  ms: total
- * milliseconds over the launches that did work; launches: their number. */
-#define SFL_NUM_KERNEL_CLASSES 11
+ * orthogonalization (five kernels per side, counted as one launch), 11 the
+ * low-rank truncation (all its kernels of a step, counted as one launch).
+ * ms: total milliseconds over the launches that did work; launches: their
+ * number. */
+#define SFL_NUM_KERNEL_CLASSES 12
 typedef struct {
   double ms[SFL_NUM_KERNEL_CLASSES];
   int32_t launches[SFL_NUM_KERNEL_CLASSES];

@@ -15,7 +15,7 @@ from . import builder as _build
 SFL_OK, SFL_EINVAL, SFL_ENOMEM, SFL_ECUDA, SFL_ENONFINITE, SFL_ETIMEOUT, SFL_EUNSUPPORTED = range(7)
 SFL_F64, SFL_F32, SFL_BF16 = 0, 1, 2
 STOP_RUNNING, STOP_DISCREPANCY, STOP_MAXIT, STOP_BREAKDOWN = 0, 1, 2, 3
-PRECOND = {"identity": 0, "diag": 1, "reweight": 2}
+PRECOND = {"identity": 0, "diag": 1, "reweight": 2, "lowrank": 3}
 STOP_RULE = {"residual": 0, "normal": 1}
 DTYPE = {"f64": SFL_F64, "f32": SFL_F32, "bf16": SFL_BF16}
 
@@ -38,7 +38,9 @@ class Opts(ctypes.Structure):
                 ("diag_w", ctypes.c_void_p), ("irw_eps", ctypes.c_double), ("vec_dtype", ctypes.c_int32),
                 ("spmm_tile", ctypes.c_int32), ("x_history", ctypes.c_void_p), ("relres_history", ctypes.c_void_p),
                 ("orth_against_z", ctypes.c_int32), ("sketch_dense", ctypes.c_void_p),
-                ("sketch_dense_stop", ctypes.c_void_p)]
+                ("sketch_dense_stop", ctypes.c_void_p), ("lowrank_rank", ctypes.c_int32),
+                ("lowrank_oversample", ctypes.c_int32), ("lowrank_power", ctypes.c_int32),
+                ("lowrank_omega", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -47,11 +49,11 @@ class Info(ctypes.Structure):
 
 
 class KernelTimes(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 11), ("launches", ctypes.c_int32 * 11)]
+    _fields_ = [("ms", ctypes.c_double * 12), ("launches", ctypes.c_int32 * 12)]
 
 
 KERNEL_CLASSES = ["sketch_init", "init_b", "init_bwd", "orth_z", "spmv_fwd", "orth_w", "spmv_bwd", "small_ls",
-                  "solution", "sketch", "orth_full"]
+                  "solution", "sketch", "orth_full", "lowrank"]
 
 
 class PlanStats(ctypes.Structure):

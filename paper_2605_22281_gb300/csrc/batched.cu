@@ -656,7 +656,7 @@ static int check_batched(const Plan &pl, int R, const sfl_opts *o) {
   if (o->window < 0) return SFL_EUNSUPPORTED;
   if (o->window > kMaxWindow) return SFL_EINVAL;
   if (o->noise_norm > 0.0 && !(o->eta > 0.0)) return SFL_EINVAL;
-  if (o->precond == SFL_PRECOND_REWEIGHT) return SFL_EUNSUPPORTED;
+  if (o->precond == SFL_PRECOND_REWEIGHT || o->precond == SFL_PRECOND_LOWRANK) return SFL_EUNSUPPORTED;
   if (o->precond != SFL_PRECOND_IDENTITY && o->precond != SFL_PRECOND_DIAG) return SFL_EINVAL;
   if (o->precond == SFL_PRECOND_DIAG && !o->diag_w) return SFL_EINVAL;
   if (o->orth_against_z != 0) return o->orth_against_z == 1 ? SFL_EUNSUPPORTED : SFL_EINVAL;

@@ -145,7 +145,7 @@ __device__ __forceinline__ void lr_load_gram(const LrParams &p, int nb, float (*
 // Cholesky G + shift I = R^T R (upper R) and R^{-1} into p.small (l x l,
 // row-major, zero below the diagonal).  All threads of one CTA.  A pivot that
 // is not positive sets *p.flag (then the step keeps tau = identity).
-__device__ void lr_cholesky_inverse(const LrParams &p, float (*G)[kLrMaxL + 1], float shift_rel, float *s_tr) {
+static __device__ void lr_cholesky_inverse(const LrParams &p, float (*G)[kLrMaxL + 1], float shift_rel, float *s_tr) {
   const int L = p.l, tid = threadIdx.x;
   if (shift_rel > 0.f) {
     if (tid == 0) {
@@ -192,7 +192,7 @@ __device__ void lr_cholesky_inverse(const LrParams &p, float (*G)[kLrMaxL + 1], 
 //   mode 1: out = in * p.small (the previous pass's R^{-1});
 // then the Gram partials of out, and in the last CTA the Cholesky factor of
 // their sum (+ shift) and its inverse into p.small.
-__global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams p, int mode, const float *in, float *out, int M,
+static __global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams p, int mode, const float *in, float *out, int M,
                                                            int KS, float shift_rel) {
   __shared__ float Xs[kLrGramRows][kLrMaxL];
   __shared__ float SG[kLrMaxL * (kLrMaxL + 1)];   // S (this pass's input factor), later G (last CTA)
@@ -242,7 +242,7 @@ __device__ __forceinline__ void lr_apply_rows(const LrParams &p, const float *S,
   }
 }
 
-__global__ void __launch_bounds__(kThreads) lr_apply_kernel(LrParams p, const float *in, int M, float *out) {
+static __global__ void __launch_bounds__(kThreads) lr_apply_kernel(LrParams p, const float *in, int M, float *out) {
   __shared__ float S[kLrMaxL * kLrMaxL];
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
   for (int t = threadIdx.x; t < p.l * p.l; t += kThreads) S[t] = __ldcg(p.small + t);
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) lr_apply_kernel(LrParams p, const fl
 // its Gram partials, and in the last CTA the eigenvectors of B B^T = (B^T)^T B^T
 // by cyclic Jacobi; the r leading ones (by decreasing eigenvalue) go to p.small
 // (l x r).
-__global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p, int KS) {
+static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p, int KS) {
   __shared__ float XV[kLrMaxL * (kLrMaxL + 1)];   // the CTA's rows of B^T, later the eigenvectors (last CTA)
   __shared__ float A[kLrMaxL][kLrMaxL + 1];
   auto Xs = reinterpret_cast<float (*)[kLrMaxL]>(XV);
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p, int K
 }
 
 // U = Q W_r (N1 x r) and V = B^T W_r (N2 x r) in one launch.
-__global__ void __launch_bounds__(kThreads) lr_uv_kernel(LrParams p) {
+static __global__ void __launch_bounds__(kThreads) lr_uv_kernel(LrParams p) {
   __shared__ float S[kLrMaxL * kLrMaxL];
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
   for (int t = threadIdx.x; t < p.l * p.r; t += kThreads) S[t] = __ldcg(p.small + t);
@@ -401,5 +401,11 @@ __global__ void __launch_bounds__(kThreads) lr_outer_kernel(LrParams p, XT *Z, i
 }
 
 static __global__ void lr_clear_flag_kernel(int *flag) { *flag = 0; }
+
+// FP32 copy of the caller's FP64 test matrix.
+static __global__ void lr_omega_kernel(const double *src, float *dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
 
 }  // namespace sfl

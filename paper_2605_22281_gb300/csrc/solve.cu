@@ -302,7 +302,43 @@ struct Engine {
   }
 
   // Kernel classes of the profiled driver (sfl_kernel_times index).
-  enum { kKSketchInit = 0, kKInitB, kKInitBwd, kKOrthZ, kKFwd, kKOrthW, kKBwd, kKLs, kKSolution, kKSketch, kKOrthFull };
+  enum { kKSketchInit = 0, kKInitB, kKInitBwd, kKOrthZ, kKFwd, kKOrthW, kKBwd, kKLs, kKSolution, kKSketch, kKOrthFull,
+         kKLowRank };
+
+  // Rank-r truncation of p~_k (Z column k - 1) by the randomized SVD: the
+  // kernels of lowrank.cuh in order (range finder, subspace iteration, small
+  // eigenproblem, z~_k = U V^T written over the column).
+  static int k_lowrank(const Plan &pl, const Session &se, cudaStream_t s) {
+    const LrParams &lp = se.lr;
+    const XT *Zc = (const XT *)se.Z;
+    XT *Zw = (XT *)se.Z;
+    const int64_t zs = pl.A.cols;
+    const int N1 = lp.N1, N2 = lp.N2, L = lp.l;
+    const int KS1 = (N1 + kLrK - 1) / kLrK, KS2 = (N2 + kLrK - 1) / kLrK;
+    auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
+    // shifted Cholesky QR, then Cholesky QR twice: the result in b (a: scratch)
+    auto orth = [&](int M, int KS, float *a, float *b) {
+      const float shift = 11.f * (float)((int64_t)M * L + (int64_t)L * (L + 1)) * 5.96e-8f;
+      lr_orth_kernel<<<cdiv(M, kLrGramRows), kThreads, 0, s>>>(lp, 0, nullptr, a, M, KS, shift);
+      lr_orth_kernel<<<cdiv(M, kLrGramRows), kThreads, 0, s>>>(lp, 1, a, b, M, 0, 0.f);
+      lr_orth_kernel<<<cdiv(M, kLrGramRows), kThreads, 0, s>>>(lp, 1, b, a, M, 0, 0.f);
+      lr_apply_kernel<<<cdiv(M * L, kThreads), kThreads, 0, s>>>(lp, a, M, b);
+    };
+    lr_clear_flag_kernel<<<1, 1, 0, s>>>(lp.flag);
+    lr_mul_kernel<XT, false><<<dim3(cdiv(N1, kLrTile), KS2), kThreads, 0, s>>>(lp, Zc, zs, lp.Omega);
+    orth(N1, KS2, lp.Y, lp.Qm);
+    for (int it = 0; it < lp.q; ++it) {
+      lr_mul_kernel<XT, true><<<dim3(cdiv(N2, kLrTile), KS1), kThreads, 0, s>>>(lp, Zc, zs, lp.Qm);
+      orth(N2, KS1, lp.Bt, lp.Qt);
+      lr_mul_kernel<XT, false><<<dim3(cdiv(N1, kLrTile), KS2), kThreads, 0, s>>>(lp, Zc, zs, lp.Qt);
+      orth(N1, KS2, lp.Y, lp.Qm);
+    }
+    lr_mul_kernel<XT, true><<<dim3(cdiv(N2, kLrTile), KS1), kThreads, 0, s>>>(lp, Zc, zs, lp.Qm);
+    lr_gram_eig_kernel<<<cdiv(N2, kLrGramRows), kThreads, 0, s>>>(lp, KS1);
+    lr_uv_kernel<<<cdiv((N1 + N2) * lp.r, kThreads), kThreads, 0, s>>>(lp);
+    lr_outer_kernel<XT><<<dim3(cdiv(N2, 32), cdiv(N1, 32)), kThreads, 0, s>>>(lp, Zw, zs);
+    return cudaGetLastError() == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  }
 
   static CgsParams<XT> cgs_params(const Plan &pl, const Session &se, int side) {
     CgsParams<XT> c{};
@@ -386,6 +422,7 @@ struct Engine {
     int r;
     if (se.full && (r = launch_one(kKOrthFull, [&] { return k_cgs(pl, se, 0, s); }, tm))) return r;
     if ((r = launch_one(kKOrthZ, [&] { return k_orth(pl, se, 0, s); }, tm))) return r;
+    if (se.lowrank && (r = launch_one(kKLowRank, [&] { return k_lowrank(pl, se, s); }, tm))) return r;
     if ((r = launch_one(kKFwd, [&] { return k_spmv(pl, se, kModeFwd, s, pdl); }, tm))) return r;
     if (se.full && (r = launch_one(kKOrthFull, [&] { return k_cgs(pl, se, 1, s); }, tm))) return r;
     if ((r = launch_one(kKOrthW, [&] { return k_orth(pl, se, 1, s, pdl); }, tm))) return r;
@@ -505,6 +542,29 @@ struct Engine {
       se->grid_cgs = (int)std::max<int64_t>(pl.num_sms * 2, (std::max(m, n) + kCgsChunk - 1) / kCgsChunk);
       SA(se->cgs_rec, sizeof(double) * (size_t)(K + 2) * se->grid_cgs);
       SA(se->cgs_coef, sizeof(double) * 2 * (kMaxIt + 2));
+    }
+    if (key.precond == SFL_PRECOND_LOWRANK) {
+      se->lowrank = true;
+      LrParams &lp = se->lr;
+      lp.st = se->st;
+      lp.N1 = pl.img_rows; lp.N2 = pl.img_cols;
+      lp.r = key.lr_rank; lp.l = key.lr_rank + key.lr_over; lp.q = key.lr_power;
+      const int64_t N1 = lp.N1, N2 = lp.N2, L = lp.l, Nm = std::max(N1, N2);
+      const int64_t KSm = (Nm + kLrK - 1) / kLrK, GBm = (Nm + kLrGramRows - 1) / kLrGramRows;
+      SA(lp.Omega, sizeof(float) * N2 * L);
+      SA(lp.Y, sizeof(float) * N1 * L);
+      SA(lp.Qm, sizeof(float) * N1 * L);
+      SA(lp.Qt, sizeof(float) * N2 * L);
+      SA(lp.Bt, sizeof(float) * N2 * L);
+      SA(lp.U, sizeof(float) * N1 * lp.r);
+      SA(lp.V, sizeof(float) * N2 * lp.r);
+      SA(lp.part, sizeof(float) * KSm * Nm * L);
+      SA(lp.gpart, sizeof(float) * GBm * L * L);
+      SA(lp.small, sizeof(float) * kLrMaxL * kLrMaxL);
+      SA(lp.flag, sizeof(int));
+      SA(lp.ticket, sizeof(int));
+      SFL_CU(cudaMemsetAsync(lp.flag, 0, sizeof(int), s));
+      SFL_CU(cudaMemsetAsync(lp.ticket, 0, sizeof(int), s));
     }
     SA(se->skM_row, sizeof(int32_t) * (S + 1));
     SA(se->skM_ent, sizeof(uint32_t) * (size_t)Z * m);
@@ -703,7 +763,14 @@ static int check_opts(const Plan &pl, int method, const sfl_opts *o) {
   if (o->window < 0 && o->orth_against_z) return SFL_EUNSUPPORTED;   // the literal z_j loop is not a projection
   if (method == kFLSQR && (o->window >= 0 || dense)) return SFL_EINVAL;
   if (o->noise_norm > 0.0 && !(o->eta > 0.0)) return SFL_EINVAL;
-  if (o->precond < 0 || o->precond > 2) return SFL_EINVAL;
+  if (o->precond < 0 || o->precond > SFL_PRECOND_LOWRANK) return SFL_EINVAL;
+  if (o->precond == SFL_PRECOND_LOWRANK) {
+    const int64_t N1 = pl.img_rows, N2 = pl.img_cols, L = (int64_t)o->lowrank_rank + o->lowrank_oversample;
+    if (N1 < 1 || N2 < 1 || N1 * N2 != pl.A.cols) return SFL_EINVAL;   // the plan must know the image shape
+    if (o->lowrank_rank < 1 || o->lowrank_oversample < 0 || L > kLrMaxL || L > std::min(N1, N2)) return SFL_EINVAL;
+    if (o->lowrank_power < 0 || o->lowrank_power > 4 || !o->lowrank_omega) return SFL_EINVAL;
+    if (o->orth_against_z) return SFL_EUNSUPPORTED;
+  }
   if (o->precond == SFL_PRECOND_DIAG && !o->diag_w) return SFL_EINVAL;
   if (o->precond == SFL_PRECOND_REWEIGHT && !(o->irw_eps > 0.0)) return SFL_EINVAL;
   if (o->stop_rule != SFL_STOP_RULE_RESIDUAL && o->stop_rule != SFL_STOP_RULE_NORMAL) return SFL_EINVAL;
@@ -729,6 +796,11 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
     key.ell = -1;
   }
   if (key.ell < 0) key.ell = -1;
+  if (o->precond == SFL_PRECOND_LOWRANK) {
+    key.lr_rank = o->lowrank_rank;
+    key.lr_over = o->lowrank_oversample;
+    key.lr_power = o->lowrank_power;
+  }
   Session *se = nullptr;
   for (auto &p : pl.sessions)
     if (p->key == key) { se = p.get(); break; }
@@ -749,6 +821,12 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
                          q.s));
   if (o->precond == SFL_PRECOND_DIAG)
     SFL_CU(cudaMemcpyAsync(se->dw, o->diag_w, sizeof(double) * n, cudaMemcpyDeviceToDevice, q.s));
+  if (se->lowrank) {
+    const int64_t no = (int64_t)se->lr.N2 * se->lr.l;
+    lr_omega_kernel<<<(unsigned)std::min<int64_t>((no + kThreads - 1) / kThreads, 1024), kThreads, 0, q.s>>>(
+        o->lowrank_omega, (float *)se->lr.Omega, no);
+    SFL_CU(cudaGetLastError());
+  }
   reset_state_kernel<<<1, 1, 0, q.s>>>(se->st, o->seed, o->eta, o->noise_norm, o->irw_eps);
   SFL_CU(cudaGetLastError());
   if (q.times) {

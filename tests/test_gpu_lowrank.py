@@ -1,0 +1,124 @@
+"""GPU parity of the low-rank truncation flexible operator in its randomized
+form (precond='lowrank': the rank-r randomized SVD of the new basis vector
+reshaped to the image, the -RND variants of Section 4.1) against the FP64
+oracle's LowRankRandomized with the same Gaussian test matrix.
+
+Bars: the GPU computes the truncation in FP32 (the small l x l problems in
+one CTA), the oracle in FP64; the truncated vector then differs at FP32
+rounding amplified by the spectral gap of the projected matrix.  Stated bar:
+relative 1e-4 for every iterate of a 20-step solve on a 64 x 64 deblurring and
+inpainting problem (rank 8, oversampling 6), and 1e-5 for the first iterate
+(one application of the operator).  Runs are bitwise reproducible.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+import torch  # noqa: E402
+
+from paper_2605_22281_gb300 import api as G  # noqa: E402
+
+RTOL_RND = 1e-4
+RTOL_RND_FIRST = 1e-5
+
+
+@pytest.fixture(autouse=True)
+def _needs_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("GPU test selected but no CUDA device is available")
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def deblur64():
+    """The deblurring recipe (Gaussian PSF of variance 0.25, half of the pixels
+    kept, 5% noise, block phantom) on a 64 x 64 image."""
+    p = wl.make("deblur512_lowrank", N=64)
+    return p, G.Plan(p.A, image_shape=(64, 64))
+
+
+def run_pair(p, plan, method, r, over, q, maxit, window=2, s=61, zeta=1, seed=48):
+    N = p.N
+    Om = np.random.default_rng(5).standard_normal((N, r + over))
+    tau = O.LowRankRandomized(r, (N, N), Om, q)
+    A = p.A.scipy()
+    if method == "sflsqr":
+        ref = O.sflsqr(A, p.b, O.SparseSign(seed, s, zeta, A.shape[0]), maxit=maxit, tol=0.0, ell=window, tau=tau,
+                       record_x=True, keep_basis=False)
+    elif method == "sflsmr":
+        ref = O.sflsmr(A, p.b, O.SparseSign(seed, s, zeta, A.shape[1]), S_stop=O.SparseSign(seed + 1, s, zeta, A.shape[0]),
+                       maxit=maxit, tol=0.0, ell=window, tau=tau, record_x=True, keep_basis=False)
+    else:   # flsqr: the exact projected problem = the sketched one with S = I
+        ref = O.sflsqr(A, p.b, O.IdentitySketch(A.shape[0]), maxit=maxit, tol=0.0, ell=-1, tau=tau, record_x=True,
+                       keep_basis=False)
+    kw = dict(s=s, zeta=zeta, seed=seed, window=window, maxit=maxit, precond="lowrank", lowrank_rank=r,
+              lowrank_oversample=over, lowrank_power=q, lowrank_omega=dev(Om), x_history=True)
+    if method == "flsqr":
+        kw.update(s=0, window=-1)
+    x, info, h = plan.solve(method, dev(p.b), **kw)
+    return ref, x, info, h, kw
+
+
+@pytest.mark.parametrize("method,q", [("sflsqr", 1), ("sflsmr", 1), ("sflsqr", 0), ("flsqr", 1)])
+def test_randomized_truncation_matches_oracle_every_step(deblur64, method, q):
+    p, plan = deblur64
+    ref, x, info, h, _ = run_pair(p, plan, method, 8, 6, q, 20)
+    assert info.iters == ref.iters == 20
+    xh = h["x"].cpu().numpy()
+    errs = [rel(xh[j], ref.xs[j]) for j in range(20)]
+    print(f"{method} q={q}: first iterate {errs[0]:.2e}, worst over 20 steps {max(errs):.2e}")
+    assert errs[0] <= RTOL_RND_FIRST
+    assert max(errs) <= RTOL_RND
+
+
+def test_truncation_changes_the_iterates(deblur64):
+    """The operator is really applied: x_1 is a rank-r image, unlike the
+    identity operator's."""
+    p, plan = deblur64
+    ref, x, info, h, kw = run_pair(p, plan, "sflsqr", 8, 6, 1, 3)
+    x1 = h["x"][0].cpu().numpy().reshape(p.N, p.N)
+    sv = np.linalg.svd(x1, compute_uv=False)
+    assert sv[8] <= 1e-5 * sv[0]                    # rank 8 up to FP32 rounding
+    xi, _, hi = plan.solve("sflsqr", dev(p.b), s=61, zeta=1, seed=48, window=2, maxit=3, x_history=True)
+    svi = np.linalg.svd(hi["x"][0].cpu().numpy().reshape(p.N, p.N), compute_uv=False)
+    assert svi[8] > 1e-3 * svi[0]
+
+
+def test_randomized_truncation_is_bitwise_reproducible(deblur64):
+    p, plan = deblur64
+    _, x1, i1, _, kw = run_pair(p, plan, "sflsmr", 8, 6, 1, 12)
+    x2, i2, _ = plan.solve("sflsmr", dev(p.b), **kw)
+    x3, i3, _ = plan.solve("sflsmr", dev(p.b), driver="host_loop", **kw)
+    assert torch.equal(x1, x2) and torch.equal(x1, x3)
+
+
+def test_lowrank_argument_checks(deblur64):
+    p, plan = deblur64
+    om = torch.zeros((64, 14), dtype=torch.float64, device="cuda")
+    kw = dict(s=61, zeta=1, window=2, maxit=5, precond="lowrank", lowrank_rank=8, lowrank_oversample=6,
+              lowrank_power=1, lowrank_omega=om)
+    no_shape = G.Plan(p.A)
+    with pytest.raises(G.N.SflError) as e:                 # the plan does not know the image shape
+        no_shape.solve("sflsqr", dev(p.b), **kw)
+    assert e.value.status == G.N.SFL_EINVAL
+    no_shape.close()
+    big = torch.zeros((64, 65), dtype=torch.float64, device="cuda")
+    with pytest.raises(G.N.SflError) as e:                 # r + p above 64
+        plan.solve("sflsqr", dev(p.b), **dict(kw, lowrank_rank=60, lowrank_oversample=5, lowrank_omega=big))
+    assert e.value.status == G.N.SFL_EINVAL
+    with pytest.raises(G.N.SflError) as e:
+        plan.solve("sflsqr", dev(p.b), orth_against="z", **kw)
+    assert e.value.status == G.N.SFL_EUNSUPPORTED
+    with pytest.raises(ValueError):                        # Omega of the wrong width
+        plan.solve("sflsqr", dev(p.b), **dict(kw, lowrank_oversample=5))

@@ -189,6 +189,47 @@ def decaying(m: int, n: int, rho: float, seed: int, level: float) -> tuple:
     return A, b, b_true, en
 
 
+def blur_inpaint_operator(N: int, psf_var: float, keep: float, rng: np.random.Generator, radius: int = 2) -> CSR:
+    """The deblurring-and-inpainting operator of the paper's motivating example
+    (Section 1.2, timings in Section 4.1): a Gaussian point-spread function of
+    variance psf_var on an N x N image (stencil of (2 radius + 1)^2 taps,
+    weights summing to 1, zero outside the image), followed by subsampling that
+    keeps a seeded `keep` fraction of the pixels (rows in increasing pixel
+    order).  Rows: kept pixels; columns: pixels (index row * N + col)."""
+    n = N * N
+    m = int(round(keep * n))
+    kept = np.sort(rng.choice(n, size=m, replace=False))
+    off = np.arange(-radius, radius + 1)
+    dy, dx = np.meshgrid(off, off, indexing="ij")
+    w = np.exp(-(dy ** 2 + dx ** 2) / (2.0 * psf_var))
+    w = (w / w.sum()).ravel()
+    dy, dx = dy.ravel(), dx.ravel()
+    iy, ix = kept // N, kept % N
+    yy = iy[:, None] + dy[None, :]
+    xx = ix[:, None] + dx[None, :]
+    ok = (yy >= 0) & (yy < N) & (xx >= 0) & (xx < N)
+    counts = ok.sum(axis=1)
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    cols = (yy * N + xx)[ok].astype(np.int32)
+    vals = np.broadcast_to(w, ok.shape)[ok].astype(np.float64)
+    return CSR((m, n), rowptr, cols, vals)
+
+
+def blocks_phantom(N: int, rng: np.random.Generator, nblocks: int = 12) -> np.ndarray:
+    """A synthetic stand-in for the paper's 'house' photograph (not available
+    here): a smooth background plus `nblocks` axis-aligned rectangles of
+    intensity U[0.2, 1] (numerically low rank, as the low-rank truncation
+    assumes).  Values in [0, ~2]."""
+    y, x = np.meshgrid(np.linspace(0, 1, N), np.linspace(0, 1, N), indexing="ij")
+    img = 0.3 + 0.2 * x + 0.1 * y
+    for _ in range(nblocks):
+        y0, x0 = rng.integers(0, N - N // 8, size=2)
+        h, wd = rng.integers(N // 16, N // 3, size=2)
+        img[y0:y0 + h, x0:x0 + wd] += rng.uniform(0.2, 1.0)
+    return img.ravel()
+
+
 @dataclass
 class Problem:
     """One synthetic CT problem: operator(s), phantoms, data and solver settings."""
@@ -228,6 +269,14 @@ WORKLOADS = {
                           unmatched=False,
                           settings=dict(method="sflsqr", s=401, zeta=8, window=2, maxit=200, eta=1.01,
                                         precond="identity", seed=45)),
+    # deblurring and inpainting with a rank-30 truncation: 512x512 image, Gaussian
+    # PSF of variance 0.25, half of the pixels kept, 5% noise, 50 steps, CountSketch
+    # with s = 101 (the timing experiment of Section 4.1).
+    "deblur512_lowrank": dict(N=512, operator="blur", psf_var=0.25, keep=0.5, phantom="blocks", nrhs=1,
+                              levels=(0.05,), data_seed=6, unmatched=False,
+                              settings=dict(method="sflsqr", s=101, zeta=1, window=2, maxit=50, eta=1.01,
+                                            precond="lowrank", rank=30, oversample=10, power=1, seed=48,
+                                            omega_seed=49)),
     # fixed-k = 30 differentiable solves, 256x256, batch 16, diagonal weight.
     "ct256_diff16": dict(N=256, n_angles=180, phantom="ellipses", nrhs=16, levels=(0.01,), data_seed=5,
                          unmatched=False,
@@ -241,15 +290,20 @@ def make(name: str, nrhs: int | None = None, **over) -> Problem:
     may override N / n_angles (for reduced-size test cases of the same recipe)."""
     spec = dict(WORKLOADS[name])
     N = over.get("N", spec["N"])
-    n_angles = over.get("n_angles", spec["n_angles"])
+    n_angles = over.get("n_angles", spec.get("n_angles", 0))
     n_bins = detector_bins(N)
-    A = siddon_projector(N, n_angles, n_bins)
+    if spec.get("operator") == "blur":
+        A = blur_inpaint_operator(N, spec["psf_var"], over.get("keep", spec["keep"]),
+                                  np.random.default_rng(spec["data_seed"] + 1000))
+        n_angles = n_bins = 0
+    else:
+        A = siddon_projector(N, n_angles, n_bins)
     B = pixel_backprojector(N, n_angles, n_bins) if spec["unmatched"] else None
     k = spec["nrhs"] if nrhs is None else nrhs
     xs, bs, enorms = [], [], []
     for j in range(k):
         rng = np.random.default_rng(spec["data_seed"] + j)
-        x = ellipse_phantom(N, rng) if spec["phantom"] == "ellipses" else sparse_phantom(N, rng)
+        x = {"ellipses": ellipse_phantom, "sparse": sparse_phantom, "blocks": blocks_phantom}[spec["phantom"]](N, rng)
         if spec["levels"] == "loguniform":
             level = float(math.exp(rng.uniform(math.log(0.005), math.log(0.05))))
         else:
@@ -259,6 +313,9 @@ def make(name: str, nrhs: int | None = None, **over) -> Problem:
     settings = dict(spec["settings"])
     if settings.get("precond") == "diag":
         settings["weight"] = np.random.default_rng(settings["weight_seed"]).uniform(0.5, 1.5, size=N * N)
+    if settings.get("precond") == "lowrank":   # Gaussian test matrix of the randomized SVD (N x (r + p))
+        settings["omega"] = np.random.default_rng(settings["omega_seed"]).standard_normal(
+            (N, settings["rank"] + settings["oversample"]))
     if k == 1:
         x_true, b = xs[0], bs[0]
     else:
