@@ -396,7 +396,7 @@ def mixed_variant(args, G, wl, np, torch, x_fp64=None):
     return out
 
 
-def flsqr_variant(args, G, wl, np, torch, steps: int = 50):
+def flsqr_variant(args, G, wl, np, torch, steps: int = 30):
     """The paper's FLSQR-against-sFLSQR timing comparison, on the GPU at
     1024x1024 (FP64, 481M nonzeros), at equal step counts: FLSQR (full
     orthogonalization by block CGS2, exact projected problem through H, no
@@ -685,7 +685,7 @@ def run_ours(args):
     if not args.no_variants:
         if args.workload == "ct1024_sflsqr":
             variants["mixed_ct1024_sflsqr"] = mixed_variant(args, G, wl, np, torch, x_fp64=leg["x"])
-            variants["flsqr_vs_sflsqr_ct1024_50_steps"] = flsqr_variant(args, G, wl, np, torch)
+            variants["flsqr_vs_sflsqr_ct1024_30_steps"] = flsqr_variant(args, G, wl, np, torch)
         if args.workload != "ct256_sflsmr_unmatched":
             variants["ct256_sflsmr_unmatched"] = ct256_variants(args, G, wl, np, torch)
         variants["batched_ct512_64rhs_f32"] = batched_variant(args, G, wl, np, torch)
