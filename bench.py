@@ -59,6 +59,8 @@ def parse_args():
                          "its geometry recipe, for profiling)")
     ap.add_argument("--only-decay", action="store_true",
                     help="run only the residual-size study (dense 1024 x 512, Gaussian sketches) and print its JSON")
+    ap.add_argument("--only-deblur", action="store_true",
+                    help="only the low-rank deblurring timing comparison (512x512, rank 30, 50 steps)")
     ap.add_argument("--only-flsqr", action="store_true",
                     help="only the FLSQR / sFLSQR comparison at equal step counts (1024x1024, FP64)")
     ap.add_argument("--only-diff", action="store_true",
@@ -431,6 +433,53 @@ def flsqr_variant(args, G, wl, np, torch, steps: int = 30):
     return out
 
 
+def deblur_variant(args, G, wl, np, torch, N: int = 512):
+    """The timing experiment of Section 4.1 on the GPU: deblurring and
+    inpainting of a 512x512 image (Gaussian PSF of variance 0.25, half of the
+    pixels kept, 5% noise, synthetic block image), 50 steps of each method
+    with no stop, rank-30 truncation by the randomized SVD (oversampling 10,
+    one subspace-iteration step), CountSketch with s = 101, window 2.  FP64
+    operator and vectors; the truncation itself is FP32."""
+    p = wl.make("deblur512_lowrank", N=N) if N != 512 else wl.make("deblur512_lowrank")
+    st = p.settings
+    plan = G.Plan(p.A, value_dtype="f64", image_shape=(p.N, p.N))
+    b = torch.as_tensor(p.b, device="cuda")
+    om = torch.as_tensor(st["omega"], device="cuda")
+    lr = dict(precond="lowrank", lowrank_rank=st["rank"], lowrank_oversample=st["oversample"],
+              lowrank_power=st["power"], lowrank_omega=om)
+    sk = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"])
+    legs = {"flsqr_identity": ("flsqr", dict(s=0, window=-1)),
+            "sflsqr_identity": ("sflsqr", dict(sk)),
+            "flsqr_rnd": ("flsqr", dict(s=0, window=-1, **lr)),
+            "sflsqr_rnd": ("sflsqr", dict(sk, **lr)),
+            "sflsmr_rnd": ("sflsmr", dict(sk, **lr))}
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"image": f"{p.N}x{p.N}", "m": p.A.shape[0], "n": p.A.shape[1], "nnz": int(p.A.nnz), "steps": st["maxit"],
+           "rank": st["rank"], "oversample": st["oversample"], "power": st["power"], "s": st["s"], "zeta": st["zeta"]}
+    for name, (method, kw) in legs.items():
+        x, info, _ = plan.solve(method, b, maxit=st["maxit"], **kw)
+        torch.cuda.synchronize()
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            plan.solve(method, b, maxit=st["maxit"], out=x, sync=False, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        xh = x.cpu().numpy()
+        leg = {"iters": info.iters, "stop": info.status_name, "ms": ms, "ms_per_step": ms / max(info.iters, 1),
+               "rel_residual": float(np.linalg.norm(p.A.matvec(xh) - p.b) / np.linalg.norm(p.b)),
+               "rel_error_vs_x_true": float(np.linalg.norm(xh - p.x_true) / np.linalg.norm(p.x_true))}
+        if name == "sflsqr_rnd":
+            _, _, hp = plan.solve(method, b, maxit=st["maxit"], driver="profiled", **kw)
+            leg["kernel_ms_per_step"] = {c: hp["kernel_ms"][c] / max(info.iters, 1) for c in hp["kernel_ms"]
+                                         if hp["kernel_launches"][c] > 0}
+        out[name] = leg
+    plan.close()
+    return out
+
+
 def diff_variant(args, G, wl, np, torch):
     """The differentiable form: 16 sinograms of 256x256 phantoms, fixed k = 30
     steps of sFLSQR with a diagonal weight (s = 61, window 2), FP32 values and
@@ -647,7 +696,7 @@ def run_ours(args):
     from paper_2605_22281_gb300 import api as G
 
     for flag, leg in (("only_batched", batched_variant), ("only_mixed", mixed_variant), ("only_diff", diff_variant),
-                      ("only_decay", decay_variant), ("only_flsqr", flsqr_variant)):
+                      ("only_decay", decay_variant), ("only_flsqr", flsqr_variant), ("only_deblur", deblur_variant)):
         if getattr(args, flag):
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             print(json.dumps(leg(args, G, wl, np, torch)), flush=True)
@@ -690,6 +739,7 @@ def run_ours(args):
             variants["ct256_sflsmr_unmatched"] = ct256_variants(args, G, wl, np, torch)
         variants["batched_ct512_64rhs_f32"] = batched_variant(args, G, wl, np, torch)
         variants["diff_ct256_16rhs_fixed_k"] = diff_variant(args, G, wl, np, torch)
+        variants["deblur512_lowrank_rnd_50_steps"] = deblur_variant(args, G, wl, np, torch)
         variants["decay_study_gaussian"] = decay_variant(args, G, wl, np, torch)
         variants["ct64_sflsqr"] = small_variant(args, G, wl, np, torch)
 
