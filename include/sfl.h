@@ -185,15 +185,18 @@ typedef struct {
   int32_t orth_against_z;
   const double *sketch_dense;
   const double *sketch_dense_stop;
-  /* SFL_PRECOND_LOWRANK: rank r (>= 1), oversampling p (l = r + p <= 64 and
-   * l <= min(image_rows, image_cols)), subspace-iteration steps q (0..4), and
-   * the Gaussian test matrix Omega: device FP64, image_cols x l, row-major,
-   * caller-owned, read at the start of every solve (the same Omega serves
-   * every step).  Ignored for the other operators. */
+  /* SFL_PRECOND_LOWRANK: rank r (>= 1), oversampling p (l = r + p <= 64, or
+   * <= 48 with lowrank_fp64, and l <= min(image_rows, image_cols)),
+   * subspace-iteration steps q (0..4), the Gaussian test matrix Omega (device
+   * FP64, image_cols x l, row-major, caller-owned, read at the start of every
+   * solve; the same Omega serves every step), and lowrank_fp64 = 1 to compute
+   * the truncation in FP64 instead of FP32 (slower; for verification).
+   * Ignored for the other operators. */
   int32_t lowrank_rank;
   int32_t lowrank_oversample;
   int32_t lowrank_power;
   const double *lowrank_omega;
+  int32_t lowrank_fp64;
 } sfl_opts;
 
 /* Result of a solve.  Filled when the call returns (the call then waits for

@@ -40,7 +40,7 @@ class Opts(ctypes.Structure):
                 ("orth_against_z", ctypes.c_int32), ("sketch_dense", ctypes.c_void_p),
                 ("sketch_dense_stop", ctypes.c_void_p), ("lowrank_rank", ctypes.c_int32),
                 ("lowrank_oversample", ctypes.c_int32), ("lowrank_power", ctypes.c_int32),
-                ("lowrank_omega", ctypes.c_void_p)]
+                ("lowrank_omega", ctypes.c_void_p), ("lowrank_fp64", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -119,25 +119,25 @@ class Plan:
         return y
 
     def _opts(self, s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, diag_w, irw_eps,
-              vec_dtype, x_hist, r_hist, orth_against="p", sk=None, sk_stop=None, lowrank=(0, 0, 0, None)):
+              vec_dtype, x_hist, r_hist, orth_against="p", sk=None, sk_stop=None, lowrank=(0, 0, 0, None, 0)):
         if orth_against not in ("p", "z"):
             raise ValueError(orth_against)
         return N.Opts(s, zeta, seed, window, maxit, float(noise_norm), float(eta), N.PRECOND[precond],
                       N.STOP_RULE[stop_rule], _ptr(diag_w), float(irw_eps), N.DTYPE[vec_dtype], 0,
                       _ptr(x_hist), _ptr(r_hist), 1 if orth_against == "z" else 0, _ptr(sk), _ptr(sk_stop),
-                      int(lowrank[0]), int(lowrank[1]), int(lowrank[2]), _ptr(lowrank[3]))
+                      int(lowrank[0]), int(lowrank[1]), int(lowrank[2]), _ptr(lowrank[3]), int(lowrank[4]))
 
-    def _lowrank(self, precond, rank, oversample, power, omega):
+    def _lowrank(self, precond, rank, oversample, power, omega, fp64=False):
         """(rank, oversample, power, Omega) of the low-rank operator, Omega as a
         contiguous FP64 device tensor (image_cols x (rank + oversample))."""
         if precond != "lowrank":
-            return (0, 0, 0, None)
+            return (0, 0, 0, None, 0)
         if omega is None:
             raise ValueError("precond='lowrank' needs lowrank_omega (image_cols x (rank + oversample))")
         om = omega.to(device=self.device, dtype=torch.float64).contiguous()
         if om.dim() != 2 or om.shape[1] != rank + oversample:
             raise ValueError(f"lowrank_omega of shape {tuple(om.shape)}, expected (image_cols, {rank + oversample})")
-        return (rank, oversample, power, om)
+        return (rank, oversample, power, om, 1 if fp64 else 0)
 
     def _dense_sketch(self, S, rows, cols):
         if S is None:
@@ -154,7 +154,7 @@ class Plan:
               driver: str = "graph", out: torch.Tensor | None = None, sync: bool = True,
               orth_against: str = "p", sketch_matrix: torch.Tensor | None = None,
               sketch_matrix_stop: torch.Tensor | None = None, lowrank_rank: int = 30, lowrank_oversample: int = 10,
-              lowrank_power: int = 1, lowrank_omega: torch.Tensor | None = None):
+              lowrank_power: int = 1, lowrank_omega: torch.Tensor | None = None, lowrank_fp64: bool = False):
         """Run sFLSQR (method='sflsqr', Algorithm 1), sFLSMR ('sflsmr', Algorithm
         2) or the unsketched FLSQR ('flsqr', eq. (FLSQR); needs window < 0).
         window < 0: full orthogonalization (block CGS2 against every earlier
@@ -168,7 +168,8 @@ class Plan:
         has run when sync=False).  precond='lowrank': z = the rank-r randomized-SVD
         truncation of p reshaped to the plan's image (lowrank_rank r,
         lowrank_oversample p, lowrank_power q subspace-iteration steps, and the
-        Gaussian test matrix lowrank_omega, image_cols x (r + p)).
+        Gaussian test matrix lowrank_omega, image_cols x (r + p); FP32
+        arithmetic, or FP64 with lowrank_fp64).
         Returns (x, info, hist) where hist holds the
         optional per-step iterates (maxit x n) and stop ratios.  With sync=False
         the call does not wait and info is None."""
@@ -182,7 +183,7 @@ class Plan:
         rh = torch.zeros(maxit, dtype=torch.float64, device=dev) if relres_history else None
         sk = self._dense_sketch(sketch_matrix, s, self.m if method == "sflsqr" else self.n)
         sks = self._dense_sketch(sketch_matrix_stop, s, self.m)
-        lr = self._lowrank(precond, lowrank_rank, lowrank_oversample, lowrank_power, lowrank_omega)
+        lr = self._lowrank(precond, lowrank_rank, lowrank_oversample, lowrank_power, lowrank_omega, lowrank_fp64)
         o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
                        xh, rh, orth_against, sk, sks, lr)
         info = N.Info()

@@ -30,12 +30,12 @@ struct SessionKey {
   double *x_hist, *r_hist;
   int orth_z;        // 1: the z window is the stored z_j (sfl_opts.orth_against_z)
   const double *dense_S, *dense_Sm;   // explicit sketches (sfl_opts.sketch_dense, sketch_dense_stop)
-  int lr_rank = 0, lr_over = 0, lr_power = 0;   // low-rank truncation (SFL_PRECOND_LOWRANK)
+  int lr_rank = 0, lr_over = 0, lr_power = 0, lr_fp64 = 0;   // low-rank truncation (SFL_PRECOND_LOWRANK)
   bool operator==(const SessionKey &o) const {
     return method == o.method && s == o.s && zeta == o.zeta && ell == o.ell && maxit == o.maxit &&
            precond == o.precond && stop_rule == o.stop_rule && vdt == o.vdt && x_hist == o.x_hist &&
            r_hist == o.r_hist && orth_z == o.orth_z && dense_S == o.dense_S && dense_Sm == o.dense_Sm &&
-           lr_rank == o.lr_rank && lr_over == o.lr_over && lr_power == o.lr_power;
+           lr_rank == o.lr_rank && lr_over == o.lr_over && lr_power == o.lr_power && lr_fp64 == o.lr_fp64;
   }
 };
 
@@ -66,7 +66,8 @@ struct Session {
   int grid_cgs = 0;
   // low-rank truncation by the randomized SVD (SFL_PRECOND_LOWRANK)
   bool lowrank = false;
-  LrParams lr{};
+  LrParams<float> lr32{};       // FP32 arithmetic (default)
+  LrParams<double> lr64{};      // FP64 arithmetic (sfl_opts.lowrank_fp64)
   int *err = nullptr;
   Partials part{};                     // per-CTA partial sums of the reducing kernels
   int32_t *wrowA = nullptr, *wrowT = nullptr;   // nnz-balanced row range of every warp

@@ -14,8 +14,9 @@
 // C_r is positively homogeneous in C, so it is applied to the unnormalised
 // p~_k and keeps the scale sig_p(k).
 //
-// Arithmetic is FP32 (a regularizing truncation; the FP64 oracle states the
-// error), with the l x l problems in one CTA:
+// Arithmetic is FP32 by default (a regularizing truncation; the FP64 oracle
+// states the error), or FP64 on request (for verification), with the l x l
+// problems in one CTA:
 //  - orth() is shifted Cholesky QR followed by plain Cholesky QR twice
 //    (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput.
 //    2020): G = Y^T Y (+ shift), G = R^T R, Q = Y R^{-1};
@@ -29,20 +30,32 @@
 
 namespace sfl {
 
-constexpr int kLrMaxL = 64;       // largest r + oversampling
 constexpr int kLrTile = 32;       // rows of a product tile
 constexpr int kLrK = 64;          // depth of one split-K chunk
-constexpr int kLrGramRows = 64;   // rows per CTA of the Gram partials
 
+// Per compute type (FP32 default, FP64 for verification): largest r +
+// oversampling, rows per CTA of the Gram partials, unit roundoff, and the
+// Jacobi stopping threshold on (off-diagonal / diagonal) squared norms.
+template <typename RT> struct LrLim;
+template <> struct LrLim<float> {
+  static constexpr int L = 64, GR = 64;
+  static constexpr float u = 5.9604645e-8f, jacobi_tol = 4e-14f;
+};
+template <> struct LrLim<double> {
+  static constexpr int L = 48, GR = 32;
+  static constexpr double u = 1.1102230246251565e-16, jacobi_tol = 1e-30;
+};
+
+template <typename RT>
 struct LrParams {
   SolveState *st;
   int N1, N2, l, r, q;
-  const float *Omega;             // N2 x l (row-major)
-  float *Y, *Qm, *Qt, *Bt;        // N1 x l, N1 x l, N2 x l, N2 x l
-  float *U, *V;                   // N1 x r, N2 x r
-  float *part;                    // split-K partials [KS][max(N1,N2)][l]
-  float *gpart;                   // Gram partials [CTAs][l * l]
-  float *small;                   // l x l factors (R^{-1} or W_r) of the latest small step
+  const RT *Omega;                // N2 x l (row-major)
+  RT *Y, *Qm, *Qt, *Bt;           // N1 x l, N1 x l, N2 x l, N2 x l
+  RT *U, *V;                      // N1 x r, N2 x r
+  RT *part;                       // split-K partials [KS][max(N1,N2)][l]
+  RT *gpart;                      // Gram partials [CTAs][l * l]
+  RT *small;                      // l x l factors (R^{-1} or W_r) of the latest small step
   int *flag;                      // nonzero: a Cholesky pivot failed (the step keeps tau = identity)
   int *ticket;                    // arrival counter of the last-CTA steps (zero between launches)
 };
@@ -54,10 +67,10 @@ __device__ __forceinline__ bool lr_running(const SolveState *st) { return __ldcg
 // from the solver's vector (type XT) at column `col` of Z.  Tiles: 32 rows x l
 // columns, K in chunks of 64 staged in shared memory; thread (row, c0) sums
 // columns c0, c0 + 8, ...
-template <typename XT, bool TRANS>
-__global__ void __launch_bounds__(kThreads) lr_mul_kernel(LrParams p, const XT *Z, int64_t zstride, const float *X) {
-  __shared__ float As[kLrTile][kLrK + 1];
-  __shared__ float Xs[kLrK][kLrMaxL];
+template <typename RT, typename XT, bool TRANS>
+__global__ void __launch_bounds__(kThreads) lr_mul_kernel(LrParams<RT> p, const XT *Z, int64_t zstride, const RT *X) {
+  __shared__ RT As[kLrTile][kLrK + 1];
+  __shared__ RT Xs[kLrK][LrLim<RT>::L];
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
   const int k = __ldcg(&p.st->k) + 1;
   const XT *C = Z + (size_t)(k - 1) * zstride;   // p~_k (the z update stored it unmodified)
@@ -69,55 +82,57 @@ __global__ void __launch_bounds__(kThreads) lr_mul_kernel(LrParams p, const XT *
     if (TRANS) { kk = t / kLrTile; ii = t % kLrTile; }   // C[k][i]: consecutive i are contiguous
     else { ii = t / kLrK; kk = t % kLrK; }              // C[i][k]: consecutive k are contiguous
     const int i = i0 + ii, kx = k0 + kk;
-    float v = 0.f;
-    if (i < M && kx < K) v = (float)(TRANS ? C[(size_t)kx * p.N2 + i] : C[(size_t)i * p.N2 + kx]);
+    RT v = RT(0.);
+    if (i < M && kx < K) v = (RT)(TRANS ? C[(size_t)kx * p.N2 + i] : C[(size_t)i * p.N2 + kx]);
     As[ii][kk] = v;
   }
   for (int t = tid; t < kLrK * L; t += kThreads) {
     const int kk = t / L, c = t % L, kx = k0 + kk;
-    Xs[kk][c] = kx < K ? X[(size_t)kx * L + c] : 0.f;
+    Xs[kk][c] = kx < K ? X[(size_t)kx * L + c] : RT(0.);
   }
   __syncthreads();
   const int row = tid >> 3, c0 = tid & 7;
-  float acc[kLrMaxL / 8];
+  RT acc[LrLim<RT>::L / 8];
 #pragma unroll
-  for (int j = 0; j < kLrMaxL / 8; ++j) acc[j] = 0.f;
+  for (int j = 0; j < LrLim<RT>::L / 8; ++j) acc[j] = RT(0.);
   for (int kk = 0; kk < kLrK; ++kk) {
-    const float a = As[row][kk];
+    const RT a = As[row][kk];
 #pragma unroll
-    for (int j = 0; j < kLrMaxL / 8; ++j) {
+    for (int j = 0; j < LrLim<RT>::L / 8; ++j) {
       const int c = c0 + 8 * j;
-      if (c < L) acc[j] = fmaf(a, Xs[kk][c], acc[j]);
+      if (c < L) acc[j] = fma(a, Xs[kk][c], acc[j]);
     }
   }
   const int i = i0 + row;
   if (i < M) {
-    float *out = p.part + ((size_t)blockIdx.y * M + i) * L;
+    RT *out = p.part + ((size_t)blockIdx.y * M + i) * L;
 #pragma unroll
-    for (int j = 0; j < kLrMaxL / 8; ++j) {
+    for (int j = 0; j < LrLim<RT>::L / 8; ++j) {
       const int c = c0 + 8 * j;
       if (c < L) out[c] = acc[j];
     }
   }
 }
 
-// Gram partials of this CTA's rows of X (kLrGramRows x l staged in Xs):
+// Gram partials of this CTA's rows of X (LrLim<RT>::GR x l staged in Xs):
 // gp[blockIdx.x][a * l + c] for a <= c, rows added in order.
-__device__ __forceinline__ void lr_gram_partial(const LrParams &p, const float (*Xs)[kLrMaxL], int nr) {
+template <typename RT>
+__device__ __forceinline__ void lr_gram_partial(const LrParams<RT> &p, const RT (*Xs)[LrLim<RT>::L], int nr) {
   const int L = p.l;
-  float *out = p.gpart + (size_t)blockIdx.x * L * L;
+  RT *out = p.gpart + (size_t)blockIdx.x * L * L;
   for (int t = threadIdx.x; t < L * L; t += kThreads) {
     const int a = t / L, c = t % L;
     if (a > c) continue;
-    float s = 0.f;
-    for (int i = 0; i < nr; ++i) s = fmaf(Xs[i][a], Xs[i][c], s);
+    RT s = RT(0.);
+    for (int i = 0; i < nr; ++i) s = fma(Xs[i][a], Xs[i][c], s);
     out[t] = s;
   }
 }
 
 // Last-arriving CTA of a launch (ticket counter, reset by that CTA): true in
 // every thread of that CTA only.  The CTA's global writes are fenced first.
-__device__ __forceinline__ bool lr_last_cta(const LrParams &p, int *s_last) {
+template <typename RT>
+__device__ __forceinline__ bool lr_last_cta(const LrParams<RT> &p, int *s_last) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) *s_last = atomicAdd(p.ticket, 1) == (int)gridDim.x - 1;
@@ -129,12 +144,13 @@ __device__ __forceinline__ bool lr_last_cta(const LrParams &p, int *s_last) {
 }
 
 // G = sum of the nb Gram partials (in order), both triangles.
-__device__ __forceinline__ void lr_load_gram(const LrParams &p, int nb, float (*G)[kLrMaxL + 1]) {
+template <typename RT>
+__device__ __forceinline__ void lr_load_gram(const LrParams<RT> &p, int nb, RT (*G)[LrLim<RT>::L + 1]) {
   const int L = p.l;
   for (int t = threadIdx.x; t < L * L; t += kThreads) {
     const int a = t / L, c = t % L;
     if (a > c) continue;
-    float s = 0.f;
+    RT s = RT(0.);
     for (int b = 0; b < nb; ++b) s += __ldcg(p.gpart + (size_t)b * L * L + t);
     G[a][c] = s;
     G[c][a] = s;
@@ -145,11 +161,12 @@ __device__ __forceinline__ void lr_load_gram(const LrParams &p, int nb, float (*
 // Cholesky G + shift I = R^T R (upper R) and R^{-1} into p.small (l x l,
 // row-major, zero below the diagonal).  All threads of one CTA.  A pivot that
 // is not positive sets *p.flag (then the step keeps tau = identity).
-static __device__ void lr_cholesky_inverse(const LrParams &p, float (*G)[kLrMaxL + 1], float shift_rel, float *s_tr) {
+template <typename RT>
+static __device__ void lr_cholesky_inverse(const LrParams<RT> &p, RT (*G)[LrLim<RT>::L + 1], RT shift_rel, RT *s_tr) {
   const int L = p.l, tid = threadIdx.x;
-  if (shift_rel > 0.f) {
+  if (shift_rel > RT(0.)) {
     if (tid == 0) {
-      float tr = 0.f;
+      RT tr = RT(0.);
       for (int a = 0; a < L; ++a) tr += G[a][a];
       *s_tr = tr;
     }
@@ -158,12 +175,12 @@ static __device__ void lr_cholesky_inverse(const LrParams &p, float (*G)[kLrMaxL
   }
   for (int j = 0; j < L; ++j) {
     __syncthreads();
-    const float d = G[j][j];
-    if (!(d > 0.f)) {
+    const RT d = G[j][j];
+    if (!(d > RT(0.))) {
       if (tid == 0) *p.flag = 1;
       return;
     }
-    const float rd = rsqrtf(d);
+    const RT rd = rsqrt(d);
     __syncthreads();
     for (int c = j + tid; c < L; c += kThreads) G[j][c] *= rd;
     __syncthreads();
@@ -176,46 +193,47 @@ static __device__ void lr_cholesky_inverse(const LrParams &p, float (*G)[kLrMaxL
   __syncthreads();
   // column c of R^{-1}: back substitution, one thread per column
   for (int c = tid; c < L; c += kThreads) {
-    float col[kLrMaxL];
-    col[c] = 1.f / G[c][c];
+    RT col[LrLim<RT>::L];
+    col[c] = RT(1.) / G[c][c];
     for (int a = c - 1; a >= 0; --a) {
-      float s = 0.f;
-      for (int t = a + 1; t <= c; ++t) s = fmaf(G[a][t], col[t], s);
+      RT s = RT(0.);
+      for (int t = a + 1; t <= c; ++t) s = fma(G[a][t], col[t], s);
       col[a] = -s / G[a][a];
     }
-    for (int a = 0; a < L; ++a) p.small[a * L + c] = a <= c ? col[a] : 0.f;
+    for (int a = 0; a < L; ++a) p.small[a * L + c] = a <= c ? col[a] : RT(0.);
   }
 }
 
-// One Cholesky-QR pass over X (M x l), rows in blocks of kLrGramRows per CTA:
+// One Cholesky-QR pass over X (M x l), rows in blocks of LrLim<RT>::GR per CTA:
 //   mode 0: X = the sum of the KS split-K partials of a product (written to out);
 //   mode 1: out = in * p.small (the previous pass's R^{-1});
 // then the Gram partials of out, and in the last CTA the Cholesky factor of
 // their sum (+ shift) and its inverse into p.small.
-static __global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams p, int mode, const float *in, float *out, int M,
-                                                           int KS, float shift_rel) {
-  __shared__ float Xs[kLrGramRows][kLrMaxL];
-  __shared__ float SG[kLrMaxL * (kLrMaxL + 1)];   // S (this pass's input factor), later G (last CTA)
+template <typename RT>
+static __global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams<RT> p, int mode, const RT *in, RT *out, int M,
+                                                           int KS, RT shift_rel) {
+  __shared__ RT Xs[LrLim<RT>::GR][LrLim<RT>::L];
+  __shared__ RT SG[LrLim<RT>::L * (LrLim<RT>::L + 1)];   // S (this pass's input factor), later G (last CTA)
   __shared__ int s_last;
-  __shared__ float s_tr;
-  float *S = SG;
-  auto G = reinterpret_cast<float (*)[kLrMaxL + 1]>(SG);
+  __shared__ RT s_tr;
+  RT *S = SG;
+  auto G = reinterpret_cast<RT (*)[LrLim<RT>::L + 1]>(SG);
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
-  const int L = p.l, r0 = blockIdx.x * kLrGramRows, tid = threadIdx.x;
-  const int nr = min(kLrGramRows, M - r0);
+  const int L = p.l, r0 = blockIdx.x * LrLim<RT>::GR, tid = threadIdx.x;
+  const int nr = min(LrLim<RT>::GR, M - r0);
   if (mode == 1)
     for (int t = tid; t < L * L; t += kThreads) S[t] = __ldcg(p.small + t);
   __syncthreads();
-  for (int t = tid; t < kLrGramRows * L; t += kThreads) {
+  for (int t = tid; t < LrLim<RT>::GR * L; t += kThreads) {
     const int i = t / L, c = t % L;
-    float v = 0.f;
+    RT v = RT(0.);
     if (i < nr) {
       const size_t idx = (size_t)(r0 + i) * L + c;
       if (mode == 0) {
         for (int ks = 0; ks < KS; ++ks) v += p.part[(size_t)ks * M * L + idx];
       } else {
-        const float *x = in + (size_t)(r0 + i) * L;
-        for (int j = 0; j < L; ++j) v = fmaf(x[j], S[j * L + c], v);
+        const RT *x = in + (size_t)(r0 + i) * L;
+        for (int j = 0; j < L; ++j) v = fma(x[j], S[j * L + c], v);
       }
       out[idx] = v;
     }
@@ -229,21 +247,23 @@ static __global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams p, in
 }
 
 // out[i][0..ncol) = in[i][0..l) * p.small (l x ncol).
-__device__ __forceinline__ void lr_apply_rows(const LrParams &p, const float *S, const float *in, int64_t M, int ncol,
-                                              float *out, int64_t t0, int64_t stride) {
+template <typename RT>
+__device__ __forceinline__ void lr_apply_rows(const LrParams<RT> &p, const RT *S, const RT *in, int64_t M, int ncol,
+                                              RT *out, int64_t t0, int64_t stride) {
   const int L = p.l;
   for (int64_t t = t0; t < M * ncol; t += stride) {
     const int64_t i = t / ncol;
     const int c = (int)(t % ncol);
-    const float *x = in + i * L;
-    float a = 0.f;
-    for (int j = 0; j < L; ++j) a = fmaf(x[j], S[j * ncol + c], a);
+    const RT *x = in + i * L;
+    RT a = RT(0.);
+    for (int j = 0; j < L; ++j) a = fma(x[j], S[j * ncol + c], a);
     out[t] = a;
   }
 }
 
-static __global__ void __launch_bounds__(kThreads) lr_apply_kernel(LrParams p, const float *in, int M, float *out) {
-  __shared__ float S[kLrMaxL * kLrMaxL];
+template <typename RT>
+static __global__ void __launch_bounds__(kThreads) lr_apply_kernel(LrParams<RT> p, const RT *in, int M, RT *out) {
+  __shared__ RT S[LrLim<RT>::L * LrLim<RT>::L];
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
   for (int t = threadIdx.x; t < p.l * p.l; t += kThreads) S[t] = __ldcg(p.small + t);
   __syncthreads();
@@ -254,23 +274,24 @@ static __global__ void __launch_bounds__(kThreads) lr_apply_kernel(LrParams p, c
 // its Gram partials, and in the last CTA the eigenvectors of B B^T = (B^T)^T B^T
 // by cyclic Jacobi; the r leading ones (by decreasing eigenvalue) go to p.small
 // (l x r).
-static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p, int KS) {
-  __shared__ float XV[kLrMaxL * (kLrMaxL + 1)];   // the CTA's rows of B^T, later the eigenvectors (last CTA)
-  __shared__ float A[kLrMaxL][kLrMaxL + 1];
-  auto Xs = reinterpret_cast<float (*)[kLrMaxL]>(XV);
-  auto Vm = reinterpret_cast<float (*)[kLrMaxL + 1]>(XV);
-  __shared__ float cs[kLrMaxL / 2][2];
-  __shared__ int pr[kLrMaxL / 2][2];
-  __shared__ int order[kLrMaxL];
-  __shared__ float red[2][kWarps];
+template <typename RT>
+static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams<RT> p, int KS) {
+  __shared__ RT XV[LrLim<RT>::L * (LrLim<RT>::L + 1)];   // the CTA's rows of B^T, later the eigenvectors (last CTA)
+  __shared__ RT A[LrLim<RT>::L][LrLim<RT>::L + 1];
+  auto Xs = reinterpret_cast<RT (*)[LrLim<RT>::L]>(XV);
+  auto Vm = reinterpret_cast<RT (*)[LrLim<RT>::L + 1]>(XV);
+  __shared__ RT cs[LrLim<RT>::L / 2][2];
+  __shared__ int pr[LrLim<RT>::L / 2][2];
+  __shared__ int order[LrLim<RT>::L];
+  __shared__ RT red[2][kWarps];
   __shared__ int s_last, s_go;
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
-  const int L = p.l, M = p.N2, r0 = blockIdx.x * kLrGramRows, tid = threadIdx.x;
+  const int L = p.l, M = p.N2, r0 = blockIdx.x * LrLim<RT>::GR, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int nr = min(kLrGramRows, M - r0);
-  for (int t = tid; t < kLrGramRows * L; t += kThreads) {
+  const int nr = min(LrLim<RT>::GR, M - r0);
+  for (int t = tid; t < LrLim<RT>::GR * L; t += kThreads) {
     const int i = t / L, c = t % L;
-    float v = 0.f;
+    RT v = RT(0.);
     if (i < nr) {
       const size_t idx = (size_t)(r0 + i) * L + c;
       for (int ks = 0; ks < KS; ++ks) v += p.part[(size_t)ks * M * L + idx];
@@ -283,19 +304,19 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p
   if (!lr_last_cta(p, &s_last)) return;
   lr_load_gram(p, gridDim.x, A);
   const int n = L + (L & 1);            // even order; a padded index is a zero row and column
-  for (int t = tid; t < kLrMaxL * kLrMaxL; t += kThreads) {
-    const int a = t / kLrMaxL, c = t % kLrMaxL;
-    Vm[a][c] = a == c ? 1.f : 0.f;
-    if (a >= L || c >= L) A[a][c] = 0.f;
+  for (int t = tid; t < LrLim<RT>::L * LrLim<RT>::L; t += kThreads) {
+    const int a = t / LrLim<RT>::L, c = t % LrLim<RT>::L;
+    Vm[a][c] = a == c ? RT(1.) : RT(0.);
+    if (a >= L || c >= L) A[a][c] = RT(0.);
   }
   __syncthreads();
   const int np = n / 2;
   for (int sweep = 0; sweep < 16; ++sweep) {
-    // stop when the off-diagonal mass is below (2e-7)^2 of the diagonal's
-    float off = 0.f, dg = 0.f;
+    // stop when the off-diagonal mass is below the type's threshold times the diagonal's
+    RT off = RT(0.), dg = RT(0.);
     for (int t = tid; t < L * L; t += kThreads) {
       const int a = t / L, c = t % L;
-      const float v = A[a][c] * A[a][c];
+      const RT v = A[a][c] * A[a][c];
       if (a == c) dg += v; else off += v;
     }
     off = warp_sum(off);
@@ -303,9 +324,9 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p
     if (lane == 0) { red[0][warp] = off; red[1][warp] = dg; }
     __syncthreads();
     if (tid == 0) {
-      float o = 0.f, d = 0.f;
+      RT o = RT(0.), d = RT(0.);
       for (int w = 0; w < kWarps; ++w) { o += red[0][w]; d += red[1][w]; }
-      s_go = o > 4e-14f * d;
+      s_go = o > LrLim<RT>::jacobi_tol * d;
     }
     __syncthreads();
     if (!s_go) break;
@@ -315,13 +336,13 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p
         int a = u == 0 ? 0 : 1 + (u - 1 + round) % (n - 1);
         int b = 1 + (v - 1 + round) % (n - 1);
         if (a > b) { const int t = a; a = b; b = t; }
-        float c = 1.f, s = 0.f;
-        const float apq = A[a][b];
-        if (b < L && fabsf(apq) > 1e-20f * sqrtf(fabsf(A[a][a] * A[b][b])) && apq != 0.f) {
-          const float tau = (A[b][b] - A[a][a]) / (2.f * apq);
-          const float t = fabsf(tau) > 1e15f ? 0.5f / tau
-                                             : copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-          c = rsqrtf(fmaf(t, t, 1.f));
+        RT c = RT(1.), s = RT(0.);
+        const RT apq = A[a][b];
+        if (b < L && fabs(apq) > RT(1e-20) * sqrt(fabs(A[a][a] * A[b][b])) && apq != RT(0.)) {
+          const RT tau = (A[b][b] - A[a][a]) / (RT(2.) * apq);
+          const RT t = fabs(tau) > RT(1e15) ? RT(0.5) / tau
+                                             : copysign(RT(1.), tau) / (fabs(tau) + sqrt(fma(tau, tau, RT(1.))));
+          c = rsqrt(fma(t, t, RT(1.)));
           s = t * c;
         }
         pr[tid][0] = a; pr[tid][1] = b;
@@ -331,8 +352,8 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p
       for (int t = tid; t < np * n; t += kThreads) {   // rows: A <- J^T A
         const int k = t / n, j = t % n;
         const int a = pr[k][0], b = pr[k][1];
-        const float c = cs[k][0], s = cs[k][1];
-        const float x = A[a][j], y = A[b][j];
+        const RT c = cs[k][0], s = cs[k][1];
+        const RT x = A[a][j], y = A[b][j];
         A[a][j] = c * x - s * y;
         A[b][j] = s * x + c * y;
       }
@@ -340,11 +361,11 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p
       for (int t = tid; t < np * n; t += kThreads) {   // columns: A <- A J, V <- V J
         const int k = t / n, i = t % n;
         const int a = pr[k][0], b = pr[k][1];
-        const float c = cs[k][0], s = cs[k][1];
-        const float x = A[i][a], y = A[i][b];
+        const RT c = cs[k][0], s = cs[k][1];
+        const RT x = A[i][a], y = A[i][b];
         A[i][a] = c * x - s * y;
         A[i][b] = s * x + c * y;
-        const float u = Vm[i][a], w = Vm[i][b];
+        const RT u = Vm[i][a], w = Vm[i][b];
         Vm[i][a] = c * u - s * w;
         Vm[i][b] = s * u + c * w;
       }
@@ -364,8 +385,9 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams p
 }
 
 // U = Q W_r (N1 x r) and V = B^T W_r (N2 x r) in one launch.
-static __global__ void __launch_bounds__(kThreads) lr_uv_kernel(LrParams p) {
-  __shared__ float S[kLrMaxL * kLrMaxL];
+template <typename RT>
+static __global__ void __launch_bounds__(kThreads) lr_uv_kernel(LrParams<RT> p) {
+  __shared__ RT S[LrLim<RT>::L * LrLim<RT>::L];
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
   for (int t = threadIdx.x; t < p.l * p.r; t += kThreads) S[t] = __ldcg(p.small + t);
   __syncthreads();
@@ -376,26 +398,26 @@ static __global__ void __launch_bounds__(kThreads) lr_uv_kernel(LrParams p) {
 
 // z~_k = vec(U V^T): Z[:, k-1][i * N2 + j] = sum_a U[i][a] V[j][a] (32 x 32
 // output tile per CTA).  If a Cholesky pivot failed, z~_k stays p~_k.
-template <typename XT>
-__global__ void __launch_bounds__(kThreads) lr_outer_kernel(LrParams p, XT *Z, int64_t zstride) {
-  __shared__ float Us[32][kLrMaxL + 1];
-  __shared__ float Vs[32][kLrMaxL + 1];
+template <typename RT, typename XT>
+__global__ void __launch_bounds__(kThreads) lr_outer_kernel(LrParams<RT> p, XT *Z, int64_t zstride) {
+  __shared__ RT Us[32][LrLim<RT>::L + 1];
+  __shared__ RT Vs[32][LrLim<RT>::L + 1];
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
   const int k = __ldcg(&p.st->k) + 1;
   XT *out = Z + (size_t)(k - 1) * zstride;
   const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32, R = p.r;
   for (int t = threadIdx.x; t < 32 * R; t += kThreads) {
     const int a = t / R, c = t % R;
-    Us[a][c] = (i0 + a < p.N1) ? p.U[(size_t)(i0 + a) * R + c] : 0.f;
-    Vs[a][c] = (j0 + a < p.N2) ? p.V[(size_t)(j0 + a) * R + c] : 0.f;
+    Us[a][c] = (i0 + a < p.N1) ? p.U[(size_t)(i0 + a) * R + c] : RT(0.);
+    Vs[a][c] = (j0 + a < p.N2) ? p.V[(size_t)(j0 + a) * R + c] : RT(0.);
   }
   __syncthreads();
   const int tj = threadIdx.x & 31, ti = threadIdx.x >> 5;   // 4 rows per thread
   for (int ii = ti; ii < 32; ii += kWarps) {
     const int i = i0 + ii, j = j0 + tj;
     if (i >= p.N1 || j >= p.N2) continue;
-    float a = 0.f;
-    for (int c = 0; c < R; ++c) a = fmaf(Us[ii][c], Vs[tj][c], a);
+    RT a = RT(0.);
+    for (int c = 0; c < R; ++c) a = fma(Us[ii][c], Vs[tj][c], a);
     out[(size_t)i * p.N2 + j] = (XT)a;
   }
 }
@@ -403,9 +425,10 @@ __global__ void __launch_bounds__(kThreads) lr_outer_kernel(LrParams p, XT *Z, i
 static __global__ void lr_clear_flag_kernel(int *flag) { *flag = 0; }
 
 // FP32 copy of the caller's FP64 test matrix.
-static __global__ void lr_omega_kernel(const double *src, float *dst, int64_t n) {
+template <typename RT>
+static __global__ void lr_omega_kernel(const double *src, RT *dst, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (float)src[i];
+    dst[i] = (RT)src[i];
 }
 
 }  // namespace sfl

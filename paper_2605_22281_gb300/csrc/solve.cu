@@ -307,37 +307,68 @@ struct Engine {
 
   // Rank-r truncation of p~_k (Z column k - 1) by the randomized SVD: the
   // kernels of lowrank.cuh in order (range finder, subspace iteration, small
-  // eigenproblem, z~_k = U V^T written over the column).
-  static int k_lowrank(const Plan &pl, const Session &se, cudaStream_t s) {
-    const LrParams &lp = se.lr;
+  // eigenproblem, z~_k = U V^T written over the column), in RT arithmetic.
+  template <typename RT>
+  static int k_lowrank_t(const Plan &pl, const Session &se, const LrParams<RT> &lp, cudaStream_t s) {
     const XT *Zc = (const XT *)se.Z;
     XT *Zw = (XT *)se.Z;
     const int64_t zs = pl.A.cols;
     const int N1 = lp.N1, N2 = lp.N2, L = lp.l;
     const int KS1 = (N1 + kLrK - 1) / kLrK, KS2 = (N2 + kLrK - 1) / kLrK;
+    constexpr int GR = LrLim<RT>::GR;
     auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
-    // shifted Cholesky QR, then Cholesky QR twice: the result in b (a: scratch)
-    auto orth = [&](int M, int KS, float *a, float *b) {
-      const float shift = 11.f * (float)((int64_t)M * L + (int64_t)L * (L + 1)) * 5.96e-8f;
-      lr_orth_kernel<<<cdiv(M, kLrGramRows), kThreads, 0, s>>>(lp, 0, nullptr, a, M, KS, shift);
-      lr_orth_kernel<<<cdiv(M, kLrGramRows), kThreads, 0, s>>>(lp, 1, a, b, M, 0, 0.f);
-      lr_orth_kernel<<<cdiv(M, kLrGramRows), kThreads, 0, s>>>(lp, 1, b, a, M, 0, 0.f);
-      lr_apply_kernel<<<cdiv(M * L, kThreads), kThreads, 0, s>>>(lp, a, M, b);
+    // shifted Cholesky QR (shift 11 (M l + l (l + 1)) u trace), then Cholesky QR twice: the result in b
+    auto orth = [&](int M, int KS, RT *a, RT *b) {
+      const RT shift = RT(11) * RT((int64_t)M * L + (int64_t)L * (L + 1)) * LrLim<RT>::u;
+      lr_orth_kernel<RT><<<cdiv(M, GR), kThreads, 0, s>>>(lp, 0, nullptr, a, M, KS, shift);
+      lr_orth_kernel<RT><<<cdiv(M, GR), kThreads, 0, s>>>(lp, 1, a, b, M, 0, RT(0));
+      lr_orth_kernel<RT><<<cdiv(M, GR), kThreads, 0, s>>>(lp, 1, b, a, M, 0, RT(0));
+      lr_apply_kernel<RT><<<cdiv(M * L, kThreads), kThreads, 0, s>>>(lp, a, M, b);
     };
     lr_clear_flag_kernel<<<1, 1, 0, s>>>(lp.flag);
-    lr_mul_kernel<XT, false><<<dim3(cdiv(N1, kLrTile), KS2), kThreads, 0, s>>>(lp, Zc, zs, lp.Omega);
+    lr_mul_kernel<RT, XT, false><<<dim3(cdiv(N1, kLrTile), KS2), kThreads, 0, s>>>(lp, Zc, zs, lp.Omega);
     orth(N1, KS2, lp.Y, lp.Qm);
     for (int it = 0; it < lp.q; ++it) {
-      lr_mul_kernel<XT, true><<<dim3(cdiv(N2, kLrTile), KS1), kThreads, 0, s>>>(lp, Zc, zs, lp.Qm);
+      lr_mul_kernel<RT, XT, true><<<dim3(cdiv(N2, kLrTile), KS1), kThreads, 0, s>>>(lp, Zc, zs, lp.Qm);
       orth(N2, KS1, lp.Bt, lp.Qt);
-      lr_mul_kernel<XT, false><<<dim3(cdiv(N1, kLrTile), KS2), kThreads, 0, s>>>(lp, Zc, zs, lp.Qt);
+      lr_mul_kernel<RT, XT, false><<<dim3(cdiv(N1, kLrTile), KS2), kThreads, 0, s>>>(lp, Zc, zs, lp.Qt);
       orth(N1, KS2, lp.Y, lp.Qm);
     }
-    lr_mul_kernel<XT, true><<<dim3(cdiv(N2, kLrTile), KS1), kThreads, 0, s>>>(lp, Zc, zs, lp.Qm);
-    lr_gram_eig_kernel<<<cdiv(N2, kLrGramRows), kThreads, 0, s>>>(lp, KS1);
-    lr_uv_kernel<<<cdiv((N1 + N2) * lp.r, kThreads), kThreads, 0, s>>>(lp);
-    lr_outer_kernel<XT><<<dim3(cdiv(N2, 32), cdiv(N1, 32)), kThreads, 0, s>>>(lp, Zw, zs);
+    lr_mul_kernel<RT, XT, true><<<dim3(cdiv(N2, kLrTile), KS1), kThreads, 0, s>>>(lp, Zc, zs, lp.Qm);
+    lr_gram_eig_kernel<RT><<<cdiv(N2, GR), kThreads, 0, s>>>(lp, KS1);
+    lr_uv_kernel<RT><<<cdiv((N1 + N2) * lp.r, kThreads), kThreads, 0, s>>>(lp);
+    lr_outer_kernel<RT, XT><<<dim3(cdiv(N2, 32), cdiv(N1, 32)), kThreads, 0, s>>>(lp, Zw, zs);
     return cudaGetLastError() == cudaSuccess ? SFL_OK : SFL_ECUDA;
+  }
+  static int k_lowrank(const Plan &pl, const Session &se, cudaStream_t s) {
+    return se.key.lr_fp64 ? k_lowrank_t<double>(pl, se, se.lr64, s) : k_lowrank_t<float>(pl, se, se.lr32, s);
+  }
+
+  template <typename RT>
+  static int alloc_lowrank(Plan &pl, Session &se, const SessionKey &key, LrParams<RT> &lp, cudaStream_t s) {
+    lp.st = se.st;
+    lp.N1 = pl.img_rows; lp.N2 = pl.img_cols;
+    lp.r = key.lr_rank; lp.l = key.lr_rank + key.lr_over; lp.q = key.lr_power;
+    const int64_t N1 = lp.N1, N2 = lp.N2, L = lp.l, Nm = std::max(N1, N2);
+    const int64_t KSm = (Nm + kLrK - 1) / kLrK, GBm = (Nm + LrLim<RT>::GR - 1) / LrLim<RT>::GR;
+    int r;
+#define LA(ptr, bytes) if ((r = session_alloc(pl, se, (void **)&(ptr), (bytes)))) return r;
+    LA(lp.Omega, sizeof(RT) * N2 * L);
+    LA(lp.Y, sizeof(RT) * N1 * L);
+    LA(lp.Qm, sizeof(RT) * N1 * L);
+    LA(lp.Qt, sizeof(RT) * N2 * L);
+    LA(lp.Bt, sizeof(RT) * N2 * L);
+    LA(lp.U, sizeof(RT) * N1 * lp.r);
+    LA(lp.V, sizeof(RT) * N2 * lp.r);
+    LA(lp.part, sizeof(RT) * KSm * Nm * L);
+    LA(lp.gpart, sizeof(RT) * GBm * L * L);
+    LA(lp.small, sizeof(RT) * LrLim<RT>::L * LrLim<RT>::L);
+    LA(lp.flag, sizeof(int));
+    LA(lp.ticket, sizeof(int));
+#undef LA
+    SFL_CU(cudaMemsetAsync(lp.flag, 0, sizeof(int), s));
+    SFL_CU(cudaMemsetAsync(lp.ticket, 0, sizeof(int), s));
+    return SFL_OK;
   }
 
   static CgsParams<XT> cgs_params(const Plan &pl, const Session &se, int side) {
@@ -545,26 +576,8 @@ struct Engine {
     }
     if (key.precond == SFL_PRECOND_LOWRANK) {
       se->lowrank = true;
-      LrParams &lp = se->lr;
-      lp.st = se->st;
-      lp.N1 = pl.img_rows; lp.N2 = pl.img_cols;
-      lp.r = key.lr_rank; lp.l = key.lr_rank + key.lr_over; lp.q = key.lr_power;
-      const int64_t N1 = lp.N1, N2 = lp.N2, L = lp.l, Nm = std::max(N1, N2);
-      const int64_t KSm = (Nm + kLrK - 1) / kLrK, GBm = (Nm + kLrGramRows - 1) / kLrGramRows;
-      SA(lp.Omega, sizeof(float) * N2 * L);
-      SA(lp.Y, sizeof(float) * N1 * L);
-      SA(lp.Qm, sizeof(float) * N1 * L);
-      SA(lp.Qt, sizeof(float) * N2 * L);
-      SA(lp.Bt, sizeof(float) * N2 * L);
-      SA(lp.U, sizeof(float) * N1 * lp.r);
-      SA(lp.V, sizeof(float) * N2 * lp.r);
-      SA(lp.part, sizeof(float) * KSm * Nm * L);
-      SA(lp.gpart, sizeof(float) * GBm * L * L);
-      SA(lp.small, sizeof(float) * kLrMaxL * kLrMaxL);
-      SA(lp.flag, sizeof(int));
-      SA(lp.ticket, sizeof(int));
-      SFL_CU(cudaMemsetAsync(lp.flag, 0, sizeof(int), s));
-      SFL_CU(cudaMemsetAsync(lp.ticket, 0, sizeof(int), s));
+      r = key.lr_fp64 ? alloc_lowrank<double>(pl, *se, key, se->lr64, s) : alloc_lowrank<float>(pl, *se, key, se->lr32, s);
+      if (r) { destroy_session(pl, *se); return r; }
     }
     SA(se->skM_row, sizeof(int32_t) * (S + 1));
     SA(se->skM_ent, sizeof(uint32_t) * (size_t)Z * m);
@@ -767,7 +780,8 @@ static int check_opts(const Plan &pl, int method, const sfl_opts *o) {
   if (o->precond == SFL_PRECOND_LOWRANK) {
     const int64_t N1 = pl.img_rows, N2 = pl.img_cols, L = (int64_t)o->lowrank_rank + o->lowrank_oversample;
     if (N1 < 1 || N2 < 1 || N1 * N2 != pl.A.cols) return SFL_EINVAL;   // the plan must know the image shape
-    if (o->lowrank_rank < 1 || o->lowrank_oversample < 0 || L > kLrMaxL || L > std::min(N1, N2)) return SFL_EINVAL;
+    const int64_t Lmax = o->lowrank_fp64 ? LrLim<double>::L : LrLim<float>::L;
+    if (o->lowrank_rank < 1 || o->lowrank_oversample < 0 || L > Lmax || L > std::min(N1, N2)) return SFL_EINVAL;
     if (o->lowrank_power < 0 || o->lowrank_power > 4 || !o->lowrank_omega) return SFL_EINVAL;
     if (o->orth_against_z) return SFL_EUNSUPPORTED;
   }
@@ -800,6 +814,7 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
     key.lr_rank = o->lowrank_rank;
     key.lr_over = o->lowrank_oversample;
     key.lr_power = o->lowrank_power;
+    key.lr_fp64 = o->lowrank_fp64 ? 1 : 0;
   }
   Session *se = nullptr;
   for (auto &p : pl.sessions)
@@ -821,10 +836,11 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
                          q.s));
   if (o->precond == SFL_PRECOND_DIAG)
     SFL_CU(cudaMemcpyAsync(se->dw, o->diag_w, sizeof(double) * n, cudaMemcpyDeviceToDevice, q.s));
-  if (se->lowrank) {
-    const int64_t no = (int64_t)se->lr.N2 * se->lr.l;
-    lr_omega_kernel<<<(unsigned)std::min<int64_t>((no + kThreads - 1) / kThreads, 1024), kThreads, 0, q.s>>>(
-        o->lowrank_omega, (float *)se->lr.Omega, no);
+  if (se->lowrank) {   // the caller's FP64 test matrix in the truncation's arithmetic
+    const int64_t no = (int64_t)pl.img_cols * (o->lowrank_rank + o->lowrank_oversample);
+    const unsigned g = (unsigned)std::min<int64_t>((no + kThreads - 1) / kThreads, 1024);
+    if (se->key.lr_fp64) lr_omega_kernel<double><<<g, kThreads, 0, q.s>>>(o->lowrank_omega, (double *)se->lr64.Omega, no);
+    else lr_omega_kernel<float><<<g, kThreads, 0, q.s>>>(o->lowrank_omega, (float *)se->lr32.Omega, no);
     SFL_CU(cudaGetLastError());
   }
   reset_state_kernel<<<1, 1, 0, q.s>>>(se->st, o->seed, o->eta, o->noise_norm, o->irw_eps);
