@@ -217,6 +217,7 @@ typedef struct {
   int32_t unmatched;                     /* 1 if B was given */
   uint64_t device_bytes;                 /* bytes the plan holds */
   int32_t tiled_At;                      /* 1 if A^T / B rows are stored in pixel tiles */
+  int32_t matrix_free;                   /* 1 for a sfl_plan_create_ct plan (nnz fields are 0) */
 } sfl_plan_stats;
 
 /* ---- plans ------------------------------------------------------------- */
@@ -231,6 +232,33 @@ typedef struct {
  * by the caller after this call returns.  popts may be NULL (FP64, no cap). */
 int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B,
                     const sfl_plan_opts *popts, sfl_stream stream);
+/* A matrix-free plan: the operators of the parallel-beam CT experiments
+ * (Section 4.2) computed on the fly by the product kernels instead of read from
+ * a stored matrix.  Geometry: image_n x image_n unit pixels centred at the
+ * origin (column iy*image_n + ix); angles a*pi/n_angles; n_bins unit bins
+ * centred at d - (n_bins-1)/2; ray (a, d) = {p : p.(cos, sin) = t_d} is row
+ * a*n_bins + d of A (m = n_angles*n_bins, n = image_n^2).
+ *   A z       Siddon's ray-driven walk with exact chord lengths;
+ *   back = 0  A^T w, pixel-driven with the exact chords (the trapezoid
+ *             footprint of a unit square), matched to A up to rounding;
+ *   back = 1  the unmatched pixel-driven back-projector B w: each pixel centre
+ *             split linearly between its two nearest bins (Section 3.2).
+ * angles_cs: host, 2*n_angles values (cos, sin of each angle), or NULL to take
+ * cos/sin of a*pi/n_angles from the C library.  popts: value_dtype SFL_F64
+ * computes the geometry and sums in FP64 (FP64 solves); SFL_F32 (or
+ * SFL_BF16) in FP32 (solves with FP32 vectors); image_rows/image_cols are
+ * set to image_n; max_device_bytes as for stored plans; the other fields are
+ * ignored.  Such a plan serves the single solves and sfl_plan_apply; batched
+ * and fixed-k calls return SFL_EUNSUPPORTED.  No matrix is stored, so the
+ * products are bound by arithmetic rather than by memory. */
+typedef struct {
+  int32_t image_n;
+  int32_t n_angles;
+  int32_t n_bins;
+  int32_t back;
+  const double *angles_cs;
+} sfl_ct_geometry;
+int sfl_plan_create_ct(sfl_plan **plan, const sfl_ct_geometry *geom, const sfl_plan_opts *popts, sfl_stream stream);
 int sfl_plan_destroy(sfl_plan *plan);
 int sfl_plan_get_stats(const sfl_plan *plan, sfl_plan_stats *stats /* host */);
 

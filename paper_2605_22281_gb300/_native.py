@@ -60,7 +60,13 @@ class PlanStats(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz_A", ctypes.c_int64),
                 ("nnz_At", ctypes.c_int64), ("padded_nnz_A", ctypes.c_int64), ("padded_nnz_At", ctypes.c_int64),
                 ("lanes_A", ctypes.c_int32), ("lanes_At", ctypes.c_int32), ("value_dtype", ctypes.c_int32),
-                ("unmatched", ctypes.c_int32), ("device_bytes", ctypes.c_uint64), ("tiled_At", ctypes.c_int32)]
+                ("unmatched", ctypes.c_int32), ("device_bytes", ctypes.c_uint64), ("tiled_At", ctypes.c_int32),
+                ("matrix_free", ctypes.c_int32)]
+
+
+class CtGeometry(ctypes.Structure):
+    _fields_ = [("image_n", ctypes.c_int32), ("n_angles", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+                ("back", ctypes.c_int32), ("angles_cs", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -68,6 +74,7 @@ _SIGNATURES = {
     "sfl_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(Csr), ctypes.POINTER(Csr),
                                         ctypes.POINTER(PlanOpts), _P]),
     "sfl_plan_destroy": (ctypes.c_int, [_P]),
+    "sfl_plan_create_ct": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(CtGeometry), ctypes.POINTER(PlanOpts), _P]),
     "sfl_plan_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(PlanStats)]),
     "sfl_plan_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "sflsqr_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(Opts), _P, ctypes.POINTER(Info), _P]),

@@ -94,6 +94,31 @@ class Plan:
         self.m, self.n = int(A.shape[0]), int(A.shape[1])
         self.value_dtype = value_dtype
 
+    @classmethod
+    def ct(cls, image_n: int, n_angles: int, n_bins: int, back: str = "matched", value_dtype: str = "f64",
+           device: str | int = 0, max_device_bytes: int = 0):
+        """A matrix-free plan for the parallel-beam CT geometry (image_n^2 pixels,
+        n_angles x n_bins rays): A z by Siddon's ray walk and, for back =
+        'matched', A^T w pixel-driven with exact chords, or for back =
+        'unmatched' the pixel-driven linear-interpolation back-projector.  The
+        products are computed on the fly in FP64 (value_dtype 'f64') or FP32."""
+        _require_cuda()
+        self = cls.__new__(cls)
+        self.lib = N.load()
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        if back not in ("matched", "unmatched"):
+            raise ValueError(back)
+        g = N.CtGeometry(image_n, n_angles, n_bins, 0 if back == "matched" else 1, None)
+        po = N.PlanOpts(N.DTYPE[value_dtype], 0, max_device_bytes, 0, 0, 0)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(self.lib.sfl_plan_create_ct(ctypes.byref(h), ctypes.byref(g), ctypes.byref(po), _stream()),
+                    "sfl_plan_create_ct")
+        self.handle = h
+        self.m, self.n = n_angles * n_bins, image_n * image_n
+        self.value_dtype = "f64" if value_dtype == "f64" else "f32"
+        return self
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.sfl_plan_destroy(self.handle)

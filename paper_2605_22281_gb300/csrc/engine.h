@@ -95,6 +95,10 @@ struct Plan {
   int img_rows = 0, img_cols = 0;   // n-side image shape: A^T / B rows stored in pixel tiles
   int slot_layout = 0;              // 0: lane-interleaved chunk slots, 1: the caller's entry order
   StoredCsr A, T;   // T: CSR of A^T (transposed copy) or of B
+  // matrix-free CT operator (sfl_plan_create_ct): no CSR arrays, products computed on the fly
+  bool matfree = false;
+  int ct_N = 0, ct_na = 0, ct_nb = 0, ct_back = 0;
+  void *ct_tab = nullptr;   // per-angle constants, kProjTab each, FP64 or FP32 (the plan's arithmetic)
   uint64_t bytes = 0, cap = 0;
   std::vector<void *> allocs;
   std::vector<std::unique_ptr<Session>> sessions;
@@ -138,6 +142,7 @@ struct Ops {
   static cudaError_t convert_in(const double *x, XT *y, int64_t n, cudaStream_t s);
   static cudaError_t convert_out(const XT *x, double *y, int64_t n, cudaStream_t s);
   static int spmv_occupancy(int lpr, bool mat, size_t smem);
+  static int proj_occupancy(size_t smem);
   static cudaError_t set_smem(int lpr, bool mat, size_t smem);
   static cudaError_t set_orth_smem(size_t smem);
 };

@@ -33,7 +33,18 @@ static void (*spmv_fn(int lpr, bool mat, bool orig))(SpmvParams<VT, XT>) {
 template <typename VT, typename XT>
 cudaError_t Ops<VT, XT>::spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, int grid, size_t smem, cudaStream_t s,
                               bool pdl) {
+  if (mat && p.ptab)   // matrix-free projector
+    return launch_k(spmv_fused_kernel<VT, XT, 32, kSpmvProj>, dim3(grid), dim3(kThreads), smem, s, pdl, p);
   return launch_k(spmv_fn<VT, XT>(lpr, mat, mat && p.orig != nullptr), dim3(grid), dim3(kThreads), smem, s, pdl, p);
+}
+
+template <typename VT, typename XT>
+int Ops<VT, XT>::proj_occupancy(size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)spmv_fused_kernel<VT, XT, 32, kSpmvProj>,
+                                                    kThreads, smem) != cudaSuccess)
+    return 0;
+  return nb;
 }
 
 // Both matrix forms (with and without the row map) get the same limit.
@@ -41,6 +52,9 @@ template <typename VT, typename XT>
 cudaError_t Ops<VT, XT>::set_smem(int lpr, bool mat, size_t smem) {
   cudaError_t e = cudaFuncSetAttribute((const void *)spmv_fn<VT, XT>(lpr, mat, false),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && mat && lpr == 32)
+    e = cudaFuncSetAttribute((const void *)spmv_fused_kernel<VT, XT, 32, kSpmvProj>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess && mat)
     e = cudaFuncSetAttribute((const void *)spmv_fn<VT, XT>(lpr, mat, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);

@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "proj.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -111,6 +112,10 @@ struct SpmvParams {
   int full;                             // full orthogonalization: no window dots (block CGS2 kernels do it)
   XT *wfull;                            // full: every w~_j (column j - 1); the vector pass writes w~_1
   double *sigWall;                      // full: 1/||w~_j|| at index j - 1
+  // matrix-free projector (the kSpmvProj form; the CSR arrays are unused)
+  int proj;                             // kProjRay, kProjBackChord or kProjBackLinear
+  int pN, pna, pnb;                     // image N x N, angles, bins
+  const void *ptab;                     // per-angle constants, kProjTab values each, in the vectors' arithmetic
   Partials part;
 };
 
@@ -392,10 +397,40 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
   }
 }
 
-// Forms of the product kernel: the vector pass (y = b), the matrix form, and
-// the matrix form writing through an original-row map (pixel-tiled rows; a
-// compile-time form, so untiled operators carry no dependent index load).
-enum : int { kSpmvVec = 0, kSpmvMat = 1, kSpmvMatOrig = 2 };
+// Forms of the product kernel: the vector pass (y = b), the matrix form, the
+// matrix form writing through an original-row map (pixel-tiled rows; a
+// compile-time form, so untiled operators carry no dependent index load), and
+// the matrix-free projector form (proj.cuh).
+enum : int { kSpmvVec = 0, kSpmvMat = 1, kSpmvMatOrig = 2, kSpmvProj = 3 };
+
+// The rows of a warp for the projector form, in 32-row blocks: for each row
+// the lanes' parts are added by a butterfly and lane r keeps row r's value,
+// then writes it and its square as the stored form does.
+template <typename VT, typename XT>
+__device__ __forceinline__ double proj_rows(const SpmvParams<VT, XT> &p, RowBlocks rb, const XT *__restrict__ x, XT *y) {
+  using RT = typename AccT<XT>::T;
+  const int lane = threadIdx.x & 31;
+  const RT *tab = reinterpret_cast<const RT *>(p.ptab);
+  double nrm = 0.0;
+  for (int64_t row0 = rb.first; row0 < rb.end; row0 += rb.stride) {
+    const int64_t r1 = min(row0 + 32, rb.end);
+    RT mine = RT(0);
+    for (int64_t row = row0; row < r1; ++row) {
+      RT v = p.proj == kProjRay ? proj_ray_partial<RT, XT>(p.pN, p.pnb, tab, x, row, lane)
+                                : proj_back_partial<RT, XT>(p.proj, p.pN, p.pna, p.pnb, tab, x, row, lane);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == (int)(row - row0)) mine = v;
+    }
+    const int64_t row = row0 + lane;
+    if (row < r1) {
+      y[row] = (XT)mine;
+      const double yd = (double)(XT)mine;
+      nrm += yd * yd;
+    }
+  }
+  return nrm;
+}
 
 // Fused SpMV of one step.  In the solve modes past the first vector pass,
 // CTA 0 books the step's scalars (above) while the other CTAs run the rows:
@@ -475,7 +510,9 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
     rb.stride = 32;
     rb.end = bound(gw + 1);
   }
-  const double nrm = spmv_rows<VT, XT, LPR, MAT, ORIG>(p, rb, x, y, stash);
+  double nrm;
+  if constexpr (FORM == kSpmvProj) nrm = proj_rows<VT, XT>(p, rb, x, y);
+  else nrm = spmv_rows<VT, XT, LPR, MAT, ORIG>(p, rb, x, y, stash);
   if (!reduce) return;
   const int32_t *og = p.orig;
   if (!MAT) {     // vector pass: no window dots

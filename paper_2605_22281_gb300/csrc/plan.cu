@@ -3,6 +3,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -380,6 +381,61 @@ int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const s
   return SFL_OK;
 }
 
+int sfl_plan_create_ct(sfl_plan **plan, const sfl_ct_geometry *g, const sfl_plan_opts *popts, sfl_stream stream) {
+  if (!plan || !g) return SFL_EINVAL;
+  *plan = nullptr;
+  if (g->image_n < 1 || g->n_angles < 1 || g->n_bins < 1 || (g->back != 0 && g->back != 1)) return SFL_EINVAL;
+  const int64_t n = (int64_t)g->image_n * g->image_n, m = (int64_t)g->n_angles * g->n_bins;
+  if (n >= (int64_t)1 << 31 || m >= (int64_t)1 << 31) return SFL_EINVAL;
+  const sfl_dtype vdt = popts ? popts->value_dtype : SFL_F64;
+  if (vdt != SFL_F64 && vdt != SFL_F32 && vdt != SFL_BF16) return SFL_EINVAL;
+  // per-angle constants (host, FP64): cos, sin, trapezoid a1, a2, H, slope, axis flag
+  std::vector<double> tab((size_t)kProjTab * g->n_angles);
+  for (int a = 0; a < g->n_angles; ++a) {
+    const double th = (double)a * M_PI / (double)g->n_angles;
+    const double c = g->angles_cs ? g->angles_cs[2 * a] : cos(th), s = g->angles_cs ? g->angles_cs[2 * a + 1] : sin(th);
+    if (!std::isfinite(c) || !std::isfinite(s)) return SFL_EINVAL;
+    const double ac = fabs(c), as = fabs(s);
+    const double a1 = 0.5 * fabs(ac - as), a2 = 0.5 * (ac + as), H = 1.0 / std::max(ac, as);
+    double *e = tab.data() + (size_t)kProjTab * a;
+    e[0] = c; e[1] = s; e[2] = a1; e[3] = a2; e[4] = H;
+    e[5] = a2 - a1 > 1e-15 ? H / (a2 - a1) : 0.0;
+    e[6] = as < 1e-15 ? 1.0 : (ac < 1e-15 ? 2.0 : 0.0);
+  }
+  sfl_plan *p = new sfl_plan();
+  Plan &pl = p->impl;
+  cudaGetDevice(&pl.device);
+  cudaDeviceGetAttribute(&pl.num_sms, cudaDevAttrMultiProcessorCount, pl.device);
+  pl.vdt = vdt == SFL_F64 ? SFL_F64 : SFL_F32;   // no stored values: BF16 means FP32 arithmetic
+  pl.unmatched = g->back == 1;
+  pl.matfree = true;
+  pl.ct_N = g->image_n; pl.ct_na = g->n_angles; pl.ct_nb = g->n_bins; pl.ct_back = g->back;
+  pl.img_rows = pl.img_cols = g->image_n;
+  pl.cap = popts ? popts->max_device_bytes : 0;
+  pl.A.rows = m; pl.A.cols = n; pl.A.lpr = 32;
+  pl.T.rows = n; pl.T.cols = m; pl.T.lpr = 32;
+  cudaStream_t s = (cudaStream_t)stream;
+  int r = SFL_OK;
+  if (pl.vdt == SFL_F64) {
+    r = plan_alloc(pl, &pl.ct_tab, sizeof(double) * tab.size());
+    if (!r && cudaMemcpyAsync(pl.ct_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      r = SFL_ECUDA;
+  } else {
+    std::vector<float> tf(tab.begin(), tab.end());
+    r = plan_alloc(pl, &pl.ct_tab, sizeof(float) * tf.size());
+    if (!r && cudaMemcpyAsync(pl.ct_tab, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      r = SFL_ECUDA;
+  }
+  if (!r && cudaStreamSynchronize(s) != cudaSuccess) r = SFL_ECUDA;
+  if (r) {
+    cudaGetLastError();
+    sfl_plan_destroy(p);
+    return r;
+  }
+  *plan = p;
+  return SFL_OK;
+}
+
 int sfl_plan_get_stats(const sfl_plan *plan, sfl_plan_stats *st) {
   if (!plan || !st) return SFL_EINVAL;
   const Plan &pl = plan->impl;
@@ -390,6 +446,7 @@ int sfl_plan_get_stats(const sfl_plan *plan, sfl_plan_stats *st) {
   st->value_dtype = pl.vdt; st->unmatched = pl.unmatched ? 1 : 0;
   st->device_bytes = pl.bytes;
   st->tiled_At = pl.T.orig != nullptr ? 1 : 0;
+  st->matrix_free = pl.matfree ? 1 : 0;
   return SFL_OK;
 }
 

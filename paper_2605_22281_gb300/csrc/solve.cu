@@ -233,6 +233,7 @@ struct Engine {
     p.Hband = se.Hband;
     p.want_h = se.key.method != kSFLSQR;
     p.hb_ell = se.hb_ell;
+    if (pl.matfree) set_proj(pl, p, mode == kModeFwd || mode == kModeInitB);
     p.full = se.full;
     if (se.full) {
       p.ell = 0;                        // the rings and scalars run as for window 0, with no window dots
@@ -240,6 +241,15 @@ struct Engine {
       p.sigWall = se.sigWall;
     }
     return p;
+  }
+
+  // Matrix-free plans: the projector of the product (forward ray walk, or the
+  // matched / unmatched pixel-driven back-projection), rows split evenly.
+  static void set_proj(const Plan &pl, SpmvParams<VT, XT> &p, bool fwd) {
+    p.ptab = pl.ct_tab;
+    p.pN = pl.ct_N; p.pna = pl.ct_na; p.pnb = pl.ct_nb;
+    p.proj = fwd ? kProjRay : (pl.ct_back ? kProjBackLinear : kProjBackChord);
+    p.wrow = nullptr;
   }
 
   static SketchParams<XT> sketch_params(const Session &se, int mode) {
@@ -612,7 +622,7 @@ struct Engine {
     SFL_CU(O::set_smem(pl.T.lpr, true, se->smem_T));
     SFL_CU(O::set_smem(1, false, se->smem_init));
     auto grid_of = [&](int lpr, bool mat, size_t smem) {
-      int occ = O::spmv_occupancy(lpr, mat, smem);
+      int occ = (mat && pl.matfree) ? O::proj_occupancy(smem) : O::spmv_occupancy(lpr, mat, smem);
       if (occ < 1) occ = 1;
       if (occ > 8) occ = 8;
       return std::min(pl.num_sms * occ, kGroup * kMaxGroups);
@@ -648,8 +658,9 @@ struct Engine {
                     : pl.vdt == SFL_F32 ? SpmvTune<float>::NCH : SpmvTune<double>::NCH;
     // FP64 products are bound by FMA issue: their rows also pay for chunk slots
     const bool fp64 = pl.vdt == SFL_F64;
-    if ((r = balance_rows(pl.A, nch * pl.A.lpr * P, WA, se->wrowA, s, fp64 ? pl.A.lpr * P : 0)) ||
-        (r = balance_rows(pl.T, nch * pl.T.lpr * P, WT, se->wrowT, s, fp64 ? pl.T.lpr * P : 0))) {
+    if (!pl.matfree &&   // matrix-free products split their rows evenly
+        ((r = balance_rows(pl.A, nch * pl.A.lpr * P, WA, se->wrowA, s, fp64 ? pl.A.lpr * P : 0)) ||
+         (r = balance_rows(pl.T, nch * pl.T.lpr * P, WT, se->wrowT, s, fp64 ? pl.T.lpr * P : 0)))) {
       destroy_session(pl, *se);
       return r;
     }
@@ -892,6 +903,11 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
   p.mode = kModeApply;
   const int grid = pl.num_sms * 2;
   p.interleave = interleave_rows(M, grid);
+  if (pl.matfree) {
+    p.ptab = pl.ct_tab;
+    p.pN = pl.ct_N; p.pna = pl.ct_na; p.pnb = pl.ct_nb;
+    p.proj = which == 0 ? kProjRay : (pl.ct_back ? kProjBackLinear : kProjBackChord);
+  }
   const size_t smem = spmv_smem_bytes(M.lpr, sizeof(typename AccT<XT>::T));
   SFL_CU(Ops<VT, XT>::set_smem(M.lpr, true, smem));
   if (std::is_same<XT, double>::value) {
