@@ -41,6 +41,7 @@ struct SolveState {
   double stop_den;  // denominator of the stop ratio
   double eta, noise_norm, irw_eps;
   double R11;       // first diagonal entry of the small QR
+  double rinv_cmax; // largest column norm of R^{-1} so far (R11 * it bounds kappa(R) from below)
   double relres;    // stop ratio of the last step
   double znorm_raw2, wnorm_raw2;  // squared norms before orthogonalization
   double alpha, betak;

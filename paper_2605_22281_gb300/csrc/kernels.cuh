@@ -987,7 +987,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
   // state that only this kernel's final block writes, read here so that no
   // later phase waits on a global load: the first diagonal of R (k > 1), the
   // stop-ratio denominator (k > 1) and the stop tolerance
-  const double R11_prev = st->R11, den_prev = st->stop_den, tol = st->tol;
+  const double R11_prev = st->R11, den_prev = st->stop_den, tol = st->tol, cmax_prev = st->rinv_cmax;
   const double inv_den_prev = 1.0 / den_prev;   // used at the stop test (k > 1)
   const int s = p.s;
   const int RB = ls_rows_per_cta(s, CL);
@@ -1031,6 +1031,7 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
   __shared__ double s_sc[2][4];     // scalar partials exchanged in the cluster
   __shared__ double s_res[2][4];
   __shared__ double s_r2n;
+  __shared__ double s_u2[kWarps];   // per-warp sums of the new R^{-1} column's squares
 
   // my block of Q rows: staged copy or the global rows
   const double *Qb = p.stage_q ? Qs : p.Q + (size_t)r0 * p.maxit;
@@ -1235,10 +1236,12 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     ecur[i] = ei;
   }
   // ---- 7. column kk of R^{-1} and y_k = [y_{k-1}; 0] + gamma_k R^{-1}[:, kk]
+  double u2 = 0.0;   // lane 0: squares of this warp's entries of the new column
   auto rinv_row = [&](int i, double a, double y_prev) {
     a = warp_sum(a);
     if (lane == 0) {
       const double u = -a * irho;
+      u2 += u * u;
       const double yn = y_prev + gamma * u;
       p.Rinv[(size_t)i * p.maxit + kk] = u;
       p.y[i] = yn;
@@ -1273,7 +1276,8 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     p.Rinv[(size_t)kk * p.maxit + kk] = irho;
     p.y[kk] = gamma * irho;
   }
-  // ---- 8. residual of the stop test
+  if (lane == 0) s_u2[warp] = u2;   // read after the barriers of step 8
+  // ---- 8. residual of the stop test (and the norm of the new R^{-1} column)
   if (resid_rule) {
     // || S_m b - S_m A Z_k y_k ||, my rows; y_k is gathered from its owners'
     // shared memory after a cluster barrier
@@ -1292,15 +1296,21 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
         const double d = p.sbm[r0 + i] - upd[i];
         a0 += d * d;
       }
-    cluster_allreduce_sc(a0, 0.0, 0.0, 1, 1);
+    cluster_allreduce_sc(a0, (warp == 0 && lane < kWarps) ? s_u2[lane] : 0.0, 0.0, 2, 1);
   } else {
     __syncthreads();   // ecur is final
     double a0 = 0.0;
     if (warp == 0)
       for (int i = lane; i < nr; i += 32) a0 += ecur[i] * ecur[i];
-    cluster_allreduce_sc(a0, 0.0, 0.0, 1, 1);
+    cluster_allreduce_sc(a0, (warp == 0 && lane < kWarps) ? s_u2[lane] : 0.0, 0.0, 2, 1);
   }
   const double res2 = s_res[1][0];
+  // condition estimate of the small triangular factor: R11 * (largest column
+  // norm of R^{-1}), a lower bound on kappa(R).  Past 1e12 the problem is
+  // numerically rank deficient and the explicit-inverse recurrence for y
+  // loses accuracy: the step's iterate is returned and the solve stops
+  // (breakdown).
+  const double cmax = fmax(cmax_prev, sqrt(s_res[1][1] + irho * irho));
   cl.sync();   // no CTA leaves while a peer may still read its shared memory
   if (rank == 0 && tid == 0) {
     if (k == 1) st->stop_den = den;
@@ -1308,11 +1318,12 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
     st->relres = rel;
     if (p.relres_hist) p.relres_hist[kk] = rel;
     if (k == 1) st->R11 = rho;
+    st->rinv_cmax = cmax;
     st->k = k;
     st->hist_pending = 1;
     int stop = 0;
     if (rel < tol) stop = SFL_STOP_DISCREPANCY;
-    else if (lucky) stop = SFL_STOP_BREAKDOWN;
+    else if (lucky || R11 * cmax > 1e12) stop = SFL_STOP_BREAKDOWN;
     else if (k >= p.maxit) stop = SFL_STOP_MAXIT;
     if (!isfinite(rel)) stop = kStopNonfinite;
     st->stop = stop;

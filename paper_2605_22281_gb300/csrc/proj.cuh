@@ -38,8 +38,10 @@ __device__ __forceinline__ RT proj_ray_partial(int N, int nb, const RT *tab, con
   const RT t = (RT)d - RT(0.5) * (RT)(nb - 1);
   const RT h = RT(0.5) * (RT)N;
   const RT px = t * c, py = t * s;   // foot point
-  const RT dx = -s, dy = c;          // unit direction
   const RT tiny = RT(1e-15);
+  // unit direction; a component below tiny (cos(pi/2) in FP64) is exactly zero,
+  // so a ray on a grid line belongs to the pixel with the floor index
+  const RT dx = fabs(s) > tiny ? -s : RT(0), dy = fabs(c) > tiny ? c : RT(0);
   RT lo = -RT(1e30), hi = RT(1e30);
   const bool use_x = fabs(dx) > tiny, use_y = fabs(dy) > tiny;
   if (use_x) {

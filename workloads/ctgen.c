@@ -33,8 +33,11 @@ static int64_t siddon_ray(int N, int n_angles, int n_bins, int64_t row, seg_t *o
   const double t = (double)d - 0.5 * (double)(n_bins - 1);
   const double h = 0.5 * (double)N;
   const double px = t * c, py = t * s;   /* foot point */
-  const double dx = -s, dy = c;          /* unit direction */
   const double tiny = 1e-15;
+  /* unit direction; a component below tiny (cos(pi/2) = 6e-17 in FP64) is
+   * taken as exactly zero, so a ray that lies on a grid line belongs to the
+   * pixel whose index is the floor of its coordinate along its whole length */
+  const double dx = fabs(s) > tiny ? -s : 0.0, dy = fabs(c) > tiny ? c : 0.0;
   double lo = -INFINITY, hi = INFINITY;
   if (fabs(dx) > tiny) {
     double l0 = (-h - px) / dx, l1 = (h - px) / dx;
