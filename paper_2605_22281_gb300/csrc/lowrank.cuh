@@ -36,7 +36,7 @@ constexpr int kLrK = 64;          // depth of one split-K chunk
 // Per compute type (FP32 default, FP64 for verification): largest r +
 // oversampling, rows per CTA of the Gram partials, unit roundoff, and the
 // Jacobi rotation threshold (a pair is rotated while |a_pq| exceeds it times
-// sqrt(|a_pp a_qq|), about ten unit roundoffs).
+// the largest diagonal entry, about ten unit roundoffs).
 template <typename RT> struct LrLim;
 template <> struct LrLim<float> {
   static constexpr int L = 64, GR = 64;
@@ -214,6 +214,97 @@ static __device__ void lr_cholesky_inverse(const LrParams<RT> &p, RT (*G)[LrLim<
   for (int t = lane; t < L * L; t += 32) p.small[t] = Ri[t / L][t % L];
 }
 
+// FP32 form of lr_cholesky_inverse with the columns in registers: lane c of
+// warp 0 holds columns c and c + 32 of G (then of R, then of R^{-1}); the
+// entries of a pivot row are exchanged by warp shuffles, so no step waits on
+// shared memory.  The loops are unrolled over the largest order (64) and
+// predicated on l.
+static __device__ void lr_cholesky_inverse_regs(const LrParams<float> &p, float (*G)[LrLim<float>::L + 1],
+                                                float shift_rel) {
+  constexpr int K = LrLim<float>::L;
+  static_assert(K == 64, "two columns per lane");
+  const int L = p.l, lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
+  const unsigned full = 0xffffffffu;
+  float cA[K], cB[K];
+  float tr = 0.f;
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    cA[a] = (a < L && lane < L) ? G[a][lane] : 0.f;
+    cB[a] = (a < L && lane + 32 < L) ? G[a][lane + 32] : 0.f;
+  }
+  if (shift_rel > 0.f) {
+    for (int a = lane; a < L; a += 32) tr += G[a][a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(full, tr, o);
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      if (a == lane) cA[a] += shift_rel * tr;
+      if (a == lane + 32) cB[a] += shift_rel * tr;
+    }
+  }
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    if (j < L) {
+      const float d = __shfl_sync(full, j < 32 ? cA[j] : cB[j], j & 31);
+      ok = ok && d > 0.f;
+      const float rd = d > 0.f ? rsqrtf(d) : 0.f;
+      if (lane >= j) cA[j] *= rd;
+      if (lane + 32 >= j) cB[j] *= rd;
+#pragma unroll
+      for (int a = j + 1; a < K; ++a) {
+        if (a < L) {
+          const float g = __shfl_sync(full, a < 32 ? cA[j] : cB[j], a & 31);   // R[j][a]
+          if (lane >= a) cA[a] -= g * cA[j];
+          if (lane + 32 >= a) cB[a] -= g * cB[j];
+        }
+      }
+    }
+  }
+  if (!ok) {
+    if (lane == 0) *p.flag = 1;
+    return;
+  }
+  // R into shared memory (rows read as broadcasts below)
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    if (a < L) {
+      if (lane < L) G[a][lane] = a <= lane ? cA[a] : 0.f;
+      if (lane + 32 < L) G[a][lane + 32] = a <= lane + 32 ? cB[a] : 0.f;
+    }
+  }
+  __syncwarp();
+  // column c of R^{-1} by back substitution in registers
+  float iA[K], iB[K];
+#pragma unroll
+  for (int a = K - 1; a >= 0; --a) {
+    iA[a] = 0.f;
+    iB[a] = 0.f;
+    if (a < L) {
+      const float inv = 1.f / G[a][a];
+      float sA = 0.f, sB = 0.f;
+#pragma unroll
+      for (int t = a + 1; t < K; ++t) {
+        if (t < L) {
+          const float r = G[a][t];
+          if (t <= lane) sA = fmaf(r, iA[t], sA);
+          if (t <= lane + 32) sB = fmaf(r, iB[t], sB);
+        }
+      }
+      iA[a] = lane == a ? inv : (lane > a ? -sA * inv : 0.f);
+      iB[a] = lane + 32 == a ? inv : (lane + 32 > a ? -sB * inv : 0.f);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    if (a < L) {
+      if (lane < L) p.small[a * L + lane] = iA[a];
+      if (lane + 32 < L) p.small[a * L + lane + 32] = iB[a];
+    }
+  }
+}
+
 // One Cholesky-QR pass over X (M x l), rows in blocks of LrLim<RT>::GR per CTA:
 //   mode 0: X = the sum of the KS split-K partials of a product (written to out);
 //   mode 1: out = in * p.small (the previous pass's R^{-1});
@@ -256,7 +347,8 @@ static __global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams<RT> p
   lr_gram_partial(p, Xs, nr);
   if (!lr_last_cta(p, &s_last)) return;
   lr_load_gram(p, gridDim.x, G);
-  lr_cholesky_inverse(p, G, Ri, shift_rel);
+  if constexpr (sizeof(RT) == sizeof(float)) lr_cholesky_inverse_regs(p, G, shift_rel);
+  else lr_cholesky_inverse(p, G, Ri, shift_rel);
 }
 
 // out[i][0..ncol) = in[i][0..l) * p.small (l x ncol).
@@ -324,8 +416,17 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams<R
   __syncthreads();
   const int np = n / 2;
   // cyclic Jacobi, round-robin pairs (index 0 fixed, the others rotate); a
-  // pair is rotated when |a_pq| > tol sqrt(|a_pp a_qq|); a sweep that rotates
+  // pair is rotated when |a_pq| > tol max_i |a_ii| (rounding-level entries are
+  // left: only the leading eigenvectors are used); a sweep that rotates
   // nothing ends the iteration
+  __shared__ RT s_amax;
+  if (tid == 0) {
+    RT mx = RT(0);
+    for (int a = 0; a < L; ++a) mx = fmax(mx, fabs(A[a][a]));
+    s_amax = mx;
+  }
+  __syncthreads();
+  const RT thr = LrLim<RT>::rot_tol * s_amax;
   for (int sweep = 0; sweep < 20; ++sweep) {
     if (tid == 0) s_go = 0;
     __syncthreads();
@@ -337,7 +438,7 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams<R
         if (a > b) { const int t = a; a = b; b = t; }
         RT c = RT(1), sn = RT(0);
         const RT apq = A[a][b];
-        if (b < L && fabs(apq) > LrLim<RT>::rot_tol * sqrt(fabs(A[a][a] * A[b][b])) && apq != RT(0)) {
+        if (b < L && fabs(apq) > thr) {
           const RT tau = (A[b][b] - A[a][a]) / (RT(2) * apq);
           const RT t = fabs(tau) > RT(1e15) ? RT(0.5) / tau
                                             : copysign(RT(1), tau) / (fabs(tau) + sqrt(fma(tau, tau, RT(1))));
