@@ -32,6 +32,8 @@ namespace sfl {
 
 constexpr int kLrTile = 32;       // rows of a product tile
 constexpr int kLrK = 64;          // depth of one split-K chunk
+constexpr int kLrSweeps = 10;     // most Jacobi sweeps
+constexpr size_t kLrOrthSmem = 200 * 1024;   // largest M x l block the one-CTA orthonormalization holds
 
 // Per compute type (FP32 default, FP64 for verification): largest r +
 // oversampling, rows per CTA of the Gram partials, unit roundoff, and the
@@ -214,94 +216,76 @@ static __device__ void lr_cholesky_inverse(const LrParams<RT> &p, RT (*G)[LrLim<
   for (int t = lane; t < L * L; t += 32) p.small[t] = Ri[t / L][t % L];
 }
 
-// FP32 form of lr_cholesky_inverse with the columns in registers: lane c of
-// warp 0 holds columns c and c + 32 of G (then of R, then of R^{-1}); the
-// entries of a pivot row are exchanged by warp shuffles, so no step waits on
-// shared memory.  The loops are unrolled over the largest order (64) and
-// predicated on l.
-static __device__ void lr_cholesky_inverse_regs(const LrParams<float> &p, float (*G)[LrLim<float>::L + 1],
-                                                float shift_rel) {
-  constexpr int K = LrLim<float>::L;
-  static_assert(K == 64, "two columns per lane");
-  const int L = p.l, lane = threadIdx.x & 31;
-  if (threadIdx.x >= 32) return;
-  const unsigned full = 0xffffffffu;
-  float cA[K], cB[K];
-  float tr = 0.f;
-#pragma unroll
-  for (int a = 0; a < K; ++a) {
-    cA[a] = (a < L && lane < L) ? G[a][lane] : 0.f;
-    cB[a] = (a < L && lane + 32 < L) ? G[a][lane + 32] : 0.f;
+// Orthonormal basis of the range of X (M x l) by one CTA, when X fits in
+// shared memory: X = the sum of the KS split-K partials of a product, held
+// column-major; classical Gram-Schmidt applied twice, column by column (warps
+// take the dots of the earlier columns, threads the updates, fixed-order
+// block sums); a column whose norm falls below 1e-5 (FP32) or 1e-12 (FP64)
+// of its norm before the passes is set to zero (rank deficient: it adds
+// nothing to the projector).  Q (M x l, row-major) is written to out.
+template <typename RT>
+static __global__ void __launch_bounds__(kThreads) lr_orth_cta_kernel(LrParams<RT> p, int M, int KS, RT *out) {
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  RT *X = reinterpret_cast<RT *>(lr_smem);      // [l][M]
+  __shared__ RT d[LrLim<RT>::L];
+  __shared__ RT wpart[kWarps];
+  __shared__ RT s_norm0, s_norm;
+  if (!lr_running(p.st) || __ldcg(p.flag)) return;
+  const int L = p.l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int t = tid; t < M * L; t += kThreads) {
+    const int i = t / L, c = t % L;
+    RT v = RT(0);
+    for (int ks = 0; ks < KS; ++ks) v += p.part[(size_t)ks * M * L + t];
+    X[(size_t)c * M + i] = v;
   }
-  if (shift_rel > 0.f) {
-    for (int a = lane; a < L; a += 32) tr += G[a][a];
+  __syncthreads();
+  auto block_sum = [&](RT v) -> RT {   // fixed order: lanes by butterfly, warps in order
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(full, tr, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wpart[warp] = v;
+    __syncthreads();
+    RT a = RT(0);
+    for (int w = 0; w < kWarps; ++w) a += wpart[w];
+    __syncthreads();
+    return a;
+  };
+  const RT drop = sizeof(RT) == sizeof(float) ? RT(1e-5) : RT(1e-12);
+  for (int j = 0; j < L; ++j) {
+    RT *v = X + (size_t)j * M;
+    RT a = RT(0);
+    for (int i = tid; i < M; i += kThreads) a += v[i] * v[i];
+    a = block_sum(a);
+    if (tid == 0) s_norm0 = sqrt(a);
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {
+      for (int t = warp; t < j; t += kWarps) {   // d_t = <q_t, v>
+        const RT *q = X + (size_t)t * M;
+        RT s = RT(0);
+        for (int i = lane; i < M; i += 32) s += q[i] * v[i];
 #pragma unroll
-    for (int a = 0; a < K; ++a) {
-      if (a == lane) cA[a] += shift_rel * tr;
-      if (a == lane + 32) cB[a] += shift_rel * tr;
-    }
-  }
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (j < L) {
-      const float d = __shfl_sync(full, j < 32 ? cA[j] : cB[j], j & 31);
-      ok = ok && d > 0.f;
-      const float rd = d > 0.f ? rsqrtf(d) : 0.f;
-      if (lane >= j) cA[j] *= rd;
-      if (lane + 32 >= j) cB[j] *= rd;
-#pragma unroll
-      for (int a = j + 1; a < K; ++a) {
-        if (a < L) {
-          const float g = __shfl_sync(full, a < 32 ? cA[j] : cB[j], a & 31);   // R[j][a]
-          if (lane >= a) cA[a] -= g * cA[j];
-          if (lane + 32 >= a) cB[a] -= g * cB[j];
-        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) d[t] = s;
       }
-    }
-  }
-  if (!ok) {
-    if (lane == 0) *p.flag = 1;
-    return;
-  }
-  // R into shared memory (rows read as broadcasts below)
-#pragma unroll
-  for (int a = 0; a < K; ++a) {
-    if (a < L) {
-      if (lane < L) G[a][lane] = a <= lane ? cA[a] : 0.f;
-      if (lane + 32 < L) G[a][lane + 32] = a <= lane + 32 ? cB[a] : 0.f;
-    }
-  }
-  __syncwarp();
-  // column c of R^{-1} by back substitution in registers
-  float iA[K], iB[K];
-#pragma unroll
-  for (int a = K - 1; a >= 0; --a) {
-    iA[a] = 0.f;
-    iB[a] = 0.f;
-    if (a < L) {
-      const float inv = 1.f / G[a][a];
-      float sA = 0.f, sB = 0.f;
-#pragma unroll
-      for (int t = a + 1; t < K; ++t) {
-        if (t < L) {
-          const float r = G[a][t];
-          if (t <= lane) sA = fmaf(r, iA[t], sA);
-          if (t <= lane + 32) sB = fmaf(r, iB[t], sB);
-        }
+      __syncthreads();
+      for (int i = tid; i < M; i += kThreads) {   // v -= Q d
+        RT s = RT(0);
+        for (int t = 0; t < j; ++t) s += X[(size_t)t * M + i] * d[t];
+        v[i] -= s;
       }
-      iA[a] = lane == a ? inv : (lane > a ? -sA * inv : 0.f);
-      iB[a] = lane + 32 == a ? inv : (lane + 32 > a ? -sB * inv : 0.f);
+      __syncthreads();
     }
+    a = RT(0);
+    for (int i = tid; i < M; i += kThreads) a += v[i] * v[i];
+    a = block_sum(a);
+    if (tid == 0) s_norm = sqrt(a);
+    __syncthreads();
+    const RT nv = s_norm, n0 = s_norm0;
+    const RT sc = (nv > drop * n0 && nv > RT(0)) ? RT(1) / nv : RT(0);
+    for (int i = tid; i < M; i += kThreads) v[i] *= sc;
+    __syncthreads();
   }
-#pragma unroll
-  for (int a = 0; a < K; ++a) {
-    if (a < L) {
-      if (lane < L) p.small[a * L + lane] = iA[a];
-      if (lane + 32 < L) p.small[a * L + lane + 32] = iB[a];
-    }
+  for (int t = tid; t < M * L; t += kThreads) {
+    const int i = t / L, c = t % L;
+    out[t] = X[(size_t)c * M + i];
   }
 }
 
@@ -347,8 +331,7 @@ static __global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams<RT> p
   lr_gram_partial(p, Xs, nr);
   if (!lr_last_cta(p, &s_last)) return;
   lr_load_gram(p, gridDim.x, G);
-  if constexpr (sizeof(RT) == sizeof(float)) lr_cholesky_inverse_regs(p, G, shift_rel);
-  else lr_cholesky_inverse(p, G, Ri, shift_rel);
+  lr_cholesky_inverse(p, G, Ri, shift_rel);
 }
 
 // out[i][0..ncol) = in[i][0..l) * p.small (l x ncol).
@@ -418,7 +401,8 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams<R
   // cyclic Jacobi, round-robin pairs (index 0 fixed, the others rotate); a
   // pair is rotated when |a_pq| > tol max_i |a_ii| (rounding-level entries are
   // left: only the leading eigenvectors are used); a sweep that rotates
-  // nothing ends the iteration
+  // nothing ends the iteration, and at most kLrSweeps sweeps run (the
+  // convergence is quadratic)
   __shared__ RT s_amax;
   if (tid == 0) {
     RT mx = RT(0);
@@ -427,7 +411,7 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams<R
   }
   __syncthreads();
   const RT thr = LrLim<RT>::rot_tol * s_amax;
-  for (int sweep = 0; sweep < 20; ++sweep) {
+  for (int sweep = 0; sweep < kLrSweeps; ++sweep) {
     if (tid == 0) s_go = 0;
     __syncthreads();
     for (int round = 0; round < n - 1; ++round) {

@@ -327,8 +327,14 @@ struct Engine {
     const int KS1 = (N1 + kLrK - 1) / kLrK, KS2 = (N2 + kLrK - 1) / kLrK;
     constexpr int GR = LrLim<RT>::GR;
     auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
-    // shifted Cholesky QR (shift 11 (M l + l (l + 1)) u trace), then Cholesky QR twice: the result in b
+    // one CTA (CGS2 in shared memory) when M x l fits, else shifted Cholesky
+    // QR (shift 11 (M l + l (l + 1)) u trace) then Cholesky QR twice: the result in b
     auto orth = [&](int M, int KS, RT *a, RT *b) {
+      const size_t cta_smem = sizeof(RT) * (size_t)M * L;
+      if (cta_smem <= kLrOrthSmem) {
+        lr_orth_cta_kernel<RT><<<1, kThreads, cta_smem, s>>>(lp, M, KS, b);
+        return;
+      }
       const RT shift = RT(11) * RT((int64_t)M * L + (int64_t)L * (L + 1)) * LrLim<RT>::u;
       lr_orth_kernel<RT><<<cdiv(M, GR), kThreads, 0, s>>>(lp, 0, nullptr, a, M, KS, shift);
       lr_orth_kernel<RT><<<cdiv(M, GR), kThreads, 0, s>>>(lp, 1, a, b, M, 0, RT(0));
@@ -376,6 +382,7 @@ struct Engine {
     LA(lp.flag, sizeof(int));
     LA(lp.ticket, sizeof(int));
 #undef LA
+    SFL_CU(cudaFuncSetAttribute(lr_orth_cta_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLrOrthSmem));
     SFL_CU(cudaMemsetAsync(lp.flag, 0, sizeof(int), s));
     SFL_CU(cudaMemsetAsync(lp.ticket, 0, sizeof(int), s));
     return SFL_OK;
