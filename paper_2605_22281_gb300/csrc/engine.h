@@ -64,6 +64,10 @@ struct Session {
   void *zcgs = nullptr, *wcgs = nullptr;   // orthogonalized product outputs (the raw ones stay for the sketch)
   double *sigWall = nullptr, *cgs_rec = nullptr, *cgs_coef = nullptr;
   int grid_cgs = 0;
+  // fused sparse-sign sketch (the products' epilogues draw and add; the small
+  // least-squares step reduces the per-CTA records): no per-step sketch launch
+  bool sk_fused = false;
+  double *skw_rec = nullptr, *skz_rec = nullptr;   // [s][grid of the product]
   // low-rank truncation by the randomized SVD (SFL_PRECOND_LOWRANK)
   bool lowrank = false;
   LrParams<float> lr32{};       // FP32 arithmetic (default)

@@ -112,6 +112,12 @@ struct SpmvParams {
   int full;                             // full orthogonalization: no window dots (block CGS2 kernels do it)
   XT *wfull;                            // full: every w~_j (column j - 1); the vector pass writes w~_1
   double *sigWall;                      // full: 1/||w~_j|| at index j - 1
+  // fused sparse-sign sketch of the product output (sk_s > 0): every CTA adds
+  // its rows' contributions into an s-vector record sk_rec[r * sk_cap + cta]
+  int sk_s, sk_zeta;
+  uint64_t sk_seed_add;                 // the sketch's seed is the solve's seed plus this
+  double *sk_rec;
+  int sk_cap;
   // matrix-free projector (the kSpmvProj form; the CSR arrays are unused)
   int proj;                             // kProjRay, kProjBackChord or kProjBackLinear
   int pN, pna, pnb;                     // image N x N, angles, bins
@@ -329,6 +335,65 @@ __host__ __device__ inline size_t spmv_smem_bytes(int lpr, size_t acc_bytes) {
   return acc_bytes * kWarps * 32 * (lpr > 1 ? lpr : 1);
 }
 
+// Fused sparse-sign sketch of the product output (Section 2.7 draws, the
+// same generator as sketch_table_kernel): each output y[o] adds
+// +-y[o] to the zeta rows drawn for column o (scale 1/sqrt(zeta) and the
+// output's scale are applied by the consumer).  Each warp accumulates into
+// its own s-vector in shared memory (acc, kWarps x s doubles); lanes that hit
+// the same row at the same draw add in lane order (match_any groups, ranks),
+// so the sums have a fixed order.  The warps' vectors are then added in warp
+// order into this CTA's record rec[r * cap + blockIdx.x].  All threads call.
+template <typename XT, bool ORIG>
+__device__ __noinline__ void spmv_sketch(int s, int zeta, uint64_t seed, RowBlocks rb, const int32_t *orig,
+                                         const XT *y, double *acc_all, double *rec, int cap) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double *acc = acc_all + (size_t)warp * s;
+  __syncthreads();   // the shared memory held the row loop's stash
+  for (int r = lane; r < s; r += 32) acc[r] = 0.0;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t row0 = rb.first; row0 < rb.end; row0 += rb.stride) {
+    const int64_t row = row0 + lane;
+    const bool valid = row < min(row0 + 32, rb.end);
+    int rows[kMaxZeta];
+    double v = 0.0;
+    uint32_t neg = 0;
+    if (valid) {
+      const int64_t o = ORIG ? orig[row] : row;
+      v = (double)y[o];
+      int cnt = 0;
+      for (uint32_t t = 0; cnt < zeta && t < 1000000u; ++t) {
+        const uint64_t h = splitmix64_first(seed ^ (((uint64_t)o << 32) + t));
+        const int r = (int)__umul64hi(h, (uint64_t)s);
+        bool dup = false;
+        for (int q = 0; q < cnt; ++q) dup |= (rows[q] == r);
+        if (dup) continue;
+        rows[cnt] = r;
+        neg |= (uint32_t)(h & 1ull) << cnt;
+        ++cnt;
+      }
+      for (int q = cnt; q < zeta; ++q) rows[q] = -1;   // never expected: the draw cap was hit
+    }
+    for (int q = 0; q < zeta; ++q) {
+      const int tg = valid ? rows[q] : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, tg);
+      const int rk = __popc(peers & lt);
+      const int mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)rk);
+      const double add = ((neg >> q) & 1u) ? -v : v;
+      for (int rr = 0; rr <= mx; ++rr) {
+        if (tg >= 0 && rk == rr) acc[tg] += add;
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < s; r += kThreads) {
+    double a = 0.0;
+    for (int w = 0; w < kWarps; ++w) a += acc_all[(size_t)w * s + r];
+    rec[(size_t)r * cap + blockIdx.x] = a;
+  }
+}
+
 // Scalars booked by CTA 0 of a product (all its threads call): it stages the
 // solve state, reduces the records of the kernel before the product and
 // writes the step's scalars to the device state.  The other CTAs never need
@@ -445,6 +510,7 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
   __shared__ double tot[kPartStride];
   // a launch with too little shared memory does nothing (never writes out of bounds)
   if (dynamic_smem_bytes() < spmv_smem_bytes(LPR, sizeof(typename AccT<XT>::T))) return;
+  if (p.sk_s && dynamic_smem_bytes() < sizeof(double) * (size_t)kWarps * p.sk_s) return;
   griddep_wait();
   griddep_launch_dependents();
   int k = 0, lo = 1, nd = 0;
@@ -483,6 +549,8 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
     if (p.mode != kModeInitB) {
       if (blockIdx.x == 0) {
         if (threadIdx.x < kPartStride) outpart[(size_t)threadIdx.x * kPartCap] = 0.0;   // CTA 0's record
+        if (p.sk_s)
+          for (int r = threadIdx.x; r < p.sk_s; r += kThreads) p.sk_rec[(size_t)r * p.sk_cap] = 0.0;
         spmv_bookkeeping(p, k, &sst, tot);
         return;
       }
@@ -531,6 +599,8 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
     case 8: spmv_finish<XT, 8, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
     default: spmv_finish<XT, 9, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
   }
+  if (p.sk_s) spmv_sketch<XT, ORIG>(p.sk_s, p.sk_zeta, __ldcg(&p.st->seed) + p.sk_seed_add, rb, og, y,
+                                   reinterpret_cast<double *>(smem_raw), p.sk_rec, p.sk_cap);
 }
 
 // Row cost for the warp partition of a product, in quarter iterations: the
@@ -918,14 +988,22 @@ struct LsParams {
   double *Rinv;       // maxit x maxit, row-major: inverse of the triangular factor
   double *y;          // maxit
   double *e;          // s: residual of the small problem
-  const double *SAZ;  // sFLSQR: LS columns; sFLSMR: m-side columns for the residual rule
-  const double *SAtW; // sFLSMR
+  double *SAZ;        // sFLSQR: LS columns; sFLSMR: m-side columns for the residual rule
+  double *SAtW;       // sFLSMR
   const double *Hband;
   const double *sbm;  // sFLSMR residual rule: S_m b
   const double *rhs;  // right-hand side of the small problem
   double *relres_hist;
   cudaGraphConditionalHandle cond;
   int use_cond;
+  // fused sketches (single solves): the products left per-CTA records of the
+  // unscaled sketches of A z_k (skw) and of A^T w_{k+1} / B w_{k+1} (skz);
+  // this step adds them (fixed order) into column k of S A Z and column k+1
+  // of S A^T W, scaled by 1/sqrt(zeta) and the outputs' scales
+  const double *skw_rec, *skz_rec;
+  int skw_cap, skz_cap;
+  double sk_isz;
+  int RW, RP;
   // several independent problems (one cluster each, problem = cluster index):
   // st is an array of states and every buffer above advances by its stride
   int64_t bQ, bRinv, by, be, bSAZ, bSAtW, bHband, bvec, bhist;   // per-problem strides (0: one problem)
@@ -1120,6 +1198,31 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
   };
 
   // ---- 0. the new column and e, my rows; the staged blocks
+  if (p.skw_rec || p.skz_rec) {
+    // the fused sketches of this step's products, my rows: warp per row, lanes over the records
+    for (int i = warp; i < nr; i += kWarps) {
+      const int row = r0 + i;
+      if (p.skw_rec) {
+        const double *rc = p.skw_rec + (size_t)row * p.skw_cap;
+        double a0 = 0.0, a1 = 0.0;
+        int b = lane;
+        for (; b + 32 < p.skw_cap; b += 64) { a0 += __ldcg(rc + b); a1 += __ldcg(rc + b + 32); }
+        if (b < p.skw_cap) a0 += __ldcg(rc + b);
+        const double a = warp_sum(a0 + a1);
+        if (lane == 0) p.SAZ[(size_t)kk * s + row] = a * p.sk_isz * __ldcg(&st->sig_p[ring_slot(k, p.RP)]);
+      }
+      if (p.skz_rec && !lucky) {
+        const double *rc = p.skz_rec + (size_t)row * p.skz_cap;
+        double a0 = 0.0, a1 = 0.0;
+        int b = lane;
+        for (; b + 32 < p.skz_cap; b += 64) { a0 += __ldcg(rc + b); a1 += __ldcg(rc + b + 32); }
+        if (b < p.skz_cap) a0 += __ldcg(rc + b);
+        const double a = warp_sum(a0 + a1);
+        if (lane == 0) p.SAtW[(size_t)k * s + row] = a * p.sk_isz * __ldcg(&st->sig_w[ring_slot(k + 1, p.RW)]);
+      }
+    }
+    __syncthreads();
+  }
   for (int i = tid; i < nr; i += kThreads) {
     const int row = r0 + i;
     double c;

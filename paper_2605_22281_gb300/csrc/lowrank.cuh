@@ -33,20 +33,18 @@ namespace sfl {
 constexpr int kLrTile = 32;       // rows of a product tile
 constexpr int kLrK = 64;          // depth of one split-K chunk
 constexpr int kLrSweeps = 10;     // most Jacobi sweeps
-constexpr size_t kLrOrthSmem = 200 * 1024;   // largest M x l block the one-CTA orthonormalization holds
 
 // Per compute type (FP32 default, FP64 for verification): largest r +
 // oversampling, rows per CTA of the Gram partials, unit roundoff, and the
-// Jacobi rotation threshold (a pair is rotated while |a_pq| exceeds it times
-// the largest diagonal entry, about ten unit roundoffs).
+// Jacobi stopping threshold on (off-diagonal / diagonal) squared norms.
 template <typename RT> struct LrLim;
 template <> struct LrLim<float> {
   static constexpr int L = 64, GR = 64;
-  static constexpr float u = 5.9604645e-8f, rot_tol = 6e-7f;
+  static constexpr float u = 5.9604645e-8f, jacobi_tol = 1e-12f;
 };
 template <> struct LrLim<double> {
   static constexpr int L = 48, GR = 32;
-  static constexpr double u = 1.1102230246251565e-16, rot_tol = 1e-15;
+  static constexpr double u = 1.1102230246251565e-16, jacobi_tol = 1e-30;
 };
 
 template <typename RT>
@@ -162,130 +160,48 @@ __device__ __forceinline__ void lr_load_gram(const LrParams<RT> &p, int nb, RT (
 }
 
 // Cholesky G + shift I = R^T R (upper R) and R^{-1} into p.small (l x l,
-// row-major, zero below the diagonal), by warp 0 of the CTA (lanes split the
-// columns; __syncwarp between the dependent steps).  A pivot that is not
-// positive sets *p.flag (then the step keeps tau = identity).  The CTA's
-// other warps return at once; G is in shared memory, Ri is scratch of the
-// same shape.
+// row-major, zero below the diagonal).  All threads of one CTA.  A pivot that
+// is not positive sets *p.flag (then the step keeps tau = identity).
 template <typename RT>
-static __device__ void lr_cholesky_inverse(const LrParams<RT> &p, RT (*G)[LrLim<RT>::L + 1],
-                                           RT (*Ri)[LrLim<RT>::L + 1], RT shift_rel) {
-  const int L = p.l, lane = threadIdx.x & 31;
-  if (threadIdx.x >= 32) return;
-  if (shift_rel > RT(0)) {
-    RT tr = RT(0);
-    for (int a = lane; a < L; a += 32) tr += G[a][a];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-    for (int a = lane; a < L; a += 32) G[a][a] += shift_rel * tr;
-    __syncwarp();
+static __device__ void lr_cholesky_inverse(const LrParams<RT> &p, RT (*G)[LrLim<RT>::L + 1], RT shift_rel, RT *s_tr) {
+  const int L = p.l, tid = threadIdx.x;
+  if (shift_rel > RT(0.)) {
+    if (tid == 0) {
+      RT tr = RT(0.);
+      for (int a = 0; a < L; ++a) tr += G[a][a];
+      *s_tr = tr;
+    }
+    __syncthreads();
+    for (int a = tid; a < L; a += kThreads) G[a][a] += shift_rel * *s_tr;
   }
-  // right-looking Cholesky: G's upper triangle becomes R
   for (int j = 0; j < L; ++j) {
+    __syncthreads();
     const RT d = G[j][j];
-    if (!(d > RT(0))) {
-      if (lane == 0) *p.flag = 1;
+    if (!(d > RT(0.))) {
+      if (tid == 0) *p.flag = 1;
       return;
     }
     const RT rd = rsqrt(d);
-    __syncwarp();
-    for (int c = j + lane; c < L; c += 32) G[j][c] *= rd;
-    __syncwarp();
-    for (int c = j + 1 + lane; c < L; c += 32) {
-      const RT gjc = G[j][c];
-      for (int a = j + 1; a <= c; ++a) G[a][c] -= G[j][a] * gjc;
+    __syncthreads();
+    for (int c = j + tid; c < L; c += kThreads) G[j][c] *= rd;
+    __syncthreads();
+    const int w = L - j - 1;
+    for (int t = tid; t < w * w; t += kThreads) {
+      const int a = j + 1 + t / w, c = j + 1 + t % w;
+      if (a <= c) G[a][c] -= G[j][a] * G[j][c];
     }
-    __syncwarp();
-  }
-  // R^{-1}, rows from the bottom: Ri[a][c] = -(sum_{a < t <= c} R[a][t] Ri[t][c]) / R[a][a]
-  for (int a = L - 1; a >= 0; --a) {
-    const RT inv = RT(1) / G[a][a];
-    for (int c = lane; c < L; c += 32) {
-      RT v = RT(0);
-      if (c == a) {
-        v = inv;
-      } else if (c > a) {
-        RT acc = RT(0);
-        for (int t = a + 1; t <= c; ++t) acc = fma(G[a][t], Ri[t][c], acc);
-        v = -acc * inv;
-      }
-      Ri[a][c] = v;
-    }
-    __syncwarp();
-  }
-  for (int t = lane; t < L * L; t += 32) p.small[t] = Ri[t / L][t % L];
-}
-
-// Orthonormal basis of the range of X (M x l) by one CTA, when X fits in
-// shared memory: X = the sum of the KS split-K partials of a product, held
-// column-major; classical Gram-Schmidt applied twice, column by column (warps
-// take the dots of the earlier columns, threads the updates, fixed-order
-// block sums); a column whose norm falls below 1e-5 (FP32) or 1e-12 (FP64)
-// of its norm before the passes is set to zero (rank deficient: it adds
-// nothing to the projector).  Q (M x l, row-major) is written to out.
-template <typename RT>
-static __global__ void __launch_bounds__(kThreads) lr_orth_cta_kernel(LrParams<RT> p, int M, int KS, RT *out) {
-  extern __shared__ __align__(16) unsigned char lr_smem[];
-  RT *X = reinterpret_cast<RT *>(lr_smem);      // [l][M]
-  __shared__ RT d[LrLim<RT>::L];
-  __shared__ RT wpart[kWarps];
-  __shared__ RT s_norm0, s_norm;
-  if (!lr_running(p.st) || __ldcg(p.flag)) return;
-  const int L = p.l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int t = tid; t < M * L; t += kThreads) {
-    const int i = t / L, c = t % L;
-    RT v = RT(0);
-    for (int ks = 0; ks < KS; ++ks) v += p.part[(size_t)ks * M * L + t];
-    X[(size_t)c * M + i] = v;
   }
   __syncthreads();
-  auto block_sum = [&](RT v) -> RT {   // fixed order: lanes by butterfly, warps in order
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wpart[warp] = v;
-    __syncthreads();
-    RT a = RT(0);
-    for (int w = 0; w < kWarps; ++w) a += wpart[w];
-    __syncthreads();
-    return a;
-  };
-  const RT drop = sizeof(RT) == sizeof(float) ? RT(1e-5) : RT(1e-12);
-  for (int j = 0; j < L; ++j) {
-    RT *v = X + (size_t)j * M;
-    RT a = RT(0);
-    for (int i = tid; i < M; i += kThreads) a += v[i] * v[i];
-    a = block_sum(a);
-    if (tid == 0) s_norm0 = sqrt(a);
-    for (int pass = 0; pass < 2 && j > 0; ++pass) {
-      for (int t = warp; t < j; t += kWarps) {   // d_t = <q_t, v>
-        const RT *q = X + (size_t)t * M;
-        RT s = RT(0);
-        for (int i = lane; i < M; i += 32) s += q[i] * v[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) d[t] = s;
-      }
-      __syncthreads();
-      for (int i = tid; i < M; i += kThreads) {   // v -= Q d
-        RT s = RT(0);
-        for (int t = 0; t < j; ++t) s += X[(size_t)t * M + i] * d[t];
-        v[i] -= s;
-      }
-      __syncthreads();
+  // column c of R^{-1}: back substitution, one thread per column
+  for (int c = tid; c < L; c += kThreads) {
+    RT col[LrLim<RT>::L];
+    col[c] = RT(1.) / G[c][c];
+    for (int a = c - 1; a >= 0; --a) {
+      RT s = RT(0.);
+      for (int t = a + 1; t <= c; ++t) s = fma(G[a][t], col[t], s);
+      col[a] = -s / G[a][a];
     }
-    a = RT(0);
-    for (int i = tid; i < M; i += kThreads) a += v[i] * v[i];
-    a = block_sum(a);
-    if (tid == 0) s_norm = sqrt(a);
-    __syncthreads();
-    const RT nv = s_norm, n0 = s_norm0;
-    const RT sc = (nv > drop * n0 && nv > RT(0)) ? RT(1) / nv : RT(0);
-    for (int i = tid; i < M; i += kThreads) v[i] *= sc;
-    __syncthreads();
-  }
-  for (int t = tid; t < M * L; t += kThreads) {
-    const int i = t / L, c = t % L;
-    out[t] = X[(size_t)c * M + i];
+    for (int a = 0; a < L; ++a) p.small[a * L + c] = a <= c ? col[a] : RT(0.);
   }
 }
 
@@ -297,15 +213,12 @@ static __global__ void __launch_bounds__(kThreads) lr_orth_cta_kernel(LrParams<R
 template <typename RT>
 static __global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams<RT> p, int mode, const RT *in, RT *out, int M,
                                                            int KS, RT shift_rel) {
-  constexpr int kL = LrLim<RT>::L, kGR = LrLim<RT>::GR;
-  constexpr int kXs = kGR * kL > kL * (kL + 1) ? kGR * kL : kL * (kL + 1);
-  __shared__ RT XR[kXs];                   // this CTA's rows (later, in the last CTA: R^{-1} scratch)
-  __shared__ RT SG[kL * (kL + 1)];         // S (this pass's input factor), later G (last CTA)
+  __shared__ RT Xs[LrLim<RT>::GR][LrLim<RT>::L];
+  __shared__ RT SG[LrLim<RT>::L * (LrLim<RT>::L + 1)];   // S (this pass's input factor), later G (last CTA)
   __shared__ int s_last;
+  __shared__ RT s_tr;
   RT *S = SG;
-  auto Xs = reinterpret_cast<RT (*)[kL]>(XR);
-  auto G = reinterpret_cast<RT (*)[kL + 1]>(SG);
-  auto Ri = reinterpret_cast<RT (*)[kL + 1]>(XR);
+  auto G = reinterpret_cast<RT (*)[LrLim<RT>::L + 1]>(SG);
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
   const int L = p.l, r0 = blockIdx.x * LrLim<RT>::GR, tid = threadIdx.x;
   const int nr = min(LrLim<RT>::GR, M - r0);
@@ -331,7 +244,7 @@ static __global__ void __launch_bounds__(kThreads) lr_orth_kernel(LrParams<RT> p
   lr_gram_partial(p, Xs, nr);
   if (!lr_last_cta(p, &s_last)) return;
   lr_load_gram(p, gridDim.x, G);
-  lr_cholesky_inverse(p, G, Ri, shift_rel);
+  lr_cholesky_inverse(p, G, shift_rel, &s_tr);
 }
 
 // out[i][0..ncol) = in[i][0..l) * p.small (l x ncol).
@@ -371,6 +284,7 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams<R
   __shared__ RT cs[LrLim<RT>::L / 2][2];
   __shared__ int pr[LrLim<RT>::L / 2][2];
   __shared__ int order[LrLim<RT>::L];
+  __shared__ RT red[2][kWarps];
   __shared__ int s_last, s_go;
   if (!lr_running(p.st) || __ldcg(p.flag)) return;
   const int L = p.l, M = p.N2, r0 = blockIdx.x * LrLim<RT>::GR, tid = threadIdx.x;
@@ -398,67 +312,66 @@ static __global__ void __launch_bounds__(kThreads) lr_gram_eig_kernel(LrParams<R
   }
   __syncthreads();
   const int np = n / 2;
-  // cyclic Jacobi, round-robin pairs (index 0 fixed, the others rotate); a
-  // pair is rotated when |a_pq| > tol max_i |a_ii| (rounding-level entries are
-  // left: only the leading eigenvectors are used); a sweep that rotates
-  // nothing ends the iteration, and at most kLrSweeps sweeps run (the
-  // convergence is quadratic)
-  __shared__ RT s_amax;
-  if (tid == 0) {
-    RT mx = RT(0);
-    for (int a = 0; a < L; ++a) mx = fmax(mx, fabs(A[a][a]));
-    s_amax = mx;
-  }
-  __syncthreads();
-  const RT thr = LrLim<RT>::rot_tol * s_amax;
-  for (int sweep = 0; sweep < kLrSweeps; ++sweep) {
-    if (tid == 0) s_go = 0;
+  for (int sweep = 0; sweep < kLrSweeps; ++sweep) {   // quadratic convergence: a few sweeps
+    // stop when the off-diagonal mass is below the type's threshold times the diagonal's
+    RT off = RT(0.), dg = RT(0.);
+    for (int t = tid; t < L * L; t += kThreads) {
+      const int a = t / L, c = t % L;
+      const RT v = A[a][c] * A[a][c];
+      if (a == c) dg += v; else off += v;
+    }
+    off = warp_sum(off);
+    dg = warp_sum(dg);
+    if (lane == 0) { red[0][warp] = off; red[1][warp] = dg; }
     __syncthreads();
+    if (tid == 0) {
+      RT o = RT(0.), d = RT(0.);
+      for (int w = 0; w < kWarps; ++w) { o += red[0][w]; d += red[1][w]; }
+      s_go = o > LrLim<RT>::jacobi_tol * d;
+    }
+    __syncthreads();
+    if (!s_go) break;
     for (int round = 0; round < n - 1; ++round) {
-      if (tid < np) {
+      if (tid < np) {   // round-robin pairing: index 0 fixed, the others rotate
         const int u = tid, v = n - 1 - tid;
         int a = u == 0 ? 0 : 1 + (u - 1 + round) % (n - 1);
         int b = 1 + (v - 1 + round) % (n - 1);
         if (a > b) { const int t = a; a = b; b = t; }
-        RT c = RT(1), sn = RT(0);
+        RT c = RT(1.), s = RT(0.);
         const RT apq = A[a][b];
-        if (b < L && fabs(apq) > thr) {
-          const RT tau = (A[b][b] - A[a][a]) / (RT(2) * apq);
+        if (b < L && fabs(apq) > RT(1e-20) * sqrt(fabs(A[a][a] * A[b][b])) && apq != RT(0.)) {
+          const RT tau = (A[b][b] - A[a][a]) / (RT(2.) * apq);
           const RT t = fabs(tau) > RT(1e15) ? RT(0.5) / tau
-                                            : copysign(RT(1), tau) / (fabs(tau) + sqrt(fma(tau, tau, RT(1))));
-          c = rsqrt(fma(t, t, RT(1)));
-          sn = t * c;
-          s_go = 1;
+                                             : copysign(RT(1.), tau) / (fabs(tau) + sqrt(fma(tau, tau, RT(1.))));
+          c = rsqrt(fma(t, t, RT(1.)));
+          s = t * c;
         }
         pr[tid][0] = a; pr[tid][1] = b;
-        cs[tid][0] = c; cs[tid][1] = sn;
+        cs[tid][0] = c; cs[tid][1] = s;
       }
       __syncthreads();
-      // A <- J^T A J in one phase: the thread of block (u, v) (rows of pair u,
-      // columns of pair v) updates its four entries; V <- V J alongside
-      for (int t = tid; t < np * np; t += kThreads) {
-        const int u = t / np, v = t % np;
-        const int ra = pr[u][0], rb = pr[u][1], ca = pr[v][0], cb = pr[v][1];
-        const RT cu = cs[u][0], su = cs[u][1], cv = cs[v][0], sv = cs[v][1];
-        const RT b00 = A[ra][ca], b01 = A[ra][cb], b10 = A[rb][ca], b11 = A[rb][cb];
-        const RT t00 = cu * b00 - su * b10, t01 = cu * b01 - su * b11;   // J_u^T B
-        const RT t10 = su * b00 + cu * b10, t11 = su * b01 + cu * b11;
-        A[ra][ca] = t00 * cv - t01 * sv;                                    // (J_u^T B) J_v
-        A[ra][cb] = t00 * sv + t01 * cv;
-        A[rb][ca] = t10 * cv - t11 * sv;
-        A[rb][cb] = t10 * sv + t11 * cv;
+      for (int t = tid; t < np * n; t += kThreads) {   // rows: A <- J^T A
+        const int k = t / n, j = t % n;
+        const int a = pr[k][0], b = pr[k][1];
+        const RT c = cs[k][0], s = cs[k][1];
+        const RT x = A[a][j], y = A[b][j];
+        A[a][j] = c * x - s * y;
+        A[b][j] = s * x + c * y;
       }
-      for (int t = tid; t < n * np; t += kThreads) {
-        const int i = t / np, v = t % np;
-        const int a = pr[v][0], b = pr[v][1];
-        const RT c = cs[v][0], sn = cs[v][1];
-        const RT x = Vm[i][a], y = Vm[i][b];
-        Vm[i][a] = c * x - sn * y;
-        Vm[i][b] = sn * x + c * y;
+      __syncthreads();
+      for (int t = tid; t < np * n; t += kThreads) {   // columns: A <- A J, V <- V J
+        const int k = t / n, i = t % n;
+        const int a = pr[k][0], b = pr[k][1];
+        const RT c = cs[k][0], s = cs[k][1];
+        const RT x = A[i][a], y = A[i][b];
+        A[i][a] = c * x - s * y;
+        A[i][b] = s * x + c * y;
+        const RT u = Vm[i][a], w = Vm[i][b];
+        Vm[i][a] = c * u - s * w;
+        Vm[i][b] = s * u + c * w;
       }
       __syncthreads();
     }
-    if (!s_go) break;
   }
   for (int a = tid; a < L; a += kThreads) {   // decreasing eigenvalue, ties by index
     int rank = 0;

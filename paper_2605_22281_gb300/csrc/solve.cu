@@ -53,6 +53,10 @@ static void destroy_session(Plan &pl, Session &se) {
   se.bytes = 0;
 }
 
+// Largest shared memory the fused sketch may add to a product (kWarps s-vectors
+// of doubles: s <= 1024).
+constexpr size_t kSketchFusedSmem = 64 * 1024;
+
 // The Q block of a CTA is staged in shared memory when the whole plan stays
 // within this budget (it then serves the four Q products of a step).
 constexpr size_t kLsStageBudget = 160 * 1024;
@@ -234,6 +238,13 @@ struct Engine {
     p.want_h = se.key.method != kSFLSQR;
     p.hb_ell = se.hb_ell;
     if (pl.matfree) set_proj(pl, p, mode == kModeFwd || mode == kModeInitB);
+    if (se.sk_fused && mode == kModeFwd && se.skw_rec) {
+      p.sk_s = se.key.s; p.sk_zeta = se.key.zeta; p.sk_rec = se.skw_rec; p.sk_cap = se.grid_spmv_A;
+      p.sk_seed_add = se.key.method == kSFLSMR ? 1 : 0;   // sFLSMR's m-side stop sketch is drawn from seed + 1
+    } else if (se.sk_fused && mode == kModeBwd && se.skz_rec) {
+      p.sk_s = se.key.s; p.sk_zeta = se.key.zeta; p.sk_rec = se.skz_rec; p.sk_cap = se.grid_spmv_T;
+      p.sk_seed_add = 0;
+    }
     p.full = se.full;
     if (se.full) {
       p.ell = 0;                        // the rings and scalars run as for window 0, with no window dots
@@ -308,6 +319,12 @@ struct Engine {
     q.SAZ = se.SAZ; q.SAtW = se.SAtW; q.Hband = se.Hband; q.sbm = se.sbm; q.rhs = se.rhs;
     q.relres_hist = se.key.r_hist;
     q.cond = h; q.use_cond = use_cond;
+    if (se.sk_fused) {
+      q.skw_rec = se.skw_rec; q.skz_rec = se.skz_rec;
+      q.skw_cap = se.grid_spmv_A; q.skz_cap = se.grid_spmv_T;
+      q.sk_isz = 1.0 / std::sqrt((double)se.key.zeta);
+      q.RW = se.RW; q.RP = se.RP;
+    }
     return q;
   }
 
@@ -327,14 +344,8 @@ struct Engine {
     const int KS1 = (N1 + kLrK - 1) / kLrK, KS2 = (N2 + kLrK - 1) / kLrK;
     constexpr int GR = LrLim<RT>::GR;
     auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
-    // one CTA (CGS2 in shared memory) when M x l fits, else shifted Cholesky
-    // QR (shift 11 (M l + l (l + 1)) u trace) then Cholesky QR twice: the result in b
+    // shifted Cholesky QR (shift 11 (M l + l (l + 1)) u trace), then Cholesky QR twice: the result in b
     auto orth = [&](int M, int KS, RT *a, RT *b) {
-      const size_t cta_smem = sizeof(RT) * (size_t)M * L;
-      if (cta_smem <= kLrOrthSmem) {
-        lr_orth_cta_kernel<RT><<<1, kThreads, cta_smem, s>>>(lp, M, KS, b);
-        return;
-      }
       const RT shift = RT(11) * RT((int64_t)M * L + (int64_t)L * (L + 1)) * LrLim<RT>::u;
       lr_orth_kernel<RT><<<cdiv(M, GR), kThreads, 0, s>>>(lp, 0, nullptr, a, M, KS, shift);
       lr_orth_kernel<RT><<<cdiv(M, GR), kThreads, 0, s>>>(lp, 1, a, b, M, 0, RT(0));
@@ -382,7 +393,6 @@ struct Engine {
     LA(lp.flag, sizeof(int));
     LA(lp.ticket, sizeof(int));
 #undef LA
-    SFL_CU(cudaFuncSetAttribute(lr_orth_cta_kernel<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLrOrthSmem));
     SFL_CU(cudaMemsetAsync(lp.flag, 0, sizeof(int), s));
     SFL_CU(cudaMemsetAsync(lp.ticket, 0, sizeof(int), s));
     return SFL_OK;
@@ -478,7 +488,8 @@ struct Engine {
     const int gsk = se.key.s * (se.key.method == kSFLSMR ? 2 : 1);
     // no programmatic edge into the sketch: its small CTAs, launched early,
     // would pile onto the first SMs the product frees (measured 2x slower)
-    if (se.key.method != kFLSQR && (r = launch_one(kKSketch, [&] { return k_sketch(se, kSkStep, gsk, s); }, tm)))
+    if (se.key.method != kFLSQR && !se.sk_fused &&
+        (r = launch_one(kKSketch, [&] { return k_sketch(se, kSkStep, gsk, s); }, tm)))
       return r;
     if ((r = launch_one(kKLs, [&] {
            return launch_ls(ls_params(se, use_cond, h), se.ls_cluster, se.smem_ls, s, pdl) == cudaSuccess
@@ -624,9 +635,19 @@ struct Engine {
     // launch shapes
     se->smem_A = spmv_smem_bytes(pl.A.lpr, sizeof(ACC));
     se->smem_T = spmv_smem_bytes(pl.T.lpr, sizeof(ACC));
+    // fused sketch: the products' epilogues need kWarps s-vectors of shared
+    // memory (the row loop's stash is reused); explicit sketches and FLSQR keep
+    // the separate sketch kernel (or none)
+    const size_t sk_smem = sizeof(double) * (size_t)kWarps * S;
+    se->sk_fused = !key.dense_S && key.method != kFLSQR && sk_smem <= kSketchFusedSmem;
+    const bool skw = se->sk_fused && (key.method == kSFLSQR || key.stop_rule == SFL_STOP_RULE_RESIDUAL);
+    const bool skz = se->sk_fused && key.method == kSFLSMR;
+    if (skw) se->smem_A = std::max(se->smem_A, sk_smem);
+    if (skz) se->smem_T = std::max(se->smem_T, sk_smem);
     se->smem_init = spmv_smem_bytes(1, sizeof(ACC));
-    SFL_CU(O::set_smem(pl.A.lpr, true, se->smem_A));
-    SFL_CU(O::set_smem(pl.T.lpr, true, se->smem_T));
+    // one limit per kernel for every session (room for the fused sketch), so no session lowers another's
+    SFL_CU(O::set_smem(pl.A.lpr, true, std::max(se->smem_A, kSketchFusedSmem)));
+    SFL_CU(O::set_smem(pl.T.lpr, true, std::max(se->smem_T, kSketchFusedSmem)));
     SFL_CU(O::set_smem(1, false, se->smem_init));
     auto grid_of = [&](int lpr, bool mat, size_t smem) {
       int occ = (mat && pl.matfree) ? O::proj_occupancy(smem) : O::spmv_occupancy(lpr, mat, smem);
@@ -656,6 +677,8 @@ struct Engine {
     SA(se->part.wn, pbytes);
     // row range of every warp of the two products, balanced by row cost; CTA 0
     // of a product books the step's scalars and runs no rows
+    if (skw) SA(se->skw_rec, sizeof(double) * (size_t)S * se->grid_spmv_A);
+    if (skz) SA(se->skz_rec, sizeof(double) * (size_t)S * se->grid_spmv_T);
     const int WA = (se->grid_spmv_A - 1) * kWarps, WT = (se->grid_spmv_T - 1) * kWarps;
     SA(se->wrowA, sizeof(int32_t) * (WA + 1));
     SA(se->wrowT, sizeof(int32_t) * (WT + 1));
@@ -916,7 +939,7 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
     p.proj = which == 0 ? kProjRay : (pl.ct_back ? kProjBackLinear : kProjBackChord);
   }
   const size_t smem = spmv_smem_bytes(M.lpr, sizeof(typename AccT<XT>::T));
-  SFL_CU(Ops<VT, XT>::set_smem(M.lpr, true, smem));
+  SFL_CU(Ops<VT, XT>::set_smem(M.lpr, true, std::max(smem, kSketchFusedSmem)));
   if (std::is_same<XT, double>::value) {
     p.x = (const XT *)x; p.y = (XT *)y;
     SFL_CU(Ops<VT, XT>::spmv(p, M.lpr, true, grid, smem, s));
