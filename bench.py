@@ -59,6 +59,8 @@ def parse_args():
                          "its geometry recipe, for profiling)")
     ap.add_argument("--only-decay", action="store_true",
                     help="run only the residual-size study (dense 1024 x 512, Gaussian sketches) and print its JSON")
+    ap.add_argument("--only-matfree", action="store_true",
+                    help="only the matrix-free 256x256 unmatched solve (FP64 and FP32 projectors)")
     ap.add_argument("--only-deblur", action="store_true",
                     help="only the low-rank deblurring timing comparison (512x512, rank 30, 50 steps)")
     ap.add_argument("--only-flsqr", action="store_true",
@@ -480,6 +482,52 @@ def deblur_variant(args, G, wl, np, torch, N: int = 512):
     return out
 
 
+def matfree_variant(args, G, wl, np, torch):
+    """The 256x256 unmatched sFLSMR workload solved with no stored operator: the
+    matrix-free plan computes A z by Siddon's ray walk and B w by the
+    pixel-driven interpolation on the fly (FP64, and FP32 geometry with FP32
+    vectors), against the stored-operator FP64 solve of the same problem.
+    Reports the products' launch times and the stored operator's bytes per
+    launch they replace (the products are bound by arithmetic, not memory)."""
+    p = wl.make("ct256_sflsmr_unmatched")
+    st = p.settings
+    kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
+              noise_norm=float(p.noise_norm[0]), eta=st["eta"], precond="reweight", irw_eps=st["irw_eps"])
+    b = torch.as_tensor(p.b, device="cuda")
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ref = G.Plan(p.A, p.B, image_shape=(p.N, p.N))
+    x_ref, i_ref, _ = ref.solve("sflsmr", b, **kw)
+    x_ref = x_ref.cpu().numpy()
+    ref.close()
+    out = {"image": f"{p.N}x{p.N}", "angles": p.n_angles, "bins": p.n_bins,
+           "stored_iters": i_ref.iters, "stored_nnz": {"A": int(p.A.nnz), "B": int(p.B.nnz)}}
+    for vdt in ("f64", "f32"):
+        plan = G.Plan.ct(p.N, p.n_angles, p.n_bins, back="unmatched", value_dtype=vdt)
+        x, info, _ = plan.solve("sflsmr", b, **kw)
+        reps = max(3, min(args.steps, 10))
+        e0.record(stream)
+        for _ in range(reps):
+            plan.solve("sflsmr", b, out=x, sync=False, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        xh = x.cpu().numpy()
+        _, _, hp = plan.solve("sflsmr", b, driver="profiled", **kw)
+        kms, kl = hp["kernel_ms"], hp["kernel_launches"]
+        vb = 8 if vdt == "f64" else 4
+        leg = {"iters": info.iters, "stop": info.status_name, "time_to_stop_ms": ms, "iters_per_s": info.iters / (ms / 1000),
+               "rel_diff_vs_stored_fp64_x": float(np.linalg.norm(xh - x_ref) / np.linalg.norm(x_ref)),
+               "rel_error_vs_x_true": float(np.linalg.norm(xh - p.x_true) / np.linalg.norm(p.x_true))}
+        for name, nnz in (("spmv_fwd", p.A.nnz), ("spmv_bwd", p.B.nnz)):
+            avg = kms[name] / max(kl[name], 1)
+            leg[name] = {"avg_us": 1000 * avg, "entries_per_s": nnz / (avg * 1e-3),
+                         "stored_bytes_replaced": int(nnz) * (vb + 4)}
+        out[vdt] = leg
+        plan.close()
+    return out
+
+
 def diff_variant(args, G, wl, np, torch):
     """The differentiable form: 16 sinograms of 256x256 phantoms, fixed k = 30
     steps of sFLSQR with a diagonal weight (s = 61, window 2), FP32 values and
@@ -696,7 +744,8 @@ def run_ours(args):
     from paper_2605_22281_gb300 import api as G
 
     for flag, leg in (("only_batched", batched_variant), ("only_mixed", mixed_variant), ("only_diff", diff_variant),
-                      ("only_decay", decay_variant), ("only_flsqr", flsqr_variant), ("only_deblur", deblur_variant)):
+                      ("only_decay", decay_variant), ("only_flsqr", flsqr_variant), ("only_deblur", deblur_variant),
+                      ("only_matfree", matfree_variant)):
         if getattr(args, flag):
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             print(json.dumps(leg(args, G, wl, np, torch)), flush=True)
@@ -740,6 +789,7 @@ def run_ours(args):
         variants["batched_ct512_64rhs_f32"] = batched_variant(args, G, wl, np, torch)
         variants["diff_ct256_16rhs_fixed_k"] = diff_variant(args, G, wl, np, torch)
         variants["deblur512_lowrank_rnd_50_steps"] = deblur_variant(args, G, wl, np, torch)
+        variants["matrix_free_ct256_sflsmr_unmatched"] = matfree_variant(args, G, wl, np, torch)
         variants["decay_study_gaussian"] = decay_variant(args, G, wl, np, torch)
         variants["ct64_sflsqr"] = small_variant(args, G, wl, np, torch)
 
