@@ -61,6 +61,7 @@ typedef enum {
   SFL_PRECOND_LOWRANK = 3     /* rank-r truncation by the randomized SVD (see sfl_opts.lowrank_*) */
 } sfl_precond;
 typedef enum { SFL_STOP_RULE_RESIDUAL = 0, SFL_STOP_RULE_NORMAL = 1 } sfl_stop_rule;
+typedef enum { SFL_SKETCH_APPLY_AUTO = 0, SFL_SKETCH_APPLY_FUSED = 1, SFL_SKETCH_APPLY_KERNEL = 2 } sfl_sketch_apply_mode;
 
 /* A CSR matrix.  rowptr has rows+1 entries with rowptr[0] = 0, nondecreasing,
  * rowptr[rows] = nnz < 2^31; colidx[i] in [0, cols).  values has nnz entries of
@@ -197,6 +198,19 @@ typedef struct {
   int32_t lowrank_power;
   const double *lowrank_omega;
   int32_t lowrank_fp64;
+  /* How the sparse-sign sketch of each new basis vector is applied (single
+   * solves; sfl_sketch_apply_mode): FUSED adds it in the epilogue of the
+   * product that makes the vector, drawing S from the hash (no stored S, no
+   * sketch launch); KERNEL runs a separate gather kernel over a row-major
+   * table of S built once per seed; AUTO (0, the default) takes FUSED when
+   * every sketched product averages at least 512 stored entries per output
+   * row (or, on a matrix-free plan, an image of at least 512 x 512), where the
+   * epilogue's per-output work is small beside the row, and KERNEL
+   * otherwise.  Both give the same sketch up to rounding: FUSED adds the
+   * terms exactly as 64-bit fixed-point integers per CTA (scale from the
+   * CTA's output norm), KERNEL in FP64.  Explicit sketches and FLSQR always
+   * take KERNEL (or no sketch). */
+  int32_t sketch_apply;
 } sfl_opts;
 
 /* Result of a solve.  Filled when the call returns (the call then waits for

@@ -17,6 +17,7 @@ SFL_F64, SFL_F32, SFL_BF16 = 0, 1, 2
 STOP_RUNNING, STOP_DISCREPANCY, STOP_MAXIT, STOP_BREAKDOWN = 0, 1, 2, 3
 PRECOND = {"identity": 0, "diag": 1, "reweight": 2, "lowrank": 3}
 STOP_RULE = {"residual": 0, "normal": 1}
+SKETCH_APPLY = {"auto": 0, "fused": 1, "kernel": 2}
 DTYPE = {"f64": SFL_F64, "f32": SFL_F32, "bf16": SFL_BF16}
 
 
@@ -40,7 +41,8 @@ class Opts(ctypes.Structure):
                 ("orth_against_z", ctypes.c_int32), ("sketch_dense", ctypes.c_void_p),
                 ("sketch_dense_stop", ctypes.c_void_p), ("lowrank_rank", ctypes.c_int32),
                 ("lowrank_oversample", ctypes.c_int32), ("lowrank_power", ctypes.c_int32),
-                ("lowrank_omega", ctypes.c_void_p), ("lowrank_fp64", ctypes.c_int32)]
+                ("lowrank_omega", ctypes.c_void_p), ("lowrank_fp64", ctypes.c_int32),
+                ("sketch_apply", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -144,13 +144,17 @@ class Plan:
         return y
 
     def _opts(self, s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, diag_w, irw_eps,
-              vec_dtype, x_hist, r_hist, orth_against="p", sk=None, sk_stop=None, lowrank=(0, 0, 0, None, 0)):
+              vec_dtype, x_hist, r_hist, orth_against="p", sk=None, sk_stop=None, lowrank=(0, 0, 0, None, 0),
+              sketch_apply="auto"):
         if orth_against not in ("p", "z"):
             raise ValueError(orth_against)
+        if sketch_apply not in N.SKETCH_APPLY:
+            raise ValueError(f"sketch_apply {sketch_apply!r}: one of {sorted(N.SKETCH_APPLY)}")
         return N.Opts(s, zeta, seed, window, maxit, float(noise_norm), float(eta), N.PRECOND[precond],
                       N.STOP_RULE[stop_rule], _ptr(diag_w), float(irw_eps), N.DTYPE[vec_dtype], 0,
                       _ptr(x_hist), _ptr(r_hist), 1 if orth_against == "z" else 0, _ptr(sk), _ptr(sk_stop),
-                      int(lowrank[0]), int(lowrank[1]), int(lowrank[2]), _ptr(lowrank[3]), int(lowrank[4]))
+                      int(lowrank[0]), int(lowrank[1]), int(lowrank[2]), _ptr(lowrank[3]), int(lowrank[4]),
+                      N.SKETCH_APPLY[sketch_apply])
 
     def _lowrank(self, precond, rank, oversample, power, omega, fp64=False):
         """(rank, oversample, power, Omega) of the low-rank operator, Omega as a
@@ -179,7 +183,8 @@ class Plan:
               driver: str = "graph", out: torch.Tensor | None = None, sync: bool = True,
               orth_against: str = "p", sketch_matrix: torch.Tensor | None = None,
               sketch_matrix_stop: torch.Tensor | None = None, lowrank_rank: int = 30, lowrank_oversample: int = 10,
-              lowrank_power: int = 1, lowrank_omega: torch.Tensor | None = None, lowrank_fp64: bool = False):
+              lowrank_power: int = 1, lowrank_omega: torch.Tensor | None = None, lowrank_fp64: bool = False,
+              sketch_apply: str = "auto"):
         """Run sFLSQR (method='sflsqr', Algorithm 1), sFLSMR ('sflsmr', Algorithm
         2) or the unsketched FLSQR ('flsqr', eq. (FLSQR); needs window < 0).
         window < 0: full orthogonalization (block CGS2 against every earlier
@@ -194,7 +199,10 @@ class Plan:
         truncation of p reshaped to the plan's image (lowrank_rank r,
         lowrank_oversample p, lowrank_power q subspace-iteration steps, and the
         Gaussian test matrix lowrank_omega, image_cols x (r + p); FP32
-        arithmetic, or FP64 with lowrank_fp64).
+        arithmetic, or FP64 with lowrank_fp64).  sketch_apply: 'fused' (the
+        sketch is added in the products' epilogues, S drawn from the hash),
+        'kernel' (a separate gather kernel over a table of S) or 'auto'
+        (fused for long operator rows; see sfl_opts.sketch_apply).
         Returns (x, info, hist) where hist holds the
         optional per-step iterates (maxit x n) and stop ratios.  With sync=False
         the call does not wait and info is None."""
@@ -210,7 +218,7 @@ class Plan:
         sks = self._dense_sketch(sketch_matrix_stop, s, self.m)
         lr = self._lowrank(precond, lowrank_rank, lowrank_oversample, lowrank_power, lowrank_omega, lowrank_fp64)
         o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
-                       xh, rh, orth_against, sk, sks, lr)
+                       xh, rh, orth_against, sk, sks, lr, sketch_apply)
         info = N.Info()
         pinfo = ctypes.byref(info) if sync else None
         with torch.cuda.device(dev):

@@ -31,11 +31,13 @@ struct SessionKey {
   int orth_z;        // 1: the z window is the stored z_j (sfl_opts.orth_against_z)
   const double *dense_S, *dense_Sm;   // explicit sketches (sfl_opts.sketch_dense, sketch_dense_stop)
   int lr_rank = 0, lr_over = 0, lr_power = 0, lr_fp64 = 0;   // low-rank truncation (SFL_PRECOND_LOWRANK)
+  int sk_apply = 0;  // sfl_opts.sketch_apply
   bool operator==(const SessionKey &o) const {
     return method == o.method && s == o.s && zeta == o.zeta && ell == o.ell && maxit == o.maxit &&
            precond == o.precond && stop_rule == o.stop_rule && vdt == o.vdt && x_hist == o.x_hist &&
            r_hist == o.r_hist && orth_z == o.orth_z && dense_S == o.dense_S && dense_Sm == o.dense_Sm &&
-           lr_rank == o.lr_rank && lr_over == o.lr_over && lr_power == o.lr_power && lr_fp64 == o.lr_fp64;
+           lr_rank == o.lr_rank && lr_over == o.lr_over && lr_power == o.lr_power && lr_fp64 == o.lr_fp64 &&
+           sk_apply == o.sk_apply;
   }
 };
 
@@ -64,8 +66,9 @@ struct Session {
   void *zcgs = nullptr, *wcgs = nullptr;   // orthogonalized product outputs (the raw ones stay for the sketch)
   double *sigWall = nullptr, *cgs_rec = nullptr, *cgs_coef = nullptr;
   int grid_cgs = 0;
-  // fused sparse-sign sketch (the products' epilogues draw and add; the small
-  // least-squares step reduces the per-CTA records): no per-step sketch launch
+  // fused sparse-sign sketch (the products' epilogues draw and add; the w
+  // update and the small least-squares step reduce the per-CTA records): no
+  // per-step sketch launch
   bool sk_fused = false;
   double *skw_rec = nullptr, *skz_rec = nullptr;   // [s][grid of the product]
   // low-rank truncation by the randomized SVD (SFL_PRECOND_LOWRANK)
@@ -158,7 +161,7 @@ int wait_stream(cudaStream_t s);
 
 // Row range of each of W warps, balanced by 4 * ceil(len / unit) + 1 per row,
 // plus 4 * ceil(len / slot) when slot > 0.
-int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s, int slot = 0);
+int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s, int slot = 0, int extra = 0);
 bool interleave_rows(const StoredCsr &M, int row_ctas);
 
 // Row-major sparse-sign table (rows of S with their entries column | sign bit).

@@ -10,6 +10,8 @@
 // Every reduction is fixed-order, so results are bitwise reproducible.
 #pragma once
 
+#include <climits>
+
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -335,63 +337,87 @@ __host__ __device__ inline size_t spmv_smem_bytes(int lpr, size_t acc_bytes) {
   return acc_bytes * kWarps * 32 * (lpr > 1 ? lpr : 1);
 }
 
-// Fused sparse-sign sketch of the product output (Section 2.7 draws, the
-// same generator as sketch_table_kernel): each output y[o] adds
-// +-y[o] to the zeta rows drawn for column o (scale 1/sqrt(zeta) and the
-// output's scale are applied by the consumer).  Each warp accumulates into
-// its own s-vector in shared memory (acc, kWarps x s doubles); lanes that hit
-// the same row at the same draw add in lane order (match_any groups, ranks),
-// so the sums have a fixed order.  The warps' vectors are then added in warp
-// order into this CTA's record rec[r * cap + blockIdx.x].  All threads call.
-template <typename XT, bool ORIG>
-__device__ __noinline__ void spmv_sketch(int s, int zeta, uint64_t seed, RowBlocks rb, const int32_t *orig,
-                                         const XT *y, double *acc_all, double *rec, int cap) {
+// Draws of sketch column c in registers: the generator of sketch_table_kernel
+// (same rows, same signs, same order); rows[q] = -1 past a draw-cap miss.
+template <int Z>
+__device__ __forceinline__ void sketch_column_draws(uint64_t seed, int64_t c, int s, int zeta, int (&rows)[Z],
+                                                    uint32_t &neg) {
+  int cnt = 0;
+  neg = 0;
+#pragma unroll
+  for (int q = 0; q < Z; ++q) rows[q] = -1;
+  for (uint32_t t = 0; cnt < zeta && t < 1000000u; ++t) {
+    const uint64_t h = splitmix64_first(seed ^ (((uint64_t)c << 32) + t));
+    const int r = (int)__umul64hi(h, (uint64_t)s);
+    bool dup = false;
+#pragma unroll
+    for (int q = 0; q < Z; ++q) dup |= (rows[q] == r);
+    if (dup) continue;
+#pragma unroll
+    for (int q = 0; q < Z; ++q)
+      if (q == cnt) rows[q] = r;
+    neg |= (uint32_t)(h & 1ull) << cnt;
+    ++cnt;
+  }
+}
+
+// round(v * 2^E) as a two's-complement integer, from the bit pattern (no
+// floating-point instruction); |v| * 2^E < 2^62 is the caller's guarantee.
+__device__ __forceinline__ long long to_fixed(double v, int E) {
+  const long long bits = __double_as_longlong(v);
+  const int ex = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long mant = (unsigned long long)(bits & 0xFFFFFFFFFFFFFll) | (ex ? (1ull << 52) : 0ull);
+  const int e2 = (ex ? ex : 1) - 1075 + E;   // v * 2^E = mant * 2^e2
+  unsigned long long mag;
+  if (e2 >= 0) mag = mant << min(e2, 9);
+  else if (e2 > -64) mag = (mant + (1ull << (-e2 - 1))) >> (-e2);   // half rounds up in magnitude
+  else mag = 0;
+  return bits < 0 ? -(long long)mag : (long long)mag;
+}
+
+// Fused sparse-sign sketch of the product output (Section 2.7 draws): this
+// CTA's record rec[r * cap + blockIdx.x] = sum over the CTA's outputs y[o] of
+// +-y[o] for the zeta rows r drawn for column o (the scale 1/sqrt(zeta) and
+// the output's scale are applied where the records are reduced).
+// The CTA's outputs are those of its rows [first, end) (through orig for
+// pixel-tiled rows), taken in 32-row blocks round-robin over the warps, so
+// the work is even whatever the warps' row counts.  The terms are fixed-point
+// integers round(+-y[o] * 2^E) and the sums exact, so their order does not
+// matter: shared-memory atomics into acc (s words, zeroed before the row loop),
+// bitwise reproducible.  E is the CTA's, from its sum of squares (wn: the
+// warps' totals of the lanes' nrm partials) and output count n: every entry
+// is at most sqrt(n) * ||y_CTA|| in magnitude and 2^E times that is below
+// 2^61.  One term's rounding is at most 2^-E / 2, about n * 2^-62 times the
+// outputs' rms.  All threads call, after a barrier that follows the rows and
+// the warps' writes of wn.
+template <typename XT, bool ORIG, int Z>
+__device__ __noinline__ void spmv_sketch(int s, int zeta, uint64_t seed, int64_t first, int64_t end,
+                                         const int32_t *orig, const XT *y, const double *wn,
+                                         unsigned long long *acc, double *rec, int cap) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double *acc = acc_all + (size_t)warp * s;
-  __syncthreads();   // the shared memory held the row loop's stash
-  for (int r = lane; r < s; r += 32) acc[r] = 0.0;
-  __syncwarp();
-  const unsigned lt = (1u << lane) - 1u;
-  for (int64_t row0 = rb.first; row0 < rb.end; row0 += rb.stride) {
-    const int64_t row = row0 + lane;
-    const bool valid = row < min(row0 + 32, rb.end);
-    int rows[kMaxZeta];
-    double v = 0.0;
-    uint32_t neg = 0;
-    if (valid) {
+  double ss = 0.0;
+  for (int w = 0; w < kWarps; ++w) ss += wn[w];
+  const double bound = sqrt((double)(end - first)) * sqrt(ss);
+  const bool live = bound > 0.0 && isfinite(bound);   // non-finite outputs stop the solve elsewhere
+  int E = 0;
+  if (live) {
+    int ex;
+    frexp(bound, &ex);   // bound < 2^ex
+    E = 61 - ex;
+    for (int64_t row = first + 32 * warp + lane; row < end; row += 32 * kWarps) {
       const int64_t o = ORIG ? orig[row] : row;
-      v = (double)y[o];
-      int cnt = 0;
-      for (uint32_t t = 0; cnt < zeta && t < 1000000u; ++t) {
-        const uint64_t h = splitmix64_first(seed ^ (((uint64_t)o << 32) + t));
-        const int r = (int)__umul64hi(h, (uint64_t)s);
-        bool dup = false;
-        for (int q = 0; q < cnt; ++q) dup |= (rows[q] == r);
-        if (dup) continue;
-        rows[cnt] = r;
-        neg |= (uint32_t)(h & 1ull) << cnt;
-        ++cnt;
-      }
-      for (int q = cnt; q < zeta; ++q) rows[q] = -1;   // never expected: the draw cap was hit
-    }
-    for (int q = 0; q < zeta; ++q) {
-      const int tg = valid ? rows[q] : -1;
-      const unsigned peers = __match_any_sync(0xffffffffu, tg);
-      const int rk = __popc(peers & lt);
-      const int mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)rk);
-      const double add = ((neg >> q) & 1u) ? -v : v;
-      for (int rr = 0; rr <= mx; ++rr) {
-        if (tg >= 0 && rk == rr) acc[tg] += add;
-        __syncwarp();
-      }
+      const long long f = to_fixed((double)y[o], E);
+      int rows[Z];
+      uint32_t neg;
+      sketch_column_draws<Z>(seed, o, s, zeta, rows, neg);
+#pragma unroll
+      for (int q = 0; q < Z; ++q)
+        if (q < zeta && rows[q] >= 0) atomicAdd(acc + rows[q], (unsigned long long)(((neg >> q) & 1u) ? -f : f));
     }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < s; r += kThreads) {
-    double a = 0.0;
-    for (int w = 0; w < kWarps; ++w) a += acc_all[(size_t)w * s + r];
-    rec[(size_t)r * cap + blockIdx.x] = a;
-  }
+  for (int r = threadIdx.x; r < s; r += kThreads)
+    rec[(size_t)r * cap + blockIdx.x] = live ? ldexp((double)(long long)acc[r], -E) : 0.0;
 }
 
 // Scalars booked by CTA 0 of a product (all its threads call): it stages the
@@ -510,7 +536,9 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
   __shared__ double tot[kPartStride];
   // a launch with too little shared memory does nothing (never writes out of bounds)
   if (dynamic_smem_bytes() < spmv_smem_bytes(LPR, sizeof(typename AccT<XT>::T))) return;
-  if (p.sk_s && dynamic_smem_bytes() < sizeof(double) * (size_t)kWarps * p.sk_s) return;
+  if (p.sk_s && dynamic_smem_bytes() < spmv_smem_bytes(LPR, sizeof(typename AccT<XT>::T)) +
+                                        sizeof(unsigned long long) * (size_t)p.sk_s)
+    return;
   griddep_wait();
   griddep_launch_dependents();
   int k = 0, lo = 1, nd = 0;
@@ -562,6 +590,11 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
   using ACC = typename AccT<XT>::T;
   const int warp = threadIdx.x >> 5;
   ACC *stash = reinterpret_cast<ACC *>(smem_raw) + warp * 32 * (LPR > 1 ? LPR : 1);
+  // fused sketch: the CTA's s-vector follows the stash
+  unsigned long long *sk_acc = reinterpret_cast<unsigned long long *>(
+      smem_raw + spmv_smem_bytes(LPR, sizeof(typename AccT<XT>::T)));
+  if (p.sk_s)
+    for (int r = threadIdx.x; r < p.sk_s; r += kThreads) sk_acc[r] = 0ull;
   // this warp's blocks: its own balanced range, or (tiled operators) every
   // kWarps-th block of the CTA's range, so the CTA's warps work on one tile
   const int gw = rcta * kWarps + warp;
@@ -583,6 +616,10 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
   else nrm = spmv_rows<VT, XT, LPR, MAT, ORIG>(p, rb, x, y, stash);
   if (!reduce) return;
   const int32_t *og = p.orig;
+  if (p.sk_s) {   // the warps' sums of squares for the sketch's scale (tot is CTA 0's scratch)
+    const double wn = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) tot[warp] = wn;
+  }
   if (!MAT) {     // vector pass: no window dots
     spmv_finish<XT, 0, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum);
     return;
@@ -599,8 +636,15 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
     case 8: spmv_finish<XT, 8, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
     default: spmv_finish<XT, 9, ORIG>(rb, og, y, win, wst, R, lo, nrm, outpart, wsum); break;
   }
-  if (p.sk_s) spmv_sketch<XT, ORIG>(p.sk_s, p.sk_zeta, __ldcg(&p.st->seed) + p.sk_seed_add, rb, og, y,
-                                   reinterpret_cast<double *>(smem_raw), p.sk_rec, p.sk_cap);
+  if (p.sk_s) {
+    __syncthreads();   // every row done: the outputs and the warps' norms are visible
+    const int64_t first = bound((int64_t)rcta * kWarps), last = bound((int64_t)(rcta + 1) * kWarps);
+    const uint64_t sd = __ldcg(&p.st->seed) + p.sk_seed_add;
+    if (p.sk_zeta <= 8)
+      spmv_sketch<XT, ORIG, 8>(p.sk_s, p.sk_zeta, sd, first, last, og, y, tot, sk_acc, p.sk_rec, p.sk_cap);
+    else
+      spmv_sketch<XT, ORIG, kMaxZeta>(p.sk_s, p.sk_zeta, sd, first, last, og, y, tot, sk_acc, p.sk_rec, p.sk_cap);
+  }
 }
 
 // Row cost for the warp partition of a product, in quarter iterations: the
@@ -610,14 +654,50 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
 // issue slot whatever the number of active lanes), plus one quarter for the
 // row's share of the per-row work.  Warps over short rows run more iterations
 // per stored entry than warps over long rows, so entries alone do not balance.
-static __global__ void row_cost_kernel(const int32_t *rowptr, int64_t rows, int unit, int slot, int64_t *cost) {
+// When cost_x is given it gets the cost plus `extra` quarters per row, the
+// price of the fused sketch's per-output work (CTA ranges are balanced on it).
+static __global__ void row_cost_kernel(const int32_t *rowptr, int64_t rows, int unit, int slot, int extra,
+                                       int64_t *cost, int64_t *cost_x) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i > rows) return;
-  if (i == rows) { cost[i] = 0; return; }
+  if (i == rows) {
+    cost[i] = 0;
+    if (cost_x) cost_x[i] = 0;
+    return;
+  }
   const int len = rowptr[i + 1] - rowptr[i];
   int64_t c = 4 * (int64_t)((len + unit - 1) / unit) + 1;
   if (slot > 0) c += 4 * (int64_t)((len + slot - 1) / slot);
   cost[i] = c;
+  if (cost_x) cost_x[i] = c + extra;
+}
+
+// First row in [lo, hi) whose prefix reaches target (hi when none does).
+__device__ __forceinline__ int64_t first_at_least(const int64_t *prefix, int64_t lo, int64_t hi, int64_t target) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (prefix[mid] < target) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Two-level row ranges for products whose CTAs also sketch their outputs:
+// CTA c's range [B_c, B_{c+1}) splits the cost with the sketch's price
+// (prefix_x) evenly over the nc CTAs, and the range's warps split its row-loop
+// cost (prefix) evenly, since the CTA's sketch work is spread over all its
+// warps.  wrow has nc * kWarps + 1 entries.
+static __global__ void balance_rows2_kernel(const int64_t *prefix, const int64_t *prefix_x, int64_t rows, int nc,
+                                            int32_t *wrow) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > nc) return;
+  if (c == nc) { wrow[(size_t)nc * kWarps] = (int32_t)rows; return; }
+  const int64_t tx = prefix_x[rows];
+  const int64_t b0 = first_at_least(prefix_x, 0, rows, (int64_t)(((__int128)tx * c) / nc));
+  const int64_t b1 = c + 1 == nc ? rows : first_at_least(prefix_x, 0, rows, (int64_t)(((__int128)tx * (c + 1)) / nc));
+  const int64_t p0 = prefix[b0], p1 = prefix[b1];
+  for (int j = 0; j < kWarps; ++j)
+    wrow[(size_t)c * kWarps + j] =
+        (int32_t)(j == 0 ? b0 : first_at_least(prefix, b0, b1, p0 + (int64_t)(((__int128)(p1 - p0) * j) / kWarps)));
 }
 
 // Row range of every warp: warp w starts at the first row whose cost prefix
@@ -748,6 +828,27 @@ __device__ __forceinline__ T dense_row_sum(const double *Srow, const VT *v, int6
   return warp_sum((a0 + a1) + (a2 + a3));
 }
 
+// This lane's parts of the sums of two rows of per-CTA sketch records
+// (ra, and rb when rb is given), records lane, lane + 32, ... of each: loads
+// in batches of 16 per row (one batch covers 512 records), all issued before
+// the batch is added in a fixed order.
+__device__ __forceinline__ void sum_records2(const double *ra, const double *rb, int cap, int lane, double &a,
+                                             double &b) {
+  a = 0.0;
+  b = 0.0;
+  for (int b0 = lane; b0 < cap; b0 += 16 * 32) {
+    double va[16], vb[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const bool in = b0 + 32 * j < cap;
+      va[j] = in ? __ldcg(ra + b0 + 32 * j) : 0.0;
+      vb[j] = in && rb ? __ldcg(rb + b0 + 32 * j) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) { a += va[j]; b += vb[j]; }
+  }
+}
+
 template <typename XT>
 __global__ void __launch_bounds__(kSkWarps * 32) sketch_rows_kernel(SketchParams<XT> p, int rows_total) {
   __shared__ double wpart[kSkWarps];
@@ -828,6 +929,13 @@ struct OrthParams {
   int want_h;               // H is recorded (sFLSMR, FLSQR)
   int full;                 // full orthogonalization: the block CGS2 kernels already orthogonalized raw
   XT *vfull;                // full: every new vector is also stored at column newj - 1
+  // w side, fused sketch: the A z_k product's per-CTA records (sk_cap per
+  // sketch row) -> column k of S A Z (sk_col, s entries), scaled by
+  // 1/sqrt(zeta) and the product output's scale
+  const double *sk_rec;
+  int sk_cap, sk_s;
+  double *sk_col_base;      // S A Z; column k - 1 starts at (k - 1) * sk_s
+  double sk_isz;
   Partials part;
 };
 
@@ -941,6 +1049,30 @@ __global__ void __launch_bounds__(kThreads) orth_update_kernel(OrthParams<XT> p)
   } else {
     // coefficients of w against w_lo..w_k (column k of H) from the A z_k product's dots
     lo = max(1, k - p.ell); nd = p.full ? 0 : k - lo + 1; newj = k + 1;
+    if (p.sk_rec) {
+      // the fused sketch of A z_k -> column k of S A Z, by the warps the
+      // reduction below leaves idle (all warps when none is): a warp per pair
+      // of sketch rows over the grid
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      const int w0 = 1 + nd < kWarps ? 1 + nd : 0, nsk = kWarps - w0;
+      if (warp >= w0) {
+        const int gw = blockIdx.x * nsk + (warp - w0), nw = gridDim.x * nsk;
+        double *col = p.sk_col_base + (size_t)(k - 1) * p.sk_s;
+        const double sc = p.sk_isz * rs;
+        for (int r = gw; r < p.sk_s; r += 2 * nw) {
+          const int r2 = r + nw;
+          double a, b;
+          sum_records2(p.sk_rec + (size_t)r * p.sk_cap, r2 < p.sk_s ? p.sk_rec + (size_t)r2 * p.sk_cap : nullptr,
+                       p.sk_cap, lane, a, b);
+          a = warp_sum(a);
+          b = warp_sum(b);
+          if (lane == 0) {
+            col[r] = a * sc;
+            if (r2 < p.sk_s) col[r2] = b * sc;
+          }
+        }
+      }
+    }
     reduce_partials(p.part.w, p.G_prev, 1 + nd, wsum, tot);
     if (threadIdx.x == 0) {
       scale_dots(1 + nd);
@@ -996,14 +1128,14 @@ struct LsParams {
   double *relres_hist;
   cudaGraphConditionalHandle cond;
   int use_cond;
-  // fused sketches (single solves): the products left per-CTA records of the
-  // unscaled sketches of A z_k (skw) and of A^T w_{k+1} / B w_{k+1} (skz);
-  // this step adds them (fixed order) into column k of S A Z and column k+1
-  // of S A^T W, scaled by 1/sqrt(zeta) and the outputs' scales
-  const double *skw_rec, *skz_rec;
-  int skw_cap, skz_cap;
+  // fused sketch (single sFLSMR solves): the A^T w_{k+1} / B w_{k+1} product
+  // left per-CTA records of its unscaled sketch; this step adds them (fixed
+  // order) into column k+1 of S A^T W, scaled by 1/sqrt(zeta) and the
+  // output's scale (the w update does the same for the A z_k product's)
+  const double *skz_rec;
+  int skz_cap;
   double sk_isz;
-  int RW, RP;
+  int RW;
   // several independent problems (one cluster each, problem = cluster index):
   // st is an array of states and every buffer above advances by its stride
   int64_t bQ, bRinv, by, be, bSAZ, bSAtW, bHband, bvec, bhist;   // per-problem strides (0: one problem)
@@ -1033,6 +1165,44 @@ __host__ __device__ inline size_t ls_smem_doubles(int s, int maxit, int cl, int 
 // reductions); partial vectors are exchanged through distributed shared
 // memory and every CTA adds the ranks' values as the same fixed tree, so all
 // CTAs hold bitwise identical totals and take the same branches.
+// Rows r0 .. r0 + nr - 1 of a sketched column from per-CTA records
+// (cap per row), times sc.  Warp w takes rows w, w + kWarps, ...; lanes go
+// over the records.  The loads of up to four rows (10 records per lane and
+// row per pass) are all issued before any is added, so a warp's rows cost
+// one L2 round trip for cap <= 320.  Each row adds its records in a fixed
+// order.  Not inlined, so its loads in flight do not weigh on the small
+// least-squares step's registers.
+static __device__ __noinline__ void ls_sketch_rows(const double *rec, int cap, int r0, int nr, double sc,
+                                                   double *col) {
+  constexpr int kRows = 4, kPer = 10;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = warp; i0 < nr; i0 += kRows * kWarps) {
+    double a[kRows];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) a[j] = 0.0;
+    for (int b0 = lane; b0 < cap; b0 += kPer * 32) {
+      double v[kRows][kPer];
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        const int i = i0 + j * kWarps;
+        const double *rc = rec + (size_t)(r0 + (i < nr ? i : 0)) * cap;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) v[j][t] = (i < nr && b0 + 32 * t < cap) ? __ldcg(rc + b0 + 32 * t) : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < kRows; ++j)
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) a[j] += v[j][t];
+    }
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+      const int i = i0 + j * kWarps;
+      const double t = warp_sum(a[j]);
+      if (lane == 0 && i < nr) col[r0 + i] = t * sc;
+    }
+  }
+}
+
 static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
@@ -1198,29 +1368,9 @@ static __global__ void __launch_bounds__(kThreads) ls_step_kernel(LsParams pin) 
   };
 
   // ---- 0. the new column and e, my rows; the staged blocks
-  if (p.skw_rec || p.skz_rec) {
-    // the fused sketches of this step's products, my rows: warp per row, lanes over the records
-    for (int i = warp; i < nr; i += kWarps) {
-      const int row = r0 + i;
-      if (p.skw_rec) {
-        const double *rc = p.skw_rec + (size_t)row * p.skw_cap;
-        double a0 = 0.0, a1 = 0.0;
-        int b = lane;
-        for (; b + 32 < p.skw_cap; b += 64) { a0 += __ldcg(rc + b); a1 += __ldcg(rc + b + 32); }
-        if (b < p.skw_cap) a0 += __ldcg(rc + b);
-        const double a = warp_sum(a0 + a1);
-        if (lane == 0) p.SAZ[(size_t)kk * s + row] = a * p.sk_isz * __ldcg(&st->sig_p[ring_slot(k, p.RP)]);
-      }
-      if (p.skz_rec && !lucky) {
-        const double *rc = p.skz_rec + (size_t)row * p.skz_cap;
-        double a0 = 0.0, a1 = 0.0;
-        int b = lane;
-        for (; b + 32 < p.skz_cap; b += 64) { a0 += __ldcg(rc + b); a1 += __ldcg(rc + b + 32); }
-        if (b < p.skz_cap) a0 += __ldcg(rc + b);
-        const double a = warp_sum(a0 + a1);
-        if (lane == 0) p.SAtW[(size_t)k * s + row] = a * p.sk_isz * __ldcg(&st->sig_w[ring_slot(k + 1, p.RW)]);
-      }
-    }
+  if (p.skz_rec && !lucky) {   // the fused sketch of this step's A^T w_{k+1} / B w_{k+1} product, my rows
+    ls_sketch_rows(p.skz_rec, p.skz_cap, r0, nr, p.sk_isz * __ldcg(&st->sig_w[ring_slot(k + 1, p.RW)]),
+                   p.SAtW + (size_t)k * s);
     __syncthreads();
   }
   for (int i = tid; i < nr; i += kThreads) {

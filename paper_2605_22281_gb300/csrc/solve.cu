@@ -53,9 +53,10 @@ static void destroy_session(Plan &pl, Session &se) {
   se.bytes = 0;
 }
 
-// Largest shared memory the fused sketch may add to a product (kWarps s-vectors
-// of doubles: s <= 1024).
-constexpr size_t kSketchFusedSmem = 64 * 1024;
+// Dynamic shared memory limit of the product kernels, set once for every
+// session: the stash (at most 64 KB) plus, with the fused sketch, an s-vector
+// of 64-bit integers.
+constexpr size_t kSpmvSmemLimit = 160 * 1024;
 
 // The Q block of a CTA is staged in shared memory when the whole plan stays
 // within this budget (it then serves the four Q products of a step).
@@ -153,9 +154,9 @@ bool interleave_rows(const StoredCsr &M, int row_ctas) {
 // Row range of each of W warps over the rows of M, balanced by row cost
 // (4 * ceil(len / unit) + 1 per row, exclusive scan, binary search per warp).
 // Temporaries are freed before returning; the stream is synchronised.
-int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s, int slot) {
+int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_t s, int slot, int extra) {
   const int64_t rows = M.rows;
-  int64_t *cost = nullptr, *prefix = nullptr;
+  int64_t *cost = nullptr, *prefix = nullptr, *cost_x = nullptr, *prefix_x = nullptr;
   void *tst = nullptr;
   size_t tb = 0;
   int r = SFL_OK;
@@ -163,23 +164,31 @@ int balance_rows(const StoredCsr &M, int unit, int W, int32_t *wrow, cudaStream_
     set_cuda_error(e, what);
     return SFL_ECUDA;
   };
+  const bool two = extra > 0 && W % kWarps == 0;   // CTA ranges priced with the sketch (see balance_rows2_kernel)
   cudaError_t e = cub::DeviceScan::ExclusiveSum(nullptr, tb, (int64_t *)nullptr, (int64_t *)nullptr, (int)(rows + 1), s);
   if (e == cudaSuccess) e = cudaMalloc(&cost, sizeof(int64_t) * (rows + 1));
   if (e == cudaSuccess) e = cudaMalloc(&prefix, sizeof(int64_t) * (rows + 1));
+  if (e == cudaSuccess && two) e = cudaMalloc(&cost_x, sizeof(int64_t) * (rows + 1));
+  if (e == cudaSuccess && two) e = cudaMalloc(&prefix_x, sizeof(int64_t) * (rows + 1));
   if (e == cudaSuccess) e = cudaMalloc(&tst, tb ? tb : 16);
   if (e == cudaSuccess) {
-    row_cost_kernel<<<(unsigned)((rows + 256) / 256), 256, 0, s>>>(M.rowptr, rows, unit, slot, cost);
+    row_cost_kernel<<<(unsigned)((rows + 256) / 256), 256, 0, s>>>(M.rowptr, rows, unit, slot, extra, cost, cost_x);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(tst, tb, cost, prefix, (int)(rows + 1), s);
+  if (e == cudaSuccess && two) e = cub::DeviceScan::ExclusiveSum(tst, tb, cost_x, prefix_x, (int)(rows + 1), s);
   if (e == cudaSuccess) {
-    balance_rows_kernel<<<(W + 256) / 256, 256, 0, s>>>(prefix, rows, W, wrow);
+    const int nc = W / kWarps;
+    if (two) balance_rows2_kernel<<<(nc + 256) / 256, 256, 0, s>>>(prefix, prefix_x, rows, nc, wrow);
+    else balance_rows_kernel<<<(W + 256) / 256, 256, 0, s>>>(prefix, rows, W, wrow);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { cudaGetLastError(); r = fail(e, "row balance"); }
   cudaFree(cost);
   cudaFree(prefix);
+  cudaFree(cost_x);
+  cudaFree(prefix_x);
   cudaFree(tst);
   return r;
 }
@@ -299,6 +308,10 @@ struct Engine {
       o.len = pl.A.rows; o.raw = (const XT *)se.wraw; o.ring = (XT *)se.wring; o.stride = pl.A.rows; o.R = se.RW;
       o.sigZ = se.sigZ;
     }
+    if (side == 1 && se.sk_fused && se.skw_rec) {   // the A z_k product's sketch records -> S A Z column k
+      o.sk_rec = se.skw_rec; o.sk_cap = se.grid_spmv_A; o.sk_s = se.key.s; o.sk_col_base = se.SAZ;
+      o.sk_isz = 1.0 / std::sqrt((double)se.key.zeta);
+    }
     if (se.full) {
       o.ell = 0;
       o.vfull = (XT *)(side == 0 ? se.Pfull : se.Wfull);
@@ -319,11 +332,10 @@ struct Engine {
     q.SAZ = se.SAZ; q.SAtW = se.SAtW; q.Hband = se.Hband; q.sbm = se.sbm; q.rhs = se.rhs;
     q.relres_hist = se.key.r_hist;
     q.cond = h; q.use_cond = use_cond;
-    if (se.sk_fused) {
-      q.skw_rec = se.skw_rec; q.skz_rec = se.skz_rec;
-      q.skw_cap = se.grid_spmv_A; q.skz_cap = se.grid_spmv_T;
+    if (se.sk_fused && se.skz_rec) {
+      q.skz_rec = se.skz_rec; q.skz_cap = se.grid_spmv_T;
       q.sk_isz = 1.0 / std::sqrt((double)se.key.zeta);
-      q.RW = se.RW; q.RP = se.RP;
+      q.RW = se.RW;
     }
     return q;
   }
@@ -633,22 +645,46 @@ struct Engine {
     if (key.precond == SFL_PRECOND_DIAG) SA(se->dw, sizeof(double) * n);
     SA(se->err, sizeof(int));
     // launch shapes
-    se->smem_A = spmv_smem_bytes(pl.A.lpr, sizeof(ACC));
-    se->smem_T = spmv_smem_bytes(pl.T.lpr, sizeof(ACC));
-    // fused sketch: the products' epilogues need kWarps s-vectors of shared
-    // memory (the row loop's stash is reused); explicit sketches and FLSQR keep
-    // the separate sketch kernel (or none)
-    const size_t sk_smem = sizeof(double) * (size_t)kWarps * S;
-    se->sk_fused = !key.dense_S && key.method != kFLSQR && sk_smem <= kSketchFusedSmem;
-    const bool skw = se->sk_fused && (key.method == kSFLSQR || key.stop_rule == SFL_STOP_RULE_RESIDUAL);
-    const bool skz = se->sk_fused && key.method == kSFLSMR;
-    if (skw) se->smem_A = std::max(se->smem_A, sk_smem);
-    if (skz) se->smem_T = std::max(se->smem_T, sk_smem);
+    const size_t stashA = spmv_smem_bytes(pl.A.lpr, sizeof(ACC)), stashT = spmv_smem_bytes(pl.T.lpr, sizeof(ACC));
+    se->smem_A = stashA;
+    se->smem_T = stashT;
     se->smem_init = spmv_smem_bytes(1, sizeof(ACC));
     // one limit per kernel for every session (room for the fused sketch), so no session lowers another's
-    SFL_CU(O::set_smem(pl.A.lpr, true, std::max(se->smem_A, kSketchFusedSmem)));
-    SFL_CU(O::set_smem(pl.T.lpr, true, std::max(se->smem_T, kSketchFusedSmem)));
+    SFL_CU(O::set_smem(pl.A.lpr, true, kSpmvSmemLimit));
+    SFL_CU(O::set_smem(pl.T.lpr, true, kSpmvSmemLimit));
     SFL_CU(O::set_smem(1, false, se->smem_init));
+    // fused sketch: a product that sketches its output keeps an s-vector of
+    // 64-bit integers after its stash; fused only where that costs the
+    // product no resident CTA (otherwise the separate sketch kernel runs).
+    // Explicit sketches and FLSQR keep the separate kernel (or none).
+    {
+      const size_t sk_smem = sizeof(unsigned long long) * (size_t)S;
+      auto occ_of = [&](int lpr, size_t smem) {
+        return pl.matfree ? O::proj_occupancy(smem) : O::spmv_occupancy(lpr, true, smem);
+      };
+      auto fits = [&](int lpr, size_t stash) {
+        return stash + sk_smem <= kSpmvSmemLimit && occ_of(lpr, stash + sk_smem) >= occ_of(lpr, stash);
+      };
+      const bool want_w = key.method == kSFLSQR || key.stop_rule == SFL_STOP_RULE_RESIDUAL;
+      const bool want_z = key.method == kSFLSMR;
+      // AUTO: fused where the sketched products' rows are long (measured on
+      // this GPU: 1.7 % faster per solve at 1024^2, 921 entries per ray; 9 %
+      // slower at 256^2, 230 per ray and 360 per pixel, where the epilogue's
+      // per-output draws and the record reduction outweigh the launch saved)
+      auto long_rows = [&](const StoredCsr &M) {
+        if (pl.matfree) return pl.ct_N >= 512;
+        return M.rows > 0 && M.nnz >= 512 * M.rows;
+      };
+      const bool pick = key.sk_apply == SFL_SKETCH_APPLY_FUSED ||
+                        (key.sk_apply == SFL_SKETCH_APPLY_AUTO && (!want_w || long_rows(pl.A)) &&
+                         (!want_z || long_rows(pl.T)));
+      se->sk_fused = pick && !key.dense_S && key.method != kFLSQR && (!want_w || fits(pl.A.lpr, stashA)) &&
+                     (!want_z || fits(pl.T.lpr, stashT));
+      if (se->sk_fused && want_w) se->smem_A += sk_smem;
+      if (se->sk_fused && want_z) se->smem_T += sk_smem;
+    }
+    const bool skw = se->sk_fused && (key.method == kSFLSQR || key.stop_rule == SFL_STOP_RULE_RESIDUAL);
+    const bool skz = se->sk_fused && key.method == kSFLSMR;
     auto grid_of = [&](int lpr, bool mat, size_t smem) {
       int occ = (mat && pl.matfree) ? O::proj_occupancy(smem) : O::spmv_occupancy(lpr, mat, smem);
       if (occ < 1) occ = 1;
@@ -688,9 +724,12 @@ struct Engine {
                     : pl.vdt == SFL_F32 ? SpmvTune<float>::NCH : SpmvTune<double>::NCH;
     // FP64 products are bound by FMA issue: their rows also pay for chunk slots
     const bool fp64 = pl.vdt == SFL_F64;
+    // a product with the fused sketch prices its per-output draws (about a
+    // load iteration per row for zeta = 8 in FP64, a quarter of that in FP32)
+    const int sk_extra = std::max(1, fp64 ? key.zeta / 2 : key.zeta / 8);
     if (!pl.matfree &&   // matrix-free products split their rows evenly
-        ((r = balance_rows(pl.A, nch * pl.A.lpr * P, WA, se->wrowA, s, fp64 ? pl.A.lpr * P : 0)) ||
-         (r = balance_rows(pl.T, nch * pl.T.lpr * P, WT, se->wrowT, s, fp64 ? pl.T.lpr * P : 0)))) {
+        ((r = balance_rows(pl.A, nch * pl.A.lpr * P, WA, se->wrowA, s, fp64 ? pl.A.lpr * P : 0, skw ? sk_extra : 0)) ||
+         (r = balance_rows(pl.T, nch * pl.T.lpr * P, WT, se->wrowT, s, fp64 ? pl.T.lpr * P : 0, skz ? sk_extra : 0)))) {
       destroy_session(pl, *se);
       return r;
     }
@@ -833,6 +872,7 @@ static int check_opts(const Plan &pl, int method, const sfl_opts *o) {
   if (o->vec_dtype == SFL_F32 && pl.vdt == SFL_F64) return SFL_EUNSUPPORTED;
   if (o->vec_dtype != SFL_F64 && o->vec_dtype != SFL_F32) return SFL_EINVAL;
   if (o->orth_against_z != 0 && o->orth_against_z != 1) return SFL_EINVAL;
+  if (o->sketch_apply < SFL_SKETCH_APPLY_AUTO || o->sketch_apply > SFL_SKETCH_APPLY_KERNEL) return SFL_EINVAL;
   return SFL_OK;
 }
 
@@ -857,6 +897,7 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
     key.lr_power = o->lowrank_power;
     key.lr_fp64 = o->lowrank_fp64 ? 1 : 0;
   }
+  key.sk_apply = o->sketch_apply;
   Session *se = nullptr;
   for (auto &p : pl.sessions)
     if (p->key == key) { se = p.get(); break; }
@@ -939,7 +980,7 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
     p.proj = which == 0 ? kProjRay : (pl.ct_back ? kProjBackLinear : kProjBackChord);
   }
   const size_t smem = spmv_smem_bytes(M.lpr, sizeof(typename AccT<XT>::T));
-  SFL_CU(Ops<VT, XT>::set_smem(M.lpr, true, std::max(smem, kSketchFusedSmem)));
+  SFL_CU(Ops<VT, XT>::set_smem(M.lpr, true, kSpmvSmemLimit));
   if (std::is_same<XT, double>::value) {
     p.x = (const XT *)x; p.y = (XT *)y;
     SFL_CU(Ops<VT, XT>::spmv(p, M.lpr, true, grid, smem, s));

@@ -228,14 +228,18 @@ def assert_iterates_conditioned(r, x_gpu_hist, relres_gpu, info, tol_stop, min_c
     return checked
 
 
-def test_sflsqr_ct64_per_iteration(ct64):
+SKETCH_APPLY = ["kernel", "fused"]
+
+
+@pytest.mark.parametrize("sketch_apply", SKETCH_APPLY)
+def test_sflsqr_ct64_per_iteration(ct64, sketch_apply):
     p, plan = ct64
     st = p.settings
     tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
     r = run_oracle_sflsqr(p.A.scipy(), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
     x, info, h = plan.solve("sflsqr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
                             maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], x_history=True,
-                            relres_history=True)
+                            relres_history=True, sketch_apply=sketch_apply)
     assert info.status == O.STOP_DISCREPANCY == r.status
     assert_iterates_flat(r, h["x"], h["relres"], info, tol)
     assert rel(x.cpu().numpy(), r.x) <= RTOL_ITER
@@ -243,20 +247,22 @@ def test_sflsqr_ct64_per_iteration(ct64):
 
 
 @pytest.mark.parametrize("ell", [0, 1, 2, 5, 8])
-def test_sflsqr_fixed_iterations_windows(ct64, ell):
+@pytest.mark.parametrize("sketch_apply", SKETCH_APPLY)
+def test_sflsqr_fixed_iterations_windows(ct64, ell, sketch_apply):
     """No stop rule, past the discrepancy point, while the small problem stays
     determined (its condition number grows to ~1e10 by the last step)."""
     p, plan = ct64
     maxit = 12 if ell == 0 else 25
     r = run_oracle_sflsqr(p.A.scipy(), p.b, 101, 8, 42, maxit, 0.0, ell)
     x, info, h = plan.solve("sflsqr", dev(p.b), s=101, zeta=8, seed=42, window=ell, maxit=maxit, x_history=True,
-                            relres_history=True)
+                            relres_history=True, sketch_apply=sketch_apply)
     assert r.iters == maxit and info.status in (O.STOP_MAXIT, O.STOP_BREAKDOWN)
     assert_iterates_conditioned(r, h["x"], h["relres"], info, 0.0)
 
 
 @pytest.mark.parametrize("precond", ["diag", "reweight"])
-def test_sflsqr_flexible_operators(ct64, precond):
+@pytest.mark.parametrize("sketch_apply", SKETCH_APPLY)
+def test_sflsqr_flexible_operators(ct64, precond, sketch_apply):
     p, plan = ct64
     n = p.A.shape[1]
     w = np.random.default_rng(47).uniform(0.5, 1.5, n)
@@ -264,25 +270,28 @@ def test_sflsqr_flexible_operators(ct64, precond):
     r = run_oracle_sflsqr(p.A.scipy(), p.b, 61, 8, 46, 20, 0.0, 2, tau=tau)
     x, info, h = plan.solve("sflsqr", dev(p.b), s=61, zeta=8, seed=46, window=2, maxit=20, precond=precond,
                             diag_w=dev(w) if precond == "diag" else None, irw_eps=1e-4, x_history=True,
-                            relres_history=True)
+                            relres_history=True, sketch_apply=sketch_apply)
     assert_iterates_conditioned(r, h["x"], h["relres"], info, 0.0)
 
 
-def test_sflsmr_unmatched_reweighted_per_iteration(ct64_unmatched):
+@pytest.mark.parametrize("sketch_apply", SKETCH_APPLY)
+def test_sflsmr_unmatched_reweighted_per_iteration(ct64_unmatched, sketch_apply):
     A, B, x_true, b, en, plan = ct64_unmatched
     tol = O.discrepancy_tol(1.01, en, np.linalg.norm(b))
     r = run_oracle_sflsmr(A.scipy(), b, 201, 8, 43, 150, tol, 2, tau=O.Reweighting(1e-4), AT=B.scipy())
     x, info, h = plan.solve("sflsmr", dev(b), s=201, zeta=8, seed=43, window=2, maxit=150, noise_norm=en, eta=1.01,
-                            precond="reweight", irw_eps=1e-4, x_history=True, relres_history=True)
+                            precond="reweight", irw_eps=1e-4, x_history=True, relres_history=True,
+                            sketch_apply=sketch_apply)
     assert info.status == r.status
     assert_iterates_conditioned(r, h["x"], h["relres"], info, tol)
 
 
-def test_sflsmr_normal_equation_stop_rule(ct64):
+@pytest.mark.parametrize("sketch_apply", SKETCH_APPLY)
+def test_sflsmr_normal_equation_stop_rule(ct64, sketch_apply):
     p, plan = ct64
     r = run_oracle_sflsmr(p.A.scipy(), p.b, 81, 4, 5, 25, 0.0, 2, stop_rule="normal")
     x, info, h = plan.solve("sflsmr", dev(p.b), s=81, zeta=4, seed=5, window=2, maxit=25, stop_rule="normal",
-                            x_history=True, relres_history=True)
+                            x_history=True, relres_history=True, sketch_apply=sketch_apply)
     assert_iterates_conditioned(r, h["x"], h["relres"], info, 0.0)
 
 
@@ -579,14 +588,40 @@ def test_image_shape_must_match_the_columns(ct64):
 
 # ---------------------------------------------------------------- determinism and drivers
 
-def test_bitwise_reproducible_and_drivers_agree(ct64_unmatched):
+@pytest.mark.parametrize("sketch_apply", SKETCH_APPLY)
+def test_bitwise_reproducible_and_drivers_agree(ct64_unmatched, sketch_apply):
     A, B, x_true, b, en, plan = ct64_unmatched
-    kw = dict(s=201, zeta=8, seed=43, window=2, maxit=60, noise_norm=en, eta=1.01, precond="reweight")
+    kw = dict(s=201, zeta=8, seed=43, window=2, maxit=60, noise_norm=en, eta=1.01, precond="reweight",
+              sketch_apply=sketch_apply)
     x1, i1, _ = plan.solve("sflsmr", dev(b), **kw)
     x2, i2, _ = plan.solve("sflsmr", dev(b), **kw)
     x3, i3, _ = plan.solve("sflsmr", dev(b), driver="host_loop", **kw)
     assert torch.equal(x1, x2) and torch.equal(x1, x3)
     assert i1.iters == i2.iters == i3.iters
+
+
+def test_sketch_apply_modes_launch_what_they_say(ct64, ct64_unmatched):
+    """'fused' runs no sketch kernel in the loop, 'kernel' one per step; on
+    these short rows (under 512 entries per output) 'auto' is 'kernel'.  The
+    two modes agree to rounding (fixed-point against FP64 sums)."""
+    p, plan = ct64
+    st = p.settings
+    kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
+              noise_norm=p.noise_norm[0], eta=st["eta"], driver="profiled")
+    runs = {m: plan.solve("sflsqr", dev(p.b), sketch_apply=m, **kw) for m in ("auto", "fused", "kernel")}
+    step = {m: h["kernel_launches"]["sketch"] for m, (_, _, h) in runs.items()}
+    assert step["fused"] == 0 and step["kernel"] == runs["kernel"][1].iters and step["auto"] == step["kernel"]
+    assert runs["fused"][1].iters == runs["kernel"][1].iters
+    xf, xk = runs["fused"][0].cpu().numpy(), runs["kernel"][0].cpu().numpy()
+    assert rel(xf, xk) <= RTOL_ITER
+    A, B, x_true, b, en, planu = ct64_unmatched
+    kw = dict(s=201, zeta=8, seed=43, window=2, maxit=60, noise_norm=en, eta=1.01, precond="reweight",
+              driver="profiled")
+    _, i_f, h_f = planu.solve("sflsmr", dev(b), sketch_apply="fused", **kw)
+    _, i_k, h_k = planu.solve("sflsmr", dev(b), sketch_apply="kernel", **kw)
+    assert h_f["kernel_launches"]["sketch"] == 0 and h_k["kernel_launches"]["sketch"] == i_k.iters
+    with pytest.raises(ValueError):
+        plan.solve("sflsqr", dev(p.b), s=st["s"], sketch_apply="sometimes")
 
 
 def test_host_buffers_entry_point(ct64):
@@ -738,6 +773,25 @@ def recipe1024_at_256():
     phantom, s = 600, window 4, maxit 300) on a 256x256 image: 360 x 363 rays,
     m = 130,680, n = 65,536, 30M nonzeros."""
     return wl.make("ct1024_sflsqr", N=256, n_angles=360)
+
+
+@pytest.mark.slow
+def test_recipe_1024_fp64_fused_sketch_every_step(recipe1024_at_256):
+    """The 1024x1024 recipe (s = 600, zeta = 8, window 4) at 256x256 in FP64
+    with the sketch fused into the forward product's epilogue, in the
+    benchmark's plan layout: the stop step, and every iterate and stop ratio
+    within relative 1e-10 of the oracle's."""
+    p = recipe1024_at_256
+    st = p.settings
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    plan = G.Plan(p.A, image_shape=(p.N, p.N))
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                            maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], x_history=True,
+                            relres_history=True, sketch_apply="fused")
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
+    assert info.status == r.status == O.STOP_DISCREPANCY
+    assert_iterates_flat(r, h["x"], h["relres"], info, tol)
+    plan.close()
 
 
 @pytest.mark.parametrize("vdt,bar_same_op,bar_fp64", [("f32", 1e-4, 1e-4), ("bf16", 1e-4, 2e-2)])
