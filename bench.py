@@ -316,6 +316,11 @@ def batched_variant(args, G, wl, np, torch):
     iters = [i.iters for i in infos]
     tiles = G.batched_tiles(plan32)
     plan32.close()
+    # algorithmic bytes of the batch: the matrix twice per batched step, the active right-hand sides' vectors
+    m, n = p.A.shape
+    alg = sum(2 * int(p.A.nnz) * 8 + sum(1 for i in iters if i >= k) * 9 * (m + n) * 4
+              for k in range(1, max(iters) + 1))
+    pk = load_peaks()
     # plain FP64 path, one solve per right-hand side, on a sample of columns
     plan64 = G.Plan(p.A, value_dtype="f64", image_shape=img(args, p))
     sample = list(range(0, R, 16))
@@ -342,6 +347,11 @@ def batched_variant(args, G, wl, np, torch):
             "nnz": int(p.A.nnz), "values": "f32", "vectors": "f32", "small_problems": "f64",
             "iters_min_median_max": [min(iters), int(statistics.median(iters)), max(iters)],
             "rel_error_median": statistics.median(err32), "spmm_tiles": {"A": tiles[0], "At": tiles[1]},
+            "roofline": {"bound": "hbm", "achieved": alg / (t_batch / 1000) / 1e9, "peak": pk["hbm_gbs"],
+                         "unit": "GB/s", "frac": alg / (t_batch / 1000) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                         "algorithmic_bytes_per_batch": alg, "peak_source": pk["source"],
+                         "scope": "whole batched solve: 2 nnz (V + I) per batched step + 9 (m + n) X per active RHS; "
+                                  "the SpMMs are bound by L2 gathers (nnz x 64 RHS x 4 B per product), not HBM"},
             "first_call_s_incl_session_and_tuning": t_first,
             "plain_fp64": {"solves_per_s": fp64_solves, "sample_columns": sample, "rel_errors": err64,
                            "equal_error_columns": f"{eq}/{len(sample)} within 1% (relative) of the FP64 error"},
