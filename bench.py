@@ -71,6 +71,11 @@ def parse_args():
                     help="graph: one CUDA graph per solve (the measured configuration); host_loop: the same "
                          "kernels launched one by one from the host, for profilers that cannot see inside "
                          "graphs with conditional nodes (skips the end-to-end leg)")
+    ap.add_argument("--sketch-apply", default="auto", choices=["auto", "fused", "kernel"],
+                    help="how the main workload's solver applies the sparse-sign sketch (auto: the library's choice)")
+    ap.add_argument("--image", type=int, default=0,
+                    help="profiling only: build the main workload at this image size (same angles and recipe); "
+                         "the line's config.workload then carries the size")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -647,7 +652,8 @@ def single_leg(args, G, wl, np, torch, p, vdt: str, *, steps: int, warmup: int, 
     method = st["method"]
     precond = {"identity": "identity", "irw": "reweight", "diag": "diag"}[st["precond"]]
     kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"], maxit=st["maxit"],
-              noise_norm=float(p.noise_norm[0]), eta=st["eta"], precond=precond, irw_eps=st.get("irw_eps", 1e-4))
+              noise_norm=float(p.noise_norm[0]), eta=st["eta"], precond=precond, irw_eps=st.get("irw_eps", 1e-4),
+              sketch_apply=getattr(args, "sketch_apply", "auto"))
     barrier = barrier or (lambda: None)
     t_plan = time.perf_counter()
     plan = G.Plan(p.A, p.B, value_dtype=vdt, image_shape=img(args, p), slot_layout=args.slot_layout)
@@ -774,10 +780,11 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    p = rank_problem(wl.make(args.workload), rank, wl, np)
+    p = rank_problem(wl.make(args.workload, **({"N": args.image} if args.image else {})), rank, wl, np)
     st = p.settings
     leg = single_leg(args, G, wl, np, torch, p, "f64", steps=args.steps, warmup=args.warmup, world=world,
-                     barrier=barrier, sampler=ClockSampler(local), e2e=True, workload=args.workload)
+                     barrier=barrier, sampler=ClockSampler(local), e2e=True,
+                     workload=args.workload if not args.image else f"{args.workload}@{args.image}")
     iters = leg["iters"]
     method = leg["method"]
     t_max_ms, total_iters, value = aggregate(gather_rank_values([leg["t_ms"], iters], world, "cuda"), args.steps)
@@ -829,7 +836,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "method": method, "image": f"{p.N}x{p.N}",
+                "config": {"workload": args.workload + (f" at {p.N}x{p.N} (profiling size)" if args.image else ""),
+                           "method": method, "image": f"{p.N}x{p.N}",
                            "angles": p.n_angles, "bins": p.n_bins, "m": m, "n": n, "nnz_A": stats["nnz_A"],
                            "nnz_B_or_At": stats["nnz_At"], "s": st["s"], "zeta": st["zeta"], "window": st["window"],
                            "maxit": st["maxit"], "precond": leg["precond"], "iters_to_stop": iters,

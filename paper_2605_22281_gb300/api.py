@@ -245,7 +245,8 @@ class Plan:
     def solve_host(self, method: str, b: np.ndarray, *, s: int, zeta: int = 8, seed: int = 0, window: int = 2,
                    maxit: int = 100, noise_norm: float = 0.0, eta: float = 1.01, precond: str = "identity",
                    stop_rule: str = "residual", diag_w: torch.Tensor | None = None, irw_eps: float = 1e-4,
-                   vec_dtype: str | None = None, x_out: np.ndarray | None = None, orth_against: str = "p"):
+                   vec_dtype: str | None = None, x_out: np.ndarray | None = None, orth_against: str = "p",
+                   sketch_apply: str = "auto"):
         """Same solve with host FP64 b and x (copies inside the call)."""
         if vec_dtype is None:
             vec_dtype = "f64" if self.value_dtype == "f64" else "f32"
@@ -253,7 +254,7 @@ class Plan:
         x = x_out if x_out is not None else np.empty(self.n, dtype=np.float64)
         dw = diag_w.to(device=self.device, dtype=torch.float64).contiguous() if diag_w is not None else None
         o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
-                       None, None, orth_against)
+                       None, None, orth_against, sketch_apply=sketch_apply)
         info = N.Info()
         fn = (self.lib.sflsqr_solve_host, self.lib.sflsmr_solve_host, self.lib.flsqr_solve_host)[METHODS[method]]
         with torch.cuda.device(self.device):
