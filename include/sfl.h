@@ -416,7 +416,13 @@ int sfl_batched_tile(const sfl_plan *plan, int32_t which);
  * Arguments as sflsqr_solve_batched without the noise levels.  The plan keeps
  * the whole forward state (every basis vector, A z_j, the coefficients and the
  * small QR) for sflsqr_adjoint_batched until its next batched call with other
- * sizes, or another fixed-k call. */
+ * sizes, or another fixed-k call.  The forward state lives in the plan, not
+ * in a state object of the caller's: one plan holds one differentiable
+ * forward at a time, so two forwards whose adjoints are both still needed
+ * take two plans (on the same operator).  The window is capped at 3 here
+ * (the adjoint's combination kernels hold the window's vectors in registers)
+ * and at 8 for the solves; wider windows are full orthogonalization
+ * (window < 0) in the single solves. */
 int sflsqr_fixed_batched(sfl_plan *plan, int32_t nrhs, const double *B, const sfl_opts *opts, double *X,
                          sfl_info *infos, sfl_stream stream);
 
