@@ -198,13 +198,15 @@ static int validate_csr(const sfl_csr *M, cudaStream_t s) {
   return SFL_OK;
 }
 
-// Lanes per row: 8, or 16 when the average row still gives every lane at
-// least twelve P-wide loads at 16 lanes.  Measured on CT operators of 230 to
-// 920 entries per row in FP64, FP32 and BF16: 32 lanes per row were the
-// slowest everywhere, 8 the fastest or within 2 % of it.
+// Lanes per row: 8, or 16 only for rows long enough to give every lane of 16
+// at least 48 P-wide loads (no CT operator here comes near).  Measured on the
+// 1024^2 operator (921 entries per ray): 8 lanes ran A z in 1138 us against
+// 1392 us at 16 in FP64, 782 against 854 us in FP32, 675 against 760 us in
+// BF16; on operators of 230 to 460 entries per row 8 was the fastest too, and
+// 32 the slowest everywhere.
 static int choose_lpr(int64_t pnnz, int64_t rows, int P) {
   const double avg = rows > 0 ? (double)pnnz / (double)rows : 0.0;
-  return avg >= 12.0 * P * 16 ? 16 : 8;
+  return avg >= 48.0 * P * 16 ? 16 : 8;
 }
 
 // Row order of 16 x 16 pixel tiles (tiles and the pixels inside one in
