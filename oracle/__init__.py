@@ -16,7 +16,8 @@ Modules:
   adjoint - fixed-k sFLSQR with tau = diag(d) in plain PyTorch CPU FP64 ops,
             differentiated by autograd (imported on demand: `oracle.adjoint`).
 """
-from .sketch import (DenseSketch, IdentitySketch, SparseSign, draw_hash, gaussian, sparse_sign_column,
+from .sketch import (SRHT, DenseSketch, GaussianHash, IdentitySketch, SparseSign, draw_hash, gaussian,
+                     gaussian_hash_dense, sparse_sign_column, srht_dense, srht_rows, srht_signs,
                      sparse_sign_rows, splitmix64_stream)
 from .sfl import (STOP_BREAKDOWN, STOP_DISCREPANCY, STOP_MAXIT, FixedDiag, Identity, Reweighting,
                   discrepancy_tol, householder_lstsq, sflsmr, sflsqr, sketches_for)

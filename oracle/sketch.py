@@ -16,6 +16,27 @@ each implement the same published generator independently:
   * candidate row r = floor(h * s / 2^64); accepted if not yet chosen for
     column c; sign = +1 if bit 0 of h is 0, else -1; value = sign / sqrt(zeta).
     Draws continue until column c has `zeta` distinct rows.
+
+Two generated dense sketches (s x len, entries regenerated from the seed, never
+stored by the solver; readings of the transform and Gaussian sketches that
+Section 2.7 names):
+
+  * SRHT, a subsampled randomized Hadamard transform
+    S = sqrt(M/s) R (H_M / sqrt(M)) D, M = 2^b the smallest power of two >= len
+    (v padded with zeros), H_M the Sylvester-Hadamard matrix
+    (H[i, j] = (-1)^popcount(i & j)), D = diag(d_c) random signs, R the s rows
+    rho(0), ..., rho(s-1) of a seeded bijection of [0, M): entries
+    S[r, c] = (-1)^(popcount(rho(r) & c) + d_c) / sqrt(s).
+    With k = h(seed ^ TAG_SRHT, 0, 0) (the SplitMix64 hash above): x0 = low 32
+    bits of k, K = (high 32 bits of k) | 1, h = max(1, b // 2), mask = M - 1;
+    rho(r) = f(f((r ^ x0) & mask)) followed by x ^= x >> h, where
+    f(x) = ((x ^ (x >> h)) * K) mod 2^32 & mask (xor-shift and odd multiplier:
+    bijections of [0, M)).  d_c = bit 63 of the SplitMix64 output of state
+    (seed ^ TAG_SIGN) ^ c.
+  * Gaussian: S[r, c] = g / sqrt(s) with g = sqrt(-2 ln u1) cos(2 pi u2)
+    (Box-Muller), u1 = (hi53(h1) + 1) 2^-53, u2 = hi53(h2) 2^-53, h1 and h2 the
+    SplitMix64 outputs of states (seed ^ TAG_GAUSS) ^ (2 key) and ^ (2 key + 1),
+    key = r * len + c, hi53 the top 53 bits.
 """
 from __future__ import annotations
 
@@ -25,6 +46,9 @@ import numpy as np
 import scipy.sparse as sp
 
 MASK64 = (1 << 64) - 1
+TAG_SRHT = 0x5352485400000000
+TAG_SIGN = 0x5352485400000001
+TAG_GAUSS = 0x4741555353000000
 GOLDEN_GAMMA = 0x9E3779B97F4A7C15
 MIX1 = 0xBF58476D1CE4E5B9
 MIX2 = 0x94D049BB133111EB
@@ -175,3 +199,93 @@ class IdentitySketch(Sketch):
 def gaussian(rng: np.random.Generator, s: int, length: int) -> DenseSketch:
     """Gaussian sketch with independent N(0,1) entries (unscaled, as in Corollary 1)."""
     return DenseSketch(rng.standard_normal((s, length)))
+
+
+# ---------------------------------------------------------------- generated dense sketches
+
+def _mix_vec(state: np.ndarray) -> np.ndarray:
+    """First SplitMix64 output of every uint64 state (numpy wraps mod 2^64)."""
+    with np.errstate(over="ignore"):
+        z = state + np.uint64(GOLDEN_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(MIX1)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(MIX2)
+        return z ^ (z >> np.uint64(31))
+
+
+def _popcount32(x: np.ndarray) -> np.ndarray:
+    """Bits set in every uint32 entry (SWAR, no library popcount)."""
+    x = x.astype(np.uint32)
+    x = x - ((x >> np.uint32(1)) & np.uint32(0x55555555))
+    x = (x & np.uint32(0x33333333)) + ((x >> np.uint32(2)) & np.uint32(0x33333333))
+    x = (x + (x >> np.uint32(4))) & np.uint32(0x0F0F0F0F)
+    with np.errstate(over="ignore"):
+        return ((x * np.uint32(0x01010101)) >> np.uint32(24)).astype(np.int64)
+
+
+def srht_order(length: int) -> int:
+    """b with M = 2^b the smallest power of two >= length."""
+    b = 0
+    while (1 << b) < length:
+        b += 1
+    return b
+
+
+def srht_rows(seed: int, s: int, length: int) -> np.ndarray:
+    """rho(0), ..., rho(s-1): the sampled rows of H_M (distinct; s <= M)."""
+    b = srht_order(length)
+    M = 1 << b
+    if not (1 <= s <= M):
+        raise ValueError("need 1 <= s <= M")
+    k = splitmix64_mix((seed ^ TAG_SRHT) + GOLDEN_GAMMA)
+    x0, K = k & 0xFFFFFFFF, ((k >> 32) | 1) & 0xFFFFFFFF
+    h, mask = max(1, b // 2), M - 1
+    out = np.empty(s, dtype=np.int64)
+    for r in range(s):
+        x = (r ^ x0) & mask
+        for _ in range(2):
+            x ^= x >> h
+            x = ((x * K) & 0xFFFFFFFF) & mask
+        x ^= x >> h
+        out[r] = x
+    return out
+
+
+def srht_signs(seed: int, length: int) -> np.ndarray:
+    """d_c in {0, 1} (the sign is (-1)^d_c) for c < length."""
+    st = np.uint64((seed ^ TAG_SIGN) & MASK64) ^ np.arange(length, dtype=np.uint64)
+    return (_mix_vec(st) >> np.uint64(63)).astype(np.int64)
+
+
+def srht_dense(seed: int, s: int, length: int) -> np.ndarray:
+    """The s x length SRHT sketch (entries +-1/sqrt(s))."""
+    rho = srht_rows(seed, s, length).astype(np.uint32)
+    c = np.arange(length, dtype=np.uint32)
+    par = (_popcount32(rho[:, None] & c[None, :]) + srht_signs(seed, length)[None, :]) & 1
+    return (1.0 - 2.0 * par) / math.sqrt(s)
+
+
+def gaussian_hash_dense(seed: int, s: int, length: int) -> np.ndarray:
+    """The s x length Gaussian sketch drawn from the hash (entries N(0, 1/s))."""
+    key = (np.arange(s, dtype=np.uint64)[:, None] * np.uint64(length) + np.arange(length, dtype=np.uint64)[None, :])
+    base = np.uint64((seed ^ TAG_GAUSS) & MASK64)
+    with np.errstate(over="ignore"):
+        h1 = _mix_vec(base ^ (key * np.uint64(2)))
+        h2 = _mix_vec(base ^ (key * np.uint64(2) + np.uint64(1)))
+    u1 = ((h1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = (h2 >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    g = np.sqrt(-2.0 * np.log(u1)) * np.cos(6.283185307179586 * u2)
+    return g / math.sqrt(s)
+
+
+class SRHT(DenseSketch):
+    """Subsampled randomized Hadamard transform drawn from the seed (dense here; the GPU regenerates it)."""
+
+    def __init__(self, seed: int, s: int, length: int):
+        super().__init__(srht_dense(seed, s, length))
+
+
+class GaussianHash(DenseSketch):
+    """Gaussian sketch drawn from the seed by Box-Muller (dense here; the GPU regenerates it)."""
+
+    def __init__(self, seed: int, s: int, length: int):
+        super().__init__(gaussian_hash_dense(seed, s, length))
