@@ -62,6 +62,7 @@ typedef enum {
 } sfl_precond;
 typedef enum { SFL_STOP_RULE_RESIDUAL = 0, SFL_STOP_RULE_NORMAL = 1 } sfl_stop_rule;
 typedef enum { SFL_SKETCH_APPLY_AUTO = 0, SFL_SKETCH_APPLY_FUSED = 1, SFL_SKETCH_APPLY_KERNEL = 2 } sfl_sketch_apply_mode;
+typedef enum { SFL_SKETCH_SPARSE_SIGN = 0, SFL_SKETCH_SRHT = 1, SFL_SKETCH_GAUSSIAN = 2 } sfl_sketch_kind;
 
 /* A CSR matrix.  rowptr has rows+1 entries with rowptr[0] = 0, nondecreasing,
  * rowptr[rows] = nnz < 2^31; colidx[i] in [0, cols).  values has nnz entries of
@@ -211,6 +212,22 @@ typedef struct {
    * CTA's output norm), KERNEL in FP64.  Explicit sketches and FLSQR always
    * take KERNEL (or no sketch). */
   int32_t sketch_apply;
+  /* The sketch drawn from the seed (single solves; sfl_sketch_kind), beside
+   * the sparse-sign default.  Both generated kinds are s x len matrices whose
+   * entries every application regenerates from (seed, row, column), with
+   * E[S^T S] = I; the two kinds Section 2.7 names next to CountSketch:
+   *  SRHT: a subsampled randomized Hadamard transform,
+   *    S[r, c] = (-1)^(popcount(rho(r) & c) + d_c) / sqrt(s), rho(0..s-1)
+   *    distinct rows of the Sylvester-Hadamard matrix of order M = 2^b >= len
+   *    (a seeded bijection of [0, M)), d_c hashed sign bits; needs s <= M;
+   *  GAUSSIAN: N(0, 1/s) entries by Box-Muller from two hash outputs of the
+   *    counter r * len + c (costly: a logarithm and a cosine per entry and
+   *    application; meant for studies at small sizes).
+   * zeta is ignored; the m-side stop sketch of sFLSMR uses seed + 1.  The
+   * definitions are restated in the oracle (oracle/sketch.py), which the
+   * tests compare against.  Not with sketch_dense or FLSQR; always applied by
+   * the separate sketch kernel. */
+  int32_t sketch_kind;
 } sfl_opts;
 
 /* Result of a solve.  Filled when the call returns (the call then waits for

@@ -18,6 +18,7 @@ STOP_RUNNING, STOP_DISCREPANCY, STOP_MAXIT, STOP_BREAKDOWN = 0, 1, 2, 3
 PRECOND = {"identity": 0, "diag": 1, "reweight": 2, "lowrank": 3}
 STOP_RULE = {"residual": 0, "normal": 1}
 SKETCH_APPLY = {"auto": 0, "fused": 1, "kernel": 2}
+SKETCH_KIND = {"sparse_sign": 0, "srht": 1, "gaussian": 2}
 DTYPE = {"f64": SFL_F64, "f32": SFL_F32, "bf16": SFL_BF16}
 
 
@@ -42,7 +43,7 @@ class Opts(ctypes.Structure):
                 ("sketch_dense_stop", ctypes.c_void_p), ("lowrank_rank", ctypes.c_int32),
                 ("lowrank_oversample", ctypes.c_int32), ("lowrank_power", ctypes.c_int32),
                 ("lowrank_omega", ctypes.c_void_p), ("lowrank_fp64", ctypes.c_int32),
-                ("sketch_apply", ctypes.c_int32)]
+                ("sketch_apply", ctypes.c_int32), ("sketch_kind", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

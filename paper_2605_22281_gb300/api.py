@@ -145,16 +145,18 @@ class Plan:
 
     def _opts(self, s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, diag_w, irw_eps,
               vec_dtype, x_hist, r_hist, orth_against="p", sk=None, sk_stop=None, lowrank=(0, 0, 0, None, 0),
-              sketch_apply="auto"):
+              sketch_apply="auto", sketch_kind="sparse_sign"):
         if orth_against not in ("p", "z"):
             raise ValueError(orth_against)
         if sketch_apply not in N.SKETCH_APPLY:
             raise ValueError(f"sketch_apply {sketch_apply!r}: one of {sorted(N.SKETCH_APPLY)}")
+        if sketch_kind not in N.SKETCH_KIND:
+            raise ValueError(f"sketch_kind {sketch_kind!r}: one of {sorted(N.SKETCH_KIND)}")
         return N.Opts(s, zeta, seed, window, maxit, float(noise_norm), float(eta), N.PRECOND[precond],
                       N.STOP_RULE[stop_rule], _ptr(diag_w), float(irw_eps), N.DTYPE[vec_dtype], 0,
                       _ptr(x_hist), _ptr(r_hist), 1 if orth_against == "z" else 0, _ptr(sk), _ptr(sk_stop),
                       int(lowrank[0]), int(lowrank[1]), int(lowrank[2]), _ptr(lowrank[3]), int(lowrank[4]),
-                      N.SKETCH_APPLY[sketch_apply])
+                      N.SKETCH_APPLY[sketch_apply], N.SKETCH_KIND[sketch_kind])
 
     def _lowrank(self, precond, rank, oversample, power, omega, fp64=False):
         """(rank, oversample, power, Omega) of the low-rank operator, Omega as a
@@ -184,7 +186,7 @@ class Plan:
               orth_against: str = "p", sketch_matrix: torch.Tensor | None = None,
               sketch_matrix_stop: torch.Tensor | None = None, lowrank_rank: int = 30, lowrank_oversample: int = 10,
               lowrank_power: int = 1, lowrank_omega: torch.Tensor | None = None, lowrank_fp64: bool = False,
-              sketch_apply: str = "auto"):
+              sketch_apply: str = "auto", sketch_kind: str = "sparse_sign"):
         """Run sFLSQR (method='sflsqr', Algorithm 1), sFLSMR ('sflsmr', Algorithm
         2) or the unsketched FLSQR ('flsqr', eq. (FLSQR); needs window < 0).
         window < 0: full orthogonalization (block CGS2 against every earlier
@@ -202,7 +204,10 @@ class Plan:
         arithmetic, or FP64 with lowrank_fp64).  sketch_apply: 'fused' (the
         sketch is added in the products' epilogues, S drawn from the hash),
         'kernel' (a separate gather kernel over a table of S) or 'auto'
-        (fused for long operator rows; see sfl_opts.sketch_apply).
+        (fused for long operator rows; see sfl_opts.sketch_apply).  sketch_kind:
+        'sparse_sign' (default), 'srht' (subsampled randomized Hadamard
+        transform) or 'gaussian' (N(0, 1/s) entries), all regenerated from
+        the seed (see sfl_opts.sketch_kind).
         Returns (x, info, hist) where hist holds the
         optional per-step iterates (maxit x n) and stop ratios.  With sync=False
         the call does not wait and info is None."""
@@ -218,7 +223,7 @@ class Plan:
         sks = self._dense_sketch(sketch_matrix_stop, s, self.m)
         lr = self._lowrank(precond, lowrank_rank, lowrank_oversample, lowrank_power, lowrank_omega, lowrank_fp64)
         o = self._opts(s, zeta, seed, window, maxit, noise_norm, eta, precond, stop_rule, dw, irw_eps, vec_dtype,
-                       xh, rh, orth_against, sk, sks, lr, sketch_apply)
+                       xh, rh, orth_against, sk, sks, lr, sketch_apply, sketch_kind)
         info = N.Info()
         pinfo = ctypes.byref(info) if sync else None
         with torch.cuda.device(dev):

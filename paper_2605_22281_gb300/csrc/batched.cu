@@ -651,6 +651,7 @@ struct AEngine {
 static int check_batched(const Plan &pl, int R, const sfl_opts *o) {
   if (!o || R < 1 || R > kBMaxRhs) return SFL_EINVAL;
   if (pl.matfree) return SFL_EUNSUPPORTED;   // the SpMMs read a stored matrix
+  if (o->sketch_kind != SFL_SKETCH_SPARSE_SIGN) return SFL_EUNSUPPORTED;   // batched sketches are sparse-sign
   if (o->maxit < 1 || o->maxit > kMaxIt) return SFL_EINVAL;
   if (o->zeta < 1 || o->zeta > kMaxZeta) return SFL_EINVAL;
   if (o->s < o->maxit + 1 || o->s < o->zeta || o->s > kMaxS) return SFL_EINVAL;

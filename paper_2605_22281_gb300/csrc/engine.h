@@ -32,12 +32,13 @@ struct SessionKey {
   const double *dense_S, *dense_Sm;   // explicit sketches (sfl_opts.sketch_dense, sketch_dense_stop)
   int lr_rank = 0, lr_over = 0, lr_power = 0, lr_fp64 = 0;   // low-rank truncation (SFL_PRECOND_LOWRANK)
   int sk_apply = 0;  // sfl_opts.sketch_apply
+  int sk_kind = 0;   // sfl_opts.sketch_kind
   bool operator==(const SessionKey &o) const {
     return method == o.method && s == o.s && zeta == o.zeta && ell == o.ell && maxit == o.maxit &&
            precond == o.precond && stop_rule == o.stop_rule && vdt == o.vdt && x_hist == o.x_hist &&
            r_hist == o.r_hist && orth_z == o.orth_z && dense_S == o.dense_S && dense_Sm == o.dense_Sm &&
            lr_rank == o.lr_rank && lr_over == o.lr_over && lr_power == o.lr_power && lr_fp64 == o.lr_fp64 &&
-           sk_apply == o.sk_apply;
+           sk_apply == o.sk_apply && sk_kind == o.sk_kind;
   }
 };
 

@@ -773,6 +773,9 @@ struct SketchParams {
   const int32_t *rowN; const uint32_t *entN;   // n-side table (S_n)
   const double *dM, *dN;                       // explicit sketches (row-major s x m, s x n) instead of the tables
   int64_t lenM, lenN;
+  int gen;                                     // generated sketch (sfl_sketch_kind SRHT or GAUSSIAN), 0: none
+  int bitsM, bitsN;                            // SRHT: log2 of the padded lengths
+  int gen_m_add;                               // the m-side sketch's seed is the solve's seed plus this
   double *SAZ, *SAtW, *rhs, *e, *sbm, *sk_out;
 };
 
@@ -828,6 +831,67 @@ __device__ __forceinline__ T dense_row_sum(const double *Srow, const VT *v, int6
   return warp_sum((a0 + a1) + (a2 + a3));
 }
 
+// Generated sketches (sfl_opts.sketch_kind): every application regenerates
+// the entries from the seed; nothing is stored.
+//   SRHT: S[r, c] = (-1)^(popcount(rho(r) & c) + d_c) / sqrt(s), the sampled
+//   rows rho(r) of the Sylvester-Hadamard matrix of order M = 2^b >= len
+//   given by a seeded bijection of [0, M) (xor-shifts and an odd multiplier),
+//   d_c a sign bit of the hash;
+//   GAUSSIAN: S[r, c] = sqrt(-2 ln u1) cos(2 pi u2) / sqrt(s), u1 and u2 the
+//   top 53 bits of two hash outputs of the counter r * len + c (Box-Muller).
+// The factor 1/sqrt(s) is applied by the caller.
+constexpr uint64_t kTagSrht = 0x5352485400000000ull, kTagSign = 0x5352485400000001ull,
+                   kTagGauss = 0x4741555353000000ull;
+
+__device__ __forceinline__ uint32_t srht_row(uint64_t seed, uint32_t r, int b) {
+  const uint64_t k = splitmix64_first(seed ^ kTagSrht);
+  const uint32_t mask = (uint32_t)((1ull << b) - 1ull), K = (uint32_t)(k >> 32) | 1u;
+  const int h = max(1, b / 2);
+  uint32_t x = (r ^ (uint32_t)k) & mask;
+  for (int i = 0; i < 2; ++i) {
+    x ^= x >> h;
+    x = (x * K) & mask;
+  }
+  return x ^ (x >> h);
+}
+
+__device__ __forceinline__ double gaussian_entry(uint64_t seed, uint64_t key) {
+  const uint64_t base = seed ^ kTagGauss;
+  const uint64_t h1 = splitmix64_first(base ^ (2ull * key)), h2 = splitmix64_first(base ^ (2ull * key + 1ull));
+  const double u1 = ((double)(h1 >> 11) + 1.0) * 0x1p-53, u2 = (double)(h2 >> 11) * 0x1p-53;
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+// Row r of a generated sketch (without the 1/sqrt(s)) times v: threads
+// strided over the columns, two accumulators, then a warp butterfly.
+template <typename T, typename VT>
+__device__ __forceinline__ T gen_row_sum(int kind, uint64_t seed, int r, int b, const VT *v, int64_t len) {
+  T a0 = 0, a1 = 0;
+  constexpr int B = kSkWarps * 32;
+  if (kind == SFL_SKETCH_SRHT) {
+    const uint32_t rho = srht_row(seed, (uint32_t)r, b);
+    const uint64_t sg = seed ^ kTagSign;
+    int64_t c = threadIdx.x;
+    for (; c + B < len; c += 2 * B) {
+      const uint32_t p0 = (__popc(rho & (uint32_t)c) + (uint32_t)(splitmix64_first(sg ^ (uint64_t)c) >> 63)) & 1u;
+      const uint32_t p1 =
+          (__popc(rho & (uint32_t)(c + B)) + (uint32_t)(splitmix64_first(sg ^ (uint64_t)(c + B)) >> 63)) & 1u;
+      const T x0 = (T)v[c], x1 = (T)v[c + B];
+      a0 += p0 ? -x0 : x0;
+      a1 += p1 ? -x1 : x1;
+    }
+    for (; c < len; c += B) {
+      const uint32_t p0 = (__popc(rho & (uint32_t)c) + (uint32_t)(splitmix64_first(sg ^ (uint64_t)c) >> 63)) & 1u;
+      const T x0 = (T)v[c];
+      a0 += p0 ? -x0 : x0;
+    }
+  } else {
+    const uint64_t row0 = (uint64_t)r * (uint64_t)len;
+    for (int64_t c = threadIdx.x; c < len; c += B) a0 += (T)gaussian_entry(seed, row0 + (uint64_t)c) * (T)v[c];
+  }
+  return warp_sum(a0 + a1);
+}
+
 // This lane's parts of the sums of two rows of per-CTA sketch records
 // (ra, and rb when rb is given), records lane, lane + 32, ... of each: loads
 // in batches of 16 per row (one batch covers 512 records), all issued before
@@ -876,7 +940,13 @@ __global__ void __launch_bounds__(kSkWarps * 32) sketch_rows_kernel(SketchParams
   const uint32_t *ent = nside ? p.entN : p.entM;
   double t;
   const double *dmat = nside ? p.dN : p.dM;
-  if (dmat) {
+  if (p.gen) {
+    const int64_t len = nside ? p.lenN : p.lenM;
+    const uint64_t seed = __ldcg(&p.st->seed) + (nside ? 0 : p.gen_m_add);
+    const int b = nside ? p.bitsN : p.bitsM;
+    if (p.mode == kSkInitB) t = gen_row_sum<double>(p.gen, seed, r, b, p.v64, len);
+    else t = (double)gen_row_sum<typename AccT<XT>::T>(p.gen, seed, r, b, nside ? p.zraw : p.wraw, len);
+  } else if (dmat) {
     const int64_t len = nside ? p.lenN : p.lenM;
     const double *Srow = dmat + (size_t)r * len;
     if (p.mode == kSkInitB) t = dense_row_sum<double>(Srow, p.v64, len);

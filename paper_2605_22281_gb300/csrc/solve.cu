@@ -58,6 +58,13 @@ static void destroy_session(Plan &pl, Session &se) {
 // of 64-bit integers.
 constexpr size_t kSpmvSmemLimit = 160 * 1024;
 
+// Smallest b with 2^b >= n (n >= 1).
+static int log2_ceil(int64_t n) {
+  int b = 0;
+  while (((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
 // The Q block of a CTA is staged in shared memory when the whole plan stays
 // within this budget (it then serves the four Q products of a step).
 constexpr size_t kLsStageBudget = 160 * 1024;
@@ -280,6 +287,13 @@ struct Engine {
       q.dM = se.key.method == kSFLSQR ? se.key.dense_S : se.key.dense_Sm;
       q.dN = se.key.method == kSFLSMR ? se.key.dense_S : nullptr;
       q.lenM = se.m; q.lenN = se.n;
+    }
+    if (se.key.sk_kind != SFL_SKETCH_SPARSE_SIGN) {   // regenerated from the seed in every application
+      q.gen = se.key.sk_kind;
+      q.isz = 1.0 / std::sqrt((double)se.key.s);
+      q.lenM = se.m; q.lenN = se.n;
+      q.bitsM = log2_ceil(se.m); q.bitsN = log2_ceil(se.n);
+      q.gen_m_add = se.key.method == kSFLSMR ? 1 : 0;
     }
     q.st = se.st;
     q.v64 = se.bbuf;
@@ -678,7 +692,8 @@ struct Engine {
       const bool pick = key.sk_apply == SFL_SKETCH_APPLY_FUSED ||
                         (key.sk_apply == SFL_SKETCH_APPLY_AUTO && (!want_w || long_rows(pl.A)) &&
                          (!want_z || long_rows(pl.T)));
-      se->sk_fused = pick && !key.dense_S && key.method != kFLSQR && (!want_w || fits(pl.A.lpr, stashA)) &&
+      se->sk_fused = pick && !key.dense_S && key.method != kFLSQR && key.sk_kind == SFL_SKETCH_SPARSE_SIGN &&
+                     (!want_w || fits(pl.A.lpr, stashA)) &&
                      (!want_z || fits(pl.T.lpr, stashT));
       if (se->sk_fused && want_w) se->smem_A += sk_smem;
       if (se->sk_fused && want_z) se->smem_T += sk_smem;
@@ -748,7 +763,8 @@ struct Engine {
 
   // Row-major sketch tables for `seed` (kept until the seed changes).
   static int ensure_tables(const Plan &pl, Session &se, uint64_t seed, cudaStream_t s) {
-    if (se.key.dense_S || se.key.method == kFLSQR) return SFL_OK;      // explicit sketch or none: no draws
+    if (se.key.dense_S || se.key.method == kFLSQR || se.key.sk_kind != SFL_SKETCH_SPARSE_SIGN)
+      return SFL_OK;   // explicit, generated or no sketch: no table
     if (se.tab_valid && se.tab_seed == seed) return SFL_OK;
     SketchTableTmp t;
     t.kin = se.sk_kin; t.vin = se.sk_vin; t.kout = se.sk_kout; t.cub = se.sk_cub; t.cub_bytes = se.sk_cub_bytes;
@@ -873,6 +889,14 @@ static int check_opts(const Plan &pl, int method, const sfl_opts *o) {
   if (o->vec_dtype != SFL_F64 && o->vec_dtype != SFL_F32) return SFL_EINVAL;
   if (o->orth_against_z != 0 && o->orth_against_z != 1) return SFL_EINVAL;
   if (o->sketch_apply < SFL_SKETCH_APPLY_AUTO || o->sketch_apply > SFL_SKETCH_APPLY_KERNEL) return SFL_EINVAL;
+  if (o->sketch_kind < SFL_SKETCH_SPARSE_SIGN || o->sketch_kind > SFL_SKETCH_GAUSSIAN) return SFL_EINVAL;
+  if (o->sketch_kind != SFL_SKETCH_SPARSE_SIGN) {
+    if (dense || method == kFLSQR) return SFL_EINVAL;
+    if (o->sketch_kind == SFL_SKETCH_SRHT) {   // s distinct rows of the Hadamard matrix of each sketched side
+      const int64_t len = method == kSFLSQR ? pl.A.rows : std::min(pl.A.rows, pl.A.cols);
+      if ((int64_t)o->s > ((int64_t)1 << log2_ceil(len))) return SFL_EINVAL;
+    }
+  }
   return SFL_OK;
 }
 
@@ -898,6 +922,8 @@ static int solve_typed(Plan &pl, const SolveRequest &q) {
     key.lr_fp64 = o->lowrank_fp64 ? 1 : 0;
   }
   key.sk_apply = o->sketch_apply;
+  key.sk_kind = q.method == kFLSQR ? 0 : o->sketch_kind;
+  if (key.sk_kind) key.zeta = 1;   // the sparse-sign draws are not used
   Session *se = nullptr;
   for (auto &p : pl.sessions)
     if (p->key == key) { se = p.get(); break; }

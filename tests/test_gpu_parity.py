@@ -439,6 +439,64 @@ def test_gaussian_sketch_matches_oracle(ct64, method):
     assert_iterates_conditioned(r, h["x"], h["relres"], info, 0.0)
 
 
+# ---------------------------------------------------------------- generated sketches (SRHT, hash-drawn Gaussian)
+
+GEN_SKETCH = {"srht": O.SRHT, "gaussian": O.GaussianHash}
+
+
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+def test_generated_sketch_sflsqr_matches_oracle(ct64, kind):
+    """sFLSQR with a sketch the kernel regenerates from the seed in every
+    application (no stored S): the stop step and every iterate within the
+    flat 1e-10 of the oracle given the same matrix (built by its own
+    restatement of the generator); two runs bitwise equal."""
+    p, plan = ct64
+    st = p.settings
+    A = p.A.scipy()
+    S = GEN_SKETCH[kind](st["seed"], st["s"], A.shape[0])
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    r = O.sflsqr(A, p.b, S, maxit=st["maxit"], tol=tol, ell=st["window"], record_x=True, keep_basis=True)
+    r.M = S.S @ (A @ r.Z)
+    kw = dict(s=st["s"], seed=st["seed"], window=st["window"], maxit=st["maxit"], noise_norm=p.noise_norm[0],
+              eta=st["eta"], sketch_kind=kind)
+    x, info, h = plan.solve("sflsqr", dev(p.b), x_history=True, relres_history=True, **kw)
+    assert info.status == r.status == O.STOP_DISCREPANCY
+    assert_iterates_flat(r, h["x"], h["relres"], info, tol)
+    x2, info2, _ = plan.solve("sflsqr", dev(p.b), **kw)
+    assert torch.equal(x, x2) and info2.iters == info.iters
+
+
+@pytest.mark.parametrize("kind", ["srht", "gaussian"])
+def test_generated_sketch_sflsmr_unmatched_matches_oracle(ct64_unmatched, kind):
+    """sFLSMR with B and reweighting, both sketches generated (S_n from the
+    seed, the stop sketch S_m from seed + 1), against the oracle."""
+    A, B, x_true, b, en, plan = ct64_unmatched
+    As, Bs = A.scipy(), B.scipy()
+    m, n = As.shape
+    Sn, Sm = GEN_SKETCH[kind](43, 201, n), GEN_SKETCH[kind](44, 201, m)
+    tol = O.discrepancy_tol(1.01, en, np.linalg.norm(b))
+    r = O.sflsmr(As, b, Sn, S_stop=Sm, maxit=150, tol=tol, ell=2, tau=O.Reweighting(1e-4), AT=Bs, record_x=True,
+                 keep_basis=True)
+    r.M = Sn.S @ (Bs @ (As @ r.Z))
+    x, info, h = plan.solve("sflsmr", dev(b), s=201, seed=43, window=2, maxit=150, noise_norm=en, eta=1.01,
+                            precond="reweight", irw_eps=1e-4, x_history=True, relres_history=True, sketch_kind=kind)
+    assert info.status == r.status
+    assert_iterates_conditioned(r, h["x"], h["relres"], info, tol)
+
+
+def test_generated_sketch_argument_checks(ct64):
+    p, plan = ct64
+    m = p.A.shape[0]
+    M = 1 << (m - 1).bit_length()
+    with pytest.raises(G.N.SflError):   # more rows than the Hadamard matrix has
+        plan.solve("sflsqr", dev(p.b), s=M + 1, maxit=20, sketch_kind="srht")
+    S = torch.zeros((61, m), dtype=torch.float64, device="cuda")
+    with pytest.raises(G.N.SflError):   # not with an explicit sketch
+        plan.solve("sflsqr", dev(p.b), s=61, maxit=20, sketch_matrix=S, sketch_kind="gaussian")
+    with pytest.raises(ValueError):
+        plan.solve("sflsqr", dev(p.b), s=61, maxit=20, sketch_kind="fourier")
+
+
 @pytest.fixture(scope="module")
 def decay105():
     """The residual-size study's problem at rho = 1.05: dense 1024 x 512, 10% noise."""
