@@ -616,7 +616,8 @@ def decay_variant(args, G, wl, np, torch):
     sketch matrices, identity operator, window 8), against the optimal residual of
     the same Krylov space (LSQR: SciPy's lsqr, 20 iterations, on the host).  Per rho:
     LSQR's ||A x - b|| / ||b|| and the sketched residuals relative to it, averaged
-    over 5 sketches."""
+    over 5 sketches; again with the Gaussian and SRHT sketches the kernel
+    regenerates from the seed ("generated")."""
     import scipy.sparse.linalg as spla
     k, s, m, n, draws = 20, 41, 1024, 512, 5
     Sm = torch.empty((s, m), dtype=torch.float64, device="cuda")
@@ -637,9 +638,20 @@ def decay_variant(args, G, wl, np, torch):
             xm, _, _ = plan.solve("sflsmr", bd, s=s, window=8, maxit=k, sketch_matrix=Sn, sketch_matrix_stop=Sm)
             rq.append(float(np.linalg.norm(A @ xq.cpu().numpy() - b)) / r_opt)
             rm.append(float(np.linalg.norm(A @ xm.cpu().numpy() - b)) / r_opt)
+        # the same with sketches the kernel regenerates from the seed (no matrices)
+        gen = {}
+        for kind in ("gaussian", "srht"):
+            gq, gm = [], []
+            for t in range(draws):
+                xq, _, _ = plan.solve("sflsqr", bd, s=s, seed=500 + t, window=8, maxit=k, sketch_kind=kind)
+                xm, _, _ = plan.solve("sflsmr", bd, s=s, seed=500 + t, window=8, maxit=k, sketch_kind=kind)
+                gq.append(float(np.linalg.norm(A @ xq.cpu().numpy() - b)) / r_opt)
+                gm.append(float(np.linalg.norm(A @ xm.cpu().numpy() - b)) / r_opt)
+            gen[kind] = {"slsqr_over_lsqr": statistics.mean(gq), "slsmr_over_lsqr": statistics.mean(gm)}
         plan.close()
         out["rho"][f"{rho:.2f}"] = {"lsqr_rel_residual": r_opt / float(np.linalg.norm(b)),
-                                    "slsqr_over_lsqr": statistics.mean(rq), "slsmr_over_lsqr": statistics.mean(rm)}
+                                    "slsqr_over_lsqr": statistics.mean(rq), "slsmr_over_lsqr": statistics.mean(rm),
+                                    "generated": gen}
     return out
 
 
