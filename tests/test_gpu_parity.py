@@ -771,6 +771,31 @@ def test_ct256_unmatched_full_size_matches_oracle():
     assert rel(x2.cpu().numpy(), r.x) <= RTOL_ITER
 
 
+@pytest.mark.slow
+def test_ct1024_fp64_full_size_matches_oracle():
+    """The 1024x1024 FP64 workload the benchmark times (480.6M entries, s =
+    600, zeta = 8, window 4), in its launch configuration (pixel-tiled A^T,
+    lane-interleaved slots, 8 lanes per row, the sketch fused into the
+    forward product): the stop step, and x_k and the stop ratio of every
+    step up to the stop within relative 1e-10 of the oracle's."""
+    p = wl.make("ct1024_sflsqr")
+    st = p.settings
+    plan = G.Plan(p.A, image_shape=(p.N, p.N))
+    assert plan.stats()["lanes_A"] == 8
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                            maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], x_history=True,
+                            relres_history=True, driver="profiled")
+    assert h["kernel_launches"]["sketch"] == 0   # fused: no sketch kernel in the loop
+    xh, rh = h["x"][: info.iters].clone(), h["relres"].clone()
+    del h
+    plan.close()
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
+    assert info.status == r.status == O.STOP_DISCREPANCY
+    assert_iterates_flat(r, xh, rh, info, tol)
+    assert rel(x.cpu().numpy(), r.x) <= RTOL_ITER
+
+
 # ---------------------------------------------------------------- reduced precision: solves
 
 def rounded(S, vdt):
