@@ -28,8 +28,13 @@ enum : int { kProjRay = 0, kProjBackChord = 1, kProjBackLinear = 2 };
 // 2: |cos| < 1e-15, the rays are y = const).
 constexpr int kProjTab = 7;
 
-// One lane's part of ray `row`: Siddon's walk over its piece of the ray, the
-// segments' pixels taken at their midpoints.
+// One lane's part of ray `row`: Siddon's walk over its piece of the ray.  The
+// pixel indices start at the cell before the first grid line ahead on each
+// axis (the same lines whose crossings the walk steps through) and step with
+// the crossings (x line: ix += sign(dx), y line: iy += sign(dy), both at a
+// corner).  Every segment then gets the pixel that contains it by the walk's
+// own crossing order, without a floor per segment, and a start within
+// rounding of a grid line cannot put the indices on the wrong side of it.
 template <typename RT, typename XT>
 __device__ __forceinline__ RT proj_ray_partial(int N, int nb, const RT *tab, const XT *__restrict__ x, int64_t row,
                                                int lane) {
@@ -65,30 +70,30 @@ __device__ __forceinline__ RT proj_ray_partial(int N, int nb, const RT *tab, con
   const RT L = (lane == 31 ? hi : lo + span * (RT)(lane + 1) / RT(32)) - a0;
   const RT X0 = px + a0 * dx + h, Y0 = py + a0 * dy + h;   // grid coordinates in [0, N]
   RT lx = RT(1e30), ly = RT(1e30), lx0 = 0, ly0 = 0, ex = 0, ey = 0;
+  int ix = (int)floor(X0), iy = (int)floor(Y0);   // kept on an axis without crossings
   if (use_x) {
-    const RT kx = dx > 0 ? floor(X0) + RT(1) : ceil(X0) - RT(1);
+    const RT kx = dx > 0 ? floor(X0) + RT(1) : ceil(X0) - RT(1);   // first x line ahead
     lx0 = lx = (kx - X0) / dx;
     ex = RT(1) / fabs(dx);
+    ix = dx > 0 ? (int)kx - 1 : (int)kx;   // the column before that line
   }
   if (use_y) {
     const RT ky = dy > 0 ? floor(Y0) + RT(1) : ceil(Y0) - RT(1);
     ly0 = ly = (ky - Y0) / dy;
     ey = RT(1) / fabs(dy);
+    iy = dy > 0 ? (int)ky - 1 : (int)ky;
   }
-  RT acc = 0, prev = 0;
-  int jx = 0, jy = 0;
+  const int sx = dx > 0 ? 1 : -1, sy = dy > 0 ? 1 : -1;
+  RT acc = 0, prev = 0, jx = 0, jy = 0;
   for (int guard = 0; guard < 4 * N + 8; ++guard) {   // a piece crosses at most 2N + 2 grid lines
     const RT next = fmin(fmin(lx, ly), L);
     if (next - prev > RT(1e-12)) {
-      const RT lm = RT(0.5) * (prev + next);
-      int ix = (int)floor(X0 + lm * dx), iy = (int)floor(Y0 + lm * dy);
-      ix = min(max(ix, 0), N - 1);
-      iy = min(max(iy, 0), N - 1);
-      acc += (next - prev) * (RT)x[(size_t)iy * N + ix];
+      const int cx = min(max(ix, 0), N - 1), cy = min(max(iy, 0), N - 1);
+      acc += (next - prev) * (RT)x[(size_t)cy * N + cx];
     }
     if (next >= L) break;
-    if (use_x && lx == next) { ++jx; lx = lx0 + (RT)jx * ex; }
-    if (use_y && ly == next) { ++jy; ly = ly0 + (RT)jy * ey; }
+    if (use_x && lx == next) { jx += RT(1); lx = lx0 + jx * ex; ix += sx; }
+    if (use_y && ly == next) { jy += RT(1); ly = ly0 + jy * ey; iy += sy; }
     prev = next;
   }
   return acc;
