@@ -107,6 +107,7 @@ struct Plan {
   bool matfree = false;
   int ct_N = 0, ct_na = 0, ct_nb = 0, ct_back = 0;
   void *ct_tab = nullptr;   // per-angle constants, kProjTab each, FP64 or FP32 (the plan's arithmetic)
+  long long *ct_fix = nullptr;   // FP64 plans: per angle round(cos 2^F), F = proj_bin_frac_bits(n_bins)
   uint64_t bytes = 0, cap = 0;
   std::vector<void *> allocs;
   std::vector<std::unique_ptr<Session>> sessions;

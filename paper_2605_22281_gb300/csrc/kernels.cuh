@@ -124,6 +124,7 @@ struct SpmvParams {
   int proj;                             // kProjRay, kProjBackChord or kProjBackLinear
   int pN, pna, pnb;                     // image N x N, angles, bins
   const void *ptab;                     // per-angle constants, kProjTab values each, in the vectors' arithmetic
+  const long long *pfix;                // FP64: per-angle bin-coordinate step round(cos 2^F) (proj.cuh)
   Partials part;
 };
 
@@ -494,8 +495,9 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
 // the matrix-free projector form (proj.cuh).
 enum : int { kSpmvVec = 0, kSpmvMat = 1, kSpmvMatOrig = 2, kSpmvProj = 3 };
 
-// The rows of a warp for the projector form, in 32-row blocks: for each row
-// the lanes' parts are added by a butterfly and lane r keeps row r's value,
+// The rows of a warp for the projector form, in 32-row blocks: lane r walks
+// ray r of the block (A x), or, for a back-projection, the lanes' parts of
+// each row are added by a butterfly and lane r keeps row r's value; lane r
 // then writes it and its square as the stored form does.
 template <typename VT, typename XT>
 __device__ __forceinline__ double proj_rows(const SpmvParams<VT, XT> &p, RowBlocks rb, const XT *__restrict__ x, XT *y) {
@@ -506,12 +508,18 @@ __device__ __forceinline__ double proj_rows(const SpmvParams<VT, XT> &p, RowBloc
   for (int64_t row0 = rb.first; row0 < rb.end; row0 += rb.stride) {
     const int64_t r1 = min(row0 + 32, rb.end);
     RT mine = RT(0);
-    for (int64_t row = row0; row < r1; ++row) {
-      RT v = p.proj == kProjRay ? proj_ray_partial<RT, XT>(p.pN, p.pnb, tab, x, row, lane)
-                                : proj_back_partial<RT, XT>(p.proj, p.pN, p.pna, p.pnb, tab, x, row, lane);
+    if (p.proj == kProjRay) {
+      if (row0 + lane < r1) mine = proj_ray<RT, XT>(p.pN, p.pnb, tab, x, row0 + lane);
+    } else if (std::is_same<RT, double>::value && p.proj == kProjBackLinear) {
+      mine = (RT)proj_back_linear_block<XT>(p.pN, p.pna, p.pnb, reinterpret_cast<const double *>(p.ptab), p.pfix, x,
+                                            row0, r1, lane);
+    } else {
+      for (int64_t row = row0; row < r1; ++row) {
+        RT v = proj_back_partial<RT, XT>(p.proj, p.pN, p.pna, p.pnb, tab, x, row, lane);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == (int)(row - row0)) mine = v;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == (int)(row - row0)) mine = v;
+      }
     }
     const int64_t row = row0 + lane;
     if (row < r1) {

@@ -391,7 +391,8 @@ int sfl_plan_create_ct(sfl_plan **plan, const sfl_ct_geometry *g, const sfl_plan
   if (n >= (int64_t)1 << 31 || m >= (int64_t)1 << 31) return SFL_EINVAL;
   const sfl_dtype vdt = popts ? popts->value_dtype : SFL_F64;
   if (vdt != SFL_F64 && vdt != SFL_F32 && vdt != SFL_BF16) return SFL_EINVAL;
-  // per-angle constants (host, FP64): cos, sin, trapezoid a1, a2, H, slope, axis flag
+  // per-angle constants (host, FP64): cos, sin, trapezoid a1, a2, H, slope, axis flag,
+  // the direction's reciprocals -1/sin and 1/cos
   std::vector<double> tab((size_t)kProjTab * g->n_angles);
   for (int a = 0; a < g->n_angles; ++a) {
     const double th = (double)a * M_PI / (double)g->n_angles;
@@ -403,6 +404,8 @@ int sfl_plan_create_ct(sfl_plan **plan, const sfl_ct_geometry *g, const sfl_plan
     e[0] = c; e[1] = s; e[2] = a1; e[3] = a2; e[4] = H;
     e[5] = a2 - a1 > 1e-15 ? H / (a2 - a1) : 0.0;
     e[6] = as < 1e-15 ? 1.0 : (ac < 1e-15 ? 2.0 : 0.0);
+    e[7] = as > 1e-15 ? -1.0 / s : 0.0;
+    e[8] = ac > 1e-15 ? 1.0 / c : 0.0;
   }
   sfl_plan *p = new sfl_plan();
   Plan &pl = p->impl;
@@ -418,9 +421,15 @@ int sfl_plan_create_ct(sfl_plan **plan, const sfl_ct_geometry *g, const sfl_plan
   pl.T.rows = n; pl.T.cols = m; pl.T.lpr = 32;
   cudaStream_t s = (cudaStream_t)stream;
   int r = SFL_OK;
+  std::vector<long long> fix(g->n_angles);
   if (pl.vdt == SFL_F64) {
+    const int F = proj_bin_frac_bits(g->n_bins);
+    for (int a = 0; a < g->n_angles; ++a) fix[a] = std::llround(std::ldexp(tab[(size_t)kProjTab * a], F));
     r = plan_alloc(pl, &pl.ct_tab, sizeof(double) * tab.size());
     if (!r && cudaMemcpyAsync(pl.ct_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      r = SFL_ECUDA;
+    if (!r) r = plan_alloc(pl, (void **)&pl.ct_fix, sizeof(long long) * fix.size());
+    if (!r && cudaMemcpyAsync(pl.ct_fix, fix.data(), sizeof(long long) * fix.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
       r = SFL_ECUDA;
   } else {
     std::vector<float> tf(tab.begin(), tab.end());

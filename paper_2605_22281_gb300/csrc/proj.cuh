@@ -10,9 +10,10 @@
 //                   unit square is the square's trapezoid footprint;
 //   kProjBackLinear y = B x, the unmatched pixel-driven back-projector: each
 //                   pixel centre split linearly between its two nearest bins.
-// A row's work is split over the 32 lanes of a warp (a ray's parameter range
-// in 32 equal pieces, or a pixel's angles lane, lane + 32, ...); the product
-// kernel adds the lanes' parts by a butterfly (a fixed order).
+// A ray of A x is walked by one thread (32 neighbouring rays per warp); a
+// pixel of a back-projection is split over the 32 lanes of a warp (angles
+// lane, lane + 32, ...), whose parts the product kernel adds by a butterfly
+// (a fixed order).
 #pragma once
 
 #include "common.cuh"
@@ -23,23 +24,52 @@ enum : int { kProjRay = 0, kProjBackChord = 1, kProjBackLinear = 2 };
 
 // Per-angle table (kProjTab values per angle): cos, sin, the trapezoid's
 // half-widths a1 = ||cos| - |sin||/2 <= a2 = (|cos| + |sin|)/2, its height
-// H = 1/max(|cos|, |sin|), its ramp slope H/(a2 - a1) (0 when a1 = a2), and the
+// H = 1/max(|cos|, |sin|), its ramp slope H/(a2 - a1) (0 when a1 = a2), the
 // axis flag (0: general; 1: |sin| < 1e-15, the rays are the lines x = const;
-// 2: |cos| < 1e-15, the rays are y = const).
-constexpr int kProjTab = 7;
+// 2: |cos| < 1e-15, the rays are y = const), and the reciprocals of the ray
+// direction (dx, dy) = (-sin, cos): -1/sin and 1/cos (0 below 1e-15).
+constexpr int kProjTab = 9;
 
-// One lane's part of ray `row`: Siddon's walk over its piece of the ray.  The
-// pixel indices start at the cell before the first grid line ahead on each
-// axis (the same lines whose crossings the walk steps through) and step with
-// the crossings (x line: ix += sign(dx), y line: iy += sign(dy), both at a
-// corner).  Every segment then gets the pixel that contains it by the walk's
-// own crossing order, without a floor per segment, and a start within
-// rounding of a grid line cannot put the indices on the wrong side of it.
+// Fractional bits of a fixed-point bin coordinate in [-2, n_bins + 2]: |q| < 2^61.
+__host__ __device__ inline int proj_bin_frac_bits(int nb) {
+  int b = 0;
+  for (unsigned v = (unsigned)nb + 2u; v; v >>= 1) ++b;
+  return 61 - b;
+}
+
+template <typename RT> __device__ __forceinline__ RT proj_pow2(int e);
+template <> __device__ __forceinline__ double proj_pow2<double>(int e) {
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+template <> __device__ __forceinline__ float proj_pow2<float>(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ long long proj_to_fixed(double v) { return __double2ll_rn(v); }
+__device__ __forceinline__ long long proj_to_fixed(float v) { return __float2ll_rn(v); }
+template <typename RT> __device__ __forceinline__ RT proj_from_fixed(long long q);
+template <> __device__ __forceinline__ double proj_from_fixed<double>(long long q) { return __ll2double_rn(q); }
+template <> __device__ __forceinline__ float proj_from_fixed<float>(long long q) { return __ll2float_rn(q); }
+
+// Ray `row` of A x, walked by one thread: Siddon's chords, column by column
+// along the ray's major axis (the axis u with the larger direction component,
+// |du| >= |dv|).  Between two major grid lines the ray rises by at most one
+// unit along the minor axis v, so a column holds one pixel, or two split at
+// one minor grid line.  The minor coordinate at the column ends is carried in
+// 64-bit fixed point (F fractional bits, Q = round(v 2^F); inner columns add
+// the per-column rise M = round(dv |1/du| 2^F)), which gives both pixels by
+// shifts and the chord before the minor line as (its distance in v) |1/dv|.
+// An inner column is |1/du| long, so its chords are |1/du| x2 + t (x1 - x2)
+// (x1, x2 the pixels before and after the minor line, t the chord in x1); the
+// walk adds x2 and t (x1 - x2) and scales the first sum by |1/du| once.  The
+// two columns cut by the ray's entry and exit take their lengths from the
+// parameters.  Pixels on a minor line count from the side the ray leaves, as
+// the crossing order of a two-axis walk gives; a ray along a grid line takes
+// the pixel with the floor index.  One thread per ray (the 32 rays of a warp
+// are neighbouring bins of one angle) keeps the per-ray setup off the FP64
+// pipe's critical count: it is issued once per 32 rays.
 template <typename RT, typename XT>
-__device__ __forceinline__ RT proj_ray_partial(int N, int nb, const RT *tab, const XT *__restrict__ x, int64_t row,
-                                               int lane) {
+__device__ __forceinline__ RT proj_ray(int N, int nb, const RT *tab, const XT *__restrict__ x, int64_t row) {
   const int a = (int)(row / nb), d = (int)(row % nb);
-  const RT c = tab[kProjTab * a], s = tab[kProjTab * a + 1];
+  const RT *g = tab + kProjTab * a;
+  const RT c = g[0], s = g[1], inv_dx = g[7], inv_dy = g[8];
   const RT t = (RT)d - RT(0.5) * (RT)(nb - 1);
   const RT h = RT(0.5) * (RT)N;
   const RT px = t * c, py = t * s;   // foot point
@@ -48,55 +78,153 @@ __device__ __forceinline__ RT proj_ray_partial(int N, int nb, const RT *tab, con
   // so a ray on a grid line belongs to the pixel with the floor index
   const RT dx = fabs(s) > tiny ? -s : RT(0), dy = fabs(c) > tiny ? c : RT(0);
   RT lo = -RT(1e30), hi = RT(1e30);
-  const bool use_x = fabs(dx) > tiny, use_y = fabs(dy) > tiny;
-  if (use_x) {
-    const RT l0 = (-h - px) / dx, l1 = (h - px) / dx;
+  if (fabs(dx) > tiny) {
+    const RT l0 = (-h - px) * inv_dx, l1 = (h - px) * inv_dx;
     lo = fmax(lo, fmin(l0, l1));
     hi = fmin(hi, fmax(l0, l1));
   } else if (!(px > -h && px < h)) {
     return RT(0);
   }
-  if (use_y) {
-    const RT l0 = (-h - py) / dy, l1 = (h - py) / dy;
+  if (fabs(dy) > tiny) {
+    const RT l0 = (-h - py) * inv_dy, l1 = (h - py) * inv_dy;
     lo = fmax(lo, fmin(l0, l1));
     hi = fmin(hi, fmax(l0, l1));
   } else if (!(py > -h && py < h)) {
     return RT(0);
   }
   if (!(hi > lo)) return RT(0);
-  // this lane's piece [a0, a0 + L] of the parameter range, walked in local parameters
-  const RT span = hi - lo;
-  const RT a0 = lo + span * (RT)lane / RT(32);
-  const RT L = (lane == 31 ? hi : lo + span * (RT)(lane + 1) / RT(32)) - a0;
-  const RT X0 = px + a0 * dx + h, Y0 = py + a0 * dy + h;   // grid coordinates in [0, N]
-  RT lx = RT(1e30), ly = RT(1e30), lx0 = 0, ly0 = 0, ex = 0, ey = 0;
-  int ix = (int)floor(X0), iy = (int)floor(Y0);   // kept on an axis without crossings
-  if (use_x) {
-    const RT kx = dx > 0 ? floor(X0) + RT(1) : ceil(X0) - RT(1);   // first x line ahead
-    lx0 = lx = (kx - X0) / dx;
-    ex = RT(1) / fabs(dx);
-    ix = dx > 0 ? (int)kx - 1 : (int)kx;   // the column before that line
-  }
-  if (use_y) {
-    const RT ky = dy > 0 ? floor(Y0) + RT(1) : ceil(Y0) - RT(1);
-    ly0 = ly = (ky - Y0) / dy;
-    ey = RT(1) / fabs(dy);
-    iy = dy > 0 ? (int)ky - 1 : (int)ky;
-  }
-  const int sx = dx > 0 ? 1 : -1, sy = dy > 0 ? 1 : -1;
-  RT acc = 0, prev = 0, jx = 0, jy = 0;
-  for (int guard = 0; guard < 4 * N + 8; ++guard) {   // a piece crosses at most 2N + 2 grid lines
-    const RT next = fmin(fmin(lx, ly), L);
-    if (next - prev > RT(1e-12)) {
-      const int cx = min(max(ix, 0), N - 1), cy = min(max(iy, 0), N - 1);
-      acc += (next - prev) * (RT)x[(size_t)cy * N + cx];
+  const bool xmaj = fabs(dx) >= fabs(dy);
+  const RT du = xmaj ? dx : dy, dv = xmaj ? dy : dx;
+  const RT inv_du = xmaj ? inv_dx : inv_dy, inv_dv = xmaj ? inv_dy : inv_dx;
+  const RT pu0 = (xmaj ? px : py) + h, pv0 = (xmaj ? py : px) + h;   // grid coordinates of the foot point
+  const int64_t ustride = xmaj ? 1 : N, vstride = xmaj ? N : 1;
+  // major grid lines strictly inside the ray: k1, k1 + su, ... (nl of them);
+  // column i (0..nl) ends at line i (the ray's exit for i = nl)
+  const bool fwd = du > RT(0);
+  const int su = fwd ? 1 : -1;
+  const RT ulo = pu0 + lo * du, uhi = pu0 + hi * du;
+  const int k1 = fwd ? (int)floor(ulo) + 1 : (int)ceil(ulo) - 1;
+  const int kl = fwd ? (int)ceil(uhi) - 1 : (int)floor(uhi) + 1;
+  const int nl = min(max(fwd ? kl - k1 + 1 : k1 - kl + 1, 0), N + 1);
+  const int F = proj_bin_frac_bits(N);   // |Q| < 2^61 for v in [-2, N + 2]
+  const long long one = 1LL << F;
+  const RT two_f = proj_pow2<RT>(F);
+  const RT eu = fabs(inv_du), scale = proj_pow2<RT>(-F) * fabs(inv_dv);
+  const RT nq = -pu0 * inv_du;
+  const long long M = proj_to_fixed(dv * eu * two_f);
+  // pixels x1 (after the column's start) and x2 (before its end) of column i,
+  // and the chord t in x1 when they differ
+  auto column = [&](int i, long long qs, long long qe, RT &x1, RT &x2) -> RT {
+    int rs, re;
+    if (dv > RT(0)) {
+      rs = (int)(qs >> F);
+      re = min(max(rs, (int)((qe - 1) >> F)), rs + 1);
+    } else if (dv < RT(0)) {
+      rs = (int)((qs - 1) >> F);
+      re = max(min(rs, (int)(qe >> F)), rs - 1);
+    } else {
+      rs = re = (int)(qs >> F);
     }
-    if (next >= L) break;
-    if (use_x && lx == next) { jx += RT(1); lx = lx0 + jx * ex; ix += sx; }
-    if (use_y && ly == next) { jy += RT(1); ly = ly0 + jy * ey; iy += sy; }
-    prev = next;
+    const long long vc = (long long)(dv > RT(0) ? rs + 1 : rs) * one;   // the minor line crossed
+    const int cu = min(max(fwd ? k1 - 1 + i : k1 - i, 0), N - 1);
+    x1 = (RT)x[cu * ustride + min(max(rs, 0), N - 1) * vstride];
+    x2 = (RT)x[cu * ustride + min(max(re, 0), N - 1) * vstride];
+    return re != rs ? proj_from_fixed<RT>(vc > qs ? vc - qs : qs - vc) * scale : RT(0);
+  };
+  RT S = RT(0), C, x1, x2;
+  long long Qs = proj_to_fixed((pv0 + lo * dv) * two_f);
+  {   // column 0: from the entry to line 0, or to the exit
+    const RT le = nl == 0 ? hi : (RT)k1 * inv_du + nq;
+    const long long Qe = proj_to_fixed((pv0 + le * dv) * two_f);
+    const RT len = le - lo;
+    const RT tc = fmin(column(0, Qs, Qe, x1, x2), len);
+    C = len * x2 + tc * (x1 - x2);
+    Qs = Qe;
   }
-  return acc;
+  for (int i = 1; i < nl; ++i) {   // inner columns, |1/du| long
+    const long long Qe = Qs + M;
+    const RT tc = column(i, Qs, Qe, x1, x2);
+    S += x2;
+    C += tc * (x1 - x2);
+    Qs = Qe;
+  }
+  if (nl > 0) {   // column nl: from line nl - 1 to the exit
+    const RT ls = (RT)(k1 + su * (nl - 1)) * inv_du + nq;
+    const long long Qe = proj_to_fixed((pv0 + hi * dv) * two_f);
+    const RT len = hi - ls;
+    const RT tc = fmin(column(nl, Qs, Qe, x1, x2), len);
+    C += len * x2 + tc * (x1 - x2);
+  }
+  return eu * S + C;
+}
+
+// The fraction f = fr 2^-F (0 <= fr < 2^F) as an FP64 value: the fraction's
+// top 52 bits as the significand of a number in [1, 2), minus one (exact).
+__device__ __forceinline__ double proj_frac(long long fr, int F) {
+  const long long m = F >= 52 ? fr >> (F - 52) : fr << (52 - F);
+  return __longlong_as_double(0x3FF0000000000000LL | m) - 1.0;
+}
+
+// Rows [row0, r1) of y = B x (pixel-driven linear interpolation), FP64, one
+// 32-row block: lane l takes the angles l, l + 32, ... (kProjLinPass per lane
+// and pass) and keeps each angle's bin coordinate u = xc cos + yc sin + off of
+// the current pixel in fixed point (F = proj_bin_frac_bits(n_bins) fractional
+// bits).  From one pixel to the next in an image row u grows by cos, a
+// per-angle integer step round(cos 2^F) from the plan; a new block or image
+// row starts from u itself.  The bins and weights then come from shifts and
+// one FP64 subtraction, so a (pixel, angle) pair costs four FP64 instructions.
+// Each pass's lane sums are added by a butterfly; lane r returns row r.
+constexpr int kProjLinPass = 8;
+template <typename XT>
+__device__ __forceinline__ double proj_back_linear_block(int N, int na, int nb, const double *tab,
+                                                         const long long *__restrict__ fix, const XT *__restrict__ w,
+                                                         int64_t row0, int64_t r1, int lane) {
+  const int F = proj_bin_frac_bits(nb);
+  const long long one = 1LL << F, mask = one - 1;
+  const double two_f = proj_pow2<double>(F);
+  // weights below 1e-12 are dropped, as in the stored operator
+  const long long thr_lo = (long long)(1e-12 * two_f), thr_hi = one - thr_lo;
+  const double h = 0.5 * (double)N, off = 0.5 * (double)(nb - 1);
+  double mine = 0.0;
+  for (int a0 = 0; a0 < na; a0 += 32 * kProjLinPass) {
+    long long U[kProjLinPass];
+    for (int64_t row = row0; row < r1; ++row) {
+      const int ix = (int)(row % N), iy = (int)(row / N);
+      if (row == row0 || ix == 0) {
+        const double xc = (double)ix - h + 0.5, yc = (double)iy - h + 0.5;
+#pragma unroll
+        for (int j = 0; j < kProjLinPass; ++j) {
+          const int a = a0 + lane + 32 * j;
+          if (a < na) U[j] = proj_to_fixed((xc * tab[kProjTab * a] + yc * tab[kProjTab * a + 1] + off) * two_f);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kProjLinPass; ++j) {
+          const int a = a0 + lane + 32 * j;
+          if (a < na) U[j] += fix[a];
+        }
+      }
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < kProjLinPass; ++j) {
+        const int a = a0 + lane + 32 * j;
+        if (a < na) {
+          const int i0 = (int)(U[j] >> F);
+          const long long fr = U[j] & mask;
+          const double f = proj_frac(fr, F);
+          const XT *wa = w + (size_t)a * nb;
+          const double w0 = i0 >= 0 && i0 < nb && fr < thr_hi ? (double)wa[i0] : 0.0;
+          const double w1 = i0 + 1 >= 0 && i0 + 1 < nb && fr > thr_lo ? (double)wa[i0 + 1] : 0.0;
+          acc = fma(1.0 - f, w0, acc);
+          acc = fma(f, w1, acc);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == (int)(row - row0)) mine += acc;
+    }
+  }
+  return mine;
 }
 
 // One lane's part of pixel `pix` of a back-projection (angles lane, lane + 32, ...).

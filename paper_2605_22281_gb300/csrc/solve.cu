@@ -274,6 +274,7 @@ struct Engine {
   // matched / unmatched pixel-driven back-projection), rows split evenly.
   static void set_proj(const Plan &pl, SpmvParams<VT, XT> &p, bool fwd) {
     p.ptab = pl.ct_tab;
+    p.pfix = pl.ct_fix;
     p.pN = pl.ct_N; p.pna = pl.ct_na; p.pnb = pl.ct_nb;
     p.proj = fwd ? kProjRay : (pl.ct_back ? kProjBackLinear : kProjBackChord);
     p.wrow = nullptr;
@@ -1002,6 +1003,7 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
   p.interleave = interleave_rows(M, grid);
   if (pl.matfree) {
     p.ptab = pl.ct_tab;
+    p.pfix = pl.ct_fix;
     p.pN = pl.ct_N; p.pna = pl.ct_na; p.pnb = pl.ct_nb;
     p.proj = which == 0 ? kProjRay : (pl.ct_back ? kProjBackLinear : kProjBackChord);
   }
