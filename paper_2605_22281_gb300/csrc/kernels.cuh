@@ -610,7 +610,16 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
     return p.wrow ? (int64_t)p.wrow[w] : (p.rows * w) / ((int64_t)ncta * kWarps);
   };
   RowBlocks rb;
-  if (p.interleave) {
+  if (FORM == kSpmvProj && p.proj == kProjRay && !p.sk_s) {
+    // one thread per ray: whole 32-ray blocks, dealt warp-major so that a
+    // CTA's warps take blocks from across the sinogram (a ray at the centre of
+    // an angle's bins crosses up to N columns, one at its edge a few).  With
+    // the fused sketch the CTA keeps its contiguous range, which the sketch
+    // epilogue reads back.
+    rb.first = 32 * ((int64_t)warp * ncta + rcta);
+    rb.stride = 32 * (int64_t)ncta * kWarps;
+    rb.end = p.rows;
+  } else if (p.interleave) {
     rb.first = bound((int64_t)rcta * kWarps) + 32 * warp;
     rb.stride = 32 * kWarps;
     rb.end = bound((int64_t)(rcta + 1) * kWarps);
