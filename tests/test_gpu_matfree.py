@@ -127,3 +127,20 @@ def test_matrix_free_plans_refuse_batched_solves():
         G.solve_batched(plan, B, [0.0, 0.0], s=21, maxit=10)
     assert e.value.status == G.N.SFL_EUNSUPPORTED
     plan.close()
+
+
+def test_matrix_free_fused_sketch_at_512():
+    """From 512^2 the sketch is fused into the forward product, whose CTAs then
+    keep contiguous ray ranges (the sketch epilogue reads its own rows back):
+    every iterate of the FP64 matrix-free solve within the flat bar of the
+    oracle on the stored operator (the 1024^2 recipe at 512^2, 90 angles)."""
+    p = wl.make("ct1024_sflsqr", N=512, n_angles=90)
+    st = p.settings
+    tol = O.discrepancy_tol(st["eta"], p.noise_norm[0], np.linalg.norm(p.b))
+    r = run_oracle_sflsqr(p.A.scipy(), p.b, st["s"], st["zeta"], st["seed"], st["maxit"], tol, st["window"])
+    plan = G.Plan.ct(p.N, p.n_angles, p.n_bins)
+    x, info, h = plan.solve("sflsqr", dev(p.b), s=st["s"], zeta=st["zeta"], seed=st["seed"], window=st["window"],
+                            maxit=st["maxit"], noise_norm=p.noise_norm[0], eta=st["eta"], sketch_apply="fused",
+                            x_history=True, relres_history=True)
+    assert_iterates_flat(r, h["x"], h["relres"], info, tol)
+    plan.close()
