@@ -297,7 +297,9 @@ int sfl_plan_get_stats(const sfl_plan *plan, sfl_plan_stats *stats /* host */);
  * operator and the same SpMV kernel the solvers use.  x and y are FP64
  * (lengths cols/rows of the chosen operator); the product is formed in the
  * plan's value precision with FP64 accumulation for FP64 plans and FP32 for
- * FP32/BF16 plans. */
+ * FP32/BF16 plans.  The first call per operator of a stored plan computes the
+ * warps' row ranges balanced by row cost (a device allocation kept by the
+ * plan, and a stream synchronisation); later calls reuse them. */
 int sfl_plan_apply(sfl_plan *plan, int which, const double *x, double *y, sfl_stream stream);
 
 /* ---- solvers ------------------------------------------------------------ */

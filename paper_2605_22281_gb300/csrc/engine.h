@@ -116,6 +116,7 @@ struct Plan {
   int64_t fixed_calls = 0;
   // scratch for sfl_plan_apply
   void *apply_x = nullptr, *apply_y = nullptr;
+  int32_t *apply_wrow[2] = {nullptr, nullptr};   // warp row ranges of A and of A^T / B, balanced by row cost
   RedScratch apply_red{};
 };
 

@@ -1001,6 +1001,20 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
   p.mode = kModeApply;
   const int grid = pl.num_sms * 2;
   p.interleave = interleave_rows(M, grid);
+  if (!pl.matfree) {   // warp row ranges balanced by row cost, as in a solve (first call per operator)
+    if (!pl.apply_wrow[which]) {
+      const int W = grid * kWarps;
+      int32_t *wrow = nullptr;
+      SFL_CU(cudaMalloc(&wrow, sizeof(int32_t) * (W + 1)));
+      pl.allocs.push_back(wrow);
+      const bool fp64 = std::is_same<VT, double>::value;
+      const int P = load_width(pl.vdt);
+      const int r = balance_rows(M, SpmvTune<VT>::NCH * M.lpr * P, W, wrow, s, fp64 ? M.lpr * P : 0, 0);
+      if (r) return r;
+      pl.apply_wrow[which] = wrow;
+    }
+    p.wrow = pl.apply_wrow[which];
+  }
   if (pl.matfree) {
     p.ptab = pl.ct_tab;
     p.pfix = pl.ct_fix;
