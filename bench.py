@@ -178,11 +178,15 @@ def recorded_traffic(kernel: str, workload: str):
     return e.get("bytes_per_launch")
 
 
-def spmv_bytes(nnz, rows, cols, vbytes, xbytes, ndots, table_bytes):
-    """Compulsory bytes of one fused SpMV launch: values + column indices + row
-    pointers, the gathered input vector once, the output vector, the window
-    vectors read by the fused dots, and the sketch table."""
-    return nnz * (vbytes + 4) + 4 * (rows + 1) + xbytes * (cols + rows) + xbytes * rows * ndots + table_bytes
+def spmv_bytes(nnz, rows, cols, vbytes, xbytes, ndots, table_bytes, ibytes=4):
+    """Compulsory bytes of one fused SpMV launch: values + column indices
+    (ibytes per entry: 4, or 2 for 16-bit column deltas, which add one 4-byte
+    base column per row) + row pointers, the gathered input vector once, the
+    output vector, the window vectors read by the fused dots, and the sketch
+    table."""
+    base = 4 * rows if ibytes == 2 else 0
+    return (nnz * (vbytes + ibytes) + 4 * (rows + 1) + base + xbytes * (cols + rows) + xbytes * rows * ndots
+            + table_bytes)
 
 
 # ---------------------------------------------------------------- oracle (CPU) legs
@@ -402,10 +406,11 @@ def mixed_variant(args, G, wl, np, torch, x_fp64=None):
             _, _, hp = plan.solve("sflsqr", b, driver="profiled", **kw)
             kms, kl = hp["kernel_ms"], hp["kernel_launches"]
             vb = 2 if vdt == "bf16" else 4
-            for name, nnz, rows, cols in (("spmv_fwd", p.A.nnz, p.A.shape[0], p.A.shape[1]),
-                                          ("spmv_bwd", p.A.nnz, p.A.shape[1], p.A.shape[0])):
+            pst = plan.stats()
+            for name, nnz, rows, cols, ib in (("spmv_fwd", p.A.nnz, p.A.shape[0], p.A.shape[1], pst["index_bytes_A"]),
+                                              ("spmv_bwd", p.A.nnz, p.A.shape[1], p.A.shape[0], pst["index_bytes_At"])):
                 avg = kms[name] / max(kl[name], 1)
-                nbytes = spmv_bytes(int(nnz), rows, cols, vb, 4, st["window"] + 1, 0)
+                nbytes = spmv_bytes(int(nnz), rows, cols, vb, 4, st["window"] + 1, 0, ib)
                 leg[name] = {"avg_us": 1000 * avg, "bytes": nbytes, "gbs": nbytes / (avg * 1e-3) / 1e9,
                              "hbm_frac_of_measured": nbytes / (avg * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]}
         out[vdt] = leg
@@ -704,8 +709,8 @@ def single_leg(args, G, wl, np, torch, p, vdt: str, *, steps: int, warmup: int, 
     ell = st["window"]
     vb = {"f64": 8, "f32": 4, "bf16": 2}[vdt]
     xb = 8 if vdt == "f64" else 4
-    fwd_bytes = spmv_bytes(stats["nnz_A"], m, n, vb, xb, ell + 1, 0)
-    bwd_bytes = spmv_bytes(stats["nnz_At"], n, m, vb, xb, ell, 0)
+    fwd_bytes = spmv_bytes(stats["nnz_A"], m, n, vb, xb, ell + 1, 0, stats["index_bytes_A"])
+    bwd_bytes = spmv_bytes(stats["nnz_At"], n, m, vb, xb, ell, 0, stats["index_bytes_At"])
     peaks = load_peaks()
     kern = {}
     for name, nbytes, nnz in (("spmv_fwd", fwd_bytes, stats["nnz_A"]), ("spmv_bwd", bwd_bytes, stats["nnz_At"])):

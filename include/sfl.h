@@ -94,13 +94,22 @@ typedef struct sfl_plan sfl_plan;
  * neighbouring entries (faster single-solve products on ray-ordered rows);
  * 1 keeps each row in the caller's entry order (faster batched SpMMs, which
  * walk a row one entry at a time).  Results depend on it only through the
- * summation order. */
+ * summation order.
+ * index_bits: 0 (default) lets the single-solve products read 16-bit column
+ * deltas (each stored entry's column minus the column of the entry before it
+ * in its lane's walk, plus one 32-bit base per row) when every delta of the
+ * operator fits in 16 bits, the row layout is lane-interleaved and 8 lanes
+ * run a row; otherwise, and with 32, they read the 32-bit column indices.
+ * The products are the same bit for bit; the 16-bit form streams 2 bytes of
+ * index per entry instead of 4.  The plan keeps the 32-bit indices as well
+ * (batched solves read them). */
 typedef struct {
   sfl_dtype value_dtype;
   int32_t lanes_per_row;
   uint64_t max_device_bytes;
   int32_t image_rows, image_cols;
   int32_t slot_layout;
+  int32_t index_bits;
 } sfl_plan_opts;
 
 /* Solve options (the Require lines of Algorithms 1 and 2).
@@ -249,6 +258,7 @@ typedef struct {
   uint64_t device_bytes;                 /* bytes the plan holds */
   int32_t tiled_At;                      /* 1 if A^T / B rows are stored in pixel tiles */
   int32_t matrix_free;                   /* 1 for a sfl_plan_create_ct plan (nnz fields are 0) */
+  int32_t index_bytes_A, index_bytes_At; /* bytes of column index the single-solve products read per entry (2 or 4) */
 } sfl_plan_stats;
 
 /* ---- plans ------------------------------------------------------------- */

@@ -30,7 +30,8 @@ class Csr(ctypes.Structure):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("value_dtype", ctypes.c_int), ("lanes_per_row", ctypes.c_int32), ("max_device_bytes", ctypes.c_uint64),
-                ("image_rows", ctypes.c_int32), ("image_cols", ctypes.c_int32), ("slot_layout", ctypes.c_int32)]
+                ("image_rows", ctypes.c_int32), ("image_cols", ctypes.c_int32), ("slot_layout", ctypes.c_int32),
+                ("index_bits", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):
@@ -64,7 +65,7 @@ class PlanStats(ctypes.Structure):
                 ("nnz_At", ctypes.c_int64), ("padded_nnz_A", ctypes.c_int64), ("padded_nnz_At", ctypes.c_int64),
                 ("lanes_A", ctypes.c_int32), ("lanes_At", ctypes.c_int32), ("value_dtype", ctypes.c_int32),
                 ("unmatched", ctypes.c_int32), ("device_bytes", ctypes.c_uint64), ("tiled_At", ctypes.c_int32),
-                ("matrix_free", ctypes.c_int32)]
+                ("matrix_free", ctypes.c_int32), ("index_bytes_A", ctypes.c_int32), ("index_bytes_At", ctypes.c_int32)]
 
 
 class CtGeometry(ctypes.Structure):

@@ -68,10 +68,13 @@ class Plan:
     index row * cols + col): the plan then stores the rows of A^T / B in pixel
     tiles (same products bit for bit, better cache reuse).  slot_layout:
     'interleaved' (single solves) or 'operator' (batched solves) entry order
-    inside each row's chunk slots."""
+    inside each row's chunk slots.  index_bits: 0 lets the single-solve
+    products read 16-bit column deltas where the operator allows it (same
+    products bit for bit, 2 bytes less per entry); 32 keeps 32-bit indices."""
 
     def __init__(self, A, B=None, value_dtype: str = "f64", device: str | int = 0, max_device_bytes: int = 0,
-                 lanes_per_row: int = 0, image_shape: tuple | None = None, slot_layout: str = "interleaved"):
+                 lanes_per_row: int = 0, image_shape: tuple | None = None, slot_layout: str = "interleaved",
+                 index_bits: int = 0):
         _require_cuda()
         self.lib = N.load()
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
@@ -83,8 +86,10 @@ class Plan:
             ir, ic = (int(image_shape[0]), int(image_shape[1])) if image_shape is not None else (0, 0)
             if slot_layout not in ("interleaved", "operator"):
                 raise ValueError(slot_layout)
+            if index_bits not in (0, 32):
+                raise ValueError(f"index_bits {index_bits!r}: 0 (16-bit deltas where they fit) or 32")
             po = N.PlanOpts(N.DTYPE[value_dtype], lanes_per_row, max_device_bytes, ir, ic,
-                            0 if slot_layout == "interleaved" else 1)
+                            0 if slot_layout == "interleaved" else 1, index_bits)
             h = ctypes.c_void_p()
             st = N.check(self.lib.sfl_plan_create(ctypes.byref(h), ctypes.byref(ca),
                                                   ctypes.byref(cb) if cb is not None else None,
@@ -109,7 +114,7 @@ class Plan:
         if back not in ("matched", "unmatched"):
             raise ValueError(back)
         g = N.CtGeometry(image_n, n_angles, n_bins, 0 if back == "matched" else 1, None)
-        po = N.PlanOpts(N.DTYPE[value_dtype], 0, max_device_bytes, 0, 0, 0)
+        po = N.PlanOpts(N.DTYPE[value_dtype], 0, max_device_bytes, 0, 0, 0, 0)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             N.check(self.lib.sfl_plan_create_ct(ctypes.byref(h), ctypes.byref(g), ctypes.byref(po), _stream()),

@@ -21,6 +21,10 @@ struct StoredCsr {
   void *val = nullptr;
   int32_t *orig = nullptr;   // stored row i is row orig[i] of the operator (nullptr: the identity)
   bool interleaved = false;  // chunk slots stored lane-interleaved (else the caller's entry order)
+  // 16-bit column deltas along each lane's walk of a row (lane-interleaved
+  // slots, lpr 8) and each row's base column, when every delta fits
+  int16_t *dcol = nullptr;
+  int32_t *rbase = nullptr;
   int64_t rows = 0, cols = 0, nnz = 0, pnnz = 0;
   int lpr = 32;
 };
@@ -102,6 +106,7 @@ struct Plan {
   int lpr_override = 0;      // lanes per row requested by the caller (0: from the row lengths)
   int img_rows = 0, img_cols = 0;   // n-side image shape: A^T / B rows stored in pixel tiles
   int slot_layout = 0;              // 0: lane-interleaved chunk slots, 1: the caller's entry order
+  int index_bits = 0;               // 0: 16-bit column deltas where every delta fits, 32: 32-bit indices only
   StoredCsr A, T;   // T: CSR of A^T (transposed copy) or of B
   // matrix-free CT operator (sfl_plan_create_ct): no CSR arrays, products computed on the fly
   bool matfree = false;

@@ -15,19 +15,21 @@ template <typename XT> __global__ void convert_out_kernel(const XT *x, double *y
 
 // The product kernel for lanes per row `lpr`: the vector pass (mat false),
 // the matrix form, or the matrix form writing through an original-row map
-// (orig: pixel-tiled A^T / B rows).
+// (orig: pixel-tiled A^T / B rows); d16: the forms reading 16-bit column
+// deltas (built for kDeltaLpr lanes per row only).
 template <typename VT, typename XT, bool ORIG>
-static void (*spmv_mat_fn(int lpr))(SpmvParams<VT, XT>) {
+static void (*spmv_mat_fn(int lpr, bool d16))(SpmvParams<VT, XT>) {
   constexpr int M = ORIG ? kSpmvMatOrig : kSpmvMat;
+  if (d16) return spmv_fused_kernel<VT, XT, kDeltaLpr, ORIG ? kSpmvMatOrig16 : kSpmvMat16>;
   if (lpr == 4) return spmv_fused_kernel<VT, XT, 4, M>;
   if (lpr == 8) return spmv_fused_kernel<VT, XT, 8, M>;
   if (lpr == 16) return spmv_fused_kernel<VT, XT, 16, M>;
   return spmv_fused_kernel<VT, XT, 32, M>;
 }
 template <typename VT, typename XT>
-static void (*spmv_fn(int lpr, bool mat, bool orig))(SpmvParams<VT, XT>) {
+static void (*spmv_fn(int lpr, bool mat, bool orig, bool d16 = false))(SpmvParams<VT, XT>) {
   if (!mat) return spmv_fused_kernel<VT, XT, 1, kSpmvVec>;
-  return orig ? spmv_mat_fn<VT, XT, true>(lpr) : spmv_mat_fn<VT, XT, false>(lpr);
+  return orig ? spmv_mat_fn<VT, XT, true>(lpr, d16) : spmv_mat_fn<VT, XT, false>(lpr, d16);
 }
 
 template <typename VT, typename XT>
@@ -35,7 +37,9 @@ cudaError_t Ops<VT, XT>::spmv(const SpmvParams<VT, XT> &p, int lpr, bool mat, in
                               bool pdl) {
   if (mat && p.ptab)   // matrix-free projector
     return launch_k(spmv_fused_kernel<VT, XT, 32, kSpmvProj>, dim3(grid), dim3(kThreads), smem, s, pdl, p);
-  return launch_k(spmv_fn<VT, XT>(lpr, mat, mat && p.orig != nullptr), dim3(grid), dim3(kThreads), smem, s, pdl, p);
+  const bool d16 = mat && p.dcol != nullptr && lpr == kDeltaLpr;
+  return launch_k(spmv_fn<VT, XT>(lpr, mat, mat && p.orig != nullptr, d16), dim3(grid), dim3(kThreads), smem, s,
+                  pdl, p);
 }
 
 template <typename VT, typename XT>
@@ -58,6 +62,9 @@ cudaError_t Ops<VT, XT>::set_smem(int lpr, bool mat, size_t smem) {
   if (e == cudaSuccess && mat)
     e = cudaFuncSetAttribute((const void *)spmv_fn<VT, XT>(lpr, mat, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
+  for (int orig = 0; orig <= 1 && e == cudaSuccess && mat && lpr == kDeltaLpr; ++orig)
+    e = cudaFuncSetAttribute((const void *)spmv_fn<VT, XT>(lpr, mat, orig != 0, true),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return e;
 }
 
@@ -67,13 +74,13 @@ cudaError_t Ops<VT, XT>::set_orth_smem(size_t smem) {
                               (int)smem);
 }
 
-// Resident CTAs per SM of the product kernel (the smaller of the two matrix forms).
+// Resident CTAs per SM of the product kernel (the smallest over the matrix forms).
 template <typename VT, typename XT>
 int Ops<VT, XT>::spmv_occupancy(int lpr, bool mat, size_t smem) {
   int best = 1 << 20;
-  for (int orig = 0; orig <= (mat ? 1 : 0); ++orig) {
+  for (int form = 0; form < (mat ? (lpr == kDeltaLpr ? 4 : 2) : 1); ++form) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)spmv_fn<VT, XT>(lpr, mat, orig != 0),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)spmv_fn<VT, XT>(lpr, mat, form & 1, form >= 2),
                                                       kThreads, smem) != cudaSuccess)
       return 0;
     best = std::min(best, nb);

@@ -89,6 +89,8 @@ struct SpmvParams {
   const int32_t *rowptr;    // padded CSR (rows start at multiples of the load width)
   const int32_t *col;
   const VT *val;
+  const int16_t *dcol;      // the 16-bit delta forms: column deltas along each lane's walk
+  const int32_t *rbase;     //   and each stored row's base column
   int64_t rows;
   const int32_t *wrow;      // row range of every warp (nnz balanced), gridDim*kWarps + 1 entries
   const int32_t *orig;      // stored row i is operator row orig[i] (read by the kSpmvMatOrig form)
@@ -166,6 +168,46 @@ template <> struct Chunk<__nv_bfloat16, 8> {
   }
 };
 
+// The same P entries with 16-bit column deltas (P*2 bytes) instead of indices.
+__device__ __forceinline__ int lo16(int w) { return (w << 16) >> 16; }
+__device__ __forceinline__ int hi16(int w) { return w >> 16; }
+template <typename VT, int P> struct DChunk;
+template <> struct DChunk<double, 4> {
+  int d[4]; double v[4];
+  __device__ __forceinline__ void load(const int16_t *dcol, const double *val, int off) {
+    const int2 di = __ldcs(reinterpret_cast<const int2 *>(dcol + off));
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(val + off));
+    const double2 b = __ldcs(reinterpret_cast<const double2 *>(val + off + 2));
+    d[0] = lo16(di.x); d[1] = hi16(di.x); d[2] = lo16(di.y); d[3] = hi16(di.y);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+template <> struct DChunk<float, 4> {
+  int d[4]; float v[4];
+  __device__ __forceinline__ void load(const int16_t *dcol, const float *val, int off) {
+    const int2 di = __ldcs(reinterpret_cast<const int2 *>(dcol + off));
+    const float4 a = __ldcs(reinterpret_cast<const float4 *>(val + off));
+    d[0] = lo16(di.x); d[1] = hi16(di.x); d[2] = lo16(di.y); d[3] = hi16(di.y);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+};
+template <> struct DChunk<__nv_bfloat16, 8> {
+  int d[8]; float v[8];
+  __device__ __forceinline__ void load(const int16_t *dcol, const __nv_bfloat16 *val, int off) {
+    const int4 di = __ldcs(reinterpret_cast<const int4 *>(dcol + off));
+    const uint4 raw = __ldcs(reinterpret_cast<const uint4 *>(val + off));
+    const int wd[4] = {di.x, di.y, di.z, di.w};
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      d[2 * q] = lo16(wd[q]);
+      d[2 * q + 1] = hi16(wd[q]);
+      v[2 * q] = __uint_as_float(w[q] << 16);
+      v[2 * q + 1] = __uint_as_float(w[q] & 0xFFFF0000u);
+    }
+  }
+};
+
 template <typename VT> struct LoadWidth { static constexpr int P = 4; };
 template <> struct LoadWidth<__nv_bfloat16> { static constexpr int P = 8; };
 
@@ -196,9 +238,24 @@ __device__ __forceinline__ void load_or_zero(Chunk<VT, P> &c, const int32_t *col
   }
 }
 
-template <typename VT, typename XT, int LPR>
+template <typename VT, int P>
+__device__ __forceinline__ void load_or_zero(DChunk<VT, P> &c, const int16_t *dcol, const VT *val, int off, bool ok) {
+  if (ok) {
+    c.load(dcol, val, off);
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q) { c.d[q] = 0; c.v[q] = 0; }
+  }
+}
+
+// D16: the columns are the running sums of the lane's 16-bit deltas from the
+// row's base column `cur` (the lane walks its chunks in slot order, so the sum
+// passes every entry of the lane once, in order; chunks past the row end add
+// zero).  The entries, their order and the gathers are those of the 32-bit
+// form, so both forms give the same sums bit for bit.
+template <typename VT, typename XT, int LPR, bool D16>
 __device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT> &p, const XT *__restrict__ x,
-                                                       int beg, int end, int gl) {
+                                                       int beg, int end, int gl, int cur) {
   constexpr int P = LoadWidth<VT>::P;
   constexpr int NCH = SpmvTune<VT>::NCH;
   constexpr int STR = LPR * P;
@@ -213,15 +270,31 @@ __device__ __forceinline__ typename AccT<XT>::T row_dot(const SpmvParams<VT, XT>
 #pragma unroll 1
   for (int j = 0; j < nmax; j += NCH) {
     const int off = beg + gl * P + j * STR;
-    Chunk<VT, P> c[NCH];
+    if constexpr (D16) {
+      DChunk<VT, P> c[NCH];
 #pragma unroll
-    for (int h = 0; h < NCH; ++h) load_or_zero(c[h], p.col, p.val, off + h * STR, off + h * STR < end);
+      for (int h = 0; h < NCH; ++h) load_or_zero(c[h], p.dcol, p.val, off + h * STR, off + h * STR < end);
 #pragma unroll
-    for (int h = 0; h < NCH; ++h) {
-      if (h > 0 && j + h >= nmax) break;
-      ACC &s = (h & 1) ? s1 : s0;
+      for (int h = 0; h < NCH; ++h) {
+        if (h > 0 && j + h >= nmax) break;
+        ACC &s = (h & 1) ? s1 : s0;
 #pragma unroll
-      for (int q = 0; q < P; ++q) s += (ACC)c[h].v[q] * (ACC)__ldg(x + c[h].c[q]);
+        for (int q = 0; q < P; ++q) {
+          cur += c[h].d[q];
+          s += (ACC)c[h].v[q] * (ACC)__ldg(x + cur);
+        }
+      }
+    } else {
+      Chunk<VT, P> c[NCH];
+#pragma unroll
+      for (int h = 0; h < NCH; ++h) load_or_zero(c[h], p.col, p.val, off + h * STR, off + h * STR < end);
+#pragma unroll
+      for (int h = 0; h < NCH; ++h) {
+        if (h > 0 && j + h >= nmax) break;
+        ACC &s = (h & 1) ? s1 : s0;
+#pragma unroll
+        for (int q = 0; q < P; ++q) s += (ACC)c[h].v[q] * (ACC)__ldg(x + c[h].c[q]);
+      }
     }
   }
   return s0 + s1;
@@ -255,7 +328,7 @@ struct RowBlocks {
 // owning row r and every FP64 instruction on a full warp.  Stored row r goes
 // to output index orig[r] (when the rows are stored in another order).  LPR = 1
 // is the vector pass (no matrix; the row value is b_r).
-template <typename VT, typename XT, int LPR, bool MAT, bool ORIG>
+template <typename VT, typename XT, int LPR, bool MAT, bool ORIG, bool D16>
 __device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, RowBlocks rb,
                                             const XT *__restrict__ x, XT *y, typename AccT<XT>::T *stash) {
   constexpr int G = 32 / LPR;
@@ -274,12 +347,14 @@ __device__ __forceinline__ double spmv_rows(const SpmvParams<VT, XT> &p, RowBloc
       const int rp_last = p.rowptr[r1];
       int rp_next = __shfl_down_sync(0xffffffffu, rp, 1);
       if (lane == 31) rp_next = rp_last;
+      const int cb = D16 && valid ? p.rbase[row] : 0;
 #pragma unroll 1
       for (int t = 0; t < LPR; ++t) {
         const int r = t * G + grp;
         const int beg = __shfl_sync(0xffffffffu, rp, r);
         const int end = __shfl_sync(0xffffffffu, rp_next, r);
-        stash[t * 32 + lane] = row_dot<VT, XT, LPR>(p, x, beg, end, gl);
+        const int base = D16 ? __shfl_sync(0xffffffffu, cb, r) : 0;
+        stash[t * 32 + lane] = row_dot<VT, XT, LPR, D16>(p, x, beg, end, gl, base);
       }
       __syncwarp();
       const int t = lane / G, g = lane % G;
@@ -491,9 +566,12 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
 
 // Forms of the product kernel: the vector pass (y = b), the matrix form, the
 // matrix form writing through an original-row map (pixel-tiled rows; a
-// compile-time form, so untiled operators carry no dependent index load), and
-// the matrix-free projector form (proj.cuh).
-enum : int { kSpmvVec = 0, kSpmvMat = 1, kSpmvMatOrig = 2, kSpmvProj = 3 };
+// compile-time form, so untiled operators carry no dependent index load), the
+// matrix-free projector form (proj.cuh), and the two matrix forms reading
+// 16-bit column deltas (StoredCsr::dcol) instead of 32-bit indices.
+enum : int { kSpmvVec = 0, kSpmvMat = 1, kSpmvMatOrig = 2, kSpmvProj = 3, kSpmvMat16 = 4, kSpmvMatOrig16 = 5 };
+// Lanes per row of the 16-bit delta forms (the only width they are built for).
+constexpr int kDeltaLpr = 8;
 
 // The rows of a warp for the projector form, in 32-row blocks: lane r walks
 // ray r of the block (A x), or, for a back-projection, the lanes' parts of
@@ -537,7 +615,8 @@ __device__ __forceinline__ double proj_rows(const SpmvParams<VT, XT> &p, RowBloc
 // ||y||^2 and the window dots <v_j, y> as per-CTA records (CTA 0's are zero).
 template <typename VT, typename XT, int LPR, int FORM>
 __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kernel(SpmvParams<VT, XT> p) {
-  constexpr bool MAT = FORM != kSpmvVec, ORIG = FORM == kSpmvMatOrig;
+  constexpr bool MAT = FORM != kSpmvVec, ORIG = FORM == kSpmvMatOrig || FORM == kSpmvMatOrig16;
+  constexpr bool D16 = FORM == kSpmvMat16 || FORM == kSpmvMatOrig16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SolveState sst;
   __shared__ double wsum[(kMaxWindow + 2) * kThreads];   // reduction scratch
@@ -630,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kerne
   }
   double nrm;
   if constexpr (FORM == kSpmvProj) nrm = proj_rows<VT, XT>(p, rb, x, y);
-  else nrm = spmv_rows<VT, XT, LPR, MAT, ORIG>(p, rb, x, y, stash);
+  else nrm = spmv_rows<VT, XT, LPR, MAT, ORIG, D16>(p, rb, x, y, stash);
   if (!reduce) return;
   const int32_t *og = p.orig;
   if (p.sk_s) {   // the warps' sums of squares for the sketch's scale (tot is CTA 0's scratch)

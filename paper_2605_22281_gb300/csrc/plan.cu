@@ -114,6 +114,32 @@ __global__ void fill_padded_kernel(const int32_t *rowptr, const int32_t *col, co
   }
 }
 
+// 16-bit column deltas of a lane-interleaved padded CSR (slots of str = lpr * P
+// entries, chunk c of a slot at c * P): the entry at chunk position q > 0
+// follows position q - 1 of the same chunk; position 0 of chunk c in slot k > 0
+// follows the last position of chunk c in slot k - 1 (full, since only a row's
+// last slot is short); position 0 of chunk c in slot 0 follows the row's base,
+// the column of its first stored entry.  *overflow is set when a delta does
+// not fit in 16 bits.
+__global__ void delta_cols_kernel(const int32_t *prow, const int32_t *pcol, int64_t rows, int P, int str,
+                                  int16_t *dcol, int32_t *rbase, int *overflow) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < rows; r += nw) {
+    const int pb = prow[r], pe = prow[r + 1];
+    const int base = pe > pb ? pcol[pb] : 0;
+    if (lane == 0) rbase[r] = base;
+    for (int i = lane; i < pe - pb; i += 32) {
+      const int k = i / str, w = i - k * str, c = w / P, q = w - c * P;
+      const int prev = q > 0 ? pcol[pb + i - 1] : (k > 0 ? pcol[pb + (k - 1) * str + c * P + P - 1] : base);
+      const int d = pcol[pb + i] - prev;
+      if (d < -32768 || d > 32767) atomicOr(overflow, 1);
+      dcol[pb + i] = (int16_t)d;
+    }
+  }
+}
+
 __global__ void row_ids_kernel(const int32_t *rowptr, int64_t rows, int32_t *rid) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -176,6 +202,17 @@ static int plan_alloc(Plan &pl, void **p, size_t bytes) {
   pl.allocs.push_back(*p);
   pl.bytes += bytes;
   return SFL_OK;
+}
+
+// Give back an allocation of plan_alloc before the plan is complete.
+static void plan_free(Plan &pl, void *p, size_t bytes) {
+  for (size_t i = 0; i < pl.allocs.size(); ++i)
+    if (pl.allocs[i] == p) {
+      pl.allocs.erase(pl.allocs.begin() + (long)i);
+      cudaFree(p);
+      pl.bytes -= bytes;
+      return;
+    }
 }
 
 static int validate_csr(const sfl_csr *M, cudaStream_t s) {
@@ -261,6 +298,26 @@ static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const i
     fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.orig, out.rowptr, P,
                                                  out.interleaved ? out.lpr * P : 0, out.col, (OT *)out.val);
     SFL_CU(cudaGetLastError());
+    // 16-bit column deltas for the single-solve products (kept only if every delta fits)
+    if (out.interleaved && out.lpr == kDeltaLpr && pl.index_bits == 0) {
+      int *ovf = nullptr;
+      SFL_CU(tmp.get(&ovf, sizeof(int)));
+      SFL_CU(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+      if ((r = plan_alloc(pl, (void **)&out.dcol, sizeof(int16_t) * (pnnz + 16)))) return r;
+      if ((r = plan_alloc(pl, (void **)&out.rbase, sizeof(int32_t) * rows))) return r;
+      SFL_CU(cudaMemsetAsync(out.dcol, 0, sizeof(int16_t) * (pnnz + 16), s));
+      delta_cols_kernel<<<2048, 256, 0, s>>>(out.rowptr, out.col, rows, P, out.lpr * P, out.dcol, out.rbase, ovf);
+      SFL_CU(cudaGetLastError());
+      int h = 0;
+      SFL_CU(cudaMemcpyAsync(&h, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SFL_CU(cudaStreamSynchronize(s));
+      if (h) {   // some delta does not fit: the products read the 32-bit indices
+        plan_free(pl, out.dcol, sizeof(int16_t) * (pnnz + 16));
+        plan_free(pl, out.rbase, sizeof(int32_t) * rows);
+        out.dcol = nullptr;
+        out.rbase = nullptr;
+      }
+    }
   }
   return SFL_OK;
 }
@@ -362,6 +419,8 @@ int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const s
   if (img_r > 0 && (int64_t)img_r * img_c != A->cols) return SFL_EINVAL;
   const int layout = popts ? popts->slot_layout : 0;
   if (layout != 0 && layout != 1) return SFL_EINVAL;
+  const int ibits = popts ? popts->index_bits : 0;
+  if (ibits != 0 && ibits != 32) return SFL_EINVAL;
   sfl_plan *p = new sfl_plan();
   Plan &pl = p->impl;
   cudaGetDevice(&pl.device);
@@ -371,6 +430,7 @@ int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const s
   pl.lpr_override = lpr;
   pl.img_rows = img_r; pl.img_cols = img_c;
   pl.slot_layout = layout;
+  pl.index_bits = ibits;
   pl.cap = popts ? popts->max_device_bytes : 0;
   if (vdt == SFL_F64) r = build_plan<double>(pl, A, B, s);
   else if (vdt == SFL_F32) r = build_plan<float>(pl, A, B, s);
@@ -458,6 +518,8 @@ int sfl_plan_get_stats(const sfl_plan *plan, sfl_plan_stats *st) {
   st->device_bytes = pl.bytes;
   st->tiled_At = pl.T.orig != nullptr ? 1 : 0;
   st->matrix_free = pl.matfree ? 1 : 0;
+  st->index_bytes_A = pl.A.dcol ? 2 : 4;
+  st->index_bytes_At = pl.T.dcol ? 2 : 4;
   return SFL_OK;
 }
 

@@ -236,6 +236,7 @@ struct Engine {
   static SpmvParams<VT, XT> base_params(const Plan &pl, const Session &se, const StoredCsr &M, int mode) {
     SpmvParams<VT, XT> p{};
     p.rowptr = M.rowptr; p.col = M.col; p.val = (const VT *)M.val; p.rows = M.rows;
+    p.dcol = M.dcol; p.rbase = M.rbase;
     p.orig = M.orig;
     p.mode = mode;
     p.method = se.key.method;
@@ -997,6 +998,7 @@ static int apply_typed(Plan &pl, int which, const double *x, double *y, cudaStre
   const StoredCsr &M = which == 0 ? pl.A : pl.T;
   SpmvParams<VT, XT> p{};
   p.rowptr = M.rowptr; p.col = M.col; p.val = (const VT *)M.val; p.rows = M.rows;
+  p.dcol = M.dcol; p.rbase = M.rbase;
   p.orig = M.orig;
   p.mode = kModeApply;
   const int grid = pl.num_sms * 2;

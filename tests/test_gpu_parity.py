@@ -593,6 +593,57 @@ def test_tiled_transpose_with_interleaved_warps_is_bit_identical():
     plain.close(); tiled.close()
 
 
+@pytest.mark.parametrize("vdt", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("tiles", [False, True])
+def test_16bit_column_deltas_are_bit_identical(ct64, ct64_unmatched, vdt, tiles):
+    """The default plan reads 16-bit column deltas (every delta of a CT
+    operator fits); index_bits=32 keeps the 32-bit indices.  The entries, their
+    order and the gathers are the same, so products and whole solves agree
+    bit for bit."""
+    p, _ = ct64
+    N = int(round(math.sqrt(p.A.shape[1])))
+    shape = (N, N) if tiles else None
+    rng = np.random.default_rng(6)
+    st = p.settings
+    for A, B in ((p.A, None), (ct64_unmatched[0], ct64_unmatched[1])):
+        d16 = G.Plan(A, B, value_dtype=vdt, image_shape=shape)
+        i32 = G.Plan(A, B, value_dtype=vdt, image_shape=shape, index_bits=32)
+        sd, si = d16.stats(), i32.stats()
+        assert (sd["index_bytes_A"], sd["index_bytes_At"]) == (2, 2)
+        assert (si["index_bytes_A"], si["index_bytes_At"]) == (4, 4)
+        assert sd["lanes_A"] == 8 and sd["lanes_At"] == 8
+        w = dev(rng.standard_normal(A.shape[0]))
+        z = dev(rng.standard_normal(A.shape[1]))
+        assert torch.equal(d16.apply(z), i32.apply(z))
+        assert torch.equal(d16.apply(w, transpose=True), i32.apply(w, transpose=True))
+        b = dev(A.matvec(rng.standard_normal(A.shape[1])))
+        method = "sflsqr" if B is None else "sflsmr"
+        kw = dict(s=st["s"], zeta=st["zeta"], seed=st["seed"], window=2, maxit=12)
+        xa, ia, _ = d16.solve(method, b, **kw)
+        xb, ib, _ = i32.solve(method, b, **kw)
+        assert ia.iters == ib.iters and torch.equal(xa, xb)
+        d16.close(); i32.close()
+
+
+def test_wide_columns_keep_32bit_indices():
+    """An operator whose deltas do not fit in 16 bits (random columns over 2^20)
+    keeps the 32-bit indices, and its products still match SciPy."""
+    rng = np.random.default_rng(8)
+    m, n, per = 300, 1 << 20, 64
+    cols = np.sort(np.stack([rng.choice(n, per, replace=False) for _ in range(m)]), axis=1)
+    A = wl.CSR((m, n), np.arange(0, m * per + 1, per, dtype=np.int64), cols.ravel().astype(np.int32),
+               rng.standard_normal(m * per))
+    plan = G.Plan(A)
+    assert plan.stats()["index_bytes_A"] == 4
+    z = rng.standard_normal(n)
+    w = rng.standard_normal(m)
+    assert rel(plan.apply(dev(z)).cpu().numpy(), A.scipy() @ z) <= 1e-14
+    assert rel(plan.apply(dev(w), transpose=True).cpu().numpy(), A.scipy().T @ w) <= 1e-14
+    plan.close()
+    with pytest.raises(Exception):
+        G.Plan(A, index_bits=16)
+
+
 def test_tiled_plan_solves_match_oracle(ct64, ct64_unmatched):
     p, _ = ct64
     N = int(round(math.sqrt(p.A.shape[1])))
