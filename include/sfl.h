@@ -98,8 +98,9 @@ typedef struct sfl_plan sfl_plan;
  * index_bits: 0 (default) lets the single-solve products read 16-bit column
  * deltas (each stored entry's column minus the column of the entry before it
  * in its lane's walk, plus one 32-bit base per row) when every delta of the
- * operator fits in 16 bits, the row layout is lane-interleaved and 8 lanes
- * run a row; otherwise, and with 32, they read the 32-bit column indices.
+ * operator fits in 16 bits, the row layout is lane-interleaved, 8 lanes run
+ * a row and the deltas fit under max_device_bytes; otherwise, and with 32,
+ * they read the 32-bit column indices.
  * The products are the same bit for bit; the 16-bit form streams 2 bytes of
  * index per entry instead of 4.  The plan keeps the 32-bit indices as well
  * (batched solves read them). */

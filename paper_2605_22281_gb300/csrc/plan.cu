@@ -298,8 +298,10 @@ static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const i
     fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.orig, out.rowptr, P,
                                                  out.interleaved ? out.lpr * P : 0, out.col, (OT *)out.val);
     SFL_CU(cudaGetLastError());
-    // 16-bit column deltas for the single-solve products (kept only if every delta fits)
-    if (out.interleaved && out.lpr == kDeltaLpr && pl.index_bits == 0) {
+    // 16-bit column deltas for the single-solve products (kept only if every
+    // delta fits; left out, not an error, when they would exceed the plan's cap)
+    const size_t dbytes = sizeof(int16_t) * (pnnz + 16) + sizeof(int32_t) * rows;
+    if (out.interleaved && out.lpr == kDeltaLpr && pl.index_bits == 0 && !(pl.cap && pl.bytes + dbytes > pl.cap)) {
       int *ovf = nullptr;
       SFL_CU(tmp.get(&ovf, sizeof(int)));
       SFL_CU(cudaMemsetAsync(ovf, 0, sizeof(int), s));
