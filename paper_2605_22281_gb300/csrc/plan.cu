@@ -298,28 +298,37 @@ static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const i
     fill_padded_kernel<OT><<<2048, 256, 0, s>>>(rowptr, col, val, rows, out.orig, out.rowptr, P,
                                                  out.interleaved ? out.lpr * P : 0, out.col, (OT *)out.val);
     SFL_CU(cudaGetLastError());
-    // 16-bit column deltas for the single-solve products (kept only if every
-    // delta fits; left out, not an error, when they would exceed the plan's cap)
-    const size_t dbytes = sizeof(int16_t) * (pnnz + 16) + sizeof(int32_t) * rows;
-    if (out.interleaved && out.lpr == kDeltaLpr && pl.index_bits == 0 && !(pl.cap && pl.bytes + dbytes > pl.cap)) {
-      int *ovf = nullptr;
-      SFL_CU(tmp.get(&ovf, sizeof(int)));
-      SFL_CU(cudaMemsetAsync(ovf, 0, sizeof(int), s));
-      if ((r = plan_alloc(pl, (void **)&out.dcol, sizeof(int16_t) * (pnnz + 16)))) return r;
-      if ((r = plan_alloc(pl, (void **)&out.rbase, sizeof(int32_t) * rows))) return r;
-      SFL_CU(cudaMemsetAsync(out.dcol, 0, sizeof(int16_t) * (pnnz + 16), s));
-      delta_cols_kernel<<<2048, 256, 0, s>>>(out.rowptr, out.col, rows, P, out.lpr * P, out.dcol, out.rbase, ovf);
-      SFL_CU(cudaGetLastError());
-      int h = 0;
-      SFL_CU(cudaMemcpyAsync(&h, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
-      SFL_CU(cudaStreamSynchronize(s));
-      if (h) {   // some delta does not fit: the products read the 32-bit indices
-        plan_free(pl, out.dcol, sizeof(int16_t) * (pnnz + 16));
-        plan_free(pl, out.rbase, sizeof(int32_t) * rows);
-        out.dcol = nullptr;
-        out.rbase = nullptr;
-      }
-    }
+  }
+  return SFL_OK;
+}
+
+// 16-bit column deltas of a stored operator for the single-solve products,
+// built once both operators are stored: kept only if every delta fits, and
+// left out (not an error) when they would exceed the plan's device-byte cap.
+static int build_deltas(Plan &pl, StoredCsr &M, cudaStream_t s) {
+  const int P = load_width(pl.vdt);
+  const int64_t rows = M.rows, pnnz = M.pnnz;
+  const size_t dbytes = sizeof(int16_t) * (pnnz + 16) + sizeof(int32_t) * rows;
+  if (rows <= 0 || !M.interleaved || M.lpr != kDeltaLpr || pl.index_bits != 0 || (pl.cap && pl.bytes + dbytes > pl.cap))
+    return SFL_OK;
+  TmpAlloc tmp;
+  int r;
+  int *ovf = nullptr;
+  SFL_CU(tmp.get(&ovf, sizeof(int)));
+  SFL_CU(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+  if ((r = plan_alloc(pl, (void **)&M.dcol, sizeof(int16_t) * (pnnz + 16)))) return r;
+  if ((r = plan_alloc(pl, (void **)&M.rbase, sizeof(int32_t) * rows))) return r;
+  SFL_CU(cudaMemsetAsync(M.dcol, 0, sizeof(int16_t) * (pnnz + 16), s));
+  delta_cols_kernel<<<2048, 256, 0, s>>>(M.rowptr, M.col, rows, P, M.lpr * P, M.dcol, M.rbase, ovf);
+  SFL_CU(cudaGetLastError());
+  int h = 0;
+  SFL_CU(cudaMemcpyAsync(&h, ovf, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SFL_CU(cudaStreamSynchronize(s));
+  if (h) {   // some delta does not fit: the products read the 32-bit indices
+    plan_free(pl, M.dcol, sizeof(int16_t) * (pnnz + 16));
+    plan_free(pl, M.rbase, sizeof(int32_t) * rows);
+    M.dcol = nullptr;
+    M.rbase = nullptr;
   }
   return SFL_OK;
 }
@@ -437,6 +446,8 @@ int sfl_plan_create(sfl_plan **plan, const sfl_csr *A, const sfl_csr *B, const s
   if (vdt == SFL_F64) r = build_plan<double>(pl, A, B, s);
   else if (vdt == SFL_F32) r = build_plan<float>(pl, A, B, s);
   else r = build_plan<__nv_bfloat16>(pl, A, B, s);
+  if (!r) r = build_deltas(pl, pl.A, s);
+  if (!r) r = build_deltas(pl, pl.T, s);
   if (r) {
     sfl_plan_destroy(p);
     return r;

@@ -625,6 +625,23 @@ def test_16bit_column_deltas_are_bit_identical(ct64, ct64_unmatched, vdt, tiles)
         d16.close(); i32.close()
 
 
+def test_delta_columns_yield_to_the_device_byte_cap(ct64):
+    """A plan capped at the bytes of its 32-bit form builds without the 16-bit
+    deltas (no error) and gives the same products."""
+    p, _ = ct64
+    full = G.Plan(p.A)
+    st = full.stats()
+    assert (st["index_bytes_A"], st["index_bytes_At"]) == (2, 2)
+    delta_bytes = sum(2 * (st[k] + 16) + 4 * r for k, r in (("padded_nnz_A", st["rows"]), ("padded_nnz_At", st["cols"])))
+    capped = G.Plan(p.A, max_device_bytes=int(st["device_bytes"]) - delta_bytes)
+    sc = capped.stats()
+    assert (sc["index_bytes_A"], sc["index_bytes_At"]) == (4, 4)
+    assert sc["device_bytes"] == st["device_bytes"] - delta_bytes
+    z = dev(np.random.default_rng(2).standard_normal(p.A.shape[1]))
+    assert torch.equal(full.apply(z), capped.apply(z))
+    full.close(); capped.close()
+
+
 def test_wide_columns_keep_32bit_indices():
     """An operator whose deltas do not fit in 16 bits (random columns over 2^20)
     keeps the 32-bit indices, and its products still match SciPy."""
