@@ -159,6 +159,29 @@ def test_adjoint_limits(small):
 
 
 @pytest.mark.slow
+def test_full_shape_gradients_match_oracle():
+    """The differentiated workload's shape (256x256, 180 angles, s = 61,
+    window 2, diagonal weight) for two of its sinograms at k = 10: the FP64
+    forward and both gradients against the oracle's autograd at the
+    small-case bars (kappa(S A Z_10) ~ 7e3)."""
+    p = wl.make("ct256_diff16")
+    st = p.settings
+    plan = G.Plan(p.A, value_dtype="f64", image_shape=(p.N, p.N))
+    B = p.b.T[[0, 9]].copy()
+    d = st["weight"]
+    Xbar = np.random.default_rng(61).standard_normal((B.shape[0], p.A.shape[1]))
+    X, infos, _ = G.fixed_batched(plan, dev(B), dev(d), s=st["s"], zeta=st["zeta"], seed=st["seed"],
+                                  window=st["window"], maxit=10)
+    assert all(i.iters == 10 for i in infos)
+    Bbar, dbar = G.adjoint(plan, dev(Xbar))
+    xo, gb, gd = oracle_grads(p.A, B, d, st["s"], st["zeta"], st["seed"], 10, st["window"], Xbar)
+    ex, eb, ed = rel(X.cpu().numpy(), xo), rel(Bbar.cpu().numpy(), gb), rel(dbar.cpu().numpy(), gd)
+    print(f"full shape k=10: x {ex:.1e}, b-gradient {eb:.1e}, d-gradient {ed:.1e}")
+    assert ex <= 1e-10 and eb <= 1e-8 and ed <= 1e-8
+    plan.close()
+
+
+@pytest.mark.slow
 def test_full_size_directional_derivative():
     """16 sinograms of 256x256 phantoms with the diagonal weight, s = 61,
     window 2, FP64: <Xbar, dX[v]> from the adjoint against a central
