@@ -212,10 +212,12 @@ template <typename VT> struct LoadWidth { static constexpr int P = 4; };
 template <> struct LoadWidth<__nv_bfloat16> { static constexpr int P = 8; };
 
 // Loads in flight per lane and resident CTAs per SM of the SpMV, per value
-// type: 4 chunks (16 entries) per iteration for FP64 and FP32 values, 2 chunks
-// (16 entries) for BF16; 2 CTAs per SM for FP64 (FP64-pipe bound, registers
-// for the deeper pipeline), more for the reduced precisions (latency bound).
-template <typename VT> struct SpmvTune { static constexpr int NCH = 4, MINB = 2; };
+// type: 3 chunks (12 entries) per iteration at 3 CTAs per SM for FP64 values
+// (measured at 1024^2 with the 16-bit column deltas: 9 % faster than 4 chunks
+// at 2 CTAs, and than 2 chunks at 3 CTAs), 4 chunks for FP32 and 2 (16
+// entries) for BF16 at 3 CTAs per SM.  The FP64 projector form keeps 2 CTAs per
+// SM (its walks need the registers; see spmv_min_blocks).
+template <typename VT> struct SpmvTune { static constexpr int NCH = 3, MINB = 3; };
 template <> struct SpmvTune<float> { static constexpr int NCH = 4, MINB = 3; };
 template <> struct SpmvTune<__nv_bfloat16> { static constexpr int NCH = 2, MINB = 3; };
 
@@ -572,6 +574,11 @@ __device__ __noinline__ void spmv_bookkeeping(const SpmvParams<VT, XT> &p, int k
 enum : int { kSpmvVec = 0, kSpmvMat = 1, kSpmvMatOrig = 2, kSpmvProj = 3, kSpmvMat16 = 4, kSpmvMatOrig16 = 5 };
 // Lanes per row of the 16-bit delta forms (the only width they are built for).
 constexpr int kDeltaLpr = 8;
+// Resident CTAs per SM the product kernel is compiled for: the FP64 projector
+// walks (fixed-point columns, stepped bin coordinates) keep 2.
+template <typename VT> constexpr int spmv_min_blocks(int form) {
+  return form == kSpmvProj && sizeof(VT) == 8 ? 2 : SpmvTune<VT>::MINB;
+}
 
 // The rows of a warp for the projector form, in 32-row blocks: lane r walks
 // ray r of the block (A x), or, for a back-projection, the lanes' parts of
@@ -614,7 +621,7 @@ __device__ __forceinline__ double proj_rows(const SpmvParams<VT, XT> &p, RowBloc
 // outputs are stored unscaled (y = A x for the stored, unnormalised x), with
 // ||y||^2 and the window dots <v_j, y> as per-CTA records (CTA 0's are zero).
 template <typename VT, typename XT, int LPR, int FORM>
-__global__ void __launch_bounds__(kThreads, SpmvTune<VT>::MINB) spmv_fused_kernel(SpmvParams<VT, XT> p) {
+__global__ void __launch_bounds__(kThreads, spmv_min_blocks<VT>(FORM)) spmv_fused_kernel(SpmvParams<VT, XT> p) {
   constexpr bool MAT = FORM != kSpmvVec, ORIG = FORM == kSpmvMatOrig || FORM == kSpmvMatOrig16;
   constexpr bool D16 = FORM == kSpmvMat16 || FORM == kSpmvMatOrig16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
