@@ -304,7 +304,8 @@ static int store_padded(Plan &pl, StoredCsr &out, const int32_t *rowptr, const i
 
 // 16-bit column deltas of a stored operator for the single-solve products,
 // built once both operators are stored: kept only if every delta fits, and
-// left out (not an error) when they would exceed the plan's device-byte cap.
+// left out (not an error) when they would exceed the plan's device-byte cap
+// or the device has no room for them.
 static int build_deltas(Plan &pl, StoredCsr &M, cudaStream_t s) {
   const int P = load_width(pl.vdt);
   const int64_t rows = M.rows, pnnz = M.pnnz;
@@ -312,12 +313,19 @@ static int build_deltas(Plan &pl, StoredCsr &M, cudaStream_t s) {
   if (rows <= 0 || !M.interleaved || M.lpr != kDeltaLpr || pl.index_bits != 0 || (pl.cap && pl.bytes + dbytes > pl.cap))
     return SFL_OK;
   TmpAlloc tmp;
-  int r;
   int *ovf = nullptr;
   SFL_CU(tmp.get(&ovf, sizeof(int)));
   SFL_CU(cudaMemsetAsync(ovf, 0, sizeof(int), s));
-  if ((r = plan_alloc(pl, (void **)&M.dcol, sizeof(int16_t) * (pnnz + 16)))) return r;
-  if ((r = plan_alloc(pl, (void **)&M.rbase, sizeof(int32_t) * rows))) return r;
+  if (plan_alloc(pl, (void **)&M.dcol, sizeof(int16_t) * (pnnz + 16))) {
+    M.dcol = nullptr;
+    return SFL_OK;
+  }
+  if (plan_alloc(pl, (void **)&M.rbase, sizeof(int32_t) * rows)) {
+    plan_free(pl, M.dcol, sizeof(int16_t) * (pnnz + 16));
+    M.dcol = nullptr;
+    M.rbase = nullptr;
+    return SFL_OK;
+  }
   SFL_CU(cudaMemsetAsync(M.dcol, 0, sizeof(int16_t) * (pnnz + 16), s));
   delta_cols_kernel<<<2048, 256, 0, s>>>(M.rowptr, M.col, rows, P, M.lpr * P, M.dcol, M.rbase, ovf);
   SFL_CU(cudaGetLastError());
