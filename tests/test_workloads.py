@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 import workloads as wl
 
@@ -57,3 +58,67 @@ def test_sparse_phantom_fraction():
     x = wl.sparse_phantom(64, np.random.default_rng(2), 0.05)
     assert np.count_nonzero(x) == round(0.05 * 4096)
     assert x.min() >= 0 and x.max() <= 1
+
+
+def _clip_length(p0, u, lo, hi):
+    """Length of the line p0 + s u inside the box [lo, hi] (Liang-Barsky clipping)."""
+    s0, s1 = -math.inf, math.inf
+    for k in range(2):
+        if abs(u[k]) < 1e-15:
+            if not (lo[k] <= p0[k] <= hi[k]):
+                return 0.0
+            continue
+        a, b = (lo[k] - p0[k]) / u[k], (hi[k] - p0[k]) / u[k]
+        s0, s1 = max(s0, min(a, b)), min(s1, max(a, b))
+    return max(0.0, s1 - s0)
+
+
+@pytest.mark.parametrize("N,na", [(8, 7), (11, 9)])
+def test_siddon_entries_are_clipped_chords(N, na):
+    """Every entry of the Siddon operator is the length of its ray clipped to
+    its unit pixel, and every ray's sum is the chord through the whole image
+    (checked for the angles off the axes; axis-aligned rays on grid lines
+    follow the walk's floor rule instead)."""
+    nb = wl.detector_bins(N)
+    S = wl.siddon_projector(N, na, nb).scipy().toarray()
+    h = N / 2
+    checked = 0
+    for a in range(na):
+        th = a * math.pi / na
+        c, s = math.cos(th), math.sin(th)
+        if abs(c) < 1e-9 or abs(s) < 1e-9:
+            continue
+        u = (-s, c)
+        for d in range(nb):
+            t = d - 0.5 * (nb - 1)
+            p0 = (t * c, t * s)
+            row = a * nb + d
+            whole = _clip_length(p0, u, (-h, -h), (h, h))
+            assert abs(S[row].sum() - whole) <= 1e-12 * max(1.0, whole)
+            for iy in range(N):
+                for ix in range(N):
+                    ref = _clip_length(p0, u, (ix - h, iy - h), (ix + 1 - h, iy + 1 - h))
+                    got = S[row, iy * N + ix]
+                    assert abs(got - ref) <= 1e-12, (a, d, ix, iy, got, ref)
+            checked += 1
+    assert checked >= (na - 1) * nb // 2
+
+
+@pytest.mark.parametrize("N,na", [(8, 7), (11, 9)])
+def test_backprojector_entries_are_hat_weights(N, na):
+    """B[pixel, (a, d)] is the linear-interpolation (hat) weight max(0, 1 - |u - d|)
+    of the pixel centre's bin coordinate u = x_c cos + y_c sin + (n_bins - 1)/2."""
+    nb = wl.detector_bins(N)
+    B = wl.pixel_backprojector(N, na, nb).scipy().toarray()
+    h = N / 2
+    off = 0.5 * (nb - 1)
+    for a in range(na):
+        th = a * math.pi / na
+        c, s = math.cos(th), math.sin(th)
+        for iy in range(N):
+            for ix in range(N):
+                u = (ix - h + 0.5) * c + (iy - h + 0.5) * s + off
+                ref = np.maximum(0.0, 1.0 - np.abs(u - np.arange(nb)))
+                ref[ref <= 1e-12] = 0.0
+                got = B[iy * N + ix, a * nb:(a + 1) * nb]
+                assert np.abs(got - ref).max() <= 1e-12, (a, ix, iy)
