@@ -177,3 +177,28 @@ def test_full_window_argument_checks(ct64):
     with pytest.raises(G.N.SflError) as e:     # FLSQR needs the full window
         plan.solve("flsqr", dev(p.b), s=0, window=2, maxit=20)
     assert e.value.status == G.N.SFL_EINVAL
+
+
+@pytest.mark.slow
+def test_more_than_256_steps_reach_the_unstaged_inverse_rows():
+    """300 steps of sFLSQR with every window vector kept (no stop rule), s = 700,
+    on a dense 1500 x 1000 operator with singular values log-spaced in
+    [1, 1000] (seeded): the small least-squares kernel keeps the first 256 rows
+    of R^-1 in registers and takes the rest from global memory, which only
+    steps past 257 reach.  The basis stays orthonormal (1e-14) and
+    cond(S A Z_300) is 7e2 here, so every iterate is held to the flat 1e-10."""
+    m, n = 1500, 1000
+    rng = np.random.default_rng(7)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (U * np.geomspace(1.0, 1000.0, n)) @ V.T
+    b = rng.standard_normal(m)
+    plan = G.Plan(wl.dense_csr(A))
+    r = run_oracle_sflsqr(A, b, 700, 8, 71, 300, 0.0, -1)
+    x, info, h = plan.solve("sflsqr", dev(b), s=700, zeta=8, seed=71, window=-1, maxit=300, x_history=True,
+                            relres_history=True)
+    assert info.iters == 300 and r.iters == 300
+    assert np.linalg.cond(r.M) < 1e4
+    checked = assert_iterates_conditioned(r, h["x"], h["relres"], info, 0.0, min_checked=300)
+    assert checked == 300
+    plan.close()
