@@ -55,6 +55,8 @@ def test_spmv_bytes_closed_form():
     # 10 entries of 8-byte values and 4-byte indices, 3 rows, 5 columns,
     # 8-byte vectors, 2 window dots, no table
     assert bench.spmv_bytes(10, 3, 5, 8, 8, 2, 0) == 10 * 12 + 4 * 4 + 8 * (5 + 3) + 8 * 3 * 2
+    # 16-bit column deltas: 2 bytes of index per entry and a 4-byte base column per row
+    assert bench.spmv_bytes(10, 3, 5, 8, 8, 2, 0, 2) == 10 * 10 + 4 * 4 + 4 * 3 + 8 * (5 + 3) + 8 * 3 * 2
 
 
 class _DoneProc:
